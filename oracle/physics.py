@@ -1,0 +1,287 @@
+"""Oracle physics modules: conserved <-> primitive maps, physical fluxes, signal speeds.
+
+TEST INFRASTRUCTURE ONLY. This package is the plain FP64 CPU oracle that the CUDA path is
+checked against; only tests, the smoke check and the bench's CPU-baseline leg use it.
+It shares no code with the CUDA library.
+
+Every function works on numpy arrays shaped (nvar, ...) with the variable axis first and
+follows the paper's Section 2.3:
+  * hd   : Eqs. 2-4 and the closure e = p/(gamma-1) + rho v^2/2 (Section 2.3.1); the
+           flux is the HD get_flux of the paper's flux listing (Section 2.3).
+  * mhd  : Eqs. 11-13 with GLM (Eq. 14), e = p/(gamma-1) + rho v^2/2 + B^2/2 (units absorb
+           4 pi), Section 2.3.3.
+  * srhd : Eqs. 15-19, ideal-gas EOS Eq. 20, con2prim as a 1-D root find in
+           xi = Gamma^2 rho h (Section 2.3.4).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+class HD:
+    """Newtonian hydrodynamics, U = (rho, m, e), P = (rho, v, p)."""
+
+    name = "hd"
+    nvar = 5
+    naux = 0
+    glm = False
+
+    def __init__(self, gamma: float):
+        self.gamma = float(gamma)
+
+    def prim2cons(self, P):
+        g = self.gamma
+        rho, v, p = P[0], P[1:4], P[4]
+        U = np.empty_like(P)
+        U[0] = rho
+        U[1:4] = rho * v
+        U[4] = p / (g - 1.0) + 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2])
+        return U
+
+    def cons2prim(self, U, aux=None):
+        g = self.gamma
+        P = np.empty_like(U)
+        rho = U[0]
+        v = U[1:4] / rho
+        P[0] = rho
+        P[1:4] = v
+        P[4] = (g - 1.0) * (U[4] - 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]))
+        return P, None
+
+    def flux(self, P, U, d):
+        """Physical flux along axis d from primitives (paper's HD get_flux listing)."""
+        g = self.gamma
+        rho, v, p = P[0], P[1:4], P[4]
+        vd = v[d]
+        F = np.empty_like(P)
+        F[0] = rho * vd
+        for i in range(3):
+            F[1 + i] = rho * v[i] * vd
+        F[1 + d] = F[1 + d] + p
+        F[4] = vd * (p / (g - 1.0) + 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) + p)
+        return F
+
+    def sound_speed(self, P):
+        return np.sqrt(self.gamma * P[4] / P[0])
+
+    def lambdas(self, P, d):
+        """Smallest and largest characteristic speed along d: v_d -/+ c_s."""
+        c = self.sound_speed(P)
+        return P[1 + d] - c, P[1 + d] + c
+
+
+class MHD:
+    """Ideal MHD with GLM divergence cleaning, U = (rho, m, e, B, psi)."""
+
+    name = "mhd"
+    nvar = 9
+    naux = 0
+    glm = True
+
+    def __init__(self, gamma: float):
+        self.gamma = float(gamma)
+
+    def prim2cons(self, P):
+        g = self.gamma
+        rho, v, p, B = P[0], P[1:4], P[4], P[5:8]
+        U = np.empty_like(P)
+        U[0] = rho
+        U[1:4] = rho * v
+        v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2]
+        b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2]
+        U[4] = p / (g - 1.0) + 0.5 * rho * v2 + 0.5 * b2
+        U[5:8] = B
+        U[8] = P[8]
+        return U
+
+    def cons2prim(self, U, aux=None):
+        g = self.gamma
+        P = np.empty_like(U)
+        rho = U[0]
+        v = U[1:4] / rho
+        B = U[5:8]
+        v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2]
+        b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2]
+        P[0] = rho
+        P[1:4] = v
+        P[4] = (g - 1.0) * (U[4] - 0.5 * rho * v2 - 0.5 * b2)
+        P[5:8] = B
+        P[8] = U[8]
+        return P, None
+
+    def flux(self, P, U, d, ch):
+        """Flux along d of Eqs. 11-13; GLM pair F(B_d) = psi, F(psi) = c_h^2 B_d (Eq. 14)."""
+        rho, v, p, B, psi = P[0], P[1:4], P[4], P[5:8], P[8]
+        vd, Bd = v[d], B[d]
+        b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2]
+        ptot = p + 0.5 * b2
+        vB = v[0] * B[0] + v[1] * B[1] + v[2] * B[2]
+        F = np.empty_like(P)
+        F[0] = rho * vd
+        for i in range(3):
+            F[1 + i] = rho * v[i] * vd - B[i] * Bd
+        F[1 + d] = F[1 + d] + ptot
+        F[4] = vd * (U[4] + ptot) - Bd * vB
+        for i in range(3):
+            F[5 + i] = vd * B[i] - Bd * v[i]
+        F[5 + d] = psi
+        F[8] = ch * ch * Bd
+        return F
+
+    def fast_speed(self, P, d):
+        """Fast magnetosonic speed along d."""
+        rho, p, B = P[0], P[4], P[5:8]
+        a2 = self.gamma * p / rho
+        b2 = (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]) / rho
+        bd2 = B[d] * B[d] / rho
+        s = a2 + b2
+        return np.sqrt(0.5 * (s + np.sqrt(s * s - 4.0 * a2 * bd2)))
+
+    def lambdas(self, P, d):
+        cf = self.fast_speed(P, d)
+        return P[1 + d] - cf, P[1 + d] + cf
+
+    def glm_interface(self, PL, PR, d, ch):
+        """Exact solution of the linear (B_d, psi) subsystem at a face (Dedner et al. 2002).
+
+        The GLM system of Eq. 14 with flux c_h^2 B_d for psi and psi for B_d has speeds
+        +/- c_h; its Riemann solution gives one interface value of B_d and psi, which both
+        face states then carry, so the face flux of B_d is psi* and of psi is c_h^2 B_d*.
+        """
+        bl, br = PL[5 + d], PR[5 + d]
+        pl, pr = PL[8], PR[8]
+        bstar = 0.5 * (bl + br) - 0.5 * (pr - pl) / ch
+        pstar = 0.5 * (pl + pr) - 0.5 * ch * (br - bl)
+        PL = PL.copy()
+        PR = PR.copy()
+        PL[5 + d] = bstar
+        PR[5 + d] = bstar
+        PL[8] = pstar
+        PR[8] = pstar
+        return PL, PR
+
+
+class SRHD:
+    """Special-relativistic hydro, U = (D, m, tau), P = (rho, u = Gamma v, p), A = (xi, Gamma)."""
+
+    name = "srhd"
+    nvar = 5
+    naux = 2
+    glm = False
+    max_iter = 50
+    tol = 1e-14
+
+    def __init__(self, gamma: float):
+        self.gamma = float(gamma)
+
+    def enthalpy(self, rho, p):
+        """Ideal-gas specific enthalpy, Eq. 20."""
+        g = self.gamma
+        return 1.0 + g / (g - 1.0) * p / rho
+
+    def prim2cons(self, P):
+        """Eq. 17 evaluated from the primitives of Eq. 18."""
+        rho, u, p = P[0], P[1:4], P[4]
+        lor = np.sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2])
+        h = self.enthalpy(rho, p)
+        U = np.empty_like(P)
+        U[0] = lor * rho
+        U[1:4] = lor * rho * h * u           # Gamma^2 rho h v with v = u / Gamma
+        U[4] = lor * lor * rho * h - p - lor * rho
+        return U
+
+    def aux_from_prim(self, P):
+        """Auxiliaries of Eq. 19: xi = Gamma^2 rho h and Gamma."""
+        rho, u, p = P[0], P[1:4], P[4]
+        lor = np.sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2])
+        A = np.empty((2,) + P.shape[1:])
+        A[0] = lor * lor * rho * self.enthalpy(rho, p)
+        A[1] = lor
+        return A
+
+    def cons2prim(self, U, aux=None):
+        """Primitive recovery as a root find in xi = Gamma^2 rho h (Section 2.3.4).
+
+        With E = tau + D and S = |m|: v^2 = S^2/xi^2, Gamma = (1 - v^2)^-1/2, rho = D/Gamma
+        and, for the ideal gas, p = (gamma-1)/gamma (xi/Gamma^2 - rho); energy gives
+        f(xi) = xi - p(xi) - E = 0. The root lies in [E, gamma E] (p >= 0 and
+        p <= (gamma-1)/gamma xi). Newton's method with the analytic derivative runs from
+        the stored auxiliary xi (when it lies inside the bracket, else the bracket's
+        midpoint); a step leaving the closed bracket is replaced by bisection. It stops when
+        |dxi| <= 1e-14 xi, at most 50 iterations. Returns (P, A) and raises on failure.
+        """
+        g = self.gamma
+        gm = (g - 1.0) / g
+        D = U[0]
+        m = U[1:4]
+        S2 = m[0] * m[0] + m[1] * m[1] + m[2] * m[2]
+        E = U[4] + D
+        lo = E.copy()
+        hi = g * E
+        if aux is not None:
+            xi = np.where((aux[0] > lo) & (aux[0] < hi), aux[0], 0.5 * (lo + hi))
+        else:
+            xi = 0.5 * (lo + hi)
+        done = np.zeros(D.shape, dtype=bool)
+        for _ in range(self.max_iter):
+            w = S2 / (xi * xi)                   # v^2
+            ig2 = 1.0 - w                        # 1/Gamma^2
+            lor = 1.0 / np.sqrt(ig2)
+            rho = D / lor
+            p = gm * (xi * ig2 - rho)
+            f = xi - p - E
+            dp = gm * (1.0 + w - D * lor * w / xi)   # dp/dxi
+            df = 1.0 - dp
+            lo = np.where(f < 0.0, xi, lo)
+            hi = np.where(f < 0.0, hi, xi)
+            xn = xi - f / df
+            inside = (xn >= lo) & (xn <= hi)
+            xn = np.where(inside, xn, 0.5 * (lo + hi))
+            conv = np.abs(xn - xi) <= self.tol * xn
+            xi = np.where(done, xi, xn)
+            done = done | conv
+            if done.all():
+                break
+        if not done.all():
+            raise FloatingPointError("srhd con2prim did not converge")
+        w = S2 / (xi * xi)
+        ig2 = 1.0 - w
+        lor = 1.0 / np.sqrt(ig2)
+        rho = D / lor
+        P = np.empty_like(U)
+        P[0] = rho
+        P[1:4] = m * (lor / xi)                  # u = Gamma v, v = m / xi
+        P[4] = gm * (xi * ig2 - rho)
+        A = np.empty((2,) + U.shape[1:])
+        A[0] = xi
+        A[1] = lor
+        return P, A
+
+    def flux(self, P, U, d):
+        """Flux along d of Eqs. 15-17: D v_d, m v_d + p e_d, m_d - D v_d."""
+        u, p = P[1:4], P[4]
+        lor = np.sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2])
+        vd = u[d] / lor
+        F = np.empty_like(P)
+        F[0] = U[0] * vd
+        for i in range(3):
+            F[1 + i] = U[1 + i] * vd
+        F[1 + d] = F[1 + d] + p
+        F[4] = U[1 + d] - U[0] * vd
+        return F
+
+    def lambdas(self, P, d):
+        """Characteristic speeds along d for an ideal gas (sound speed cs^2 = gamma p/(rho h))."""
+        rho, u, p = P[0], P[1:4], P[4]
+        lor2 = 1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]
+        v2 = 1.0 - 1.0 / lor2
+        vd = u[d] / np.sqrt(lor2)
+        cs2 = self.gamma * p / (rho * self.enthalpy(rho, p))
+        cs = np.sqrt(cs2)
+        den = 1.0 - v2 * cs2
+        root = cs * np.sqrt((1.0 - v2) * (1.0 - v2 * cs2 - vd * vd * (1.0 - cs2)))
+        return (vd * (1.0 - cs2) - root) / den, (vd * (1.0 - cs2) + root) / den
+
+
+def make_physics(name: str, gamma: float):
+    return {"hd": HD, "mhd": MHD, "srhd": SRHD}[name](gamma)
