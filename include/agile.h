@@ -1,0 +1,214 @@
+/*
+ * agile.h - C ABI of the GB300 block-AMR finite-volume library (libagile.so).
+ *
+ * The library advances near-conservation laws dU/dt + div F(U) = S (paper Eq. 1) for
+ * Newtonian hydrodynamics (Section 2.3.1, Eqs. 2-6), ideal MHD with GLM divergence
+ * cleaning (Section 2.3.3, Eqs. 11-14) and special-relativistic hydrodynamics
+ * (Section 2.3.4, Eqs. 15-20) on a block-structured octree of 16^3-cell blocks with two
+ * ghost layers (Section 3.1). One call of agile_step is one full SSP Runge-Kutta step of
+ * the time loop of Fig. 2: per stage a ghost fill (same-level copy, restriction,
+ * prolongation, physical boundaries), the per-block update (primitive recovery, limited
+ * linear reconstruction, HLL or TVDLF flux, flux divergence, stage combine; the macro-kernel
+ * of Section 2.1.3) and the coarse-fine flux correction; the global CFL time step and the
+ * GLM damping (Section 2.3.3) around it. Initialisation follows Fig. 1.
+ *
+ * Conventions
+ *  - Every call returns an agile_status; no call throws, exits or traps. On failure the
+ *    message is available from agile_last_error(mesh).
+ *  - All host buffers are owned by the caller and only read/written during the call.
+ *  - Device memory (state pools, ghost slots, flux registers, descriptors) is owned by
+ *    the mesh and comes from the allocator given at creation (cudaMallocAsync on the
+ *    mesh's stream when NULL). All kernels run on the mesh's stream.
+ *  - Errors found on the device (primitive recovery that does not converge, non-positive
+ *    density or pressure) latch into a device status word and are returned by the next
+ *    synchronising call (agile_cfl_dt, agile_get_state, agile_conserved_sums,
+ *    agile_estimate, agile_regrid, agile_sync).
+ *  - Block order: leaves sorted by refinement level, then by Morton (Z-order) index of
+ *    their integer block coordinates (x lowest bit). Arrays of per-block data follow it.
+ *  - Cell order inside a block: [z][y][x], x fastest, 16 cells per edge, interior only.
+ *  - Floating-point data crosses the ABI in FP64, whatever the stencil precision.
+ */
+#ifndef AGILE_H
+#define AGILE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct agile_mesh agile_mesh;
+
+typedef enum {
+  AGILE_OK = 0,
+  AGILE_EINVAL = 1,     /* invalid argument or configuration */
+  AGILE_ENOMEM = 2,     /* the allocator returned NULL */
+  AGILE_EBUDGET = 3,    /* a requested size exceeds a documented limit */
+  AGILE_ECUDA = 4,      /* a CUDA runtime call failed */
+  AGILE_ENOCONV = 5,    /* SRHD primitive recovery did not converge in 50 iterations */
+  AGILE_EUNPHYS = 6,    /* non-positive density or pressure, or NaN, met on the device */
+  AGILE_ETIMEOUT = 7    /* a bounded device wait gave up */
+} agile_status;
+
+enum { AGILE_HD = 0, AGILE_MHD_GLM = 1, AGILE_SRHD = 2 };      /* physics */
+enum { AGILE_MINMOD = 0, AGILE_VANLEER = 1 };                  /* limiter */
+enum { AGILE_TVDLF = 0, AGILE_HLL = 1 };                       /* Riemann flux */
+enum { AGILE_PERIODIC = 0, AGILE_OUTFLOW = 1, AGILE_REFLECT = 2 }; /* boundaries */
+
+/* Device allocator: alloc(bytes, stream, ctx) returns device memory or NULL;
+ * free(ptr, stream, ctx) releases it. Both are called only from the calling thread. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, void* stream, void* ctx);
+  void* ctx;
+} agile_allocator;
+
+/* Problem description.
+ *  physics        AGILE_HD | AGILE_MHD_GLM | AGILE_SRHD
+ *  limiter        slope limiter of the piecewise-linear reconstruction on primitives
+ *  flux           AGILE_HLL (hd, mhd) or AGILE_TVDLF (all); srhd supports TVDLF only
+ *                 (paper Table 1)
+ *  rk             2 or 3: SSPRK2 (Heun) or SSPRK3 (Shu-Osher "threestep")
+ *  real_bytes     8 (FP64 stencil) or 4 (FP32 stencil; FP64 kept for the SRHD primitive
+ *                 recovery, the CFL reduction and the conserved sums)
+ *  gamma          ratio of specific heats (ideal gas)
+ *  cfl            Courant number: dt = cfl / max_cells sum_d (|v_d| + c_d) / dx_d
+ *  glm_alpha      GLM damping parameter alpha (Section 2.3.3; 0.5 in the paper)
+ *  base_blocks    level-1 blocks per dimension
+ *  xmin, xmax     domain box
+ *  bc             boundary kind per face -x, +x, -y, +y, -z, +z; periodic on both faces
+ *                 of a dimension or on none
+ *  max_level      finest refinement level (1 = uniform grid)
+ *  refine_nvars, refine_vars, refine_weights
+ *                 conserved variables (indices) and weights of the Loehner estimator
+ *  refine_tol     a block refines when its maximum estimate exceeds refine_tol
+ *  derefine_ratio a block may coarsen when its maximum estimate is below
+ *                 refine_tol * derefine_ratio
+ *  lohner_eps     noise filter epsilon of the estimator (0.01)
+ */
+typedef struct {
+  int physics;
+  int limiter;
+  int flux;
+  int rk;
+  int real_bytes;
+  double gamma;
+  double cfl;
+  double glm_alpha;
+  int base_blocks[3];
+  double xmin[3];
+  double xmax[3];
+  int bc[6];
+  int max_level;
+  int refine_nvars;
+  int refine_vars[9];
+  double refine_weights[9];
+  double refine_tol;
+  double derefine_ratio;
+  double lohner_eps;
+} agile_config;
+
+/* Create a mesh of level-1 blocks (Fig. 1, "init level one") with uninitialised state.
+ * alloc: NULL selects cudaMallocAsync / cudaFreeAsync on the stream. cuda_stream: a
+ * cudaStream_t or NULL for the legacy default stream. On success *out owns everything.
+ * Errors: AGILE_EINVAL (bad config), AGILE_ENOMEM, AGILE_ECUDA. */
+agile_status agile_mesh_create(const agile_config* cfg, const agile_allocator* alloc,
+                               void* cuda_stream, agile_mesh** out);
+
+/* Free all device memory of the mesh (through its allocator) and the mesh itself. */
+void agile_mesh_destroy(agile_mesh* mesh);
+
+/* Initial condition callback: fill PRIMITIVE variables prim[var * n + i] for the n cell
+ * centres (x[i], y[i], z[i]) of one block (the user module's initial condition, Fig. 1).
+ * Primitives: hd (rho, vx, vy, vz, p); mhd (rho, v, p, B, psi); srhd (rho, Gamma v, p). */
+typedef void (*agile_ic_fn)(const double* x, const double* y, const double* z, int n,
+                            double* prim, void* user);
+
+/* Evaluate the initial condition on every leaf and upload it (prim -> cons on the device).
+ * The callback is remembered for agile_regrid(init = 1). Errors: AGILE_EINVAL, AGILE_ECUDA,
+ * AGILE_EUNPHYS. */
+agile_status agile_set_state(agile_mesh* mesh, agile_ic_fn ic, void* user);
+
+/* Set the conserved interiors of all leaves: cons[nblk][nvar][16^3] in block order.
+ * nblk must equal the current number of leaves. SRHD auxiliaries are cleared (the next
+ * primitive recovery starts from the bracket midpoint). */
+agile_status agile_set_state_blocks(agile_mesh* mesh, const double* cons, size_t nblk);
+
+/* Global CFL time step of the current state ("Set dt", Fig. 2):
+ * dt = cfl / max over leaf cells of sum_d (|v_d| + c_d) / dx_d, with c_d the sound speed
+ * (hd), the fast magnetosonic speed along d (mhd) or the largest |characteristic speed|
+ * along d (srhd). Also latches c_max = max_cells,d (|v_d| + c_d), the GLM speed c_h.
+ * Synchronises the stream. */
+agile_status agile_cfl_dt(agile_mesh* mesh, double* dt_out);
+
+/* One full SSPRK step of all leaves with time step dt. dt <= 0 takes the CFL step of the
+ * current state from device memory without a host round trip. For MHD the GLM source
+ * psi *= exp(-dt/2 c_h alpha / min dx) is applied before and after the step (Strang
+ * split, Section 2.3.3) with c_h = c_max of the state at the start of the step.
+ * Asynchronous: returns after enqueueing on the mesh's stream. */
+agile_status agile_step(agile_mesh* mesh, double dt);
+
+/* Refine and coarsen from the Loehner estimator (Fig. 2, "error estimator",
+ * "refine/coarsen", "prolong/restrict"): a leaf below max_level whose maximum estimate
+ * exceeds refine_tol refines, and so do its face/edge/corner neighbours at a lower
+ * level (2:1 balance); 8 sibling leaves all below refine_tol * derefine_ratio coarsen
+ * unless a block adjacent to their parent is refined. New children are prolonged
+ * (limited linear, minmod) from the parent; a new parent is the mean of its children.
+ * init = 1 evaluates the initial condition on the new blocks instead (Fig. 1).
+ * n_refined / n_coarsened (may be NULL) receive the counts of refined leaves and of
+ * coarsened parents. Synchronises. */
+agile_status agile_regrid(agile_mesh* mesh, int init, int* n_refined, int* n_coarsened);
+
+/* Regrid with caller-chosen flags instead of the estimator: flags[nblk] in block order,
+ * +1 refine, -1 coarsen candidate, 0 keep; the same 2:1 rules apply. */
+agile_status agile_regrid_flags(agile_mesh* mesh, const int* flags, int init,
+                                int* n_refined, int* n_coarsened);
+
+/* Number of leaves and of conserved variables (5 hd/srhd, 9 mhd). */
+agile_status agile_get_layout(agile_mesh* mesh, size_t* nblocks, int* nvar);
+
+/* Copy the state to the host: level[nblk] (1-based), ijk[nblk][3] integer block
+ * coordinates at that level, cons[nblk][nvar][16^3] (FP64). Any pointer may be NULL.
+ * Synchronises. */
+agile_status agile_get_state(agile_mesh* mesh, int* level, int* ijk, double* cons);
+
+/* SRHD auxiliaries (xi, Gamma) of the interiors: aux[nblk][2][16^3]. AGILE_EINVAL for
+ * other physics. Synchronises. */
+agile_status agile_get_aux(agile_mesh* mesh, double* aux);
+
+/* Volume integrals of the conserved variables over the leaves (FP64 sums of
+ * U * cell volume; the paper's high-cadence mass/energy log, Section 4.1). Synchronises. */
+agile_status agile_conserved_sums(agile_mesh* mesh, double* sums);
+
+/* Maximum Loehner estimate of every leaf (block order) on the current state after a
+ * full ghost fill, computed in FP64 without fused multiply-add so that refinement
+ * decisions are reproducible bit for bit. Synchronises. */
+agile_status agile_estimate(agile_mesh* mesh, double* emax);
+
+/* Face-ghost view of one leaf after a full ghost fill of the current state:
+ * out[nvar + naux][20][20][20] (FP64) with the interior at [2, 18) and the six face-ghost
+ * slabs filled; edge and corner cells are NaN (the face-based stencil never reads them).
+ * Synchronises. */
+agile_status agile_get_halo(agile_mesh* mesh, size_t block, double* out);
+
+/* Wait for all work on the mesh's stream and return any latched device error. */
+agile_status agile_sync(agile_mesh* mesh);
+
+/* Kernel timing with CUDA events recorded on the mesh's stream around every launch of the
+ * stage (update) kernel. enable = 1 resets and starts accumulating; agile_kernel_timing
+ * synchronises and returns the summed milliseconds and the launch count. */
+agile_status agile_set_kernel_timing(agile_mesh* mesh, int enable);
+agile_status agile_kernel_timing(agile_mesh* mesh, double* stage_ms, long long* stage_launches,
+                                 long long* total_launches);
+
+/* Message of the last failed call on this mesh (static storage owned by the mesh). */
+const char* agile_last_error(const agile_mesh* mesh);
+
+/* Library version string. */
+const char* agile_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AGILE_H */

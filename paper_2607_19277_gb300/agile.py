@@ -1,0 +1,298 @@
+"""Thin Python binding of libagile.so (ctypes): argument marshalling only.
+
+Every numerical step runs in the library's CUDA kernels. PyTorch supplies device memory
+(its caching allocator, injected through agile_allocator) and the CUDA stream. There is no
+fallback: if the compiled library is missing, loading raises.
+
+The functions keep the C names (agile_mesh_create, agile_set_state, agile_cfl_dt,
+agile_step, agile_regrid, agile_get_state, ...); `Mesh` wraps one mesh handle.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libagile.so")
+NCELL = 4096
+
+PHYSICS = {"hd": 0, "mhd": 1, "srhd": 2}
+LIMITER = {"minmod": 0, "vanleer": 1}
+FLUX = {"tvdlf": 0, "hll": 1}
+BC = {"periodic": 0, "outflow": 1, "reflect": 2}
+STATUS = {0: "AGILE_OK", 1: "AGILE_EINVAL", 2: "AGILE_ENOMEM", 3: "AGILE_EBUDGET",
+          4: "AGILE_ECUDA", 5: "AGILE_ENOCONV", 6: "AGILE_EUNPHYS", 7: "AGILE_ETIMEOUT"}
+
+# Symbols declared in include/agile.h (checked by the CPU test suite).
+EXPORTS = ["agile_mesh_create", "agile_mesh_destroy", "agile_set_state", "agile_set_state_blocks",
+           "agile_cfl_dt", "agile_step", "agile_regrid", "agile_regrid_flags", "agile_get_layout",
+           "agile_get_state", "agile_get_aux", "agile_conserved_sums", "agile_estimate",
+           "agile_get_halo", "agile_sync", "agile_set_kernel_timing", "agile_kernel_timing",
+           "agile_last_error", "agile_version"]
+
+
+class agile_config(C.Structure):
+    _fields_ = [("physics", C.c_int), ("limiter", C.c_int), ("flux", C.c_int), ("rk", C.c_int),
+                ("real_bytes", C.c_int), ("gamma", C.c_double), ("cfl", C.c_double),
+                ("glm_alpha", C.c_double), ("base_blocks", C.c_int * 3), ("xmin", C.c_double * 3),
+                ("xmax", C.c_double * 3), ("bc", C.c_int * 6), ("max_level", C.c_int),
+                ("refine_nvars", C.c_int), ("refine_vars", C.c_int * 9),
+                ("refine_weights", C.c_double * 9), ("refine_tol", C.c_double),
+                ("derefine_ratio", C.c_double), ("lohner_eps", C.c_double)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+IC_FN = C.CFUNCTYPE(None, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                    C.c_int, C.POINTER(C.c_double), C.c_void_p)
+
+
+class agile_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+class AgileError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libagile.so (build it first with paper_2607_19277_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError("libagile.so not built at %s; run paper_2607_19277_gb300.build.build()" % path)
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    dp = C.POINTER(C.c_double)
+    ip = C.POINTER(C.c_int)
+    sig = {
+        "agile_mesh_create": (C.c_int, [C.POINTER(agile_config), C.POINTER(agile_allocator), P, C.POINTER(P)]),
+        "agile_mesh_destroy": (None, [P]),
+        "agile_set_state": (C.c_int, [P, IC_FN, P]),
+        "agile_set_state_blocks": (C.c_int, [P, dp, C.c_size_t]),
+        "agile_cfl_dt": (C.c_int, [P, dp]),
+        "agile_step": (C.c_int, [P, C.c_double]),
+        "agile_regrid": (C.c_int, [P, C.c_int, ip, ip]),
+        "agile_regrid_flags": (C.c_int, [P, ip, C.c_int, ip, ip]),
+        "agile_get_layout": (C.c_int, [P, C.POINTER(C.c_size_t), ip]),
+        "agile_get_state": (C.c_int, [P, ip, ip, dp]),
+        "agile_get_aux": (C.c_int, [P, dp]),
+        "agile_conserved_sums": (C.c_int, [P, dp]),
+        "agile_estimate": (C.c_int, [P, dp]),
+        "agile_get_halo": (C.c_int, [P, C.c_size_t, dp]),
+        "agile_sync": (C.c_int, [P]),
+        "agile_set_kernel_timing": (C.c_int, [P, C.c_int]),
+        "agile_kernel_timing": (C.c_int, [P, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+        "agile_last_error": (C.c_char_p, [P]),
+        "agile_version": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def make_config(physics="hd", limiter="minmod", flux="hll", rk=2, real_bytes=8, gamma=5.0 / 3.0,
+                cfl=0.4, glm_alpha=0.5, base_blocks=(4, 4, 4), xmin=(0.0, 0.0, 0.0),
+                xmax=(1.0, 1.0, 1.0), bc=("periodic",) * 6, max_level=1, refine_vars=(0,),
+                refine_weights=(1.0,), refine_tol=0.2, derefine_ratio=1.0 / 8.0,
+                lohner_eps=0.01) -> agile_config:
+    c = agile_config()
+    c.physics = PHYSICS[physics]
+    c.limiter = LIMITER[limiter]
+    c.flux = FLUX[flux]
+    c.rk = rk
+    c.real_bytes = real_bytes
+    c.gamma = gamma
+    c.cfl = cfl
+    c.glm_alpha = glm_alpha
+    for d in range(3):
+        c.base_blocks[d] = base_blocks[d]
+        c.xmin[d] = xmin[d]
+        c.xmax[d] = xmax[d]
+    for f in range(6):
+        c.bc[f] = BC[bc[f]] if isinstance(bc[f], str) else bc[f]
+    c.max_level = max_level
+    c.refine_nvars = len(refine_vars)
+    for i, (v, w) in enumerate(zip(refine_vars, refine_weights)):
+        c.refine_vars[i] = v
+        c.refine_weights[i] = w
+    c.refine_tol = refine_tol
+    c.derefine_ratio = derefine_ratio
+    c.lohner_eps = lohner_eps
+    return c
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _iptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+class _TorchAllocator:
+    """Device memory from PyTorch's caching allocator on the mesh's stream."""
+
+    def __init__(self, device):
+        import torch
+        self.torch = torch
+        self.device = device
+
+        def alloc(nbytes, stream, ctx):
+            try:
+                return self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, int(stream or 0))
+            except Exception:
+                return None
+
+        def free(ptr, stream, ctx):
+            if ptr:
+                self.torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.c_alloc = ALLOC_FN(alloc)
+        self.c_free = FREE_FN(free)
+        self.struct = agile_allocator(self.c_alloc, self.c_free, None)
+
+
+def _check(lib, mesh_ptr, st):
+    if st != 0:
+        msg = lib.agile_last_error(mesh_ptr) if mesh_ptr else b""
+        raise AgileError(st, (msg or b"").decode())
+
+
+def agile_mesh_create(cfg: agile_config, allocator=None, stream: int = 0):
+    lib = load()
+    out = C.c_void_p()
+    st = lib.agile_mesh_create(C.byref(cfg), C.byref(allocator) if allocator is not None else None,
+                               C.c_void_p(stream), C.byref(out))
+    _check(lib, None, st)
+    return out
+
+
+class Mesh:
+    """One block-AMR mesh on the current CUDA device and stream (torch's allocator)."""
+
+    def __init__(self, cfg: agile_config, stream=None, use_torch_allocator=True):
+        import torch
+        self.lib = load()
+        self.cfg = cfg
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self._alloc = _TorchAllocator(torch.cuda.current_device()) if use_torch_allocator else None
+        self.ptr = agile_mesh_create(cfg, self._alloc.struct if self._alloc else None,
+                                     int(stream.cuda_stream))
+        self.nvar = 9 if cfg.physics == 1 else 5
+        self.naux = 2 if cfg.physics == 2 else 0
+        self._ic = None
+
+    def close(self):
+        if self.ptr:
+            self.lib.agile_mesh_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, st):
+        _check(self.lib, self.ptr, st)
+
+    # --- calls of the C ABI -------------------------------------------------------------
+    def set_state(self, ic):
+        """ic(x, y, z) -> prim[nvar, n] (numpy); evaluated per block on the host."""
+        nvar = self.nvar
+
+        def cb(x, y, z, n, prim, user):
+            xs = np.ctypeslib.as_array(x, shape=(n,)).copy()
+            ys = np.ctypeslib.as_array(y, shape=(n,)).copy()
+            zs = np.ctypeslib.as_array(z, shape=(n,)).copy()
+            out = np.ctypeslib.as_array(prim, shape=(nvar * n,))
+            out[:] = np.asarray(ic(xs, ys, zs), dtype=np.float64).reshape(nvar * n)
+
+        self._ic = IC_FN(cb)   # kept alive: the library calls it again at regrid(init=1)
+        self._ck(self.lib.agile_set_state(self.ptr, self._ic, None))
+
+    def set_state_blocks(self, cons):
+        cons = np.ascontiguousarray(cons, dtype=np.float64)
+        self._ck(self.lib.agile_set_state_blocks(self.ptr, _dptr(cons), cons.shape[0]))
+
+    def cfl_dt(self) -> float:
+        dt = C.c_double()
+        self._ck(self.lib.agile_cfl_dt(self.ptr, C.byref(dt)))
+        return dt.value
+
+    def step(self, dt: float = 0.0):
+        self._ck(self.lib.agile_step(self.ptr, float(dt)))
+
+    def regrid(self, init=False):
+        nr, nc = C.c_int(), C.c_int()
+        self._ck(self.lib.agile_regrid(self.ptr, int(init), C.byref(nr), C.byref(nc)))
+        return nr.value, nc.value
+
+    def regrid_flags(self, flags, init=False):
+        f = np.ascontiguousarray(flags, dtype=np.int32)
+        nr, nc = C.c_int(), C.c_int()
+        self._ck(self.lib.agile_regrid_flags(self.ptr, _iptr(f), int(init), C.byref(nr), C.byref(nc)))
+        return nr.value, nc.value
+
+    def layout(self):
+        n = C.c_size_t()
+        nv = C.c_int()
+        self._ck(self.lib.agile_get_layout(self.ptr, C.byref(n), C.byref(nv)))
+        return n.value, nv.value
+
+    def get_state(self):
+        n, nv = self.layout()
+        lev = np.zeros(n, dtype=np.int32)
+        ijk = np.zeros((n, 3), dtype=np.int32)
+        cons = np.zeros((n, nv, 16, 16, 16))
+        self._ck(self.lib.agile_get_state(self.ptr, _iptr(lev), _iptr(ijk), _dptr(cons)))
+        return lev, ijk, cons
+
+    def get_aux(self):
+        n, _ = self.layout()
+        aux = np.zeros((n, 2, 16, 16, 16))
+        self._ck(self.lib.agile_get_aux(self.ptr, _dptr(aux)))
+        return aux
+
+    def conserved_sums(self):
+        s = np.zeros(self.nvar)
+        self._ck(self.lib.agile_conserved_sums(self.ptr, _dptr(s)))
+        return s
+
+    def estimate(self):
+        n, _ = self.layout()
+        e = np.zeros(n)
+        self._ck(self.lib.agile_estimate(self.ptr, _dptr(e)))
+        return e
+
+    def get_halo(self, block):
+        out = np.zeros((self.nvar + self.naux, 20, 20, 20))
+        self._ck(self.lib.agile_get_halo(self.ptr, block, _dptr(out)))
+        return out
+
+    def sync(self):
+        self._ck(self.lib.agile_sync(self.ptr))
+
+    def set_kernel_timing(self, enable=True):
+        self._ck(self.lib.agile_set_kernel_timing(self.ptr, int(enable)))
+
+    def kernel_timing(self):
+        ms = C.c_double()
+        n = C.c_longlong()
+        tot = C.c_longlong()
+        self._ck(self.lib.agile_kernel_timing(self.ptr, C.byref(ms), C.byref(n), C.byref(tot)))
+        return ms.value, n.value, tot.value

@@ -1,0 +1,552 @@
+// Non-update kernels: coarse-fine ghost slots (restriction, limited-linear prolongation),
+// coarse-fine flux correction, global signal-speed reduction for the CFL step, GLM damping,
+// Loehner estimator, regrid prolongation/restriction, state packing and conserved sums.
+#include <math.h>
+
+#include "kernels.cuh"
+#include "launch.h"
+
+namespace agile {
+
+int phys_nvar(int phys) { return phys == PH_MHD ? 9 : 5; }
+int phys_naux(int phys) { return phys == PH_SRHD ? 2 : 0; }
+
+// ------------------------------------------------------------------------------ helpers
+template <typename R>
+__device__ __forceinline__ R minmod_(R a, R b) {
+  return (a > R(0) && b > R(0)) ? (a < b ? a : b) : ((a < R(0) && b < R(0)) ? (a > b ? a : b) : R(0));
+}
+
+// Mean of the 8 fine cells with lower corner (fx, fy, fz) of block fb; x fastest, then
+// y, then z, added in that order and scaled by 1/8 (volume-average restriction).
+template <typename R, int NT>
+__device__ __forceinline__ void restrict8(const R* __restrict__ U, int fb, int fx, int fy, int fz,
+                                          R* out) {
+  const R* p = U + (size_t)fb * NT * NCELL + fz * 256 + fy * 16 + fx;
+#pragma unroll
+  for (int v = 0; v < NT; ++v) {
+    const R* q = p + (size_t)v * NCELL;
+    R s = q[0] + q[1];
+    s = s + q[16];
+    s = s + q[17];
+    s = s + q[256];
+    s = s + q[257];
+    s = s + q[272];
+    s = s + q[273];
+    out[v] = s * R(0.125);
+  }
+}
+
+// Value of cell (x, y, z) in the halo view of a COARSE block C as the prolongation sees it:
+// the interior, and face ghosts from a same-level copy, a physical boundary or restriction
+// of the finer neighbour. A face whose neighbour is still coarser is not available (false).
+template <class P, typename R>
+__device__ __forceinline__ bool coarse_view(const R* __restrict__ U, const BlockDesc* __restrict__ bd,
+                                            int C, int x, int y, int z, R* u) {
+  constexpr int NT = P::NV + P::NA;
+  int f = -1;
+  if (x < 0) f = 0;
+  else if (x > NB - 1) f = 1;
+  else if (y < 0) f = 2;
+  else if (y > NB - 1) f = 3;
+  else if (z < 0) f = 4;
+  else if (z > NB - 1) f = 5;
+  if (f >= 0) {
+    const int kind = bd[C].kind[f];
+    if (kind == FK_COARSER) return false;
+    if (kind == FK_FINER) {
+      const int d = f >> 1, s = f & 1;
+      int q[3] = {x, y, z};
+      const int t1 = d == 0 ? q[1] : q[0];
+      const int t2 = d == 2 ? q[1] : q[2];
+      const int fb = bd[C].nbr[f][(t1 >> 3) + 2 * (t2 >> 3)];
+      int fq[3];
+      fq[d] = s ? 0 : NB - 2;
+      const int t1d = d == 0 ? 1 : 0, t2d = d == 2 ? 1 : 2;
+      fq[t1d] = 2 * (t1 & 7);
+      fq[t2d] = 2 * (t2 & 7);
+      restrict8<R, NT>(U, fb, fq[0], fq[1], fq[2], u);
+      return true;
+    }
+  }
+  int src[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) src[i] = bd[C].src[i];
+  load_cell<P, R>(U, (const R*)nullptr, src, C, x, y, z, u);
+  return true;
+}
+
+// ------------------------------------------------------------------------------ ghost slots
+template <template <typename> class PT, typename R>
+__global__ void __launch_bounds__(256) ghost_kernel(const R* __restrict__ U, R* __restrict__ G,
+                                                     const BlockDesc* __restrict__ bd,
+                                                     const GhostTask* __restrict__ tasks) {
+  using P = PT<R>;
+  constexpr int NT = P::NV + P::NA;
+  const GhostTask tk = tasks[blockIdx.x];
+  const int d = tk.face >> 1, s = tk.face & 1;
+  const int t1d = d == 0 ? 1 : 0, t2d = d == 2 ? 1 : 2;
+  for (int c = threadIdx.x; c < 512; c += 256) {
+    const int layer = c >> 8, t2 = (c >> 4) & 15, t1 = c & 15;
+    R out[NT];
+    if (tk.kind == FK_FINER) {
+      const int fb = tk.nbr[(t1 >> 3) + 2 * (t2 >> 3)];
+      int fq[3];
+      fq[d] = s ? 2 * layer : NB - 4 + 2 * layer;
+      fq[t1d] = 2 * (t1 & 7);
+      fq[t2d] = 2 * (t2 & 7);
+      restrict8<R, NT>(U, fb, fq[0], fq[1], fq[2], out);
+    } else {
+      // fine ghost cell in neighbour-position-local fine coordinates f, coarse cell c
+      int f3[3];
+      f3[d] = s ? layer : NB - 2 + layer;
+      f3[t1d] = t1;
+      f3[t2d] = t2;
+      int cc[3];
+      R sg[3];
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        cc[e] = 8 * tk.par[e] + (f3[e] >> 1);
+        sg[e] = (f3[e] & 1) ? R(1) : R(-1);
+      }
+      const int C = tk.nbr[0];
+      R uc[NT], up[NT], um[NT];
+      coarse_view<P, R>(U, bd, C, cc[0], cc[1], cc[2], uc);
+      R acc[NT];
+#pragma unroll
+      for (int v = 0; v < NT; ++v) acc[v] = R(0);
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        int pp[3] = {cc[0], cc[1], cc[2]}, mm[3] = {cc[0], cc[1], cc[2]};
+        pp[e] += 1;
+        mm[e] -= 1;
+        const bool okp = coarse_view<P, R>(U, bd, C, pp[0], pp[1], pp[2], up);
+        const bool okm = coarse_view<P, R>(U, bd, C, mm[0], mm[1], mm[2], um);
+#pragma unroll
+        for (int v = 0; v < NT; ++v) {
+          const R sig = (okp && okm) ? minmod_(up[v] - uc[v], uc[v] - um[v]) : R(0);
+          if (e == 0) acc[v] = sg[0] * sig;
+          else acc[v] = acc[v] + sg[e] * sig;
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < NT; ++v) out[v] = uc[v] + R(0.25) * acc[v];
+    }
+    R* g = G + (size_t)tk.slot * NT * 512 + layer * 256 + t2 * 16 + t1;
+#pragma unroll
+    for (int v = 0; v < NT; ++v) g[(size_t)v * 512] = out[v];
+  }
+}
+
+// ------------------------------------------------------------------------------ flux fix-up
+template <typename R, int NV, int NT>
+__global__ void __launch_bounds__(256) fixup_kernel(R* __restrict__ U, const R* __restrict__ FR,
+                                                     const BlockDesc* __restrict__ bd,
+                                                     const FixupTask* __restrict__ tasks, double b,
+                                                     const double* __restrict__ dtch) {
+  const FixupTask tk = tasks[blockIdx.x];
+  const int d = tk.face >> 1, s = tk.face & 1;
+  const int t1 = threadIdx.x & 15, t2 = threadIdx.x >> 4;
+  const int t1d = d == 0 ? 1 : 0, t2d = d == 2 ? 1 : 2;
+  int q[3];
+  q[d] = s ? NB - 1 : 0;
+  q[t1d] = t1;
+  q[t2d] = t2;
+  const size_t cell = (size_t)q[2] * 256 + q[1] * 16 + q[0];
+  const int sf = tk.slot_f[(t1 >> 3) + 2 * (t2 >> 3)];
+  const int a0 = 2 * (t1 & 7), b0 = 2 * (t2 & 7);
+  const R w = R(b * dtch[0] / bd[tk.blk].dx[d]) * (s ? R(1) : R(-1));
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const R fc = FR[((size_t)tk.slot_c * NV + v) * 256 + t2 * 16 + t1];
+    const R* ff = FR + ((size_t)sf * NV + v) * 256;
+    R avg = ff[b0 * 16 + a0] + ff[b0 * 16 + a0 + 1];
+    avg = avg + ff[(b0 + 1) * 16 + a0];
+    avg = avg + ff[(b0 + 1) * 16 + a0 + 1];
+    avg = avg * R(0.25);
+    R* u = U + ((size_t)tk.blk * NT + v) * NCELL + cell;
+    *u = *u + w * (fc - avg);
+  }
+}
+
+// ------------------------------------------------------------------------------ CFL speeds
+template <template <typename> class PT, typename R>
+__global__ void __launch_bounds__(256) speeds_kernel(const R* __restrict__ U,
+                                                      const BlockDesc* __restrict__ bd, double gamma,
+                                                      unsigned long long* speeds, int* status) {
+  using P = PT<double>;
+  constexpr int NV = P::NV, NA = P::NA, NT = NV + NA;
+  const int b = blockIdx.x;
+  const double dx[3] = {bd[b].dx[0], bd[b].dx[1], bd[b].dx[2]};
+  PhysParams pp;
+  pp.gamma = gamma;
+  pp.ch = 0.0;
+  double ssum = 0.0, smax = 0.0;
+  int st = 0;
+  const R* base = U + (size_t)b * NT * NCELL;
+  for (int c = threadIdx.x; c < NCELL; c += 256) {
+    double u[NT], aux[2] = {0.0, 0.0};
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u[v] = (double)base[(size_t)v * NCELL + c];
+    if constexpr (NA > 0) aux[0] = (double)base[(size_t)NV * NCELL + c];
+    cell_speeds<PT>(u, aux, pp, dx, ssum, smax, st);
+  }
+  block_max2<256>(ssum, smax, speeds);
+  if (st) atomicOr(status, st);
+}
+
+__global__ void set_dt_kernel(const unsigned long long* speeds, double* dtch, double dt_host,
+                              double cfl) {
+  const double smax = __longlong_as_double((long long)speeds[0]);
+  const double cmax = __longlong_as_double((long long)speeds[1]);
+  dtch[0] = dt_host > 0.0 ? dt_host : cfl / smax;
+  dtch[1] = cmax;
+}
+
+// ------------------------------------------------------------------------------ GLM source
+template <typename R>
+__global__ void glm_decay_kernel(R* __restrict__ U, const BlockDesc* __restrict__ bd,
+                                 const double* __restrict__ dtch, double alpha) {
+  const int b = blockIdx.x;
+  const double dxm = fmin(fmin(bd[b].dx[0], bd[b].dx[1]), bd[b].dx[2]);
+  const double f = exp(-0.5 * dtch[0] * dtch[1] * alpha / dxm);
+  R* psi = U + ((size_t)b * 9 + 8) * NCELL;
+  for (int c = threadIdx.x; c < NCELL; c += blockDim.x) psi[c] = R((double)psi[c] * f);
+}
+
+// ------------------------------------------------------------------------------ estimator
+// Loehner (1987) second-derivative estimate per cell and variable (axis terms only):
+// E_u = sqrt(sum_d (u+ - 2u0 + u-)^2 / sum_d (|u+ - u0| + |u0 - u-| + eps (|u+| + 2|u0| + |u-|))^2),
+// E = sum_u w_u E_u; every operation rounded on its own (no FMA) in this order.
+template <template <typename> class PT, typename R>
+__global__ void __launch_bounds__(256) estimate_kernel(const R* __restrict__ U, const R* __restrict__ G,
+                                                        const BlockDesc* __restrict__ bd,
+                                                        const int* __restrict__ vars,
+                                                        const double* __restrict__ weights, int nvars,
+                                                        double eps, double* __restrict__ emax) {
+  using P = PT<R>;
+  constexpr int NT = P::NV + P::NA;
+  const int b = blockIdx.x;
+  int src[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) src[i] = bd[b].src[i];
+  double best = 0.0;
+  for (int c = threadIdx.x; c < NCELL; c += 256) {
+    const int x = c & 15, y = (c >> 4) & 15, z = c >> 8;
+    R u0[NT], up[3][NT], um[3][NT];
+    load_cell<P, R>(U, G, src, b, x, y, z, u0);
+    for (int d = 0; d < 3; ++d) {
+      int p[3] = {x, y, z}, m[3] = {x, y, z};
+      p[d] += 1;
+      m[d] -= 1;
+      load_cell<P, R>(U, G, src, b, p[0], p[1], p[2], up[d]);
+      load_cell<P, R>(U, G, src, b, m[0], m[1], m[2], um[d]);
+    }
+    double etot = 0.0;
+    for (int i = 0; i < nvars; ++i) {
+      const int iv = vars[i];
+      double num = 0.0, den = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        const double a = (double)up[d][iv], o = (double)u0[iv], m = (double)um[d][iv];
+        const double t = __dadd_rn(__dsub_rn(a, __dmul_rn(2.0, o)), m);
+        const double q = __dadd_rn(__dadd_rn(fabs(__dsub_rn(a, o)), fabs(__dsub_rn(o, m))),
+                                   __dmul_rn(eps, __dadd_rn(__dadd_rn(fabs(a), __dmul_rn(2.0, fabs(o))),
+                                                            fabs(m))));
+        const double t2 = __dmul_rn(t, t), q2 = __dmul_rn(q, q);
+        num = d == 0 ? t2 : __dadd_rn(num, t2);
+        den = d == 0 ? q2 : __dadd_rn(den, q2);
+      }
+      const double e = den > 0.0 ? __dsqrt_rn(__ddiv_rn(num, den)) : 0.0;
+      const double we = __dmul_rn(weights[i], e);
+      etot = i == 0 ? we : __dadd_rn(etot, we);
+    }
+    best = fmax(best, etot);
+  }
+  __shared__ double red[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = red[0];
+    for (int i = 1; i < 8; ++i) m = fmax(m, red[i]);
+    emax[b] = m;
+  }
+}
+
+// ------------------------------------------------------------------------------ regrid
+template <template <typename> class PT, typename R>
+__global__ void __launch_bounds__(256) regrid_kernel(const R* __restrict__ Uold, const R* __restrict__ Gold,
+                                                      const BlockDesc* __restrict__ bdold,
+                                                      R* __restrict__ Unew,
+                                                      const RegridSrc* __restrict__ srcs) {
+  using P = PT<R>;
+  constexpr int NT = P::NV + P::NA;
+  const int nb = blockIdx.x;
+  const RegridSrc rs = srcs[nb];
+  R* out = Unew + (size_t)nb * NT * NCELL;
+  if (rs.mode == 0) {
+    const R* in = Uold + (size_t)rs.src[0] * NT * NCELL;
+    for (int i = threadIdx.x; i < NT * NCELL; i += 256) out[i] = in[i];
+    return;
+  }
+  for (int c = threadIdx.x; c < NCELL; c += 256) {
+    const int x = c & 15, y = (c >> 4) & 15, z = c >> 8;
+    R val[NT];
+    if (rs.mode == 2) {
+      const int o = (x >> 3) + 2 * (y >> 3) + 4 * (z >> 3);
+      restrict8<R, NT>(Uold, rs.src[o], 2 * (x & 7), 2 * (y & 7), 2 * (z & 7), val);
+    } else {
+      const int P0 = rs.src[0];
+      int src[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) src[i] = bdold[P0].src[i];
+      const int fo[3] = {16 * (rs.octant & 1), 16 * ((rs.octant >> 1) & 1), 16 * (rs.octant >> 2)};
+      const int f3[3] = {fo[0] + x, fo[1] + y, fo[2] + z};
+      int cc[3];
+      R sg[3];
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        cc[e] = f3[e] >> 1;
+        sg[e] = (f3[e] & 1) ? R(1) : R(-1);
+      }
+      R uc[NT], up[NT], um[NT], acc[NT];
+      load_cell<P, R>(Uold, Gold, src, P0, cc[0], cc[1], cc[2], uc);
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        int pp[3] = {cc[0], cc[1], cc[2]}, mm[3] = {cc[0], cc[1], cc[2]};
+        pp[e] += 1;
+        mm[e] -= 1;
+        load_cell<P, R>(Uold, Gold, src, P0, pp[0], pp[1], pp[2], up);
+        load_cell<P, R>(Uold, Gold, src, P0, mm[0], mm[1], mm[2], um);
+#pragma unroll
+        for (int v = 0; v < NT; ++v) {
+          const R sig = minmod_(up[v] - uc[v], uc[v] - um[v]);
+          acc[v] = e == 0 ? sg[0] * sig : acc[v] + sg[e] * sig;
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < NT; ++v) val[v] = uc[v] + R(0.25) * acc[v];
+    }
+#pragma unroll
+    for (int v = 0; v < NT; ++v) out[(size_t)v * NCELL + c] = val[v];
+  }
+}
+
+// ------------------------------------------------------------------------------ state I/O
+template <template <typename> class PT, typename R>
+__global__ void prim2cons_kernel(R* __restrict__ U, const double* __restrict__ prim,
+                                 const int* __restrict__ blocks, double gamma) {
+  using P = PT<double>;
+  constexpr int NV = P::NV, NA = P::NA, NT = NV + NA;
+  const int i = blockIdx.x;
+  const int b = blocks[i];
+  PhysParams pp;
+  pp.gamma = gamma;
+  pp.ch = 0.0;
+  for (int c = threadIdx.x; c < NCELL; c += blockDim.x) {
+    double p[NV], u[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) p[v] = prim[((size_t)i * NV + v) * NCELL + c];
+    P::prim2cons(p, u, pp);
+    R* o = U + (size_t)b * NT * NCELL + c;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) o[(size_t)v * NCELL] = R(u[v]);
+    if constexpr (NA > 0) {
+      // xi = Gamma^2 rho h and Gamma from the primitives (Eq. 19)
+      const double lor = sqrt(1.0 + p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+      const double h = 1.0 + gamma / (gamma - 1.0) * p[4] / p[0];
+      o[(size_t)NV * NCELL] = R(lor * lor * p[0] * h);
+      o[(size_t)(NV + 1) * NCELL] = R(lor);
+    }
+  }
+}
+
+template <typename R>
+__global__ void unpack_kernel(R* __restrict__ U, const double* __restrict__ cons, int nv, int na) {
+  const int b = blockIdx.x;
+  const int nt = nv + na;
+  for (int i = threadIdx.x; i < nt * NCELL; i += blockDim.x) {
+    const int v = i / NCELL;
+    U[(size_t)b * nt * NCELL + i] = v < nv ? R(cons[(size_t)b * nv * NCELL + i]) : R(0);
+  }
+}
+
+template <typename R>
+__global__ void pack_kernel(const R* __restrict__ U, double* __restrict__ cons, double* __restrict__ aux,
+                            int nv, int na) {
+  const int b = blockIdx.x;
+  const int nt = nv + na;
+  for (int i = threadIdx.x; i < nt * NCELL; i += blockDim.x) {
+    const int v = i / NCELL;
+    const double val = (double)U[(size_t)b * nt * NCELL + i];
+    if (v < nv) {
+      if (cons) cons[(size_t)b * nv * NCELL + i] = val;
+    } else if (aux) {
+      aux[(size_t)b * na * NCELL + (i - nv * NCELL)] = val;
+    }
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) sums_kernel(const R* __restrict__ U, const BlockDesc* __restrict__ bd,
+                                                    double* __restrict__ part, int nv, int na) {
+  const int b = blockIdx.x;
+  const int nt = nv + na;
+  const double dv = bd[b].dx[0] * bd[b].dx[1] * bd[b].dx[2];
+  __shared__ double red[8];
+  for (int v = 0; v < nv; ++v) {
+    const R* p = U + ((size_t)b * nt + v) * NCELL;
+    double s = 0.0;
+    for (int c = threadIdx.x; c < NCELL; c += 256) s += (double)p[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int i = 0; i < 8; ++i) t += red[i];
+      part[(size_t)b * nv + v] = t * dv;
+    }
+    __syncthreads();
+  }
+}
+
+template <template <typename> class PT, typename R>
+__global__ void halo_kernel(const R* __restrict__ U, const R* __restrict__ G,
+                            const BlockDesc* __restrict__ bd, int b, double* __restrict__ out) {
+  using P = PT<R>;
+  constexpr int NT = P::NV + P::NA;
+  int src[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) src[i] = bd[b].src[i];
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < 8000; c += gridDim.x * blockDim.x) {
+    const int x = c % 20 - 2, y = (c / 20) % 20 - 2, z = c / 400 - 2;
+    const int outside = (x < 0 || x > 15) + (y < 0 || y > 15) + (z < 0 || z > 15);
+    if (outside > 1) {
+      for (int v = 0; v < NT; ++v) out[(size_t)v * 8000 + c] = __longlong_as_double(0x7ff8000000000000LL);
+      continue;
+    }
+    R u[NT];
+    load_cell<P, R>(U, G, src, b, x, y, z, u);
+    for (int v = 0; v < NT; ++v) out[(size_t)v * 8000 + c] = (double)u[v];
+  }
+}
+
+// ------------------------------------------------------------------------------ dispatch
+#define AGILE_DISPATCH(phys, rb, CALL)                         \
+  do {                                                         \
+    if ((phys) == PH_HD) {                                     \
+      if ((rb) == 8) { using R = double; CALL(HdPhys); }       \
+      else { using R = float; CALL(HdPhys); }                  \
+    } else if ((phys) == PH_MHD) {                             \
+      if ((rb) == 8) { using R = double; CALL(MhdPhys); }      \
+      else { using R = float; CALL(MhdPhys); }                 \
+    } else {                                                   \
+      if ((rb) == 8) { using R = double; CALL(SrhdPhys); }     \
+      else { using R = float; CALL(SrhdPhys); }                \
+    }                                                          \
+  } while (0)
+
+cudaError_t launch_ghosts(const AuxArgs& a, const GhostTask* tasks, int ntasks, cudaStream_t s) {
+  if (ntasks == 0) return cudaSuccess;
+#define CALL(PT) ghost_kernel<PT, R><<<ntasks, 256, 0, s>>>((const R*)a.U, (R*)a.Gw, a.bd, tasks)
+  AGILE_DISPATCH(a.phys, a.real_bytes, CALL);
+#undef CALL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fixup(const AuxArgs& a, const FixupTask* tasks, int ntasks, double b,
+                         const double* dtch, cudaStream_t s) {
+  if (ntasks == 0) return cudaSuccess;
+  const int nv = phys_nvar(a.phys), nt = nv + phys_naux(a.phys);
+  if (a.real_bytes == 8) {
+    if (nv == 9) fixup_kernel<double, 9, 9><<<ntasks, 256, 0, s>>>((double*)a.Uw, (const double*)a.FR, a.bd, tasks, b, dtch);
+    else if (nt == 5) fixup_kernel<double, 5, 5><<<ntasks, 256, 0, s>>>((double*)a.Uw, (const double*)a.FR, a.bd, tasks, b, dtch);
+    else fixup_kernel<double, 5, 7><<<ntasks, 256, 0, s>>>((double*)a.Uw, (const double*)a.FR, a.bd, tasks, b, dtch);
+  } else {
+    if (nv == 9) fixup_kernel<float, 9, 9><<<ntasks, 256, 0, s>>>((float*)a.Uw, (const float*)a.FR, a.bd, tasks, b, dtch);
+    else if (nt == 5) fixup_kernel<float, 5, 5><<<ntasks, 256, 0, s>>>((float*)a.Uw, (const float*)a.FR, a.bd, tasks, b, dtch);
+    else fixup_kernel<float, 5, 7><<<ntasks, 256, 0, s>>>((float*)a.Uw, (const float*)a.FR, a.bd, tasks, b, dtch);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_speeds(const AuxArgs& a, unsigned long long* speeds, cudaStream_t s) {
+  if (a.nblk == 0) return cudaSuccess;
+#define CALL(PT) speeds_kernel<PT, R><<<a.nblk, 256, 0, s>>>((const R*)a.U, a.bd, a.gamma, speeds, a.status)
+  AGILE_DISPATCH(a.phys, a.real_bytes, CALL);
+#undef CALL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_dt(const unsigned long long* speeds, double* dtch, double dt_host,
+                          double cfl, cudaStream_t s) {
+  set_dt_kernel<<<1, 1, 0, s>>>(speeds, dtch, dt_host, cfl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_glm_decay(const AuxArgs& a, const double* dtch, cudaStream_t s) {
+  if (a.nblk == 0) return cudaSuccess;
+  if (a.real_bytes == 8) glm_decay_kernel<double><<<a.nblk, 256, 0, s>>>((double*)a.Uw, a.bd, dtch, a.glm_alpha);
+  else glm_decay_kernel<float><<<a.nblk, 256, 0, s>>>((float*)a.Uw, a.bd, dtch, a.glm_alpha);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_estimate(const AuxArgs& a, const int* vars, const double* weights, int nvars,
+                            double eps, double* emax, cudaStream_t s) {
+  if (a.nblk == 0) return cudaSuccess;
+#define CALL(PT) estimate_kernel<PT, R><<<a.nblk, 256, 0, s>>>((const R*)a.U, (const R*)a.G, a.bd, vars, weights, nvars, eps, emax)
+  AGILE_DISPATCH(a.phys, a.real_bytes, CALL);
+#undef CALL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_regrid(const AuxArgs& a, void* Unew, const RegridSrc* src, int nnew, cudaStream_t s) {
+  if (nnew == 0) return cudaSuccess;
+#define CALL(PT) regrid_kernel<PT, R><<<nnew, 256, 0, s>>>((const R*)a.U, (const R*)a.G, a.bd, (R*)Unew, src)
+  AGILE_DISPATCH(a.phys, a.real_bytes, CALL);
+#undef CALL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prim2cons(const AuxArgs& a, const double* prim, const int* blocks, int n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+#define CALL(PT) prim2cons_kernel<PT, R><<<n, 256, 0, s>>>((R*)a.Uw, prim, blocks, a.gamma)
+  AGILE_DISPATCH(a.phys, a.real_bytes, CALL);
+#undef CALL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const AuxArgs& a, const double* cons, cudaStream_t s) {
+  if (a.nblk == 0) return cudaSuccess;
+  const int nv = phys_nvar(a.phys), na = phys_naux(a.phys);
+  if (a.real_bytes == 8) unpack_kernel<double><<<a.nblk, 256, 0, s>>>((double*)a.Uw, cons, nv, na);
+  else unpack_kernel<float><<<a.nblk, 256, 0, s>>>((float*)a.Uw, cons, nv, na);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const AuxArgs& a, double* cons, double* aux, cudaStream_t s) {
+  if (a.nblk == 0) return cudaSuccess;
+  const int nv = phys_nvar(a.phys), na = phys_naux(a.phys);
+  if (a.real_bytes == 8) pack_kernel<double><<<a.nblk, 256, 0, s>>>((const double*)a.U, cons, aux, nv, na);
+  else pack_kernel<float><<<a.nblk, 256, 0, s>>>((const float*)a.U, cons, aux, nv, na);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sums(const AuxArgs& a, double* part, cudaStream_t s) {
+  if (a.nblk == 0) return cudaSuccess;
+  const int nv = phys_nvar(a.phys), na = phys_naux(a.phys);
+  if (a.real_bytes == 8) sums_kernel<double><<<a.nblk, 256, 0, s>>>((const double*)a.U, a.bd, part, nv, na);
+  else sums_kernel<float><<<a.nblk, 256, 0, s>>>((const float*)a.U, a.bd, part, nv, na);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_halo(const AuxArgs& a, int block, double* out, cudaStream_t s) {
+#define CALL(PT) halo_kernel<PT, R><<<32, 256, 0, s>>>((const R*)a.U, (const R*)a.G, a.bd, block, out)
+  AGILE_DISPATCH(a.phys, a.real_bytes, CALL);
+#undef CALL
+  return cudaGetLastError();
+}
+
+}  // namespace agile

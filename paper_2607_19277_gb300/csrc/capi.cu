@@ -1,0 +1,612 @@
+// C ABI of the block-AMR library: mesh lifecycle, device pools, the SSPRK step driver
+// (paper Fig. 2), regrid (Figs. 1-2), state transfer and diagnostics.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/agile.h"
+#include "kernels.cuh"
+#include "launch.h"
+#include "mesh.h"
+
+using namespace agile;
+
+struct agile_mesh {
+  agile_config cfg;
+  cudaStream_t stream = nullptr;
+  agile_allocator alloc{};
+  bool default_alloc = true;
+  int nv = 5, na = 0, nt = 5, rb = 8;
+  HostMesh* mesh = nullptr;
+  int nblk = 0;
+  void* U[3] = {nullptr, nullptr, nullptr};
+  void* G = nullptr;
+  void* FR = nullptr;
+  int nslots = 0;
+  BlockDesc* d_bd = nullptr;
+  GhostTask* d_ghosts = nullptr;
+  FixupTask* d_fix = nullptr;
+  int nghost = 0, nfix = 0;
+  int* d_status = nullptr;
+  unsigned long long* d_speeds = nullptr;
+  double* d_dtch = nullptr;
+  int* d_vars = nullptr;
+  double* d_weights = nullptr;
+  bool speeds_valid = false;
+  agile_ic_fn ic = nullptr;
+  void* ic_user = nullptr;
+  std::string err;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  long long stage_launches = 0, total_launches = 0;
+};
+
+namespace {
+
+void* dalloc(agile_mesh* m, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  if (m->default_alloc) {
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, m->stream) != cudaSuccess) return nullptr;
+    return p;
+  }
+  return m->alloc.alloc(bytes, (void*)m->stream, m->alloc.ctx);
+}
+
+void dfree(agile_mesh* m, void*& p) {
+  if (!p) return;
+  if (m->default_alloc) cudaFreeAsync(p, m->stream);
+  else m->alloc.free(p, (void*)m->stream, m->alloc.ctx);
+  p = nullptr;
+}
+
+template <typename T>
+void dfree_t(agile_mesh* m, T*& p) {
+  void* q = (void*)p;
+  dfree(m, q);
+  p = nullptr;
+}
+
+agile_status fail(agile_mesh* m, agile_status s, const std::string& msg) {
+  if (m) m->err = msg;
+  return s;
+}
+
+#define CK(m, call)                                                                          \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail((m), AGILE_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_));        \
+  } while (0)
+
+size_t pool_bytes(const agile_mesh* m, int nblk) {
+  return (size_t)nblk * m->nt * NCELL * m->rb;
+}
+
+AuxArgs aux_args(agile_mesh* m, void* U) {
+  AuxArgs a;
+  a.phys = m->cfg.physics;
+  a.real_bytes = m->rb;
+  a.gamma = m->cfg.gamma;
+  a.cfl = m->cfg.cfl;
+  a.glm_alpha = m->cfg.glm_alpha;
+  a.U = U;
+  a.Uw = U;
+  a.G = m->G;
+  a.Gw = m->G;
+  a.FR = m->FR;
+  a.bd = m->d_bd;
+  a.nblk = m->nblk;
+  a.status = m->d_status;
+  return a;
+}
+
+agile_status check_status(agile_mesh* m) {
+  CK(m, cudaStreamSynchronize(m->stream));
+  int st = 0;
+  CK(m, cudaMemcpy(&st, m->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) {
+    CK(m, cudaMemset(m->d_status, 0, sizeof(int)));
+    if (st & ST_ENOCONV) return fail(m, AGILE_ENOCONV, "primitive recovery did not converge");
+    return fail(m, AGILE_EUNPHYS, "non-positive density or pressure on the device");
+  }
+  return AGILE_OK;
+}
+
+// (Re)build descriptors, slots and scratch for the current host mesh; U[0] must already
+// hold nblk blocks.
+agile_status rebuild(agile_mesh* m) {
+  std::vector<BlockDesc> desc;
+  std::vector<GhostTask> ghosts;
+  std::vector<FixupTask> fix;
+  std::string err;
+  int nslots = 0;
+  m->mesh->build_descs(&desc, &ghosts, &fix, &nslots, &err);
+  if (!err.empty()) return fail(m, AGILE_EINVAL, err);
+  m->nblk = (int)desc.size();
+  dfree_t(m, m->d_bd);
+  dfree_t(m, m->d_ghosts);
+  dfree_t(m, m->d_fix);
+  dfree(m, m->G);
+  dfree(m, m->FR);
+  dfree(m, m->U[1]);
+  dfree(m, m->U[2]);
+  m->d_bd = (BlockDesc*)dalloc(m, desc.size() * sizeof(BlockDesc));
+  m->d_ghosts = (GhostTask*)dalloc(m, ghosts.size() * sizeof(GhostTask));
+  m->d_fix = (FixupTask*)dalloc(m, fix.size() * sizeof(FixupTask));
+  m->G = dalloc(m, (size_t)nslots * m->nt * 512 * m->rb);
+  m->FR = dalloc(m, (size_t)nslots * m->nv * 256 * m->rb);
+  m->U[1] = dalloc(m, pool_bytes(m, m->nblk));
+  m->U[2] = m->cfg.rk == 3 ? dalloc(m, pool_bytes(m, m->nblk)) : nullptr;
+  if (!m->d_bd || !m->d_ghosts || !m->d_fix || !m->G || !m->FR || !m->U[1] ||
+      (m->cfg.rk == 3 && !m->U[2]))
+    return fail(m, AGILE_ENOMEM, "device allocation failed");
+  CK(m, cudaMemcpyAsync(m->d_bd, desc.data(), desc.size() * sizeof(BlockDesc), cudaMemcpyHostToDevice, m->stream));
+  if (!ghosts.empty())
+    CK(m, cudaMemcpyAsync(m->d_ghosts, ghosts.data(), ghosts.size() * sizeof(GhostTask), cudaMemcpyHostToDevice, m->stream));
+  if (!fix.empty())
+    CK(m, cudaMemcpyAsync(m->d_fix, fix.data(), fix.size() * sizeof(FixupTask), cudaMemcpyHostToDevice, m->stream));
+  m->nghost = (int)ghosts.size();
+  m->nfix = (int)fix.size();
+  m->nslots = nslots;
+  CK(m, cudaStreamSynchronize(m->stream));   // host vectors go out of scope
+  m->speeds_valid = false;
+  return AGILE_OK;
+}
+
+agile_status fill_ghosts(agile_mesh* m, void* U) {
+  if (m->nghost == 0) return AGILE_OK;
+  AuxArgs a = aux_args(m, U);
+  CK(m, launch_ghosts(a, m->d_ghosts, m->nghost, m->stream));
+  m->total_launches++;
+  return AGILE_OK;
+}
+
+// Evaluate the initial condition on the listed blocks (host callback, then prim -> cons on
+// the device), in chunks to bound host and device staging.
+agile_status apply_ic(agile_mesh* m, void* U, const std::vector<int>& blocks) {
+  const int chunk = 256;
+  std::vector<double> prim((size_t)chunk * m->nv * NCELL);
+  std::vector<double> xs(NCELL), ys(NCELL), zs(NCELL);
+  double* d_prim = (double*)dalloc(m, prim.size() * sizeof(double));
+  int* d_blocks = (int*)dalloc(m, chunk * sizeof(int));
+  if (!d_prim || !d_blocks) return fail(m, AGILE_ENOMEM, "device allocation failed");
+  const auto& keys = m->mesh->blocks();
+  for (size_t c0 = 0; c0 < blocks.size(); c0 += chunk) {
+    const int n = (int)std::min(blocks.size() - c0, (size_t)chunk);
+    for (int i = 0; i < n; ++i) {
+      const Key& k = keys[blocks[c0 + i]];
+      const double dx = m->mesh->dx(k.lev, 0), dy = m->mesh->dx(k.lev, 1), dz = m->mesh->dx(k.lev, 2);
+      for (int z = 0; z < NB; ++z)
+        for (int y = 0; y < NB; ++y)
+          for (int x = 0; x < NB; ++x) {
+            const int c = z * 256 + y * 16 + x;
+            xs[c] = m->cfg.xmin[0] + ((double)(k.x * NB + x) + 0.5) * dx;
+            ys[c] = m->cfg.xmin[1] + ((double)(k.y * NB + y) + 0.5) * dy;
+            zs[c] = m->cfg.xmin[2] + ((double)(k.z * NB + z) + 0.5) * dz;
+          }
+      m->ic(xs.data(), ys.data(), zs.data(), NCELL, prim.data() + (size_t)i * m->nv * NCELL, m->ic_user);
+    }
+    CK(m, cudaMemcpyAsync(d_prim, prim.data(), (size_t)n * m->nv * NCELL * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+    CK(m, cudaMemcpyAsync(d_blocks, blocks.data() + c0, n * sizeof(int), cudaMemcpyHostToDevice, m->stream));
+    AuxArgs a = aux_args(m, U);
+    CK(m, launch_prim2cons(a, d_prim, d_blocks, n, m->stream));
+    m->total_launches++;
+    CK(m, cudaStreamSynchronize(m->stream));
+  }
+  dfree_t(m, d_prim);
+  dfree_t(m, d_blocks);
+  return AGILE_OK;
+}
+
+agile_status ensure_speeds(agile_mesh* m) {
+  if (m->speeds_valid) return AGILE_OK;
+  CK(m, cudaMemsetAsync(m->d_speeds, 0, 2 * sizeof(unsigned long long), m->stream));
+  AuxArgs a = aux_args(m, m->U[0]);
+  CK(m, launch_speeds(a, m->d_speeds, m->stream));
+  m->total_launches++;
+  m->speeds_valid = true;
+  return AGILE_OK;
+}
+
+agile_status do_regrid(agile_mesh* m, const std::vector<int>& flags, int init, int* nr, int* nc) {
+  RegridPlan plan = m->mesh->plan(flags);
+  if (nr) *nr = plan.n_refined;
+  if (nc) *nc = plan.n_coarsened;
+  if (plan.n_refined == 0 && plan.n_coarsened == 0) return AGILE_OK;
+  agile_status s = fill_ghosts(m, m->U[0]);
+  if (s) return s;
+  const int nnew = (int)plan.blocks.size();
+  void* Unew = dalloc(m, pool_bytes(m, nnew));
+  RegridSrc* d_src = (RegridSrc*)dalloc(m, plan.src.size() * sizeof(RegridSrc));
+  if (!Unew || !d_src) return fail(m, AGILE_ENOMEM, "device allocation failed");
+  CK(m, cudaMemcpyAsync(d_src, plan.src.data(), plan.src.size() * sizeof(RegridSrc), cudaMemcpyHostToDevice, m->stream));
+  AuxArgs a = aux_args(m, m->U[0]);
+  CK(m, launch_regrid(a, Unew, d_src, nnew, m->stream));
+  m->total_launches++;
+  CK(m, cudaStreamSynchronize(m->stream));
+  dfree_t(m, d_src);
+  dfree(m, m->U[0]);
+  m->U[0] = Unew;
+  m->mesh->apply(plan);
+  s = rebuild(m);
+  if (s) return s;
+  if (init && m->ic) {
+    s = apply_ic(m, m->U[0], plan.created);
+    if (s) return s;
+  }
+  return check_status(m);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* agile_version(void) { return "agile-gb300 1.0 (sm_103a)"; }
+
+const char* agile_last_error(const agile_mesh* m) { return m ? m->err.c_str() : "null mesh"; }
+
+agile_status agile_mesh_create(const agile_config* cfg, const agile_allocator* alloc, void* stream,
+                               agile_mesh** out) {
+  if (!cfg || !out) return AGILE_EINVAL;
+  *out = nullptr;
+  if (cfg->physics < 0 || cfg->physics > 2 || (cfg->limiter != 0 && cfg->limiter != 1) ||
+      (cfg->flux != 0 && cfg->flux != 1) || (cfg->rk != 2 && cfg->rk != 3) ||
+      (cfg->real_bytes != 4 && cfg->real_bytes != 8) || !(cfg->gamma > 1.0) || !(cfg->cfl > 0.0) ||
+      cfg->max_level < 1 || cfg->max_level > 12 || cfg->refine_nvars < 0 || cfg->refine_nvars > 9)
+    return AGILE_EINVAL;
+  if (cfg->physics == AGILE_SRHD && cfg->flux != AGILE_TVDLF) return AGILE_EINVAL;
+  for (int d = 0; d < 3; ++d) {
+    if (cfg->base_blocks[d] < 1 || cfg->base_blocks[d] > 4096 || !(cfg->xmax[d] > cfg->xmin[d]))
+      return AGILE_EINVAL;
+    const bool p0 = cfg->bc[2 * d] == AGILE_PERIODIC, p1 = cfg->bc[2 * d + 1] == AGILE_PERIODIC;
+    if (p0 != p1) return AGILE_EINVAL;
+    for (int s = 0; s < 2; ++s)
+      if (cfg->bc[2 * d + s] < 0 || cfg->bc[2 * d + s] > 2) return AGILE_EINVAL;
+  }
+  const int nvar = cfg->physics == AGILE_MHD_GLM ? 9 : 5;
+  for (int i = 0; i < cfg->refine_nvars; ++i)
+    if (cfg->refine_vars[i] < 0 || cfg->refine_vars[i] >= nvar) return AGILE_EINVAL;
+  agile_mesh* m = new agile_mesh();
+  m->cfg = *cfg;
+  m->stream = (cudaStream_t)stream;
+  if (alloc && alloc->alloc && alloc->free) {
+    m->alloc = *alloc;
+    m->default_alloc = false;
+  }
+  m->nv = nvar;
+  m->na = cfg->physics == AGILE_SRHD ? 2 : 0;
+  m->nt = m->nv + m->na;
+  m->rb = cfg->real_bytes;
+  m->mesh = new HostMesh(cfg->base_blocks, cfg->max_level, cfg->bc, cfg->xmin, cfg->xmax);
+  m->nblk = (int)m->mesh->blocks().size();
+  m->U[0] = dalloc(m, pool_bytes(m, m->nblk));
+  m->d_status = (int*)dalloc(m, sizeof(int));
+  m->d_speeds = (unsigned long long*)dalloc(m, 2 * sizeof(unsigned long long));
+  m->d_dtch = (double*)dalloc(m, 2 * sizeof(double));
+  m->d_vars = (int*)dalloc(m, 9 * sizeof(int));
+  m->d_weights = (double*)dalloc(m, 9 * sizeof(double));
+  if (!m->U[0] || !m->d_status || !m->d_speeds || !m->d_dtch || !m->d_vars || !m->d_weights) {
+    agile_mesh_destroy(m);
+    return AGILE_ENOMEM;
+  }
+  if (cudaMemsetAsync(m->d_status, 0, sizeof(int), m->stream) != cudaSuccess ||
+      cudaMemsetAsync(m->U[0], 0, pool_bytes(m, m->nblk), m->stream) != cudaSuccess ||
+      cudaMemcpyAsync(m->d_vars, cfg->refine_vars, 9 * sizeof(int), cudaMemcpyHostToDevice, m->stream) != cudaSuccess ||
+      cudaMemcpyAsync(m->d_weights, cfg->refine_weights, 9 * sizeof(double), cudaMemcpyHostToDevice, m->stream) != cudaSuccess) {
+    agile_mesh_destroy(m);
+    return AGILE_ECUDA;
+  }
+  if (rebuild(m) != AGILE_OK) {
+    agile_mesh_destroy(m);
+    return AGILE_ECUDA;
+  }
+  *out = m;
+  return AGILE_OK;
+}
+
+void agile_mesh_destroy(agile_mesh* m) {
+  if (!m) return;
+  cudaStreamSynchronize(m->stream);
+  for (int i = 0; i < 3; ++i) dfree(m, m->U[i]);
+  dfree(m, m->G);
+  dfree(m, m->FR);
+  dfree_t(m, m->d_bd);
+  dfree_t(m, m->d_ghosts);
+  dfree_t(m, m->d_fix);
+  dfree_t(m, m->d_status);
+  dfree_t(m, m->d_speeds);
+  dfree_t(m, m->d_dtch);
+  dfree_t(m, m->d_vars);
+  dfree_t(m, m->d_weights);
+  for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
+  cudaStreamSynchronize(m->stream);
+  delete m->mesh;
+  delete m;
+}
+
+agile_status agile_set_state(agile_mesh* m, agile_ic_fn ic, void* user) {
+  if (!m || !ic) return fail(m, AGILE_EINVAL, "null argument");
+  m->ic = ic;
+  m->ic_user = user;
+  std::vector<int> all(m->nblk);
+  for (int i = 0; i < m->nblk; ++i) all[i] = i;
+  agile_status s = apply_ic(m, m->U[0], all);
+  if (s) return s;
+  m->speeds_valid = false;
+  return check_status(m);
+}
+
+agile_status agile_set_state_blocks(agile_mesh* m, const double* cons, size_t nblk) {
+  if (!m || !cons) return fail(m, AGILE_EINVAL, "null argument");
+  if ((int)nblk != m->nblk) return fail(m, AGILE_EINVAL, "block count does not match the mesh");
+  const size_t bytes = nblk * m->nv * NCELL * sizeof(double);
+  double* d = (double*)dalloc(m, bytes);
+  if (!d) return fail(m, AGILE_ENOMEM, "device allocation failed");
+  CK(m, cudaMemcpyAsync(d, cons, bytes, cudaMemcpyHostToDevice, m->stream));
+  AuxArgs a = aux_args(m, m->U[0]);
+  CK(m, launch_unpack(a, d, m->stream));
+  m->total_launches++;
+  CK(m, cudaStreamSynchronize(m->stream));
+  dfree_t(m, d);
+  m->speeds_valid = false;
+  return AGILE_OK;
+}
+
+agile_status agile_cfl_dt(agile_mesh* m, double* dt_out) {
+  if (!m || !dt_out) return fail(m, AGILE_EINVAL, "null argument");
+  agile_status s = ensure_speeds(m);
+  if (s) return s;
+  unsigned long long h[2];
+  CK(m, cudaMemcpyAsync(h, m->d_speeds, sizeof(h), cudaMemcpyDeviceToHost, m->stream));
+  s = check_status(m);
+  if (s) return s;
+  double smax;
+  memcpy(&smax, &h[0], sizeof(double));
+  if (!(smax > 0.0)) return fail(m, AGILE_EUNPHYS, "zero or invalid signal speed");
+  *dt_out = m->cfg.cfl / smax;
+  return AGILE_OK;
+}
+
+agile_status agile_step(agile_mesh* m, double dt) {
+  if (!m) return AGILE_EINVAL;
+  agile_status s = ensure_speeds(m);
+  if (s) return s;
+  CK(m, launch_set_dt(m->d_speeds, m->d_dtch, dt, m->cfg.cfl, m->stream));
+  m->total_launches++;
+  const bool mhd = m->cfg.physics == AGILE_MHD_GLM;
+  if (mhd) {
+    AuxArgs a = aux_args(m, m->U[0]);
+    CK(m, launch_glm_decay(a, m->d_dtch, m->stream));
+    m->total_launches++;
+  }
+  static const double w2[2][2] = {{0.0, 1.0}, {0.5, 0.5}};
+  static const double w3[3][2] = {{0.0, 1.0}, {0.75, 0.25}, {1.0 / 3.0, 2.0 / 3.0}};
+  const int nst = m->cfg.rk;
+  const bool fuse = m->nfix == 0;
+  for (int st = 0; st < nst; ++st) {
+    const bool last = st == nst - 1;
+    void* Us = st == 0 ? m->U[0] : m->U[st];
+    void* Uo = last ? m->U[0] : m->U[st + 1];
+    s = fill_ghosts(m, Us);
+    if (s) return s;
+    if (last && fuse) CK(m, cudaMemsetAsync(m->d_speeds, 0, 2 * sizeof(unsigned long long), m->stream));
+    StageArgs A;
+    A.Us = Us;
+    A.Un = m->U[0];
+    A.Uout = Uo;
+    A.bd = m->d_bd;
+    A.gs = m->G;
+    A.fr = m->nfix ? m->FR : nullptr;
+    A.dtch = m->d_dtch;
+    A.a = nst == 2 ? w2[st][0] : w3[st][0];
+    A.b = nst == 2 ? w2[st][1] : w3[st][1];
+    A.gamma = m->cfg.gamma;
+    A.glm_alpha = m->cfg.glm_alpha;
+    A.glm_post = (mhd && last && fuse) ? 1 : 0;
+    A.nblk = m->nblk;
+    A.status = m->d_status;
+    A.speeds = (last && fuse) ? m->d_speeds : nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (m->timing) {
+      CK(m, cudaEventCreate(&e0));
+      CK(m, cudaEventCreate(&e1));
+      CK(m, cudaEventRecord(e0, m->stream));
+    }
+    cudaError_t e;
+    if (m->cfg.physics == AGILE_HD) e = launch_stage_hd(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
+    else if (mhd) e = launch_stage_mhd(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
+    else e = launch_stage_srhd(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
+    if (e != cudaSuccess) return fail(m, AGILE_ECUDA, std::string("stage kernel: ") + cudaGetErrorString(e));
+    if (m->timing) {
+      CK(m, cudaEventRecord(e1, m->stream));
+      m->ev.push_back(e0);
+      m->ev.push_back(e1);
+    }
+    m->stage_launches++;
+    m->total_launches++;
+    if (m->nfix) {
+      AuxArgs a = aux_args(m, Uo);
+      CK(m, launch_fixup(a, m->d_fix, m->nfix, A.b, m->d_dtch, m->stream));
+      m->total_launches++;
+    }
+  }
+  if (mhd && !fuse) {
+    AuxArgs a = aux_args(m, m->U[0]);
+    CK(m, launch_glm_decay(a, m->d_dtch, m->stream));
+    m->total_launches++;
+  }
+  if (fuse) {
+    m->speeds_valid = true;
+  } else {
+    m->speeds_valid = false;
+    s = ensure_speeds(m);
+    if (s) return s;
+  }
+  return AGILE_OK;
+}
+
+agile_status agile_estimate(agile_mesh* m, double* emax) {
+  if (!m || !emax) return fail(m, AGILE_EINVAL, "null argument");
+  agile_status s = fill_ghosts(m, m->U[0]);
+  if (s) return s;
+  double* d = (double*)dalloc(m, m->nblk * sizeof(double));
+  if (!d) return fail(m, AGILE_ENOMEM, "device allocation failed");
+  AuxArgs a = aux_args(m, m->U[0]);
+  CK(m, launch_estimate(a, m->d_vars, m->d_weights, m->cfg.refine_nvars, m->cfg.lohner_eps, d, m->stream));
+  m->total_launches++;
+  CK(m, cudaMemcpyAsync(emax, d, m->nblk * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  s = check_status(m);
+  dfree_t(m, d);
+  return s;
+}
+
+agile_status agile_regrid(agile_mesh* m, int init, int* nr, int* nc) {
+  if (!m) return AGILE_EINVAL;
+  if (nr) *nr = 0;
+  if (nc) *nc = 0;
+  std::vector<double> emax(m->nblk);
+  agile_status s = agile_estimate(m, emax.data());
+  if (s) return s;
+  std::vector<int> flags(m->nblk, 0);
+  const auto& keys = m->mesh->blocks();
+  for (int i = 0; i < m->nblk; ++i) {
+    if (emax[i] > m->cfg.refine_tol && keys[i].lev < m->cfg.max_level) flags[i] = 1;
+    else if (emax[i] < m->cfg.refine_tol * m->cfg.derefine_ratio && keys[i].lev > 1) flags[i] = -1;
+  }
+  return do_regrid(m, flags, init, nr, nc);
+}
+
+agile_status agile_regrid_flags(agile_mesh* m, const int* flags, int init, int* nr, int* nc) {
+  if (!m || !flags) return fail(m, AGILE_EINVAL, "null argument");
+  std::vector<int> f(flags, flags + m->nblk);
+  return do_regrid(m, f, init, nr, nc);
+}
+
+agile_status agile_get_layout(agile_mesh* m, size_t* nblocks, int* nvar) {
+  if (!m) return AGILE_EINVAL;
+  if (nblocks) *nblocks = (size_t)m->nblk;
+  if (nvar) *nvar = m->nv;
+  return AGILE_OK;
+}
+
+agile_status agile_get_state(agile_mesh* m, int* level, int* ijk, double* cons) {
+  if (!m) return AGILE_EINVAL;
+  const auto& keys = m->mesh->blocks();
+  for (int i = 0; i < m->nblk; ++i) {
+    if (level) level[i] = keys[i].lev;
+    if (ijk) {
+      ijk[3 * i] = keys[i].x;
+      ijk[3 * i + 1] = keys[i].y;
+      ijk[3 * i + 2] = keys[i].z;
+    }
+  }
+  if (cons) {
+    const size_t bytes = (size_t)m->nblk * m->nv * NCELL * sizeof(double);
+    double* d = (double*)dalloc(m, bytes);
+    if (!d) return fail(m, AGILE_ENOMEM, "device allocation failed");
+    AuxArgs a = aux_args(m, m->U[0]);
+    CK(m, launch_pack(a, d, nullptr, m->stream));
+    m->total_launches++;
+    CK(m, cudaMemcpyAsync(cons, d, bytes, cudaMemcpyDeviceToHost, m->stream));
+    agile_status s = check_status(m);
+    dfree_t(m, d);
+    return s;
+  }
+  return check_status(m);
+}
+
+agile_status agile_get_aux(agile_mesh* m, double* aux) {
+  if (!m || !aux) return fail(m, AGILE_EINVAL, "null argument");
+  if (m->na == 0) return fail(m, AGILE_EINVAL, "physics has no auxiliary variables");
+  const size_t bytes = (size_t)m->nblk * m->na * NCELL * sizeof(double);
+  double* d = (double*)dalloc(m, bytes);
+  if (!d) return fail(m, AGILE_ENOMEM, "device allocation failed");
+  AuxArgs a = aux_args(m, m->U[0]);
+  CK(m, launch_pack(a, nullptr, d, m->stream));
+  m->total_launches++;
+  CK(m, cudaMemcpyAsync(aux, d, bytes, cudaMemcpyDeviceToHost, m->stream));
+  agile_status s = check_status(m);
+  dfree_t(m, d);
+  return s;
+}
+
+agile_status agile_conserved_sums(agile_mesh* m, double* sums) {
+  if (!m || !sums) return fail(m, AGILE_EINVAL, "null argument");
+  std::vector<double> part((size_t)m->nblk * m->nv);
+  double* d = (double*)dalloc(m, part.size() * sizeof(double));
+  if (!d) return fail(m, AGILE_ENOMEM, "device allocation failed");
+  AuxArgs a = aux_args(m, m->U[0]);
+  CK(m, launch_sums(a, d, m->stream));
+  m->total_launches++;
+  CK(m, cudaMemcpyAsync(part.data(), d, part.size() * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  agile_status s = check_status(m);
+  dfree_t(m, d);
+  if (s) return s;
+  for (int v = 0; v < m->nv; ++v) {
+    double sum = 0.0, comp = 0.0;   // Neumaier compensated sum over blocks
+    for (int b = 0; b < m->nblk; ++b) {
+      const double x = part[(size_t)b * m->nv + v];
+      const double t = sum + x;
+      if (fabs(sum) >= fabs(x)) comp += (sum - t) + x;
+      else comp += (x - t) + sum;
+      sum = t;
+    }
+    sums[v] = sum + comp;
+  }
+  return AGILE_OK;
+}
+
+agile_status agile_get_halo(agile_mesh* m, size_t block, double* out) {
+  if (!m || !out || block >= (size_t)m->nblk) return fail(m, AGILE_EINVAL, "bad argument");
+  agile_status s = fill_ghosts(m, m->U[0]);
+  if (s) return s;
+  const size_t bytes = (size_t)m->nt * 8000 * sizeof(double);
+  double* d = (double*)dalloc(m, bytes);
+  if (!d) return fail(m, AGILE_ENOMEM, "device allocation failed");
+  AuxArgs a = aux_args(m, m->U[0]);
+  CK(m, launch_halo(a, (int)block, d, m->stream));
+  m->total_launches++;
+  CK(m, cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, m->stream));
+  s = check_status(m);
+  dfree_t(m, d);
+  return s;
+}
+
+agile_status agile_sync(agile_mesh* m) {
+  if (!m) return AGILE_EINVAL;
+  return check_status(m);
+}
+
+agile_status agile_set_kernel_timing(agile_mesh* m, int enable) {
+  if (!m) return AGILE_EINVAL;
+  CK(m, cudaStreamSynchronize(m->stream));
+  for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
+  m->ev.clear();
+  m->timing = enable != 0;
+  m->stage_launches = 0;
+  m->total_launches = 0;
+  return AGILE_OK;
+}
+
+agile_status agile_kernel_timing(agile_mesh* m, double* stage_ms, long long* stage_launches,
+                                 long long* total_launches) {
+  if (!m) return AGILE_EINVAL;
+  CK(m, cudaStreamSynchronize(m->stream));
+  double tot = 0.0;
+  for (size_t i = 0; i + 1 < m->ev.size(); i += 2) {
+    float ms = 0.f;
+    CK(m, cudaEventElapsedTime(&ms, m->ev[i], m->ev[i + 1]));
+    tot += ms;
+  }
+  if (stage_ms) *stage_ms = tot;
+  if (stage_launches) *stage_launches = m->stage_launches;
+  if (total_launches) *total_launches = m->total_launches;
+  return AGILE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+// Host-side launchers of the device kernels (one translation unit per kernel family).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "agile_internal.h"
+
+namespace agile {
+
+struct StageArgs;
+
+// Per-stage update (macro-kernel), dispatched on physics / precision / limiter / flux.
+cudaError_t launch_stage_hd(int real_bytes, int lim, int flux, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_stage_mhd(int real_bytes, int lim, int flux, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_stage_srhd(int real_bytes, int lim, int flux, const StageArgs& a, cudaStream_t s);
+
+struct AuxArgs {
+  int phys;
+  int real_bytes;
+  double gamma;
+  double cfl;
+  double glm_alpha;
+  const void* U;            // state pool
+  void* Uw;                 // writable pool (kernels that update in place)
+  const void* G;            // ghost slots of U
+  void* Gw;
+  void* FR;                 // flux registers
+  const BlockDesc* bd;
+  int nblk;
+  int* status;
+};
+
+// Fill ghost slots of coarse-fine faces from U (restriction / limited prolongation).
+cudaError_t launch_ghosts(const AuxArgs& a, const GhostTask* tasks, int ntasks, cudaStream_t s);
+// Coarse-fine flux correction of the stage output a.Uw with stage weight b and dt.
+cudaError_t launch_fixup(const AuxArgs& a, const FixupTask* tasks, int ntasks, double b,
+                         const double* dtch, cudaStream_t s);
+// Max signal-speed reduction of U into speeds[2] (double bits; caller zeroes them).
+cudaError_t launch_speeds(const AuxArgs& a, unsigned long long* speeds, cudaStream_t s);
+// dtch = {dt, c_h}: dt from the host value or (dt <= 0) cfl / max sum_d s_d / dx_d.
+cudaError_t launch_set_dt(const unsigned long long* speeds, double* dtch, double dt_host,
+                          double cfl, cudaStream_t s);
+// psi *= exp(-dt/2 c_h alpha / min dx) on every block.
+cudaError_t launch_glm_decay(const AuxArgs& a, const double* dtch, cudaStream_t s);
+// Loehner estimate: emax[nblk] (FP64, no FMA).
+cudaError_t launch_estimate(const AuxArgs& a, const int* vars, const double* weights, int nvars,
+                            double eps, double* emax, cudaStream_t s);
+// New pool from the old one (copy / prolong / restrict per block).
+cudaError_t launch_regrid(const AuxArgs& old_pool, void* Unew, const RegridSrc* src, int nnew,
+                          cudaStream_t s);
+// Primitive (double) -> conserved (R) for the listed blocks; aux from primitives (SRHD).
+cudaError_t launch_prim2cons(const AuxArgs& a, const double* prim, const int* blocks, int n,
+                             cudaStream_t s);
+// Conserved (double) -> pool (R) for all blocks; aux cleared.
+cudaError_t launch_unpack(const AuxArgs& a, const double* cons, cudaStream_t s);
+// Pool (R) -> conserved (double) [nblk][nv][4096], and aux [nblk][na][4096] if aux != nullptr.
+cudaError_t launch_pack(const AuxArgs& a, double* cons, double* aux, cudaStream_t s);
+// Per-block FP64 sums of every conserved variable times the cell volume: part[nblk][nv].
+cudaError_t launch_sums(const AuxArgs& a, double* part, cudaStream_t s);
+// Face-ghost view of one block: out[nt][20][20][20] (NaN at edges / corners).
+cudaError_t launch_halo(const AuxArgs& a, int block, double* out, cudaStream_t s);
+
+int phys_nvar(int phys);
+int phys_naux(int phys);
+
+}  // namespace agile

@@ -1,0 +1,323 @@
+// Device physics traits for the finite-volume stage kernel (sm_103a).
+//
+// Each trait gives the conserved <-> primitive maps, the physical flux along one axis and
+// the approximate Riemann flux at a face, evaluated per cell in registers (the paper's
+// cell-local physics routines, Section 2.3):
+//   HdPhys   : Eqs. 2-4 with e = p/(gamma-1) + rho v^2/2 (Section 2.3.1; HD flux listing)
+//   MhdPhys  : Eqs. 11-13 with GLM (Eq. 14), e = p/(gamma-1) + rho v^2/2 + B^2/2 (Section 2.3.3)
+//   SrhdPhys : Eqs. 15-19 with the ideal-gas enthalpy of Eq. 20 (Section 2.3.4); the
+//              conserved-to-primitive recovery is a Newton root find in xi = Gamma^2 rho h,
+//              always in FP64.
+// Riemann fluxes: HLL with Davis wave-speed estimates, or TVDLF (Rusanov) with the larger
+// of the two sides' fastest speeds (paper Table 1 lists the solvers per module).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace agile {
+
+enum : int { LIM_MINMOD = 0, LIM_VANLEER = 1 };
+enum : int { FLUX_TVDLF = 0, FLUX_HLL = 1 };
+enum : int { ST_ENOCONV = 1, ST_EUNPHYS = 2 };
+
+struct PhysParams {
+  double gamma;
+  double ch;      // GLM cleaning speed (MHD only): c_max of U^n
+};
+
+template <typename R>
+__device__ __forceinline__ R rabs(R a) { return a < R(0) ? -a : a; }
+template <typename R>
+__device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
+template <typename R>
+__device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
+__device__ __forceinline__ float rsqrt_(float a) { return sqrtf(a); }
+__device__ __forceinline__ double rsqrt_(double a) { return sqrt(a); }
+
+// Slope limiters on the two one-sided differences (van Leer 1974; minmod).
+template <typename R, int LIM>
+__device__ __forceinline__ R limit(R a, R b) {
+  const bool same = (a > R(0) && b > R(0)) || (a < R(0) && b < R(0));
+  if (LIM == LIM_MINMOD) {
+    return same ? (a > R(0) ? rmin(a, b) : rmax(a, b)) : R(0);
+  } else {
+    return same ? (R(2) * a * b) / (a + b) : R(0);
+  }
+}
+
+// ------------------------------------------------------------------------------ hydro
+template <typename R>
+struct HdPhys {
+  static constexpr int NV = 5;   // rho, m, e
+  static constexpr int NA = 0;
+  static constexpr int BOFF = -1;  // no magnetic field
+
+  __device__ static __forceinline__ void cons2prim(const R* u, R* p, R*, const PhysParams& pp,
+                                                   int& st) {
+    const R g1 = R(pp.gamma - 1.0);
+    const R rho = u[0];
+    const R vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
+    p[0] = rho;
+    p[1] = vx;
+    p[2] = vy;
+    p[3] = vz;
+    p[4] = g1 * (u[4] - R(0.5) * rho * (vx * vx + vy * vy + vz * vz));
+    if (!(rho > R(0)) || !(p[4] > R(0))) st |= ST_EUNPHYS;
+  }
+
+  __device__ static __forceinline__ void prim2cons(const R* p, R* u, const PhysParams& pp) {
+    const R ig1 = R(1.0 / (pp.gamma - 1.0));
+    u[0] = p[0];
+    u[1] = p[0] * p[1];
+    u[2] = p[0] * p[2];
+    u[3] = p[0] * p[3];
+    u[4] = p[4] * ig1 + R(0.5) * p[0] * (p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+  }
+
+  template <int D>
+  __device__ static __forceinline__ void flux(const R* p, const R* u, R* f, const PhysParams&) {
+    const R vd = p[1 + D];
+    f[0] = u[0] * vd;
+    f[1] = u[1] * vd;
+    f[2] = u[2] * vd;
+    f[3] = u[3] * vd;
+    f[1 + D] += p[4];
+    f[4] = vd * (u[4] + p[4]);
+  }
+
+  template <int D>
+  __device__ static __forceinline__ void lambdas(const R* p, R& lm, R& lp, const PhysParams& pp) {
+    const R c = rsqrt_(R(pp.gamma) * p[4] / p[0]);
+    lm = p[1 + D] - c;
+    lp = p[1 + D] + c;
+  }
+
+  template <int D>
+  __device__ static __forceinline__ void interface(R*, R*, const PhysParams&) {}
+};
+
+// ------------------------------------------------------------------------------ MHD + GLM
+template <typename R>
+struct MhdPhys {
+  static constexpr int NV = 9;   // rho, m, e, B, psi
+  static constexpr int NA = 0;
+  static constexpr int BOFF = 5;   // B_x is variable 5
+
+  __device__ static __forceinline__ void cons2prim(const R* u, R* p, R*, const PhysParams& pp,
+                                                   int& st) {
+    const R g1 = R(pp.gamma - 1.0);
+    const R rho = u[0];
+    const R vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
+    const R b2 = u[5] * u[5] + u[6] * u[6] + u[7] * u[7];
+    p[0] = rho;
+    p[1] = vx;
+    p[2] = vy;
+    p[3] = vz;
+    p[4] = g1 * (u[4] - R(0.5) * rho * (vx * vx + vy * vy + vz * vz) - R(0.5) * b2);
+    p[5] = u[5];
+    p[6] = u[6];
+    p[7] = u[7];
+    p[8] = u[8];
+    if (!(rho > R(0)) || !(p[4] > R(0))) st |= ST_EUNPHYS;
+  }
+
+  __device__ static __forceinline__ void prim2cons(const R* p, R* u, const PhysParams& pp) {
+    const R ig1 = R(1.0 / (pp.gamma - 1.0));
+    u[0] = p[0];
+    u[1] = p[0] * p[1];
+    u[2] = p[0] * p[2];
+    u[3] = p[0] * p[3];
+    u[4] = p[4] * ig1 + R(0.5) * p[0] * (p[1] * p[1] + p[2] * p[2] + p[3] * p[3]) +
+           R(0.5) * (p[5] * p[5] + p[6] * p[6] + p[7] * p[7]);
+    u[5] = p[5];
+    u[6] = p[6];
+    u[7] = p[7];
+    u[8] = p[8];
+  }
+
+  template <int D>
+  __device__ static __forceinline__ void flux(const R* p, const R* u, R* f, const PhysParams& pp) {
+    const R vd = p[1 + D], bd = p[5 + D];
+    const R ptot = p[4] + R(0.5) * (p[5] * p[5] + p[6] * p[6] + p[7] * p[7]);
+    const R vb = p[1] * p[5] + p[2] * p[6] + p[3] * p[7];
+    f[0] = u[0] * vd;
+    f[1] = u[1] * vd - p[5] * bd;
+    f[2] = u[2] * vd - p[6] * bd;
+    f[3] = u[3] * vd - p[7] * bd;
+    f[1 + D] += ptot;
+    f[4] = vd * (u[4] + ptot) - bd * vb;
+    f[5] = vd * p[5] - bd * p[1];
+    f[6] = vd * p[6] - bd * p[2];
+    f[7] = vd * p[7] - bd * p[3];
+    f[5 + D] = p[8];
+    const R ch = R(pp.ch);
+    f[8] = ch * ch * bd;
+  }
+
+  template <int D>
+  __device__ static __forceinline__ void lambdas(const R* p, R& lm, R& lp, const PhysParams& pp) {
+    const R ir = R(1) / p[0];
+    const R a2 = R(pp.gamma) * p[4] * ir;
+    const R b2 = (p[5] * p[5] + p[6] * p[6] + p[7] * p[7]) * ir;
+    const R bd2 = p[5 + D] * p[5 + D] * ir;
+    const R s = a2 + b2;
+    const R disc = rmax(s * s - R(4) * a2 * bd2, R(0));
+    const R cf = rsqrt_(R(0.5) * (s + rsqrt_(disc)));
+    lm = p[1 + D] - cf;
+    lp = p[1 + D] + cf;
+  }
+
+  // Exact solution of the linear (B_d, psi) subsystem at the face (Dedner et al. 2002):
+  // both face states carry B_d* and psi*, so the face flux of B_d is psi* and of psi is
+  // c_h^2 B_d*.
+  template <int D>
+  __device__ static __forceinline__ void interface(R* pl, R* pr, const PhysParams& pp) {
+    const R ch = R(pp.ch);
+    const R bl = pl[5 + D], br = pr[5 + D], sl = pl[8], sr = pr[8];
+    const R bs = R(0.5) * (bl + br) - R(0.5) * (sr - sl) / ch;
+    const R ss = R(0.5) * (sl + sr) - R(0.5) * ch * (br - bl);
+    pl[5 + D] = bs;
+    pr[5 + D] = bs;
+    pl[8] = ss;
+    pr[8] = ss;
+  }
+};
+
+// ------------------------------------------------------------------------------ SRHD
+template <typename R>
+struct SrhdPhys {
+  static constexpr int NV = 5;   // D, m, tau ; primitives rho, u = Gamma v, p
+  static constexpr int NA = 2;   // xi = Gamma^2 rho h, Gamma
+  static constexpr int BOFF = -1;
+
+  // Newton root find for f(xi) = xi - p(xi) - (tau + D) = 0 inside the bracket
+  // [E, gamma E]; starts from the stored xi when it lies strictly inside the bracket,
+  // else from the midpoint; a step leaving the closed bracket is replaced by bisection;
+  // stops when |dxi| <= 1e-14 xi; at most 50 iterations. FP64 throughout.
+  __device__ static __forceinline__ void cons2prim(const R* u, R* p, R* aux, const PhysParams& pp,
+                                                   int& st) {
+    const double g = pp.gamma;
+    const double gm = (g - 1.0) / g;
+    const double D = (double)u[0];
+    const double mx = (double)u[1], my = (double)u[2], mz = (double)u[3];
+    const double s2 = mx * mx + my * my + mz * mz;
+    const double E = (double)u[4] + D;
+    double lo = E, hi = g * E;
+    double xi = (double)aux[0];
+    if (!(xi > lo && xi < hi)) xi = 0.5 * (lo + hi);
+    bool ok = false;
+    for (int it = 0; it < 50; ++it) {
+      const double w = s2 / (xi * xi);
+      const double ig2 = 1.0 - w;
+      const double lor = 1.0 / sqrt(ig2);
+      const double rho = D / lor;
+      const double pr = gm * (xi * ig2 - rho);
+      const double f = xi - pr - E;
+      const double df = 1.0 - gm * (1.0 + w - D * lor * w / xi);
+      if (f < 0.0) lo = xi; else hi = xi;
+      double xn = xi - f / df;
+      if (!(xn >= lo && xn <= hi)) xn = 0.5 * (lo + hi);
+      const bool conv = fabs(xn - xi) <= 1e-14 * xn;
+      xi = xn;
+      if (conv) { ok = true; break; }
+    }
+    if (!ok) st |= ST_ENOCONV;
+    const double w = s2 / (xi * xi);
+    const double ig2 = 1.0 - w;
+    const double lor = 1.0 / sqrt(ig2);
+    const double rho = D / lor;
+    const double sc = lor / xi;
+    p[0] = (R)rho;
+    p[1] = (R)(mx * sc);
+    p[2] = (R)(my * sc);
+    p[3] = (R)(mz * sc);
+    const double pr = gm * (xi * ig2 - rho);
+    p[4] = (R)pr;
+    aux[0] = (R)xi;
+    aux[1] = (R)lor;
+    if (!(rho > 0.0) || !(pr > 0.0)) st |= ST_EUNPHYS;
+  }
+
+  __device__ static __forceinline__ void prim2cons(const R* p, R* u, const PhysParams& pp) {
+    const R g = R(pp.gamma);
+    const R lor = rsqrt_(R(1) + p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+    const R h = R(1) + g / (g - R(1)) * p[4] / p[0];
+    const R lr = lor * p[0];
+    const R lrh = lr * h;
+    u[0] = lr;
+    u[1] = lrh * p[1];
+    u[2] = lrh * p[2];
+    u[3] = lrh * p[3];
+    u[4] = lor * lrh - p[4] - lr;
+  }
+
+  template <int D>
+  __device__ static __forceinline__ void flux(const R* p, const R* u, R* f, const PhysParams&) {
+    const R lor = rsqrt_(R(1) + p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+    const R vd = p[1 + D] / lor;
+    f[0] = u[0] * vd;
+    f[1] = u[1] * vd;
+    f[2] = u[2] * vd;
+    f[3] = u[3] * vd;
+    f[1 + D] += p[4];
+    f[4] = u[1 + D] - u[0] * vd;
+  }
+
+  template <int D>
+  __device__ static __forceinline__ void lambdas(const R* p, R& lm, R& lp, const PhysParams& pp) {
+    const R g = R(pp.gamma);
+    const R lor2 = R(1) + p[1] * p[1] + p[2] * p[2] + p[3] * p[3];
+    const R v2 = R(1) - R(1) / lor2;
+    const R vd = p[1 + D] / rsqrt_(lor2);
+    const R h = R(1) + g / (g - R(1)) * p[4] / p[0];
+    const R cs2 = g * p[4] / (p[0] * h);
+    const R cs = rsqrt_(cs2);
+    const R den = R(1) - v2 * cs2;
+    const R root = cs * rsqrt_(rmax((R(1) - v2) * (R(1) - v2 * cs2 - vd * vd * (R(1) - cs2)), R(0)));
+    lm = (vd * (R(1) - cs2) - root) / den;
+    lp = (vd * (R(1) - cs2) + root) / den;
+  }
+
+  template <int D>
+  __device__ static __forceinline__ void interface(R*, R*, const PhysParams&) {}
+};
+
+// Riemann flux at a face from reconstructed primitive states (modified in place).
+template <class P, typename R, int D, int FLUX>
+__device__ __forceinline__ void riemann(R* pl, R* pr, R* f, const PhysParams& pp) {
+  constexpr int NV = P::NV;
+  P::template interface<D>(pl, pr, pp);
+  R ul[NV], ur[NV], fl[NV], fr[NV];
+  P::prim2cons(pl, ul, pp);
+  P::prim2cons(pr, ur, pp);
+  P::template flux<D>(pl, ul, fl, pp);
+  P::template flux<D>(pr, ur, fr, pp);
+  R lml, lpl, lmr, lpr;
+  P::template lambdas<D>(pl, lml, lpl, pp);
+  P::template lambdas<D>(pr, lmr, lpr, pp);
+  if (FLUX == FLUX_TVDLF) {
+    const R c = rmax(rmax(rabs(lml), rabs(lpl)), rmax(rabs(lmr), rabs(lpr)));
+#pragma unroll
+    for (int v = 0; v < NV; ++v) f[v] = R(0.5) * (fl[v] + fr[v]) - R(0.5) * c * (ur[v] - ul[v]);
+  } else {
+    const R sl = rmin(rmin(lml, lmr), R(0));
+    const R sr = rmax(rmax(lpl, lpr), R(0));
+    const R inv = R(1) / (sr - sl);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) f[v] = (sr * fl[v] - sl * fr[v] + sl * sr * (ur[v] - ul[v])) * inv;
+  }
+}
+
+// PLM face states: pl = P_i + phi_i / 2, pr = P_{i+1} - phi_{i+1} / 2 from the four cells
+// i-1, i, i+1, i+2 around face i+1/2.
+template <int NV, typename R, int LIM>
+__device__ __forceinline__ void plm(const R* a, const R* b, const R* c, const R* d, R* pl, R* pr) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const R d0 = b[v] - a[v], d1 = c[v] - b[v], d2 = d[v] - c[v];
+    pl[v] = b[v] + R(0.5) * limit<R, LIM>(d0, d1);
+    pr[v] = c[v] - R(0.5) * limit<R, LIM>(d1, d2);
+  }
+}
+
+}  // namespace agile

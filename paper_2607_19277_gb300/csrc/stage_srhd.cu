@@ -1,0 +1,27 @@
+// Instantiations of the per-stage update kernel for the srhd physics module.
+#include "kernels.cuh"
+#include "launch.h"
+
+namespace agile {
+
+template <typename R, int LIM, int FLUX>
+static cudaError_t go(const StageArgs& a, cudaStream_t s) {
+  auto k = stage_kernel<SrhdPhys, R, LIM, FLUX>;
+  const size_t smem = stage_smem_bytes<SrhdPhys, R>();
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<a.nblk, 256, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t go_r(int lim, int flux, const StageArgs& a, cudaStream_t s) {
+  if (flux != FLUX_TVDLF) return cudaErrorInvalidValue;   // srhd: TVDLF only (paper Table 1)
+  return lim == LIM_MINMOD ? go<R, LIM_MINMOD, FLUX_TVDLF>(a, s) : go<R, LIM_VANLEER, FLUX_TVDLF>(a, s);
+}
+
+cudaError_t launch_stage_srhd(int real_bytes, int lim, int flux, const StageArgs& a, cudaStream_t s) {
+  return real_bytes == 8 ? go_r<double>(lim, flux, a, s) : go_r<float>(lim, flux, a, s);
+}
+
+}  // namespace agile

@@ -1,0 +1,163 @@
+"""GPU parity on AMR meshes: ghost fill (same-level copy, restriction, prolongation),
+Loehner estimate and refinement decisions (bit-exact), regrid (prolong / restrict),
+coarse-fine flux correction and the full Sedov-type AMR evolution against the oracle."""
+import numpy as np
+import pytest
+
+from paper_2607_19277_gb300 import workloads as W
+from parity_util import TOL_FP64, gpu_mesh, oracle_solver, rel_l1
+
+pytestmark = pytest.mark.gpu
+OUT, PER, REF = "outflow", "periodic", "reflect"
+
+
+def _oracle_flags(o, refine=(), coarsen=()):
+    keys = o.ordered_keys()
+    return np.array([1 if k in refine else (-1 if k in coarsen else 0) for k in keys], np.int32)
+
+
+def _forced(o, m, refine=(), coarsen=()):
+    """Apply the same hand-set flags to both meshes; the resulting meshes must match."""
+    flags = _oracle_flags(o, refine, coarsen)
+    orig = o.flags
+
+    def forced():
+        fl, est = orig()
+        for k in fl:
+            fl[k] = 1 if k in refine else (-1 if k in coarsen else 0)
+        return fl, est
+    o.flags = forced
+    try:
+        ro = o.regrid()
+    finally:
+        o.flags = orig
+    rg = m.regrid_flags(flags)
+    assert tuple(rg) == tuple(ro)
+    lev, ijk, _ = m.get_state()
+    olev, oijk, _ = o.get_state()
+    assert np.array_equal(lev, olev) and np.array_equal(ijk, oijk)
+
+
+def _three_level(spec, ic):
+    o = oracle_solver(spec)
+    o.set_state(ic)
+    m = gpu_mesh(spec)
+    m.set_state(ic)
+    _forced(o, m, refine={(1, 1, 1, 1)})
+    _forced(o, m, refine={(2, 3, 3, 3), (2, 2, 2, 2)})
+    assert sorted(set(o.get_state()[0].tolist())) == [1, 2, 3]
+    # identical conserved inputs on both sides for the bit-exact checks
+    _, _, cons = o.get_state()
+    m.set_state_blocks(cons)
+    if o.naux:
+        o.set_state_blocks(cons)
+    return o, m
+
+
+SPEC3 = dict(physics="hd", limiter="minmod", flux="hll", rk=3, base_blocks=(3, 3, 2),
+             max_level=3, bc=(OUT, OUT, PER, PER, REF, REF), refine_vars=(0, 4),
+             refine_weights=(0.5, 0.5))
+
+
+@pytest.mark.parametrize("physics", ["hd", "mhd", "srhd"])
+def test_ghost_fill_bit_exact(physics):
+    spec = dict(SPEC3, physics=physics, flux="tvdlf" if physics == "srhd" else "hll",
+                gamma=4.0 / 3.0 if physics == "srhd" else 5.0 / 3.0)
+    nvar = 9 if physics == "mhd" else 5
+    o, m = _three_level(spec, W.random_smooth(nvar, 21, physics))
+    o.fill_ghosts()
+    keys = o.ordered_keys()
+    kinds = set()
+    for i, k in enumerate(keys):
+        h = m.get_halo(i)
+        ref = o.leaves[k]
+        for d in range(3):
+            for s in (-1, 1):
+                kinds.add(o.face_kind(k, d, s)[0])
+                r = o._ghost_slab(d, s)
+                sl = (slice(0, nvar), r[2], r[1], r[0])
+                assert np.array_equal(h[sl], ref[sl]), (k, d, s, o.face_kind(k, d, s)[0])
+    assert {"same", "bc", "finer", "coarser"} <= kinds
+    m.close()
+
+
+def test_estimator_bit_exact_and_flags():
+    o, m = _three_level(SPEC3, W.sedov(r0=0.35, centre=(0.5, 0.5, 0.5)))
+    e_g = m.estimate()
+    est = o.estimate()
+    e_o = np.array([est[k] for k in o.ordered_keys()])
+    assert np.array_equal(e_g, e_o)
+    m.close()
+
+
+def test_amr_steps_with_fixup_match_oracle_and_conserve():
+    spec = dict(SPEC3, bc=(PER,) * 6)
+    o, m = _three_level(spec, W.random_smooth(5, 3, "hd"))
+    s0 = o.conserved_sums()
+    for _ in range(3):
+        dt = o.cfl_dt()
+        assert abs(m.cfl_dt() - dt) <= 1e-13 * dt
+        o.step(dt)
+        m.step(dt)
+    lev, _, g = m.get_state()
+    _, _, r = o.get_state()
+    assert rel_l1(g, r, lev).max() < TOL_FP64
+    sg = m.conserved_sums()
+    assert np.max(np.abs(sg - s0)) <= 1e-13 * np.abs(s0).max()
+    m.close()
+
+
+def test_amr_mhd_and_srhd_steps():
+    for physics, flux, gam in (("mhd", "hll", 5.0 / 3.0), ("srhd", "tvdlf", 4.0 / 3.0)):
+        spec = dict(SPEC3, physics=physics, flux=flux, gamma=gam, rk=2)
+        nvar = 9 if physics == "mhd" else 5
+        o, m = _three_level(spec, W.random_smooth(nvar, 14, physics))
+        for _ in range(2):
+            dt = o.cfl_dt()
+            o.step(dt)
+            m.step(dt)
+        lev, _, g = m.get_state()
+        _, _, r = o.get_state()
+        assert rel_l1(g, r, lev, physics=physics).max() < TOL_FP64, physics
+        m.close()
+
+
+def test_regrid_prolong_restrict_match_oracle():
+    o, m = _three_level(SPEC3, W.random_smooth(5, 6, "hd"))
+    keys = o.ordered_keys()
+    fine = [k for k in keys if k[0] == 3]
+    _forced(o, m, coarsen=set(fine))
+    lev, _, g = m.get_state()
+    _, _, r = o.get_state()
+    assert rel_l1(g, r, lev).max() < 1e-15
+    _forced(o, m, refine={k for k in o.ordered_keys() if k[0] == 2})
+    lev, _, g = m.get_state()
+    _, _, r = o.get_state()
+    assert rel_l1(g, r, lev).max() < 1e-15
+    m.close()
+
+
+def test_sedov_amr_evolution_matches_oracle():
+    """Sedov blast on a 3-level octree: initial refinement by the estimator with the
+    initial condition re-applied, regrid every 3 steps, HLL, minmod, SSPRK2."""
+    spec = dict(physics="hd", limiter="minmod", flux="hll", rk=2, base_blocks=(2, 2, 2),
+                xmin=(-0.5,) * 3, xmax=(0.5,) * 3, bc=(OUT,) * 6, max_level=3,
+                refine_vars=(0, 4), refine_weights=(0.5, 0.5), refine_tol=0.2)
+    ic = W.sedov(r0=0.12)
+    o = oracle_solver(spec)
+    o.set_state(ic)
+    m = gpu_mesh(spec)
+    m.set_state(ic)
+    for _ in range(2):
+        assert tuple(m.regrid(init=True)) == tuple(o.regrid(init=True))
+    for n in range(6):
+        dt = o.cfl_dt()
+        o.step(dt)
+        m.step(dt)
+        if n % 3 == 2:
+            assert tuple(m.regrid()) == tuple(o.regrid())
+    lev, ijk, g = m.get_state()
+    olev, oijk, r = o.get_state()
+    assert np.array_equal(lev, olev) and np.array_equal(ijk, oijk)
+    assert rel_l1(g, r, lev).max() < TOL_FP64
+    m.close()

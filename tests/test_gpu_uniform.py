@@ -1,0 +1,126 @@
+"""GPU parity on uniform grids: the CUDA library (C ABI) against the FP64 oracle.
+
+FP64 stencil: relative L1 per variable <= 1e-12 (the bound the FP64 path is held to);
+FP32 stencil on smooth runs: <= 1e-5. Every case evolves the same initial condition on
+both sides with the same dt per step; sizes span several blocks, ragged block counts,
+every boundary kind and all three physics modules.
+"""
+import numpy as np
+import pytest
+
+from paper_2607_19277_gb300 import workloads as W
+from parity_util import TOL_FP32, TOL_FP64, gpu_mesh, oracle_solver, rel_l1, run_both
+
+pytestmark = pytest.mark.gpu
+OUT, PER, REF = "outflow", "periodic", "reflect"
+
+
+def test_sod_config1_fp64_20_steps():
+    """3-D Euler Sod tube, 64^3 as 4x4x4 blocks, PLM minmod, HLL, SSPRK2, CFL 0.4, 20 steps."""
+    spec = dict(physics="hd", limiter="minmod", flux="hll", rk=2, cfl=0.4, base_blocks=(4, 4, 4),
+                bc=(OUT, OUT, PER, PER, PER, PER))
+    m, o, g, r, lev, dts = run_both(spec, W.sod_x, 20)
+    err = rel_l1(g, r)
+    assert err.max() < TOL_FP64, err
+    assert abs(m.cfl_dt() - o.cfl_dt()) <= 1e-13 * o.cfl_dt()
+    s_g, s_o = m.conserved_sums(), o.conserved_sums()
+    assert np.max(np.abs(s_g - s_o)) <= 1e-13 * np.abs(s_o).max()
+    m.close()
+
+
+@pytest.mark.parametrize("rb,tol", [(8, TOL_FP64), (4, TOL_FP32)])
+def test_mhd_orszag_tang_glm(rb, tol):
+    """Ideal MHD + GLM, Orszag-Tang-like field with seeded 1% velocity noise, van Leer, HLL,
+    SSPRK3, periodic (the 256^3 workload's physics on 32^3)."""
+    spec = dict(physics="mhd", limiter="vanleer", flux="hll", rk=3, base_blocks=(2, 2, 2))
+    m, o, g, r, lev, _ = run_both(spec, W.orszag_tang_3d(32), 4, real_bytes=rb)
+    err = rel_l1(g, r, physics="mhd")
+    assert err.max() < tol, err
+    m.close()
+
+
+def test_mhd_tvdlf_minmod_fp64():
+    spec = dict(physics="mhd", limiter="minmod", flux="tvdlf", rk=2, base_blocks=(2, 1, 2),
+                bc=(OUT, OUT, PER, PER, REF, REF))
+    m, o, g, r, lev, _ = run_both(spec, W.random_smooth(9, 31, "mhd"), 3)
+    assert rel_l1(g, r, physics="mhd").max() < TOL_FP64
+    m.close()
+
+
+@pytest.mark.parametrize("rb,tol", [(8, TOL_FP64), (4, 2e-5)])
+def test_srhd_shells(rb, tol):
+    """SRHD with seeded shells (Lorentz factors up to 5), LF flux, minmod, SSPRK2; the
+    primitive recovery runs in FP64 in both precisions."""
+    spec = dict(physics="srhd", limiter="minmod", flux="tvdlf", rk=2, gamma=4.0 / 3.0,
+                base_blocks=(2, 2, 2))
+    ic = W.srhd_shells(W.SEED_BASE + 4, 32, lorentz_max=5.0, p_amb=0.1)
+    m, o, g, r, lev, _ = run_both(spec, ic, 3, real_bytes=rb)
+    assert rel_l1(g, r).max() < tol
+    if rb == 8:
+        aux = m.get_aux()
+        assert np.max(np.abs(aux - o.get_aux()) / np.abs(o.get_aux())) < 1e-12
+    m.close()
+
+
+def test_srhd_vanleer_smooth_fp64():
+    spec = dict(physics="srhd", limiter="vanleer", flux="tvdlf", rk=3, gamma=4.0 / 3.0,
+                base_blocks=(1, 2, 1), bc=(PER, PER, OUT, OUT, PER, PER))
+    m, o, g, r, lev, _ = run_both(spec, W.random_smooth(5, 12, "srhd"), 3)
+    assert rel_l1(g, r).max() < TOL_FP64
+    m.close()
+
+
+@pytest.mark.parametrize("flux,lim,rk", [("hll", "vanleer", 3), ("tvdlf", "minmod", 2),
+                                         ("tvdlf", "vanleer", 3)])
+def test_hd_ragged_mesh_all_boundaries(flux, lim, rk):
+    """6 blocks (3x2x1: a ragged, non-cubic count), reflecting, outflow and periodic faces."""
+    spec = dict(physics="hd", limiter=lim, flux=flux, rk=rk, base_blocks=(3, 2, 1),
+                bc=(REF, OUT, OUT, REF, PER, PER))
+    m, o, g, r, lev, _ = run_both(spec, W.random_smooth(5, 8, "hd"), 4)
+    assert rel_l1(g, r).max() < TOL_FP64
+    m.close()
+
+
+def test_single_block_periodic_self_neighbour():
+    spec = dict(physics="hd", limiter="vanleer", flux="hll", rk=3, base_blocks=(1, 1, 1))
+    m, o, g, r, lev, _ = run_both(spec, W.density_wave((1.0, 1.0, 1.0)), 5)
+    assert rel_l1(g, r).max() < TOL_FP64
+    m.close()
+
+
+def test_hd_fp32_smooth_wave():
+    spec = dict(physics="hd", limiter="vanleer", flux="hll", rk=3, base_blocks=(2, 2, 2))
+    m, o, g, r, lev, _ = run_both(spec, W.density_wave((1.0, 1.0, 0.0)), 6, real_bytes=4)
+    assert rel_l1(g, r).max() < TOL_FP32
+    m.close()
+
+
+def test_device_dt_matches_cfl_dt():
+    """agile_step(dt <= 0) takes the CFL step on the device: same result as passing it."""
+    spec = dict(physics="mhd", limiter="vanleer", flux="hll", rk=3, base_blocks=(1, 1, 2))
+    a = gpu_mesh(spec)
+    b = gpu_mesh(spec)
+    ic = W.orszag_tang_3d(16)
+    a.set_state(ic)
+    b.set_state(ic)
+    for _ in range(3):
+        a.step(0.0)
+        b.step(b.cfl_dt())
+    ga = a.get_state()[2]
+    gb = b.get_state()[2]
+    assert np.array_equal(ga, gb)
+    a.close()
+    b.close()
+
+
+def test_set_get_state_round_trip_and_sums():
+    spec = dict(physics="mhd", limiter="vanleer", flux="hll", rk=3, base_blocks=(2, 1, 1))
+    o = oracle_solver(spec)
+    o.set_state(W.random_smooth(9, 4, "mhd"))
+    _, _, cons = o.get_state()
+    m = gpu_mesh(spec)
+    m.set_state_blocks(cons)
+    assert np.array_equal(m.get_state()[2], cons)
+    s = m.conserved_sums()
+    assert np.max(np.abs(s - o.conserved_sums())) <= 1e-14 * np.abs(s).max()
+    m.close()

@@ -1,0 +1,88 @@
+"""CPU checks of the C ABI library: it builds for sm_103a, loads, exports every symbol that
+include/agile.h declares, and its host-side argument checks and allocator-failure handling
+return status codes without touching a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "agile.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2607_19277_gb300 import agile, build
+    if not os.path.exists(agile.LIB_PATH):
+        build.build()
+    return agile.load()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(agile_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    syms = declared_symbols()
+    assert "agile_step" in syms and "agile_mesh_create" in syms
+    for s in syms:
+        assert hasattr(lib, s), s
+    from paper_2607_19277_gb300 import agile
+    assert sorted(agile.EXPORTS) == syms
+
+
+def test_version(lib):
+    assert b"sm_103a" in lib.agile_version()
+
+
+@pytest.mark.parametrize("field,value", [("physics", 7), ("rk", 4), ("real_bytes", 2),
+                                         ("gamma", 1.0), ("max_level", 0), ("limiter", 3)])
+def test_invalid_config_rejected_on_host(lib, field, value):
+    from paper_2607_19277_gb300 import agile
+    cfg = agile.make_config()
+    setattr(cfg, field, value)
+    out = C.c_void_p()
+    st = lib.agile_mesh_create(C.byref(cfg), None, None, C.byref(out))
+    assert st == 1 and not out.value     # AGILE_EINVAL
+
+
+def test_half_periodic_and_srhd_hll_rejected(lib):
+    from paper_2607_19277_gb300 import agile
+    out = C.c_void_p()
+    cfg = agile.make_config(bc=("periodic", "outflow", "periodic", "periodic", "periodic", "periodic"))
+    assert lib.agile_mesh_create(C.byref(cfg), None, None, C.byref(out)) == 1
+    cfg = agile.make_config(physics="srhd", flux="hll")
+    assert lib.agile_mesh_create(C.byref(cfg), None, None, C.byref(out)) == 1
+
+
+def test_allocator_failure_returns_enomem(lib):
+    """A caller-supplied allocator that fails: creation reports AGILE_ENOMEM cleanly."""
+    from paper_2607_19277_gb300 import agile
+    calls = []
+
+    def alloc(n, stream, ctx):
+        calls.append(n)
+        return None
+
+    def free(p, stream, ctx):
+        raise AssertionError("nothing was allocated")
+
+    a = agile.agile_allocator(agile.ALLOC_FN(alloc), agile.FREE_FN(free), None)
+    out = C.c_void_p()
+    st = lib.agile_mesh_create(C.byref(agile.make_config()), C.byref(a), None, C.byref(out))
+    assert st == 2 and not out.value     # AGILE_ENOMEM
+    assert len(calls) >= 1
+
+
+def test_binding_refuses_missing_library(tmp_path):
+    from paper_2607_19277_gb300 import agile
+    saved = agile._lib
+    agile._lib = None
+    try:
+        with pytest.raises(OSError):
+            agile.load(str(tmp_path / "missing.so"))
+    finally:
+        agile._lib = saved
