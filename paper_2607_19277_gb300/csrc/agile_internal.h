@@ -49,11 +49,12 @@ struct GhostTask {      // one coarse-fine face of a block, filled before each s
   int pad;
 };
 
-struct FixupTask {      // one coarse face shared with 4 finer blocks
+struct FixupTask {      // all faces of one coarse block shared with 4 finer blocks each
   int blk;
-  int face;
-  int slot_c;
-  int slot_f[4];
+  int nface;
+  int face[NFACE];
+  int slot_c[NFACE];
+  int slot_f[NFACE][4];
 };
 
 struct RegridSrc {      // how a block of the new mesh is made from the old one

@@ -139,33 +139,40 @@ __global__ void __launch_bounds__(256) ghost_kernel(const R* __restrict__ U, R* 
 }
 
 // ------------------------------------------------------------------------------ flux fix-up
+// One CTA per coarse block: its coarse-fine faces are corrected one after the other (a
+// cell on an edge between two such faces receives both corrections without a race).
+// U += b dt (+/-)(F_coarse - mean of the 2x2 fine face fluxes) / dx on the adjacent cells.
 template <typename R, int NV, int NT>
 __global__ void __launch_bounds__(256) fixup_kernel(R* __restrict__ U, const R* __restrict__ FR,
                                                      const BlockDesc* __restrict__ bd,
                                                      const FixupTask* __restrict__ tasks, double b,
                                                      const double* __restrict__ dtch) {
-  const FixupTask tk = tasks[blockIdx.x];
-  const int d = tk.face >> 1, s = tk.face & 1;
+  const FixupTask& tk = tasks[blockIdx.x];
   const int t1 = threadIdx.x & 15, t2 = threadIdx.x >> 4;
-  const int t1d = d == 0 ? 1 : 0, t2d = d == 2 ? 1 : 2;
-  int q[3];
-  q[d] = s ? NB - 1 : 0;
-  q[t1d] = t1;
-  q[t2d] = t2;
-  const size_t cell = (size_t)q[2] * 256 + q[1] * 16 + q[0];
-  const int sf = tk.slot_f[(t1 >> 3) + 2 * (t2 >> 3)];
-  const int a0 = 2 * (t1 & 7), b0 = 2 * (t2 & 7);
-  const R w = R(b * dtch[0] / bd[tk.blk].dx[d]) * (s ? R(1) : R(-1));
+  for (int j = 0; j < tk.nface; ++j) {
+    const int face = tk.face[j];
+    const int d = face >> 1, s = face & 1;
+    const int t1d = d == 0 ? 1 : 0, t2d = d == 2 ? 1 : 2;
+    int q[3];
+    q[d] = s ? NB - 1 : 0;
+    q[t1d] = t1;
+    q[t2d] = t2;
+    const size_t cell = (size_t)q[2] * 256 + q[1] * 16 + q[0];
+    const int sf = tk.slot_f[j][(t1 >> 3) + 2 * (t2 >> 3)];
+    const int a0 = 2 * (t1 & 7), b0 = 2 * (t2 & 7);
+    const R w = R(b * dtch[0] / bd[tk.blk].dx[d]) * (s ? R(1) : R(-1));
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const R fc = FR[((size_t)tk.slot_c * NV + v) * 256 + t2 * 16 + t1];
-    const R* ff = FR + ((size_t)sf * NV + v) * 256;
-    R avg = ff[b0 * 16 + a0] + ff[b0 * 16 + a0 + 1];
-    avg = avg + ff[(b0 + 1) * 16 + a0];
-    avg = avg + ff[(b0 + 1) * 16 + a0 + 1];
-    avg = avg * R(0.25);
-    R* u = U + ((size_t)tk.blk * NT + v) * NCELL + cell;
-    *u = *u + w * (fc - avg);
+    for (int v = 0; v < NV; ++v) {
+      const R fc = FR[((size_t)tk.slot_c[j] * NV + v) * 256 + t2 * 16 + t1];
+      const R* ff = FR + ((size_t)sf * NV + v) * 256;
+      R avg = ff[b0 * 16 + a0] + ff[b0 * 16 + a0 + 1];
+      avg = avg + ff[(b0 + 1) * 16 + a0];
+      avg = avg + ff[(b0 + 1) * 16 + a0 + 1];
+      avg = avg * R(0.25);
+      R* u = U + ((size_t)tk.blk * NT + v) * NCELL + cell;
+      *u = *u + w * (fc - avg);
+    }
+    __syncthreads();
   }
 }
 

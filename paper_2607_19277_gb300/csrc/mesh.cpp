@@ -296,24 +296,27 @@ void HostMesh::build_descs(std::vector<BlockDesc>* desc, std::vector<GhostTask>*
       }
     }
   }
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i) {
+    const BlockDesc& bd = (*desc)[i];
+    FixupTask t;
+    t.blk = i;
+    t.nface = 0;
     for (int f = 0; f < 6; ++f) {
-      const BlockDesc& bd = (*desc)[i];
       if (bd.kind[f] != FK_FINER) continue;
-      FixupTask t;
-      t.blk = i;
-      t.face = f;
-      t.slot_c = bd.slot[f];
+      const int j = t.nface++;
+      t.face[j] = f;
+      t.slot_c[j] = bd.slot[f];
       for (int q = 0; q < 4; ++q) {
         const int fb = bd.nbr[f][q];
-        t.slot_f[q] = (*desc)[fb].slot[f ^ 1];
-        if (t.slot_f[q] < 0 || (*desc)[fb].kind[f ^ 1] != FK_COARSER) {
+        t.slot_f[j][q] = (*desc)[fb].slot[f ^ 1];
+        if (t.slot_f[j][q] < 0 || (*desc)[fb].kind[f ^ 1] != FK_COARSER) {
           if (err) *err = "inconsistent coarse-fine face";
           return;
         }
       }
-      fixups->push_back(t);
     }
+    if (t.nface) fixups->push_back(t);
+  }
   *nslots = ns;
 }
 

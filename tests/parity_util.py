@@ -17,12 +17,14 @@ def gpu_mesh(spec, real_bytes=8):
     return agile.Mesh(agile.make_config(real_bytes=real_bytes, **spec))
 
 
-def rel_l1(gpu_cons, ora_cons, levels=None, physics="hd"):
+def rel_l1(gpu_cons, ora_cons, levels=None, physics="hd", cmax=None):
     """Relative L1 error per variable: sum |a - b| dV / sum |b| dV over the leaves.
 
     When the reference norm of a variable is below 1e-12 of the density norm (e.g. a
     momentum component that stays zero), the density norm (energy norm for B and psi)
-    is the denominator instead.
+    is the denominator instead. The GLM scalar psi vanishes in the exact solution and
+    grows only from discretisation errors of div B; its natural scale is c_h |B|, so with
+    cmax given its denominator is at least c_max * sum |B| dV.
     """
     if levels is None:
         w = np.ones(gpu_cons.shape[0])
@@ -38,6 +40,8 @@ def rel_l1(gpu_cons, ora_cons, levels=None, physics="hd"):
         d = den[v]
         if d < 1e-12 * rho:
             d = e if (physics == "mhd" and v >= 5) else rho
+        if physics == "mhd" and v == 8 and cmax is not None:
+            d = max(d, cmax * (den[5] + den[6] + den[7]))
         out[v] = num[v] / d
     return out
 
