@@ -20,6 +20,9 @@ CU_SOURCES = ["stage_hd.cu", "stage_mhd.cu", "stage_srhd.cu", "aux_kernels.cu", 
 CPP_SOURCES = ["mesh.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
+# The stage kernels' FP32 instantiations use the fast single-precision divide and square
+# root (max 2 ulp); FP64 arithmetic is unaffected by these flags.
+FAST_FP32 = ["--prec-div=false", "--prec-sqrt=false", "--ftz=true"]
 
 
 def _nvcc():
@@ -48,7 +51,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
         o = os.path.join(OUT, src + ".o")
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            jobs.append([nvcc] + ARCH + NVCC_FLAGS + ["-c", s, "-o", o])
+            extra = FAST_FP32 if src.startswith("stage_") else []
+            jobs.append([nvcc] + ARCH + NVCC_FLAGS + extra + ["-c", s, "-o", o])
     for src in CPP_SOURCES:
         s = os.path.join(CSRC, src)
         o = os.path.join(OUT, src + ".o")

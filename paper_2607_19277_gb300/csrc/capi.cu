@@ -1,5 +1,6 @@
 // C ABI of the block-AMR library: mesh lifecycle, device pools, the SSPRK step driver
 // (paper Fig. 2), regrid (Figs. 1-2), state transfer and diagnostics.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -40,6 +41,7 @@ struct agile_mesh {
   agile_ic_fn ic = nullptr;
   void* ic_user = nullptr;
   std::string err;
+  CUtensorMap tmap[3];
   bool timing = false;
   std::vector<cudaEvent_t> ev;
   long long stage_launches = 0, total_launches = 0;
@@ -117,6 +119,42 @@ agile_status check_status(agile_mesh* m) {
   return AGILE_OK;
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// Tensor map of one state pool as a 4-D array (x, y, z, block * var) whose TMA box is one
+// z-plane of every variable of a block: {16, 16, 1, nvar + naux}.
+agile_status make_tmap(agile_mesh* m, void* U, CUtensorMap* out) {
+  memset(out, 0, sizeof(*out));
+  if (!U) return AGILE_OK;
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return fail(m, AGILE_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  const cuuint64_t dims[4] = {16, 16, 16, (cuuint64_t)m->nblk * m->nt};
+  const cuuint64_t strides[3] = {(cuuint64_t)m->rb * 16, (cuuint64_t)m->rb * 256, (cuuint64_t)m->rb * 4096};
+  const cuuint32_t box[4] = {16, 16, 1, (cuuint32_t)m->nt};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(out, m->rb == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, U,
+                  dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(m, AGILE_ECUDA, "cuTensorMapEncodeTiled failed");
+  return AGILE_OK;
+}
+
 // (Re)build descriptors, slots and scratch for the current host mesh; U[0] must already
 // hold nblk blocks.
 agile_status rebuild(agile_mesh* m) {
@@ -155,6 +193,10 @@ agile_status rebuild(agile_mesh* m) {
   m->nslots = nslots;
   CK(m, cudaStreamSynchronize(m->stream));   // host vectors go out of scope
   m->speeds_valid = false;
+  for (int i = 0; i < 3; ++i) {
+    agile_status s = make_tmap(m, m->U[i], &m->tmap[i]);
+    if (s) return s;
+  }
   return AGILE_OK;
 }
 
@@ -411,6 +453,7 @@ agile_status agile_step(agile_mesh* m, double dt) {
     A.nblk = m->nblk;
     A.status = m->d_status;
     A.speeds = (last && fuse) ? m->d_speeds : nullptr;
+    A.tmap = &m->tmap[st == 0 ? 0 : st];
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (m->timing) {
       CK(m, cudaEventCreate(&e0));

@@ -9,7 +9,9 @@
 // paper's OpenACC version recomputes each face from both sides; here every face flux is
 // evaluated once.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include "agile_internal.h"
 #include "physics.cuh"
@@ -31,6 +33,7 @@ struct StageArgs {
   int nblk;
   int* status;
   unsigned long long* speeds;   // fused reduction of [max sum_d s_d/dx_d, max s_d] or nullptr
+  const void* tmap;             // host CUtensorMap of the pool Us (x, y, z, block*var)
 };
 
 // Conserved + auxiliary values of the cell (x, y, z) of block b in the halo view: the
@@ -132,15 +135,89 @@ __device__ __forceinline__ void block_max2(double a, double b, unsigned long lon
   }
 }
 
-template <template <typename> class PT, typename R, int LIM, int FLUX>
-__global__ void __launch_bounds__(256) stage_kernel(StageArgs A) {
+// --------------------------------------------------------------------------- TMA / mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after `limit` polls and reports it (no endless spin).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i)
+    if (mbar_test(bar, parity)) return true;
+  return false;
+}
+// Whole-box tile load (4-D tensor map: x, y, z, block*var) into shared memory.
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, uint64_t* bar, int c0, int c1,
+                                            int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+      "%4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+constexpr uint32_t WAIT_LIMIT = 1u << 22;   // ~0.1 s of polling per wait at most
+constexpr int ST_ETIMEOUT = 4;
+
+template <template <typename> class PT, typename R>
+struct StageSmem {
+  static constexpr int NV = PT<R>::NV, NT = PT<R>::NV + PT<R>::NA;
+  static constexpr size_t bars = 128;                                  // 4 mbarriers (+pad)
+  static constexpr size_t raw = bars;                                  // [4][NT][256]
+  static constexpr size_t prim = raw + sizeof(R) * 4 * NT * 256;       // [4][NT][256]
+  static constexpr size_t cur = prim + sizeof(R) * 4 * NT * 256;       // [NV][20][20]
+  static constexpr size_t fx = cur + sizeof(R) * NV * 400;             // [NV][16][17]
+  static constexpr size_t fy = fx + sizeof(R) * NV * 272;              // [NV][17][16]
+  static constexpr size_t total = fy + sizeof(R) * NV * 272;
+};
+
+// The per-stage macro-kernel. Plane k of the block is processed in three phases
+// separated by CTA barriers:
+//   1. primitives of plane k+2 (own column; raw data landed in the TMA ring) into the
+//      primitive ring, plane k (interior from the ring + x/y halo converted here) into
+//      the current-plane buffer;
+//   2. the x- and y-face fluxes of plane k (shared memory) and the z-face flux at k+1/2
+//      (from the primitive ring of this column, carried to the next plane in registers);
+//   3. flux divergence, SSPRK combine and store of cell (x, y, k).
+// Raw planes arrive by TMA one iteration ahead: the ring holds planes k .. k+3.
+template <template <typename> class PT, typename R, int LIM, int FLUX, int MINB>
+__global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                           StageArgs A) {
   using P = PT<R>;
+  using S = StageSmem<PT, R>;
   constexpr int NV = P::NV, NA = P::NA, NT = NV + NA;
   constexpr int NAW = NA > 0 ? NA : 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sP = reinterpret_cast<R*>(smem_raw);      // [NV][20][20] primitives of plane k
-  R* sFx = sP + NV * 400;                       // [NV][16][17] x-face fluxes
-  R* sFy = sFx + NV * 272;                      // [NV][17][16] y-face fluxes
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  R* sRaw = reinterpret_cast<R*>(smem_raw + S::raw);
+  R* sPr = reinterpret_cast<R*>(smem_raw + S::prim);
+  R* sC = reinterpret_cast<R*>(smem_raw + S::cur);
+  R* sFx = reinterpret_cast<R*>(smem_raw + S::fx);
+  R* sFy = reinterpret_cast<R*>(smem_raw + S::fy);
 
   const R* __restrict__ Us = static_cast<const R*>(A.Us);
   const R* __restrict__ Un = static_cast<const R*>(A.Un);
@@ -151,6 +228,8 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs A) {
   const int b = blockIdx.x;
   const int t = threadIdx.x;
   const int tx = t & 15, ty = t >> 4;
+  const int warp = t >> 5;
+  const int cell2 = ty * 16 + tx;
   const BlockDesc& bd = A.bd[b];
   int src[6], slot[6];
 #pragma unroll
@@ -166,55 +245,121 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs A) {
   const R rdt = R(dt);
   const R ra = R(A.a), rb = R(A.b);
   int st = 0;
+  constexpr uint32_t PLANE_BYTES = (uint32_t)(sizeof(R) * NT * 256);
 
-  R W[4][NV];     // primitives of planes k-1 .. k+2 of this column
-  R WA[4][NAW];   // auxiliaries recovered with them
-  R fzd[NV], fzu[NV];
-
-  auto load_prim = [&](int x, int y, int z, R* p, R* aux) {
+  // plane p (-2 .. 17) -> TMA sequence q = p + 2, ring slot q & 3, phase parity (q >> 2) & 1
+  auto plane_tma = [&](int p) -> bool {   // does plane p come by TMA (else loaded directly)?
+    if (p >= 0 && p < NB) return true;
+    return src[p < 0 ? 4 : 5] >= 0;
+  };
+  auto issue = [&](int p) {               // thread 0 only
+    const int q = p + 2;
+    uint64_t* br = bar + (q & 3);
+    if (plane_tma(p)) {
+      int blk = b, z = p;
+      if (p < 0 || p >= NB) {
+        blk = src[p < 0 ? 4 : 5];
+        z = p & (NB - 1);
+      }
+      mbar_expect_tx(br, PLANE_BYTES);
+      tma_load_4d(sRaw + (size_t)(q & 3) * NT * 256, &tmap, br, 0, 0, z, blk * NT);
+    } else {
+      mbar_arrive(br);
+    }
+  };
+  // Primitive recovery of this thread's own column at plane p into the primitive ring.
+  auto convert_own = [&](int p) {
+    const int q = p + 2;
     R u[NT];
-    load_cell<P, R>(Us, G, src, b, x, y, z, u);
-    R a_[NAW];
+    if (plane_tma(p)) {
+      if (!mbar_wait(bar + (q & 3), (q >> 2) & 1, WAIT_LIMIT)) st |= ST_ETIMEOUT;
+      const R* r = sRaw + (size_t)(q & 3) * NT * 256 + cell2;
+#pragma unroll
+      for (int v = 0; v < NT; ++v) u[v] = r[v * 256];
+    } else {
+      load_cell<P, R>(Us, G, src, b, tx, ty, p, u);
+    }
+    R pr[NV], aux[NAW];
     if constexpr (NA > 0) {
 #pragma unroll
-      for (int i = 0; i < NA; ++i) a_[i] = u[NV + i];
+      for (int i = 0; i < NA; ++i) aux[i] = u[NV + i];
     } else {
-      a_[0] = R(0);
+      aux[0] = R(0);
     }
-    P::cons2prim(u, p, a_, pp, st);
+    P::cons2prim(u, pr, aux, pp, st);
+    R* w = sPr + (size_t)(p & 3) * NT * 256 + cell2;
 #pragma unroll
-    for (int i = 0; i < NAW; ++i) aux[i] = a_[i];
+    for (int v = 0; v < NV; ++v) w[v * 256] = pr[v];
+    if constexpr (NA > 0) {
+#pragma unroll
+      for (int i = 0; i < NA; ++i) w[(NV + i) * 256] = aux[i];
+    }
+  };
+  auto zface = [&](int k, R* f) {          // z-face flux at k + 1/2 of this column
+    R a[NV], bq[NV], c[NV], d[NV], pl[NV], pr[NV];
+    const R* r0 = sPr + (size_t)((k - 1) & 3) * NT * 256 + cell2;
+    const R* r1 = sPr + (size_t)(k & 3) * NT * 256 + cell2;
+    const R* r2 = sPr + (size_t)((k + 1) & 3) * NT * 256 + cell2;
+    const R* r3 = sPr + (size_t)((k + 2) & 3) * NT * 256 + cell2;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      a[v] = r0[v * 256]; bq[v] = r1[v * 256]; c[v] = r2[v * 256]; d[v] = r3[v * 256];
+    }
+    plm<NV, R, LIM>(a, bq, c, d, pl, pr);
+    riemann<P, R, 2, FLUX>(pl, pr, f, pp);
+  };
+  auto xface = [&](int fi, int row, R* f) {  // x-face fi - 1/2 of row `row` in plane buffer
+    R a[NV], bq[NV], c[NV], d[NV], pl[NV], pr[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const R* r = sC + v * 400 + (row + 2) * 20 + fi;
+      a[v] = r[0]; bq[v] = r[1]; c[v] = r[2]; d[v] = r[3];
+    }
+    plm<NV, R, LIM>(a, bq, c, d, pl, pr);
+    riemann<P, R, 0, FLUX>(pl, pr, f, pp);
+  };
+  auto yface = [&](int fj, int col, R* f) {  // y-face fj - 1/2 of column `col`
+    R a[NV], bq[NV], c[NV], d[NV], pl[NV], pr[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const R* r = sC + v * 400 + fj * 20 + col + 2;
+      a[v] = r[0]; bq[v] = r[20]; c[v] = r[40]; d[v] = r[60];
+    }
+    plm<NV, R, LIM>(a, bq, c, d, pl, pr);
+    riemann<P, R, 1, FLUX>(pl, pr, f, pp);
   };
 
-  // Prologue: planes -2, -1, 0, 1 of this column and the z-face at -1/2.
+  if (t == 0) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) load_prim(tx, ty, i - 2, W[i], WA[i]);
-  {
-    R pl[NV], pr[NV];
-    plm<NV, R, LIM>(W[0], W[1], W[2], W[3], pl, pr);
-    riemann<P, R, 2, FLUX>(pl, pr, fzd, pp);
+    for (int i = 0; i < 4; ++i) mbar_init(bar + i, 1);
+    fence_mbar_init();
   }
+  __syncthreads();
+  if (t == 0) {
+    for (int p = -2; p <= 1; ++p) issue(p);
+  }
+  // Prologue: planes -2 .. 1 of this column, then the z-face at -1/2. Ring slots at
+  // iteration k: k&3 -> plane k+2 (converted now), (k+1)&3 -> plane k+3 (in flight),
+  // (k+2)&3 -> plane k (its update), (k+3)&3 -> plane k+1.
+  convert_own(-2);
+  convert_own(-1);
+  __syncthreads();   // raw slots of planes -2 and -1 are free
+  if (t == 0) {
+    fence_proxy_async();
+    issue(2);
+    issue(3);
+  }
+  convert_own(0);
+  convert_own(1);
+  R fzd[NV], fzu[NV];
+  zface(-1, fzd);
   if (FR && slot[4] >= 0) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) FR[((size_t)slot[4] * NV + v) * 256 + ty * 16 + tx] = fzd[v];
+    for (int v = 0; v < NV; ++v) FR[((size_t)slot[4] * NV + v) * 256 + cell2] = fzd[v];
   }
-  // shift in plane 2
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    W[0][v] = W[1][v];
-    W[1][v] = W[2][v];
-    W[2][v] = W[3][v];
-  }
-#pragma unroll
-  for (int i = 0; i < NAW; ++i) {
-    WA[0][i] = WA[1][i];
-    WA[1][i] = WA[2][i];
-    WA[2][i] = WA[3][i];
-  }
-  load_prim(tx, ty, 2, W[3], WA[3]);
 
   double ssum = 0.0, smax = 0.0;
-  double dxd[3] = {bd.dx[0], bd.dx[1], bd.dx[2]};
+  const double dxd[3] = {bd.dx[0], bd.dx[1], bd.dx[2]};
   double glm_f = 1.0;
   if (A.glm_post) {
     const double dxm = fmin(fmin(bd.dx[0], bd.dx[1]), bd.dx[2]);
@@ -222,75 +367,67 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs A) {
   }
 
   for (int k = 0; k < NB; ++k) {
-    // 1. primitives of plane k into shared memory: own column + x/y halo
+    // ---- phase 1
+    if (k + 2 <= NB + 1) convert_own(k + 2);
+    {
+      const R* r = sPr + (size_t)(k & 3) * NT * 256 + cell2;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sP[v * 400 + (ty + 2) * 20 + tx + 2] = W[1][v];
-    if (t < 128) {
-      const int side = (t >> 5) & 1, layer = (t >> 4) & 1, r = t & 15;
-      const int c = side ? NB + layer : layer - 2;
-      int x, y;
-      if (t < 64) { x = c; y = r; } else { x = r; y = c; }
-      R p[NV], aux[NAW];
-      load_prim(x, y, k, p, aux);
+      for (int v = 0; v < NV; ++v) sC[v * 400 + (ty + 2) * 20 + tx + 2] = r[v * 256];
+    }
+    {
+      const int h = t - 128 * (k & 1);       // halves of the CTA take turns on the halo
+      if (h >= 0 && h < 128) {
+        const int side = (h >> 5) & 1, layer = (h >> 4) & 1, rr = h & 15;
+        const int c = side ? NB + layer : layer - 2;
+        int x, y;
+        if (h < 64) { x = c; y = rr; } else { x = rr; y = c; }
+        R u[NT], p[NV], aux[NAW];
+        load_cell<P, R>(Us, G, src, b, x, y, k, u);
+        if constexpr (NA > 0) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) sP[v * 400 + (y + 2) * 20 + x + 2] = p[v];
+          for (int i = 0; i < NA; ++i) aux[i] = u[NV + i];
+        } else {
+          aux[0] = R(0);
+        }
+        P::cons2prim(u, p, aux, pp, st);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sC[v * 400 + (y + 2) * 20 + x + 2] = p[v];
+      }
     }
     __syncthreads();
-    // 2. x- and y-face fluxes of plane k (17 x 16 each); warp 0 takes the 32 extra faces
+    // ---- phase 2
+    if (t == 0 && k >= 1 && k + 3 <= NB + 1) {
+      fence_proxy_async();
+      issue(k + 3);   // slot (k+1)&3: plane k-1's raw data, read by its update before this barrier
+    }
     {
-      R a[NV], bq[NV], c[NV], d[NV], pl[NV], pr[NV], f[NV];
-      // x-face at tx - 1/2 of row ty
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const R* row = sP + v * 400 + (ty + 2) * 20 + tx;
-        a[v] = row[0]; bq[v] = row[1]; c[v] = row[2]; d[v] = row[3];
-      }
-      plm<NV, R, LIM>(a, bq, c, d, pl, pr);
-      riemann<P, R, 0, FLUX>(pl, pr, f, pp);
+      R f[NV];
+      xface(tx, ty, f);
 #pragma unroll
       for (int v = 0; v < NV; ++v) sFx[v * 272 + ty * 17 + tx] = f[v];
       if (FR && tx == 0 && slot[0] >= 0) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) FR[((size_t)slot[0] * NV + v) * 256 + k * 16 + ty] = f[v];
       }
-      // y-face at ty - 1/2 of column tx
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const R* col = sP + v * 400 + ty * 20 + tx + 2;
-        a[v] = col[0]; bq[v] = col[20]; c[v] = col[40]; d[v] = col[60];
-      }
-      plm<NV, R, LIM>(a, bq, c, d, pl, pr);
-      riemann<P, R, 1, FLUX>(pl, pr, f, pp);
+      yface(ty, tx, f);
 #pragma unroll
       for (int v = 0; v < NV; ++v) sFy[v * 272 + ty * 16 + tx] = f[v];
       if (FR && ty == 0 && slot[2] >= 0) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) FR[((size_t)slot[2] * NV + v) * 256 + k * 16 + tx] = f[v];
       }
-      if (t < 32) {
-        const int r = t & 15;
-        if (t < 16) {   // x-face 16 - 1/2 of row r
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            const R* row = sP + v * 400 + (r + 2) * 20 + 16;
-            a[v] = row[0]; bq[v] = row[1]; c[v] = row[2]; d[v] = row[3];
-          }
-          plm<NV, R, LIM>(a, bq, c, d, pl, pr);
-          riemann<P, R, 0, FLUX>(pl, pr, f, pp);
+      if (warp == (k & 7)) {      // the 32 block-boundary faces, one warp per plane in turn
+        const int lane = t & 31, r = lane & 15;
+        if (lane < 16) {
+          xface(16, r, f);
 #pragma unroll
           for (int v = 0; v < NV; ++v) sFx[v * 272 + r * 17 + 16] = f[v];
           if (FR && slot[1] >= 0) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) FR[((size_t)slot[1] * NV + v) * 256 + k * 16 + r] = f[v];
           }
-        } else {        // y-face 16 - 1/2 of column r
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            const R* col = sP + v * 400 + 16 * 20 + r + 2;
-            a[v] = col[0]; bq[v] = col[20]; c[v] = col[40]; d[v] = col[60];
-          }
-          plm<NV, R, LIM>(a, bq, c, d, pl, pr);
-          riemann<P, R, 1, FLUX>(pl, pr, f, pp);
+        } else {
+          yface(16, r, f);
 #pragma unroll
           for (int v = 0; v < NV; ++v) sFy[v * 272 + 16 * 16 + r] = f[v];
           if (FR && slot[3] >= 0) {
@@ -299,19 +436,18 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs A) {
           }
         }
       }
-      // z-face at k + 1/2 of this column
-      plm<NV, R, LIM>(W[0], W[1], W[2], W[3], pl, pr);
-      riemann<P, R, 2, FLUX>(pl, pr, fzu, pp);
+      zface(k, fzu);
       if (FR && k == NB - 1 && slot[5] >= 0) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) FR[((size_t)slot[5] * NV + v) * 256 + ty * 16 + tx] = fzu[v];
+        for (int v = 0; v < NV; ++v) FR[((size_t)slot[5] * NV + v) * 256 + cell2] = fzu[v];
       }
     }
     __syncthreads();
-    // 3. flux divergence and stage combine for cell (tx, ty, k)
+    // ---- phase 3: flux divergence and stage combine of cell (tx, ty, k)
     {
-      const size_t cell = (size_t)k * 256 + ty * 16 + tx;
+      const size_t cell = (size_t)k * 256 + cell2;
       const size_t base = (size_t)b * NT * NCELL + cell;
+      const R* raw = sRaw + (size_t)((k + 2) & 3) * NT * 256 + cell2;
       R out[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -319,41 +455,34 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs A) {
         const R ly = (sFy[v * 272 + (ty + 1) * 16 + tx] - sFy[v * 272 + ty * 16 + tx]) * idy;
         const R lz = (fzu[v] - fzd[v]) * idz;
         const R L = -((lx + ly) + lz);
-        R val = Us[base + (size_t)v * NCELL] + rdt * L;
+        R val = raw[v * 256] + rdt * L;
         if (A.a != 0.0) val = ra * Un[base + (size_t)v * NCELL] + rb * val;
         out[v] = val;
+        fzd[v] = fzu[v];
       }
       if (P::BOFF >= 0 && A.glm_post) out[NV - 1] = R((double)out[NV - 1] * glm_f);
 #pragma unroll
       for (int v = 0; v < NV; ++v) Uo[base + (size_t)v * NCELL] = out[v];
+      R auxk[NAW];
       if constexpr (NA > 0) {
+        const R* pa = sPr + (size_t)(k & 3) * NT * 256 + cell2;
 #pragma unroll
-        for (int i = 0; i < NA; ++i) Uo[base + (size_t)(NV + i) * NCELL] = WA[1][i];
+        for (int i = 0; i < NA; ++i) {
+          auxk[i] = pa[(NV + i) * 256];
+          Uo[base + (size_t)(NV + i) * NCELL] = auxk[i];
+        }
+      } else {
+        auxk[0] = R(0);
       }
       if (A.speeds) {
         double ud[NV], ad[2];
 #pragma unroll
         for (int v = 0; v < NV; ++v) ud[v] = (double)out[v];
-        ad[0] = NA > 0 ? (double)WA[1][0] : 0.0;
+        ad[0] = (double)auxk[0];
         ad[1] = 0.0;
         cell_speeds<PT>(ud, ad, pp, dxd, ssum, smax, st);
       }
     }
-    // 4. advance the column window
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      fzd[v] = fzu[v];
-      W[0][v] = W[1][v];
-      W[1][v] = W[2][v];
-      W[2][v] = W[3][v];
-    }
-#pragma unroll
-    for (int i = 0; i < NAW; ++i) {
-      WA[0][i] = WA[1][i];
-      WA[1][i] = WA[2][i];
-      WA[2][i] = WA[3][i];
-    }
-    if (k + 3 <= NB + 1) load_prim(tx, ty, k + 3, W[3], WA[3]);
   }
   if (A.speeds) block_max2<256>(ssum, smax, A.speeds);
   if (st) atomicOr(A.status, st);
@@ -361,7 +490,7 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs A) {
 
 template <template <typename> class PT, typename R>
 constexpr size_t stage_smem_bytes() {
-  return sizeof(R) * (size_t)PT<R>::NV * (400 + 272 + 272);
+  return StageSmem<PT, R>::total;
 }
 
 }  // namespace agile

@@ -6,11 +6,16 @@ namespace agile {
 
 template <typename R, int LIM, int FLUX>
 static cudaError_t go(const StageArgs& a, cudaStream_t s) {
-  auto k = stage_kernel<SrhdPhys, R, LIM, FLUX>;
+  constexpr int MINB = sizeof(R) == 4 ? 2 : 1;   // CTAs per SM the register budget targets
+  auto k = stage_kernel<SrhdPhys, R, LIM, FLUX, MINB>;
   const size_t smem = stage_smem_bytes<SrhdPhys, R>();
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k<<<a.nblk, 256, smem, s>>>(a);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k<<<a.nblk, 256, smem, s>>>(*static_cast<const CUtensorMap*>(a.tmap), a);
   return cudaGetLastError();
 }
 

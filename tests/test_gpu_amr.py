@@ -111,7 +111,16 @@ def test_amr_mhd_and_srhd_steps():
     for physics, flux, gam in (("mhd", "hll", 5.0 / 3.0), ("srhd", "tvdlf", 4.0 / 3.0)):
         spec = dict(SPEC3, physics=physics, flux=flux, gamma=gam, rk=2)
         nvar = 9 if physics == "mhd" else 5
-        o, m = _three_level(spec, W.random_smooth(nvar, 14, physics))
+        base = W.random_smooth(nvar, 14, physics)
+
+        def ic(x, y, z, base=base, physics=physics):
+            p = base(x, y, z)
+            if physics == "srhd":
+                # milder four-velocities: prolongation of conserved SRHD variables across
+                # two levels of a strong state can leave |m| > tau + D (no root)
+                p[1:4] *= 0.3
+            return p
+        o, m = _three_level(spec, ic)
         for _ in range(2):
             dt = o.cfl_dt()
             o.step(dt)
