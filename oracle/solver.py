@@ -640,7 +640,7 @@ class Solver:
         """
         fl, _ = self.flags()          # also fills ghosts (both phases)
         dirs = self._dirs26()
-        R = {k for k, f in fl.items() if f == 1}
+        R = {k for k, f in fl.items() if f == 1 and k[0] < self.cfg.max_level}
         changed = True
         while changed:
             changed = False
