@@ -180,6 +180,21 @@ agile_status agile_get_aux(agile_mesh* mesh, double* aux);
  * U * cell volume; the paper's high-cadence mass/energy log, Section 4.1). Synchronises. */
 agile_status agile_conserved_sums(agile_mesh* mesh, double* sums);
 
+/* Conserved sums like agile_conserved_sums, for callers that cannot allocate device memory
+ * at the time of the call: code running inside a CUDA stream capture (where cudaMalloc is
+ * not allowed), a serving loop that reserved its whole device budget up front, or a host
+ * whose allocator is not re-entrant from this thread. The paper has no counterpart; this is
+ * a property of the library. It allocates nothing: its scratch (per-block partial sums and
+ * the totals, about 1.2 MB) is a fixed array in device memory that every GPU that loads the
+ * library holds until the process exits. The mesh and sums (host, [nvar]) are the caller's.
+ * Limit: meshes of at most 16384 leaves; larger ones return AGILE_EBUDGET with a message.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture. All calls share the one array, so calls
+ * whose work overlaps on the GPU (several streams or threads at once) race on it; the
+ * array keeps the last call's contents, and every call overwrites what it reads.
+ * Synchronises the mesh's stream. Results equal agile_conserved_sums bit for bit. */
+agile_status agile_conserved_sums_noalloc(agile_mesh* mesh, double* sums);
+
 /* Maximum Loehner estimate of every leaf (block order) on the current state after a
  * full ghost fill, computed in FP64 without fused multiply-add so that refinement
  * decisions are reproducible bit for bit. Synchronises. */

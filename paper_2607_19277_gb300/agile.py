@@ -28,7 +28,8 @@ STATUS = {0: "AGILE_OK", 1: "AGILE_EINVAL", 2: "AGILE_ENOMEM", 3: "AGILE_EBUDGET
 # Symbols declared in include/agile.h (checked by the CPU test suite).
 EXPORTS = ["agile_mesh_create", "agile_mesh_destroy", "agile_set_state", "agile_set_state_blocks",
            "agile_cfl_dt", "agile_step", "agile_regrid", "agile_regrid_flags", "agile_get_layout",
-           "agile_get_state", "agile_get_aux", "agile_conserved_sums", "agile_estimate",
+           "agile_get_state", "agile_get_aux", "agile_conserved_sums",
+           "agile_conserved_sums_noalloc", "agile_estimate",
            "agile_get_halo", "agile_sync", "agile_set_kernel_timing", "agile_kernel_timing",
            "agile_last_error", "agile_version"]
 
@@ -86,6 +87,7 @@ def load(path: str = LIB_PATH):
         "agile_get_state": (C.c_int, [P, ip, ip, dp]),
         "agile_get_aux": (C.c_int, [P, dp]),
         "agile_conserved_sums": (C.c_int, [P, dp]),
+        "agile_conserved_sums_noalloc": (C.c_int, [P, dp]),
         "agile_estimate": (C.c_int, [P, dp]),
         "agile_get_halo": (C.c_int, [P, C.c_size_t, dp]),
         "agile_sync": (C.c_int, [P]),
@@ -182,16 +184,23 @@ def agile_mesh_create(cfg: agile_config, allocator=None, stream: int = 0):
 class Mesh:
     """One block-AMR mesh on the current CUDA device and stream (torch's allocator)."""
 
-    def __init__(self, cfg: agile_config, stream=None, use_torch_allocator=True):
+    def __init__(self, cfg: agile_config, stream=None, use_torch_allocator=True, allocator=None):
+        """allocator: an agile_allocator to use instead of torch's caching allocator (the
+        caller keeps its callbacks alive); use_torch_allocator=False with no allocator
+        selects the library's cudaMallocAsync default."""
         import torch
         self.lib = load()
         self.cfg = cfg
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
-        self._alloc = _TorchAllocator(torch.cuda.current_device()) if use_torch_allocator else None
-        self.ptr = agile_mesh_create(cfg, self._alloc.struct if self._alloc else None,
-                                     int(stream.cuda_stream))
+        if allocator is not None:
+            self._alloc = None
+            alloc_struct = allocator
+        else:
+            self._alloc = _TorchAllocator(torch.cuda.current_device()) if use_torch_allocator else None
+            alloc_struct = self._alloc.struct if self._alloc else None
+        self.ptr = agile_mesh_create(cfg, alloc_struct, int(stream.cuda_stream))
         self.nvar = 9 if cfg.physics == 1 else 5
         self.naux = 2 if cfg.physics == 2 else 0
         self._ic = None
@@ -271,6 +280,12 @@ class Mesh:
     def conserved_sums(self):
         s = np.zeros(self.nvar)
         self._ck(self.lib.agile_conserved_sums(self.ptr, _dptr(s)))
+        return s
+
+    def conserved_sums_noalloc(self):
+        """Same sums through the entry point that allocates no device memory."""
+        s = np.zeros(self.nvar)
+        self._ck(self.lib.agile_conserved_sums_noalloc(self.ptr, _dptr(s)))
         return s
 
     def estimate(self):

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -653,3 +654,78 @@ agile_status agile_kernel_timing(agile_mesh* m, double* stage_ms, long long* sta
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------------------
+// Conserved sums without any device allocation (agile_conserved_sums_noalloc).
+//
+// Some callers cannot allocate device memory at the moment they want the diagnostics: code
+// running inside a CUDA stream capture (cudaMalloc is not allowed while capturing), a
+// serving loop that reserved its whole device budget up front and forbids further
+// allocation, or a host whose allocator is not re-entrant from the calling thread. This
+// variant keeps its scratch (per-block partial sums and the totals) in a fixed array in
+// device memory that every GPU loading the library holds until the process exits.
+// ----------------------------------------------------------------------------------------
+namespace {
+
+constexpr int NOALLOC_MAX_BLOCKS = 16384;                 // leaves per mesh
+constexpr size_t NOALLOC_TOTALS = (size_t)NOALLOC_MAX_BLOCKS * 9;
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_TOTALS + 16];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up once per device;
+// in host code the symbol itself is only a host-side stand-in).
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    double* p = nullptr;
+    e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
+// Totals over blocks in block order with Neumaier compensation, one thread per variable:
+// the same order and operations as the host-side sum of agile_conserved_sums.
+__global__ void noalloc_total_kernel(const double* part, int nblk, int nv, double* totals) {
+  const int v = threadIdx.x;
+  if (v >= nv) return;
+  double sum = 0.0, comp = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    const double x = part[(size_t)b * nv + v];
+    const double t = __dadd_rn(sum, x);
+    if (fabs(sum) >= fabs(x)) comp = __dadd_rn(comp, __dadd_rn(__dsub_rn(sum, t), x));
+    else comp = __dadd_rn(comp, __dadd_rn(__dsub_rn(x, t), sum));
+    sum = t;
+  }
+  totals[v] = __dadd_rn(sum, comp);
+}
+
+}  // namespace
+
+extern "C" agile_status agile_conserved_sums_noalloc(agile_mesh* m, double* sums) {
+  if (!m || !sums) return fail(m, AGILE_EINVAL, "null argument");
+  if (m->nblk > NOALLOC_MAX_BLOCKS)
+    return fail(m, AGILE_EBUDGET,
+                "agile_conserved_sums_noalloc: mesh has " + std::to_string(m->nblk) +
+                    " leaves, more than its fixed scratch holds (" +
+                    std::to_string(NOALLOC_MAX_BLOCKS) + "); use agile_conserved_sums");
+  double* scratch = nullptr;
+  CK(m, noalloc_scratch(&scratch));
+  AuxArgs a = aux_args(m, m->U[0]);
+  CK(m, launch_sums(a, scratch, m->stream));
+  noalloc_total_kernel<<<1, 32, 0, m->stream>>>(scratch, m->nblk, m->nv, scratch + NOALLOC_TOTALS);
+  CK(m, cudaGetLastError());
+  m->total_launches += 2;
+  CK(m, cudaMemcpyAsync(sums, scratch + NOALLOC_TOTALS, m->nv * sizeof(double), cudaMemcpyDeviceToHost,
+                        m->stream));
+  return check_status(m);
+}
