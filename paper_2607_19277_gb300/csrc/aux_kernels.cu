@@ -181,7 +181,7 @@ template <template <typename> class PT, typename R>
 __global__ void __launch_bounds__(256) speeds_kernel(const R* __restrict__ U,
                                                       const BlockDesc* __restrict__ bd, double gamma,
                                                       unsigned long long* speeds, int* status) {
-  using P = PT<double>;
+  using P = PT<R>;
   constexpr int NV = P::NV, NA = P::NA, NT = NV + NA;
   const int b = blockIdx.x;
   const double dx[3] = {bd[b].dx[0], bd[b].dx[1], bd[b].dx[2]};
@@ -192,11 +192,11 @@ __global__ void __launch_bounds__(256) speeds_kernel(const R* __restrict__ U,
   int st = 0;
   const R* base = U + (size_t)b * NT * NCELL;
   for (int c = threadIdx.x; c < NCELL; c += 256) {
-    double u[NT], aux[2] = {0.0, 0.0};
+    R u[NV], aux[2] = {R(0), R(0)};
 #pragma unroll
-    for (int v = 0; v < NV; ++v) u[v] = (double)base[(size_t)v * NCELL + c];
-    if constexpr (NA > 0) aux[0] = (double)base[(size_t)NV * NCELL + c];
-    cell_speeds<PT>(u, aux, pp, dx, ssum, smax, st);
+    for (int v = 0; v < NV; ++v) u[v] = base[(size_t)v * NCELL + c];
+    if constexpr (NA > 0) aux[0] = base[(size_t)NV * NCELL + c];
+    cell_speeds<PT, R>(u, aux, pp, dx, ssum, smax, st);
   }
   block_max2<256>(ssum, smax, speeds);
   if (st) atomicOr(status, st);

@@ -87,27 +87,25 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long* addr, double 
   atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }
 
-// Signal speeds of one cell in FP64: s_d = max |lambda_+-| along d.
-template <template <typename> class PT>
-__device__ __forceinline__ void cell_speeds(const double* u, double* aux, const PhysParams& pp,
+// Signal speeds of one cell, s_d = max |lambda_+-| along d, evaluated in the stencil
+// precision R (the SRHD primitive recovery inside is FP64 always); the maxima are
+// accumulated in FP64: ssum = max sum_d s_d / dx_d, smax = max_d s_d.
+template <template <typename> class PT, typename R>
+__device__ __forceinline__ void cell_speeds(const R* u, R* aux, const PhysParams& pp,
                                             const double* dx, double& ssum, double& smax, int& st) {
-  using P = PT<double>;
-  double p[P::NV];
+  using P = PT<R>;
+  R p[P::NV];
   P::cons2prim(u, p, aux, pp, st);
-  double lm, lp, s;
+  R lm, lp;
   P::template lambdas<0>(p, lm, lp, pp);
-  s = fmax(fabs(lm), fabs(lp));
-  smax = fmax(smax, s);
-  double acc = s / dx[0];
+  const R s0 = rmax(rabs(lm), rabs(lp));
   P::template lambdas<1>(p, lm, lp, pp);
-  s = fmax(fabs(lm), fabs(lp));
-  smax = fmax(smax, s);
-  acc = acc + s / dx[1];
+  const R s1 = rmax(rabs(lm), rabs(lp));
   P::template lambdas<2>(p, lm, lp, pp);
-  s = fmax(fabs(lm), fabs(lp));
-  smax = fmax(smax, s);
-  acc = acc + s / dx[2];
-  ssum = fmax(ssum, acc);
+  const R s2 = rmax(rabs(lm), rabs(lp));
+  smax = fmax(smax, (double)rmax(rmax(s0, s1), s2));
+  const R acc = (s0 / R(dx[0]) + s1 / R(dx[1])) + s2 / R(dx[2]);
+  ssum = fmax(ssum, (double)acc);
 }
 
 template <int NTHREADS>
@@ -180,6 +178,71 @@ __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+template <typename R>
+__device__ __forceinline__ void cp_async_elem(R* dst, const R* src) {
+  if constexpr (sizeof(R) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Address of variable 0 of cell (x, y, z) in the halo view of block b and the variable
+// stride there (same pointer rules as load_cell); *neg_d is the dimension whose normal
+// components a reflecting boundary negates, or -1.
+template <class P, typename R>
+__device__ __forceinline__ const R* cell_addr(const R* __restrict__ U, const R* __restrict__ G,
+                                              const int* src, int b, int x, int y, int z, int* vstride,
+                                              int* neg_d) {
+  constexpr int NT = P::NV + P::NA;
+  int f = -1;
+  if (x < 0) f = 0;
+  else if (x > NB - 1) f = 1;
+  else if (y < 0) f = 2;
+  else if (y > NB - 1) f = 3;
+  else if (z < 0) f = 4;
+  else if (z > NB - 1) f = 5;
+  int q[3] = {x, y, z};
+  int blk = b;
+  *neg_d = -1;
+  *vstride = NCELL;
+  if (f >= 0) {
+    const int d = f >> 1, s = f & 1;
+    const int sv = src[f];
+    if (sv >= 0) {
+      q[d] &= NB - 1;
+      blk = sv;
+    } else if (sv == SRC_OUTFLOW) {
+      q[d] = s ? NB - 1 : 0;
+    } else if (sv == SRC_REFLECT) {
+      q[d] = s ? 2 * NB - 1 - q[d] : -1 - q[d];
+      *neg_d = d;
+    } else {
+      const int slot = SRC_SLOT0 - sv;
+      const int layer = s ? q[d] - NB : q[d] + 2;
+      const int t1 = d == 0 ? q[1] : q[0];
+      const int t2 = d == 2 ? q[1] : q[2];
+      *vstride = 512;
+      return G + (size_t)slot * NT * 512 + layer * 256 + t2 * 16 + t1;
+    }
+  }
+  return U + (size_t)blk * NT * NCELL + q[2] * 256 + q[1] * 16 + q[0];
+}
+
+// x/y component swap used to evaluate a y-face with the x-face solver.
+template <class P, typename R>
+__device__ __forceinline__ void swap_xy(R* v, bool yd) {
+  const R a = v[1], c = v[2];
+  v[1] = yd ? c : a;
+  v[2] = yd ? a : c;
+  if constexpr (P::BOFF >= 0) {
+    const R e = v[P::BOFF], g = v[P::BOFF + 1];
+    v[P::BOFF] = yd ? g : e;
+    v[P::BOFF + 1] = yd ? e : g;
+  }
+}
+
 constexpr uint32_t WAIT_LIMIT = 1u << 22;   // ~0.1 s of polling per wait at most
 constexpr int ST_ETIMEOUT = 4;
 
@@ -192,7 +255,8 @@ struct StageSmem {
   static constexpr size_t cur = prim + sizeof(R) * 4 * NT * 256;       // [NV][20][20]
   static constexpr size_t fx = cur + sizeof(R) * NV * 400;             // [NV][16][17]
   static constexpr size_t fy = fx + sizeof(R) * NV * 272;              // [NV][17][16]
-  static constexpr size_t total = fy + sizeof(R) * NV * 272;
+  static constexpr size_t halo = fy + sizeof(R) * NV * 272;            // [NT][128] raw halo
+  static constexpr size_t total = halo + sizeof(R) * NT * 128;
 };
 
 // The per-stage macro-kernel. Plane k of the block is processed in three phases
@@ -218,6 +282,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   R* sC = reinterpret_cast<R*>(smem_raw + S::cur);
   R* sFx = reinterpret_cast<R*>(smem_raw + S::fx);
   R* sFy = reinterpret_cast<R*>(smem_raw + S::fy);
+  R* sHalo = reinterpret_cast<R*>(smem_raw + S::halo);
 
   const R* __restrict__ Us = static_cast<const R*>(A.Us);
   const R* __restrict__ Un = static_cast<const R*>(A.Un);
@@ -329,11 +394,32 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     riemann<P, R, 1, FLUX>(pl, pr, f, pp);
   };
 
+  // Halo cell h (0..127) of plane k: x-faces for h < 64, y-faces above; the half of the
+  // CTA with t - 128 (k & 1) in [0, 128) owns plane k's halo. Its raw values are fetched
+  // one plane ahead with cp.async into sHalo[v][h] by the same thread.
+  auto halo_xy = [&](int h, int& x, int& y) {
+    const int side = (h >> 5) & 1, layer = (h >> 4) & 1, rr = h & 15;
+    const int c = side ? NB + layer : layer - 2;
+    if (h < 64) { x = c; y = rr; } else { x = rr; y = c; }
+  };
+  auto prefetch_halo = [&](int k) {
+    const int h = t - 128 * (k & 1);
+    if (h >= 0 && h < 128) {
+      int x, y, vs, nd;
+      halo_xy(h, x, y);
+      const R* a = cell_addr<P, R>(Us, G, src, b, x, y, k, &vs, &nd);
+#pragma unroll
+      for (int v = 0; v < NT; ++v) cp_async_elem(sHalo + v * 128 + h, a + (size_t)v * vs);
+      cp_async_commit();
+    }
+  };
+
   if (t == 0) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) mbar_init(bar + i, 1);
     fence_mbar_init();
   }
+  prefetch_halo(0);
   __syncthreads();
   if (t == 0) {
     for (int p = -2; p <= 1; ++p) issue(p);
@@ -377,12 +463,17 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     {
       const int h = t - 128 * (k & 1);       // halves of the CTA take turns on the halo
       if (h >= 0 && h < 128) {
-        const int side = (h >> 5) & 1, layer = (h >> 4) & 1, rr = h & 15;
-        const int c = side ? NB + layer : layer - 2;
-        int x, y;
-        if (h < 64) { x = c; y = rr; } else { x = rr; y = c; }
+        int x, y, vs, nd;
+        halo_xy(h, x, y);
+        cell_addr<P, R>(Us, G, src, b, x, y, k, &vs, &nd);
+        cp_async_wait_all();
         R u[NT], p[NV], aux[NAW];
-        load_cell<P, R>(Us, G, src, b, x, y, k, u);
+#pragma unroll
+        for (int v = 0; v < NT; ++v) u[v] = sHalo[v * 128 + h];
+        if (nd >= 0) {
+          u[1 + nd] = -u[1 + nd];
+          if (P::BOFF >= 0) u[P::BOFF + nd] = -u[P::BOFF + nd];
+        }
         if constexpr (NA > 0) {
 #pragma unroll
           for (int i = 0; i < NA; ++i) aux[i] = u[NV + i];
@@ -400,6 +491,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       fence_proxy_async();
       issue(k + 3);   // slot (k+1)&3: plane k-1's raw data, read by its update before this barrier
     }
+    if (k + 1 < NB) prefetch_halo(k + 1);   // the other half of the CTA; sHalo is free now
     {
       R f[NV];
       xface(tx, ty, f);
@@ -417,23 +509,33 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
         for (int v = 0; v < NV; ++v) FR[((size_t)slot[2] * NV + v) * 256 + k * 16 + tx] = f[v];
       }
       if (warp == (k & 7)) {      // the 32 block-boundary faces, one warp per plane in turn
+        // lanes 0-15: x-face 16 - 1/2 of row r; lanes 16-31: y-face 16 - 1/2 of column r,
+        // evaluated with the x-face solver on x/y-swapped states (no divergence)
         const int lane = t & 31, r = lane & 15;
-        if (lane < 16) {
-          xface(16, r, f);
+        const bool yd = lane >= 16;
+        const int base = yd ? 16 * 20 + r + 2 : (r + 2) * 20 + 16;
+        const int stp = yd ? 20 : 1;
+        R a[NV], bq[NV], c[NV], d[NV], pl[NV], pr[NV];
 #pragma unroll
-          for (int v = 0; v < NV; ++v) sFx[v * 272 + r * 17 + 16] = f[v];
-          if (FR && slot[1] >= 0) {
+        for (int v = 0; v < NV; ++v) {
+          const R* q = sC + v * 400 + base;
+          a[v] = q[0]; bq[v] = q[stp]; c[v] = q[2 * stp]; d[v] = q[3 * stp];
+        }
+        swap_xy<P, R>(a, yd);
+        swap_xy<P, R>(bq, yd);
+        swap_xy<P, R>(c, yd);
+        swap_xy<P, R>(d, yd);
+        plm<NV, R, LIM>(a, bq, c, d, pl, pr);
+        riemann<P, R, 0, FLUX>(pl, pr, f, pp);
+        swap_xy<P, R>(f, yd);
+        const int fs = yd ? 1 : 0;
+        R* dstp = yd ? sFy + 16 * 16 + r : sFx + r * 17 + 16;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) FR[((size_t)slot[1] * NV + v) * 256 + k * 16 + r] = f[v];
-          }
-        } else {
-          yface(16, r, f);
+        for (int v = 0; v < NV; ++v) dstp[v * 272] = f[v];
+        const int sl = slot[1 + 2 * fs];
+        if (FR && sl >= 0) {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) sFy[v * 272 + 16 * 16 + r] = f[v];
-          if (FR && slot[3] >= 0) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) FR[((size_t)slot[3] * NV + v) * 256 + k * 16 + r] = f[v];
-          }
+          for (int v = 0; v < NV; ++v) FR[((size_t)sl * NV + v) * 256 + k * 16 + r] = f[v];
         }
       }
       zface(k, fzu);
@@ -475,12 +577,10 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
         auxk[0] = R(0);
       }
       if (A.speeds) {
-        double ud[NV], ad[2];
+        R ad[NAW];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) ud[v] = (double)out[v];
-        ad[0] = (double)auxk[0];
-        ad[1] = 0.0;
-        cell_speeds<PT>(ud, ad, pp, dxd, ssum, smax, st);
+        for (int i = 0; i < NAW; ++i) ad[i] = auxk[i];
+        cell_speeds<PT, R>(out, ad, pp, dxd, ssum, smax, st);
       }
     }
   }
