@@ -185,9 +185,8 @@ __global__ void __launch_bounds__(256) speeds_kernel(const R* __restrict__ U,
   constexpr int NV = P::NV, NA = P::NA, NT = NV + NA;
   const int b = blockIdx.x;
   const double dx[3] = {bd[b].dx[0], bd[b].dx[1], bd[b].dx[2]};
-  PhysParams pp;
-  pp.gamma = gamma;
-  pp.ch = 0.0;
+  PhysParamsT<R> pp;
+  pp.set(gamma, 0.0);
   double ssum = 0.0, smax = 0.0;
   int st = 0;
   const R* base = U + (size_t)b * NT * NCELL;
@@ -348,9 +347,8 @@ __global__ void prim2cons_kernel(R* __restrict__ U, const double* __restrict__ p
   constexpr int NV = P::NV, NA = P::NA, NT = NV + NA;
   const int i = blockIdx.x;
   const int b = blocks[i];
-  PhysParams pp;
-  pp.gamma = gamma;
-  pp.ch = 0.0;
+  PhysParamsT<double> pp;
+  pp.set(gamma, 0.0);
   for (int c = threadIdx.x; c < NCELL; c += blockDim.x) {
     double p[NV], u[NV];
 #pragma unroll

@@ -91,7 +91,7 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long* addr, double 
 // precision R (the SRHD primitive recovery inside is FP64 always); the maxima are
 // accumulated in FP64: ssum = max sum_d s_d / dx_d, smax = max_d s_d.
 template <template <typename> class PT, typename R>
-__device__ __forceinline__ void cell_speeds(const R* u, R* aux, const PhysParams& pp,
+__device__ __forceinline__ void cell_speeds(const R* u, R* aux, const PhysParamsT<R>& pp,
                                             const double* dx, double& ssum, double& smax, int& st) {
   using P = PT<R>;
   R p[P::NV];
@@ -303,9 +303,8 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     slot[f] = bd.slot[f];
   }
   const double dt = A.dtch[0];
-  PhysParams pp;
-  pp.gamma = A.gamma;
-  pp.ch = A.dtch[1];
+  PhysParamsT<R> pp;
+  pp.set(A.gamma, A.dtch[1]);
   const R idx = R(1.0 / bd.dx[0]), idy = R(1.0 / bd.dx[1]), idz = R(1.0 / bd.dx[2]);
   const R rdt = R(dt);
   const R ra = R(A.a), rb = R(A.b);
@@ -449,8 +448,9 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   double glm_f = 1.0;
   if (A.glm_post) {
     const double dxm = fmin(fmin(bd.dx[0], bd.dx[1]), bd.dx[2]);
-    glm_f = exp(-0.5 * dt * pp.ch * A.glm_alpha / dxm);
+    glm_f = exp(-0.5 * dt * A.dtch[1] * A.glm_alpha / dxm);
   }
+  const R glm_fr = R(glm_f);
 
   for (int k = 0; k < NB; ++k) {
     // ---- phase 1
@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
         out[v] = val;
         fzd[v] = fzu[v];
       }
-      if (P::BOFF >= 0 && A.glm_post) out[NV - 1] = R((double)out[NV - 1] * glm_f);
+      if (P::BOFF >= 0 && A.glm_post) out[NV - 1] = out[NV - 1] * glm_fr;
 #pragma unroll
       for (int v = 0; v < NV; ++v) Uo[base + (size_t)v * NCELL] = out[v];
       R auxk[NAW];

@@ -20,9 +20,23 @@ enum : int { LIM_MINMOD = 0, LIM_VANLEER = 1 };
 enum : int { FLUX_TVDLF = 0, FLUX_HLL = 1 };
 enum : int { ST_ENOCONV = 1, ST_EUNPHYS = 2 };
 
-struct PhysParams {
-  double gamma;
-  double ch;      // GLM cleaning speed (MHD only): c_max of U^n
+// Equation parameters in the stencil precision R, derived once per CTA (the FP64 copy of
+// gamma serves the SRHD primitive recovery, which always runs in FP64).
+template <typename R>
+struct PhysParamsT {
+  double gamma_d;
+  R gamma, g1, ig1, gg1;   // gamma, gamma - 1, 1 / (gamma - 1), gamma / (gamma - 1)
+  R ch, ich, ch2;          // GLM cleaning speed c_h = c_max of U^n (MHD), 1 / c_h, c_h^2
+  __host__ __device__ void set(double gamma_, double ch_) {
+    gamma_d = gamma_;
+    gamma = R(gamma_);
+    g1 = R(gamma_ - 1.0);
+    ig1 = R(1.0 / (gamma_ - 1.0));
+    gg1 = R(gamma_ / (gamma_ - 1.0));
+    ch = R(ch_);
+    ich = ch_ > 0.0 ? R(1.0 / ch_) : R(0);
+    ch2 = R(ch_ * ch_);
+  }
 };
 
 template <typename R>
@@ -52,9 +66,9 @@ struct HdPhys {
   static constexpr int NA = 0;
   static constexpr int BOFF = -1;  // no magnetic field
 
-  __device__ static __forceinline__ void cons2prim(const R* u, R* p, R*, const PhysParams& pp,
+  __device__ static __forceinline__ void cons2prim(const R* u, R* p, R*, const PhysParamsT<R>& pp,
                                                    int& st) {
-    const R g1 = R(pp.gamma - 1.0);
+    const R g1 = pp.g1;
     const R rho = u[0];
     const R vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
     p[0] = rho;
@@ -65,8 +79,8 @@ struct HdPhys {
     if (!(rho > R(0)) || !(p[4] > R(0))) st |= ST_EUNPHYS;
   }
 
-  __device__ static __forceinline__ void prim2cons(const R* p, R* u, const PhysParams& pp) {
-    const R ig1 = R(1.0 / (pp.gamma - 1.0));
+  __device__ static __forceinline__ void prim2cons(const R* p, R* u, const PhysParamsT<R>& pp) {
+    const R ig1 = pp.ig1;
     u[0] = p[0];
     u[1] = p[0] * p[1];
     u[2] = p[0] * p[2];
@@ -75,7 +89,7 @@ struct HdPhys {
   }
 
   template <int D>
-  __device__ static __forceinline__ void flux(const R* p, const R* u, R* f, const PhysParams&) {
+  __device__ static __forceinline__ void flux(const R* p, const R* u, R* f, const PhysParamsT<R>&) {
     const R vd = p[1 + D];
     f[0] = u[0] * vd;
     f[1] = u[1] * vd;
@@ -86,14 +100,14 @@ struct HdPhys {
   }
 
   template <int D>
-  __device__ static __forceinline__ void lambdas(const R* p, R& lm, R& lp, const PhysParams& pp) {
-    const R c = rsqrt_(R(pp.gamma) * p[4] / p[0]);
+  __device__ static __forceinline__ void lambdas(const R* p, R& lm, R& lp, const PhysParamsT<R>& pp) {
+    const R c = rsqrt_(pp.gamma * p[4] / p[0]);
     lm = p[1 + D] - c;
     lp = p[1 + D] + c;
   }
 
   template <int D>
-  __device__ static __forceinline__ void interface(R*, R*, const PhysParams&) {}
+  __device__ static __forceinline__ void interface(R*, R*, const PhysParamsT<R>&) {}
 };
 
 // ------------------------------------------------------------------------------ MHD + GLM
@@ -103,9 +117,9 @@ struct MhdPhys {
   static constexpr int NA = 0;
   static constexpr int BOFF = 5;   // B_x is variable 5
 
-  __device__ static __forceinline__ void cons2prim(const R* u, R* p, R*, const PhysParams& pp,
+  __device__ static __forceinline__ void cons2prim(const R* u, R* p, R*, const PhysParamsT<R>& pp,
                                                    int& st) {
-    const R g1 = R(pp.gamma - 1.0);
+    const R g1 = pp.g1;
     const R rho = u[0];
     const R vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
     const R b2 = u[5] * u[5] + u[6] * u[6] + u[7] * u[7];
@@ -121,8 +135,8 @@ struct MhdPhys {
     if (!(rho > R(0)) || !(p[4] > R(0))) st |= ST_EUNPHYS;
   }
 
-  __device__ static __forceinline__ void prim2cons(const R* p, R* u, const PhysParams& pp) {
-    const R ig1 = R(1.0 / (pp.gamma - 1.0));
+  __device__ static __forceinline__ void prim2cons(const R* p, R* u, const PhysParamsT<R>& pp) {
+    const R ig1 = pp.ig1;
     u[0] = p[0];
     u[1] = p[0] * p[1];
     u[2] = p[0] * p[2];
@@ -136,7 +150,7 @@ struct MhdPhys {
   }
 
   template <int D>
-  __device__ static __forceinline__ void flux(const R* p, const R* u, R* f, const PhysParams& pp) {
+  __device__ static __forceinline__ void flux(const R* p, const R* u, R* f, const PhysParamsT<R>& pp) {
     const R vd = p[1 + D], bd = p[5 + D];
     const R ptot = p[4] + R(0.5) * (p[5] * p[5] + p[6] * p[6] + p[7] * p[7]);
     const R vb = p[1] * p[5] + p[2] * p[6] + p[3] * p[7];
@@ -150,14 +164,13 @@ struct MhdPhys {
     f[6] = vd * p[6] - bd * p[2];
     f[7] = vd * p[7] - bd * p[3];
     f[5 + D] = p[8];
-    const R ch = R(pp.ch);
-    f[8] = ch * ch * bd;
+    f[8] = pp.ch2 * bd;
   }
 
   template <int D>
-  __device__ static __forceinline__ void lambdas(const R* p, R& lm, R& lp, const PhysParams& pp) {
+  __device__ static __forceinline__ void lambdas(const R* p, R& lm, R& lp, const PhysParamsT<R>& pp) {
     const R ir = R(1) / p[0];
-    const R a2 = R(pp.gamma) * p[4] * ir;
+    const R a2 = pp.gamma * p[4] * ir;
     const R b2 = (p[5] * p[5] + p[6] * p[6] + p[7] * p[7]) * ir;
     const R bd2 = p[5 + D] * p[5 + D] * ir;
     const R s = a2 + b2;
@@ -171,10 +184,10 @@ struct MhdPhys {
   // both face states carry B_d* and psi*, so the face flux of B_d is psi* and of psi is
   // c_h^2 B_d*.
   template <int D>
-  __device__ static __forceinline__ void interface(R* pl, R* pr, const PhysParams& pp) {
-    const R ch = R(pp.ch);
+  __device__ static __forceinline__ void interface(R* pl, R* pr, const PhysParamsT<R>& pp) {
+    const R ch = pp.ch;
     const R bl = pl[5 + D], br = pr[5 + D], sl = pl[8], sr = pr[8];
-    const R bs = R(0.5) * (bl + br) - R(0.5) * (sr - sl) / ch;
+    const R bs = R(0.5) * (bl + br) - R(0.5) * (sr - sl) * pp.ich;
     const R ss = R(0.5) * (sl + sr) - R(0.5) * ch * (br - bl);
     pl[5 + D] = bs;
     pr[5 + D] = bs;
@@ -194,9 +207,9 @@ struct SrhdPhys {
   // [E, gamma E]; starts from the stored xi when it lies strictly inside the bracket,
   // else from the midpoint; a step leaving the closed bracket is replaced by bisection;
   // stops when |dxi| <= 1e-14 xi; at most 50 iterations. FP64 throughout.
-  __device__ static __forceinline__ void cons2prim(const R* u, R* p, R* aux, const PhysParams& pp,
+  __device__ static __forceinline__ void cons2prim(const R* u, R* p, R* aux, const PhysParamsT<R>& pp,
                                                    int& st) {
-    const double g = pp.gamma;
+    const double g = pp.gamma_d;
     const double gm = (g - 1.0) / g;
     const double D = (double)u[0];
     const double mx = (double)u[1], my = (double)u[2], mz = (double)u[3];
@@ -238,10 +251,9 @@ struct SrhdPhys {
     if (!(rho > 0.0) || !(pr > 0.0)) st |= ST_EUNPHYS;
   }
 
-  __device__ static __forceinline__ void prim2cons(const R* p, R* u, const PhysParams& pp) {
-    const R g = R(pp.gamma);
+  __device__ static __forceinline__ void prim2cons(const R* p, R* u, const PhysParamsT<R>& pp) {
     const R lor = rsqrt_(R(1) + p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
-    const R h = R(1) + g / (g - R(1)) * p[4] / p[0];
+    const R h = R(1) + pp.gg1 * p[4] / p[0];
     const R lr = lor * p[0];
     const R lrh = lr * h;
     u[0] = lr;
@@ -252,7 +264,7 @@ struct SrhdPhys {
   }
 
   template <int D>
-  __device__ static __forceinline__ void flux(const R* p, const R* u, R* f, const PhysParams&) {
+  __device__ static __forceinline__ void flux(const R* p, const R* u, R* f, const PhysParamsT<R>&) {
     const R lor = rsqrt_(R(1) + p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
     const R vd = p[1 + D] / lor;
     f[0] = u[0] * vd;
@@ -264,13 +276,12 @@ struct SrhdPhys {
   }
 
   template <int D>
-  __device__ static __forceinline__ void lambdas(const R* p, R& lm, R& lp, const PhysParams& pp) {
-    const R g = R(pp.gamma);
+  __device__ static __forceinline__ void lambdas(const R* p, R& lm, R& lp, const PhysParamsT<R>& pp) {
     const R lor2 = R(1) + p[1] * p[1] + p[2] * p[2] + p[3] * p[3];
     const R v2 = R(1) - R(1) / lor2;
     const R vd = p[1 + D] / rsqrt_(lor2);
-    const R h = R(1) + g / (g - R(1)) * p[4] / p[0];
-    const R cs2 = g * p[4] / (p[0] * h);
+    const R h = R(1) + pp.gg1 * p[4] / p[0];
+    const R cs2 = pp.gamma * p[4] / (p[0] * h);
     const R cs = rsqrt_(cs2);
     const R den = R(1) - v2 * cs2;
     const R root = cs * rsqrt_(rmax((R(1) - v2) * (R(1) - v2 * cs2 - vd * vd * (R(1) - cs2)), R(0)));
@@ -279,12 +290,12 @@ struct SrhdPhys {
   }
 
   template <int D>
-  __device__ static __forceinline__ void interface(R*, R*, const PhysParams&) {}
+  __device__ static __forceinline__ void interface(R*, R*, const PhysParamsT<R>&) {}
 };
 
 // Riemann flux at a face from reconstructed primitive states (modified in place).
 template <class P, typename R, int D, int FLUX>
-__device__ __forceinline__ void riemann(R* pl, R* pr, R* f, const PhysParams& pp) {
+__device__ __forceinline__ void riemann(R* pl, R* pr, R* f, const PhysParamsT<R>& pp) {
   constexpr int NV = P::NV;
   P::template interface<D>(pl, pr, pp);
   R ul[NV], ur[NV], fl[NV], fr[NV];
