@@ -53,7 +53,7 @@ def peaks():
 class Clocks:
     """nvidia-smi sampling during the timed region (SM clock, throttle reasons)."""
 
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
@@ -77,26 +77,38 @@ class Clocks:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
+        """Median SM clock and active throttle reasons of the samples taken between the
+        host times t0 and t1 (the timed region); the nearest later sample if none fell in."""
+        import datetime
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        samples = []
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 7:
+            if len(parts) < 8:
                 continue
             try:
-                sm.append(float(parts[0]))
-                smax.append(float(parts[1]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                samples.append((ts, float(parts[1]), float(parts[2]), parts[4:8]))
             except ValueError:
                 continue
-            for n, v in zip(names, parts[3:7]):
+        inside = [x for x in samples if t0 is None or (t0 <= x[0] <= t1)]
+        if not inside and samples and t0 is not None:
+            later = [x for x in samples if x[0] >= t0]
+            inside = later[:1] if later else samples[-1:]
+        sm = [x[1] for x in inside]
+        smax = [x[2] for x in inside]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for x in inside:
+            for n, v in zip(names, x[3]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None,
@@ -123,23 +135,26 @@ def run_gpu(real_bytes, steps, warmup, rank, world, dev):
     stream = torch.cuda.current_stream()
     m = agile.Mesh(agile.make_config(real_bytes=real_bytes, **sp), stream=stream)
     m.set_state(W.orszag_tang_3d(N_SIDE))
+    clocks = Clocks(dev)
+    clocks.start()          # started early so that it samples throughout the timed region
     for _ in range(warmup):
         m.step(0.0)
     m.sync()
+    time.sleep(0.3)
     # ---- device-timed region: inputs resident in HBM
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     m.set_kernel_timing(True)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
-    clocks = Clocks(dev)
-    clocks.start()
+    t_start = time.time()
     ev[0].record(stream)
     for i in range(steps):
         m.step(0.0)
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
-    clk = clocks.stop()
+    t_end = time.time()
+    clk = clocks.stop(t_start, t_end)
     if world > 1:
         torch.distributed.barrier()
     per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
@@ -231,7 +246,7 @@ def reference_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-fp64", action="store_true")

@@ -216,6 +216,14 @@ agile_status agile_set_kernel_timing(agile_mesh* mesh, int enable);
 agile_status agile_kernel_timing(agile_mesh* mesh, double* stage_ms, long long* stage_launches,
                                  long long* total_launches);
 
+/* Failure-detection check of the bounded device waits: launches one kernel that waits on
+ * an mbarrier nothing arrives on, polling it at most `limit` times (1 .. 2^24), then returns
+ * AGILE_ETIMEOUT with *timed_out = 1 (AGILE_OK and 0 would mean the barrier completed).
+ * The stage kernel bounds its TMA-plane waits the same way (about 2^22 polls) and reports
+ * AGILE_ETIMEOUT at the next synchronising call instead of spinning forever; the context
+ * stays usable. Synchronises `stream` (a cudaStream_t, NULL for the default stream). */
+agile_status agile_selftest_bounded_wait(void* stream, unsigned int limit, int* timed_out);
+
 /* Message of the last failed call on this mesh (static storage owned by the mesh). */
 const char* agile_last_error(const agile_mesh* mesh);
 

@@ -31,7 +31,7 @@ EXPORTS = ["agile_mesh_create", "agile_mesh_destroy", "agile_set_state", "agile_
            "agile_get_state", "agile_get_aux", "agile_conserved_sums",
            "agile_conserved_sums_noalloc", "agile_estimate",
            "agile_get_halo", "agile_sync", "agile_set_kernel_timing", "agile_kernel_timing",
-           "agile_last_error", "agile_version"]
+           "agile_selftest_bounded_wait", "agile_last_error", "agile_version"]
 
 
 class agile_config(C.Structure):
@@ -93,6 +93,7 @@ def load(path: str = LIB_PATH):
         "agile_sync": (C.c_int, [P]),
         "agile_set_kernel_timing": (C.c_int, [P, C.c_int]),
         "agile_kernel_timing": (C.c_int, [P, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+        "agile_selftest_bounded_wait": (C.c_int, [P, C.c_uint, ip]),
         "agile_last_error": (C.c_char_p, [P]),
         "agile_version": (C.c_char_p, []),
     }

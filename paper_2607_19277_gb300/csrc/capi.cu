@@ -114,6 +114,7 @@ agile_status check_status(agile_mesh* m) {
   CK(m, cudaMemcpy(&st, m->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st) {
     CK(m, cudaMemset(m->d_status, 0, sizeof(int)));
+    if (st & ST_ETIMEOUT) return fail(m, AGILE_ETIMEOUT, "a bounded wait for a TMA plane gave up");
     if (st & ST_ENOCONV) return fail(m, AGILE_ENOCONV, "primitive recovery did not converge");
     return fail(m, AGILE_EUNPHYS, "non-positive density or pressure on the device");
   }
@@ -287,11 +288,40 @@ agile_status do_regrid(agile_mesh* m, const std::vector<int>& flags, int init, i
 
 }  // namespace
 
+namespace {
+// Bounded-wait check: one thread initialises an mbarrier that expects one arrival, nobody
+// arrives, and the thread polls it at most `limit` times (the same bounded wait the stage
+// kernel uses for its TMA planes), then records whether the wait ran out.
+__global__ void selftest_wait_kernel(uint32_t limit, int* out) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    out[0] = mbar_wait(&bar, 0, limit) ? 0 : 1;
+  }
+}
+}  // namespace
+
 extern "C" {
 
 const char* agile_version(void) { return "agile-gb300 1.0 (sm_103a)"; }
 
 const char* agile_last_error(const agile_mesh* m) { return m ? m->err.c_str() : "null mesh"; }
+
+agile_status agile_selftest_bounded_wait(void* stream, unsigned int limit, int* timed_out) {
+  if (!timed_out || limit == 0 || limit > (1u << 24)) return AGILE_EINVAL;
+  int* d = nullptr;
+  if (cudaMallocAsync(&d, sizeof(int), (cudaStream_t)stream) != cudaSuccess) return AGILE_ENOMEM;
+  selftest_wait_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(limit, d);
+  int h = -1;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  cudaFreeAsync(d, (cudaStream_t)stream);
+  if (e != cudaSuccess) return AGILE_ECUDA;
+  *timed_out = h;
+  return h ? AGILE_ETIMEOUT : AGILE_OK;
+}
 
 agile_status agile_mesh_create(const agile_config* cfg, const agile_allocator* alloc, void* stream,
                                agile_mesh** out) {

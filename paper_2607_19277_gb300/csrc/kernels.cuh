@@ -308,6 +308,8 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   const R idx = R(1.0 / bd.dx[0]), idy = R(1.0 / bd.dx[1]), idz = R(1.0 / bd.dx[2]);
   const R rdt = R(dt);
   const R ra = R(A.a), rb = R(A.b);
+  const bool combine = A.a != 0.0;
+  const bool glm_post = A.glm_post != 0;
   int st = 0;
   constexpr uint32_t PLANE_BYTES = (uint32_t)(sizeof(R) * NT * 256);
 
@@ -558,11 +560,11 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
         const R lz = (fzu[v] - fzd[v]) * idz;
         const R L = -((lx + ly) + lz);
         R val = raw[v * 256] + rdt * L;
-        if (A.a != 0.0) val = ra * Un[base + (size_t)v * NCELL] + rb * val;
+        if (combine) val = ra * Un[base + (size_t)v * NCELL] + rb * val;
         out[v] = val;
         fzd[v] = fzu[v];
       }
-      if (P::BOFF >= 0 && A.glm_post) out[NV - 1] = out[NV - 1] * glm_fr;
+      if (P::BOFF >= 0 && glm_post) out[NV - 1] = out[NV - 1] * glm_fr;
 #pragma unroll
       for (int v = 0; v < NV; ++v) Uo[base + (size_t)v * NCELL] = out[v];
       R auxk[NAW];

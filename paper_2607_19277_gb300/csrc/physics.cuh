@@ -39,23 +39,32 @@ struct PhysParamsT {
   }
 };
 
-template <typename R>
-__device__ __forceinline__ R rabs(R a) { return a < R(0) ? -a : a; }
-template <typename R>
-__device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
-template <typename R>
-__device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
+__device__ __forceinline__ float rabs(float a) { return fabsf(a); }
+__device__ __forceinline__ double rabs(double a) { return fabs(a); }
+__device__ __forceinline__ float rmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double rmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float rmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double rmax(double a, double b) { return fmax(a, b); }
 __device__ __forceinline__ float rsqrt_(float a) { return sqrtf(a); }
 __device__ __forceinline__ double rsqrt_(double a) { return sqrt(a); }
+__device__ __forceinline__ float rsign(float a) { return copysignf(1.0f, a); }
+__device__ __forceinline__ double rsign(double a) { return copysign(1.0, a); }
+template <typename R> __device__ __forceinline__ R rtiny();
+template <> __device__ __forceinline__ float rtiny<float>() { return 1e-30f; }
+template <> __device__ __forceinline__ double rtiny<double>() { return 1e-300; }
 
-// Slope limiters on the two one-sided differences (van Leer 1974; minmod).
+// Slope limiters on the two one-sided differences, written without branches:
+//   minmod(a, b) = (sgn a + sgn b)/2 * min(|a|, |b|)  (0 unless a, b share a sign);
+//   van Leer (1974): 2 max(ab, 0) / (a + b), the denominator nudged by a tiny value of its
+//   own sign so that a = -b gives 0 instead of 0/0 (below half an ulp otherwise).
 template <typename R, int LIM>
 __device__ __forceinline__ R limit(R a, R b) {
-  const bool same = (a > R(0) && b > R(0)) || (a < R(0) && b < R(0));
   if (LIM == LIM_MINMOD) {
-    return same ? (a > R(0) ? rmin(a, b) : rmax(a, b)) : R(0);
+    return R(0.5) * (rsign(a) + rsign(b)) * rmin(rabs(a), rabs(b));
   } else {
-    return same ? (R(2) * a * b) / (a + b) : R(0);
+    const R ab = a * b;
+    const R den = a + b;
+    return (R(2) * rmax(ab, R(0))) / (den + rsign(den) * rtiny<R>());
   }
 }
 
@@ -76,7 +85,7 @@ struct HdPhys {
     p[2] = vy;
     p[3] = vz;
     p[4] = g1 * (u[4] - R(0.5) * rho * (vx * vx + vy * vy + vz * vz));
-    if (!(rho > R(0)) || !(p[4] > R(0))) st |= ST_EUNPHYS;
+    st |= (!(rho > R(0)) | !(p[4] > R(0))) ? ST_EUNPHYS : 0;
   }
 
   __device__ static __forceinline__ void prim2cons(const R* p, R* u, const PhysParamsT<R>& pp) {
@@ -132,7 +141,7 @@ struct MhdPhys {
     p[6] = u[6];
     p[7] = u[7];
     p[8] = u[8];
-    if (!(rho > R(0)) || !(p[4] > R(0))) st |= ST_EUNPHYS;
+    st |= (!(rho > R(0)) | !(p[4] > R(0))) ? ST_EUNPHYS : 0;
   }
 
   __device__ static __forceinline__ void prim2cons(const R* p, R* u, const PhysParamsT<R>& pp) {

@@ -53,3 +53,21 @@ def test_regrid_flags_length_checked_and_mesh_reusable():
     assert m.regrid_flags([1, 0]) == (1, 0)
     assert m.layout()[0] == 9
     m.close()
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """A device wait on a barrier that nothing completes gives up after its poll limit and
+    reports AGILE_ETIMEOUT; the same process keeps working afterwards."""
+    import ctypes as C
+    lib = agile.load()
+    flag = C.c_int(-1)
+    st = lib.agile_selftest_bounded_wait(None, 4096, C.byref(flag))
+    assert st == 7 and flag.value == 1
+    spec = dict(physics="hd", base_blocks=(1, 1, 1))
+    m = gpu_mesh(spec)
+    cons = np.ones((1, 5, 16, 16, 16))
+    cons[:, 1:4] = 0.0
+    m.set_state_blocks(cons)
+    m.step(m.cfl_dt())
+    m.sync()
+    m.close()
