@@ -116,6 +116,22 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def replica_throughput(zones_per_rank, stages, steps, local_ms, world):
+    """Whole-job zone-updates/s of `world` independent replicas (weak scaling): every rank
+    advanced zones_per_rank cells by stages * steps substeps; the job time is the slowest
+    rank's (max over ranks through the default process group when world > 1). Returns
+    (zone-updates/s, max time in ms)."""
+    t_ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    return zones_per_rank * stages * steps * world / (t_ms / 1e3), t_ms
+
+
 def algorithmic_bytes_per_zone(nvar, w, rk):
     """Compulsory bytes per zone-update, averaged over the stages of one step: read U_s and
     write U_out every stage, read U^n in the stages that combine with it."""
@@ -246,7 +262,7 @@ def reference_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
@@ -270,26 +286,18 @@ def main():
         torch.distributed.barrier()
     args.warmup = max(args.warmup, 3)
     r32 = run_gpu(4, args.steps, args.warmup, rank, world, local)
-    r64 = None if args.no_fp64 else run_gpu(8, max(2, args.steps // 2), args.warmup, rank, world, local)
-
-    def reduce_max(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+    steps64 = max(2, min(args.steps // 4, 20))
+    r64 = None if args.no_fp64 else run_gpu(8, steps64, args.warmup, rank, world, local)
 
     hbm, peak_kind = peaks()
 
     def summarize(r, w, steps):
-        t_ms = reduce_max(r["total_ms"])
+        zu, t_ms = replica_throughput(r["zones"], 3, steps, r["total_ms"], world)
         ms_step = t_ms / steps
-        zu = r["zones"] * 3 * steps * world / (t_ms / 1e3)
         bpz = algorithmic_bytes_per_zone(r["nvar"], w, 3)
         launch_ms = r["stage_ms"] / max(1, r["stage_launches"])
         achieved = bpz * r["zones"] / (launch_ms / 1e3) / 1e9
-        e2e_s = reduce_max(r["e2e_s"])
-        e2e = r["zones"] * 3 * steps * world / e2e_s
+        e2e, _ = replica_throughput(r["zones"], 3, steps, 1e3 * r["e2e_s"], world)
         ps = sorted(r["per_step"])
         return dict(value=zu, ms_per_step=ms_step, bytes_per_zone=bpz, launch_ms=launch_ms,
                     achieved=achieved, e2e=e2e, p50=ps[len(ps) // 2],
@@ -298,7 +306,7 @@ def main():
                     launches=r["total_launches"], clocks=r["clocks"])
 
     s32 = summarize(r32, 4, args.steps)
-    s64 = summarize(r64, 8, max(2, args.steps // 2)) if r64 else None
+    s64 = summarize(r64, 8, steps64) if r64 else None
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()

@@ -141,6 +141,12 @@ agile_status agile_set_state_blocks(agile_mesh* mesh, const double* cons, size_t
  * Synchronises the stream. */
 agile_status agile_cfl_dt(agile_mesh* mesh, double* dt_out);
 
+/* The two maxima behind agile_cfl_dt for the current state: sum_over_dx = max over leaf
+ * cells of sum_d s_d / dx_d (dt = cfl / sum_over_dx) and cmax = max over cells and d of
+ * s_d, the GLM cleaning speed c_h of the next step (Section 2.3.3). Either may be NULL.
+ * Synchronises. */
+agile_status agile_max_speeds(agile_mesh* mesh, double* sum_over_dx, double* cmax);
+
 /* One full SSPRK step of all leaves with time step dt. dt <= 0 takes the CFL step of the
  * current state from device memory without a host round trip. For MHD the GLM source
  * psi *= exp(-dt/2 c_h alpha / min dx) is applied before and after the step (Strang

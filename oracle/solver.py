@@ -540,12 +540,16 @@ class Solver:
             dxm = min(self.dx(key[0]))
             blk[(8,) + (slice(G, G + NB),) * 3] *= math.exp(-0.5 * dt * ch * self.cfg.glm_alpha / dxm)
 
-    def step(self, dt=None):
-        """One full SSPRK step of every leaf (ghost fill, update and fix-up per stage)."""
+    def step(self, dt=None, ch=None):
+        """One full SSPRK step of every leaf (ghost fill, update and fix-up per stage).
+
+        dt and the GLM speed c_h default to the CFL step and c_max of this mesh's state;
+        a caller evolving a sub-domain of a larger mesh passes the global values."""
         cmax, smax = self.signal_speeds()
         if dt is None or dt <= 0:
             dt = self.cfg.cfl / smax
-        ch = cmax
+        if ch is None:
+            ch = cmax
         if self.phys.glm:
             self._glm_decay(dt, ch)
         inner = (slice(G, G + NB),) * 3

@@ -27,7 +27,7 @@ STATUS = {0: "AGILE_OK", 1: "AGILE_EINVAL", 2: "AGILE_ENOMEM", 3: "AGILE_EBUDGET
 
 # Symbols declared in include/agile.h (checked by the CPU test suite).
 EXPORTS = ["agile_mesh_create", "agile_mesh_destroy", "agile_set_state", "agile_set_state_blocks",
-           "agile_cfl_dt", "agile_step", "agile_regrid", "agile_regrid_flags", "agile_get_layout",
+           "agile_cfl_dt", "agile_max_speeds", "agile_step", "agile_regrid", "agile_regrid_flags", "agile_get_layout",
            "agile_get_state", "agile_get_aux", "agile_conserved_sums",
            "agile_conserved_sums_noalloc", "agile_estimate",
            "agile_get_halo", "agile_sync", "agile_set_kernel_timing", "agile_kernel_timing",
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
         "agile_set_state": (C.c_int, [P, IC_FN, P]),
         "agile_set_state_blocks": (C.c_int, [P, dp, C.c_size_t]),
         "agile_cfl_dt": (C.c_int, [P, dp]),
+        "agile_max_speeds": (C.c_int, [P, dp, dp]),
         "agile_step": (C.c_int, [P, C.c_double]),
         "agile_regrid": (C.c_int, [P, C.c_int, ip, ip]),
         "agile_regrid_flags": (C.c_int, [P, ip, C.c_int, ip, ip]),
@@ -243,6 +244,12 @@ class Mesh:
         dt = C.c_double()
         self._ck(self.lib.agile_cfl_dt(self.ptr, C.byref(dt)))
         return dt.value
+
+    def max_speeds(self):
+        """(max_cells sum_d s_d / dx_d, c_max) of the current state."""
+        a, b = C.c_double(), C.c_double()
+        self._ck(self.lib.agile_max_speeds(self.ptr, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def step(self, dt: float = 0.0):
         self._ck(self.lib.agile_step(self.ptr, float(dt)))

@@ -445,6 +445,19 @@ agile_status agile_cfl_dt(agile_mesh* m, double* dt_out) {
   return AGILE_OK;
 }
 
+agile_status agile_max_speeds(agile_mesh* m, double* sum_over_dx, double* cmax) {
+  if (!m) return AGILE_EINVAL;
+  agile_status s = ensure_speeds(m);
+  if (s) return s;
+  unsigned long long h[2];
+  CK(m, cudaMemcpyAsync(h, m->d_speeds, sizeof(h), cudaMemcpyDeviceToHost, m->stream));
+  s = check_status(m);
+  if (s) return s;
+  if (sum_over_dx) memcpy(sum_over_dx, &h[0], sizeof(double));
+  if (cmax) memcpy(cmax, &h[1], sizeof(double));
+  return AGILE_OK;
+}
+
 agile_status agile_step(agile_mesh* m, double dt) {
   if (!m) return AGILE_EINVAL;
   agile_status s = ensure_speeds(m);
