@@ -27,6 +27,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -209,6 +211,77 @@ def run_gpu(real_bytes, steps, warmup, rank, world, dev):
                 e2e_s=e2e_s, state_bytes=state_bytes, nvar=9)
 
 
+BATCH_SIDES = (32, 48, 64, 80, 96, 112, 128)
+
+
+def batch_workload(nsolve=256, seed=20260004):
+    """Seeded batch of SRHD solves: side from {32, ..., 128} per solve, 1-3 shells each."""
+    from paper_2607_19277_gb300 import workloads as W
+    u = W.uniform01(seed, np.arange(nsolve))
+    sides = [BATCH_SIDES[min(len(BATCH_SIDES) - 1, int(x * len(BATCH_SIDES)))] for x in u]
+    ics = [W.srhd_shells(seed + 1 + i, sides[i], lorentz_max=5.0, p_amb=0.1) for i in range(nsolve)]
+    return sides, ics
+
+
+def run_batched(steps, warmup, nsolve=256, fp64_solves=8):
+    """Batched FP32 SRHD solves (one launch per RK stage over all of them, CUDA-graph
+    steps) against the plain FP64 per-solve path on the first fp64_solves solves."""
+    import torch
+    from paper_2607_19277_gb300 import agile
+    sides, ics = batch_workload(nsolve)
+
+    def cfg(side, rb):
+        return agile.make_config(physics="srhd", limiter="minmod", flux="tvdlf", rk=2, gamma=4.0 / 3.0,
+                                 cfl=0.4, real_bytes=rb, base_blocks=(side // 16,) * 3)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = agile.Batch([cfg(sd, 4) for sd in sides], stream=stream)
+        for i in range(nsolve):
+            b.set_state(i, ics[i])
+        for _ in range(warmup):
+            b.step()
+        b.sync()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record(stream)
+        for i in range(steps):
+            b.step()
+            ev[i + 1].record(stream)
+        stream.synchronize()
+        per = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(steps))
+        total = ev[0].elapsed_time(ev[steps])
+        b.sync()
+        launches = b.launches()
+        b.close()
+    zones = sum(sd ** 3 for sd in sides)
+    out = {"value": zones * 2 * steps / (total / 1e3), "unit": UNIT, "solves": nsolve,
+           "cells": zones, "ms_per_step": total / steps, "step_latency_ms": {
+               "p50": per[len(per) // 2], "p99": per[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)]},
+           "dtype": "f32 stencil, f64 con2prim", "graph_launches_per_step": "1 graph (set_dt + 2 stages)",
+           "kernel_launches_in_timed_region": launches}
+    # plain FP64 per-solve path: each solve its own mesh, solved one after the other
+    z64 = 0
+    t64 = 0.0
+    st64 = max(2, steps // 4)
+    for i in range(fp64_solves):
+        m = agile.Mesh(cfg(sides[i], 8))
+        m.set_state(ics[i])
+        m.step(0.0)
+        m.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(st64):
+            m.step(0.0)
+        e1.record()
+        torch.cuda.synchronize()
+        t64 += e0.elapsed_time(e1)
+        z64 += sides[i] ** 3 * 2 * st64
+        m.close()
+    out["fp64_plain_per_solve"] = {"value": z64 / (t64 / 1e3), "unit": UNIT, "solves": fp64_solves,
+                                   "steps": st64}
+    return out
+
+
 def cpu_baseline(seconds_budget=20.0):
     """The FP64 oracle as it stands on a bounded sample: the same physics and scheme on a
     32^3 periodic box (8 blocks) of the same initial-condition family, whole SSPRK3 steps."""
@@ -267,6 +340,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -342,6 +416,9 @@ def main():
                                      "bytes_per_zone_update": s64["bytes_per_zone"]},
                         "e2e": s64["e2e"], "step_latency_ms": {"p50": s64["p50"], "p99": s64["p99"]},
                         "gpu_launches": s64["launches"], "clocks": s64["clocks"]}
+    if not args.no_batched:
+        line["batched"] = run_batched(max(4, min(args.steps // 20, 10)), args.warmup)
+        line["batched"]["workload"] = "256 SRHD solves 32^3-128^3 (16^3 blocks), seeded shells Gamma <= 5, TVDLF minmod SSPRK2"
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

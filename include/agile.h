@@ -222,6 +222,51 @@ agile_status agile_set_kernel_timing(agile_mesh* mesh, int enable);
 agile_status agile_kernel_timing(agile_mesh* mesh, double* stage_ms, long long* stage_launches,
                                  long long* total_launches);
 
+/* ---------------------------------------------------------------------------------------
+ * Batched independent solves. Several uniform-grid problems that share one scheme
+ * (physics, limiter, flux, rk, real_bytes, gamma, cfl, glm_alpha) but differ in size, box
+ * and boundaries advance together: one pool holds the blocks of all solves, every RK stage
+ * is one persistent launch of the update kernel over all of them (each block with its
+ * solve's CFL dt and GLM speed), and from the second step on a whole step is replayed from
+ * a captured CUDA graph (dt stays on the device). Each solve's result is the same as when
+ * it runs alone as an agile_mesh (same kernels, same per-block arithmetic).
+ * The paper runs one problem per job; batching is this library's serving form of the
+ * same per-block update (macro-kernel of Section 2.1.3, time loop of Fig. 2 per solve).
+ * --------------------------------------------------------------------------------------- */
+typedef struct agile_batch agile_batch;
+
+/* Create nsolve solves from cfgs[nsolve] (max_level must be 1). alloc as for meshes;
+ * cuda_stream NULL makes the batch create its own non-blocking stream (graphs cannot be
+ * captured on the legacy default stream). Errors: AGILE_EINVAL, AGILE_ENOMEM, AGILE_ECUDA. */
+agile_status agile_batch_create(const agile_config* cfgs, int nsolve, const agile_allocator* alloc,
+                                void* cuda_stream, agile_batch** out);
+void agile_batch_destroy(agile_batch* batch);
+
+/* Number of blocks and conserved variables of one solve. */
+agile_status agile_batch_layout(agile_batch* batch, int solve, size_t* nblocks, int* nvar);
+
+/* Initial condition of one solve (as agile_set_state). Synchronises. */
+agile_status agile_batch_set_state(agile_batch* batch, int solve, agile_ic_fn ic, void* user);
+
+/* One full SSPRK step of every solve with its own on-device CFL dt (as agile_step(dt <= 0)).
+ * The first call runs eagerly; later calls launch one captured CUDA graph. Asynchronous. */
+agile_status agile_batch_step(agile_batch* batch);
+
+/* CFL time step of every solve: dt[nsolve]. Synchronises. */
+agile_status agile_batch_cfl_dt(agile_batch* batch, double* dt);
+
+/* State of one solve, as agile_get_state. Synchronises. */
+agile_status agile_batch_get_state(agile_batch* batch, int solve, int* level, int* ijk, double* cons);
+
+/* Wait for the batch stream and return any latched device error. */
+agile_status agile_batch_sync(agile_batch* batch);
+
+/* Kernel launches enqueued by agile_batch_step so far (graph nodes counted per step). */
+long long agile_batch_launches(const agile_batch* batch);
+
+/* Message of the last failed call on this batch. */
+const char* agile_batch_last_error(const agile_batch* batch);
+
 /* Failure-detection check of the bounded device waits: launches one kernel that waits on
  * an mbarrier nothing arrives on, polling it at most `limit` times (1 .. 2^24), then returns
  * AGILE_ETIMEOUT with *timed_out = 1 (AGILE_OK and 0 would mean the barrier completed).

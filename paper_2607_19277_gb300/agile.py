@@ -31,7 +31,11 @@ EXPORTS = ["agile_mesh_create", "agile_mesh_destroy", "agile_set_state", "agile_
            "agile_get_state", "agile_get_aux", "agile_conserved_sums",
            "agile_conserved_sums_noalloc", "agile_estimate",
            "agile_get_halo", "agile_sync", "agile_set_kernel_timing", "agile_kernel_timing",
-           "agile_selftest_bounded_wait", "agile_last_error", "agile_version"]
+           "agile_selftest_bounded_wait", "agile_last_error", "agile_version",
+           "agile_batch_create", "agile_batch_destroy", "agile_batch_layout",
+           "agile_batch_set_state", "agile_batch_step", "agile_batch_cfl_dt",
+           "agile_batch_get_state", "agile_batch_sync", "agile_batch_launches",
+           "agile_batch_last_error"]
 
 
 class agile_config(C.Structure):
@@ -97,6 +101,16 @@ def load(path: str = LIB_PATH):
         "agile_selftest_bounded_wait": (C.c_int, [P, C.c_uint, ip]),
         "agile_last_error": (C.c_char_p, [P]),
         "agile_version": (C.c_char_p, []),
+        "agile_batch_create": (C.c_int, [C.POINTER(agile_config), C.c_int, C.POINTER(agile_allocator), P, C.POINTER(P)]),
+        "agile_batch_destroy": (None, [P]),
+        "agile_batch_layout": (C.c_int, [P, C.c_int, C.POINTER(C.c_size_t), ip]),
+        "agile_batch_set_state": (C.c_int, [P, C.c_int, IC_FN, P]),
+        "agile_batch_step": (C.c_int, [P]),
+        "agile_batch_cfl_dt": (C.c_int, [P, dp]),
+        "agile_batch_get_state": (C.c_int, [P, C.c_int, ip, ip, dp]),
+        "agile_batch_sync": (C.c_int, [P]),
+        "agile_batch_launches": (C.c_longlong, [P]),
+        "agile_batch_last_error": (C.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -319,3 +333,83 @@ class Mesh:
         tot = C.c_longlong()
         self._ck(self.lib.agile_kernel_timing(self.ptr, C.byref(ms), C.byref(n), C.byref(tot)))
         return ms.value, n.value, tot.value
+
+
+def _ic_callback(ic, nvar):
+    def cb(x, y, z, n, prim, user):
+        xs = np.ctypeslib.as_array(x, shape=(n,)).copy()
+        ys = np.ctypeslib.as_array(y, shape=(n,)).copy()
+        zs = np.ctypeslib.as_array(z, shape=(n,)).copy()
+        out = np.ctypeslib.as_array(prim, shape=(nvar * n,))
+        out[:] = np.asarray(ic(xs, ys, zs), dtype=np.float64).reshape(nvar * n)
+    return IC_FN(cb)
+
+
+class Batch:
+    """Independent uniform-grid solves advanced together (one launch per RK stage over all
+    of them, each step replayed from a CUDA graph)."""
+
+    def __init__(self, cfgs, stream=None, use_torch_allocator=True):
+        import torch
+        self.lib = load()
+        self.cfgs = list(cfgs)
+        arr = (agile_config * len(self.cfgs))(*self.cfgs)
+        self.stream = stream
+        self._alloc = _TorchAllocator(torch.cuda.current_device()) if use_torch_allocator else None
+        out = C.c_void_p()
+        st = self.lib.agile_batch_create(arr, len(self.cfgs), self._alloc.struct if self._alloc else None,
+                                         C.c_void_p(int(stream.cuda_stream) if stream is not None else 0),
+                                         C.byref(out))
+        _check(self.lib, None, st)
+        self.ptr = out
+        self.nvar = 9 if self.cfgs[0].physics == 1 else 5
+        self._ics = {}
+
+    def _ck(self, st):
+        if st != 0:
+            msg = self.lib.agile_batch_last_error(self.ptr)
+            raise AgileError(st, (msg or b"").decode())
+
+    def close(self):
+        if self.ptr:
+            self.lib.agile_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def layout(self, solve):
+        n = C.c_size_t()
+        nv = C.c_int()
+        self._ck(self.lib.agile_batch_layout(self.ptr, solve, C.byref(n), C.byref(nv)))
+        return n.value, nv.value
+
+    def set_state(self, solve, ic):
+        cb = _ic_callback(ic, self.nvar)
+        self._ics[solve] = cb
+        self._ck(self.lib.agile_batch_set_state(self.ptr, solve, cb, None))
+
+    def step(self):
+        self._ck(self.lib.agile_batch_step(self.ptr))
+
+    def cfl_dt(self):
+        dt = np.zeros(len(self.cfgs))
+        self._ck(self.lib.agile_batch_cfl_dt(self.ptr, _dptr(dt)))
+        return dt
+
+    def get_state(self, solve):
+        n, nv = self.layout(solve)
+        lev = np.zeros(n, dtype=np.int32)
+        ijk = np.zeros((n, 3), dtype=np.int32)
+        cons = np.zeros((n, nv, 16, 16, 16))
+        self._ck(self.lib.agile_batch_get_state(self.ptr, solve, _iptr(lev), _iptr(ijk), _dptr(cons)))
+        return lev, ijk, cons
+
+    def sync(self):
+        self._ck(self.lib.agile_batch_sync(self.ptr))
+
+    def launches(self):
+        return int(self.lib.agile_batch_launches(self.ptr))

@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(256) fixup_kernel(R* __restrict__ U, const R* 
 template <template <typename> class PT, typename R>
 __global__ void __launch_bounds__(256) speeds_kernel(const R* __restrict__ U,
                                                       const BlockDesc* __restrict__ bd, double gamma,
-                                                      unsigned long long* speeds, int* status) {
+                                                      unsigned long long* speeds, int* status,
+                                                      const int* __restrict__ solve_of) {
   using P = PT<R>;
   constexpr int NV = P::NV, NA = P::NA, NT = NV + NA;
   const int b = blockIdx.x;
@@ -197,25 +198,29 @@ __global__ void __launch_bounds__(256) speeds_kernel(const R* __restrict__ U,
     if constexpr (NA > 0) aux[0] = base[(size_t)NV * NCELL + c];
     cell_speeds<PT, R>(u, aux, pp, dx, ssum, smax, st);
   }
-  block_max2<256>(ssum, smax, speeds);
+  block_max2<256>(ssum, smax, speeds + 2 * (solve_of ? solve_of[b] : 0));
   if (st) atomicOr(status, st);
 }
 
 __global__ void set_dt_kernel(const unsigned long long* speeds, double* dtch, double dt_host,
-                              double cfl) {
-  const double smax = __longlong_as_double((long long)speeds[0]);
-  const double cmax = __longlong_as_double((long long)speeds[1]);
-  dtch[0] = dt_host > 0.0 ? dt_host : cfl / smax;
-  dtch[1] = cmax;
+                              double cfl, int nsolve) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nsolve) return;
+  const double smax = __longlong_as_double((long long)speeds[2 * i]);
+  const double cmax = __longlong_as_double((long long)speeds[2 * i + 1]);
+  dtch[2 * i] = dt_host > 0.0 ? dt_host : cfl / smax;
+  dtch[2 * i + 1] = cmax;
 }
 
 // ------------------------------------------------------------------------------ GLM source
 template <typename R>
 __global__ void glm_decay_kernel(R* __restrict__ U, const BlockDesc* __restrict__ bd,
-                                 const double* __restrict__ dtch, double alpha) {
+                                 const double* __restrict__ dtch, double alpha,
+                                 const int* __restrict__ solve_of) {
   const int b = blockIdx.x;
+  const double* dc = dtch + 2 * (solve_of ? solve_of[b] : 0);
   const double dxm = fmin(fmin(bd[b].dx[0], bd[b].dx[1]), bd[b].dx[2]);
-  const double f = exp(-0.5 * dtch[0] * dtch[1] * alpha / dxm);
+  const double f = exp(-0.5 * dc[0] * dc[1] * alpha / dxm);
   R* psi = U + ((size_t)b * 9 + 8) * NCELL;
   for (int c = threadIdx.x; c < NCELL; c += blockDim.x) psi[c] = R((double)psi[c] * f);
 }
@@ -479,22 +484,22 @@ cudaError_t launch_fixup(const AuxArgs& a, const FixupTask* tasks, int ntasks, d
 
 cudaError_t launch_speeds(const AuxArgs& a, unsigned long long* speeds, cudaStream_t s) {
   if (a.nblk == 0) return cudaSuccess;
-#define CALL(PT) speeds_kernel<PT, R><<<a.nblk, 256, 0, s>>>((const R*)a.U, a.bd, a.gamma, speeds, a.status)
+#define CALL(PT) speeds_kernel<PT, R><<<a.nblk, 256, 0, s>>>((const R*)a.U, a.bd, a.gamma, speeds, a.status, a.solve_of)
   AGILE_DISPATCH(a.phys, a.real_bytes, CALL);
 #undef CALL
   return cudaGetLastError();
 }
 
 cudaError_t launch_set_dt(const unsigned long long* speeds, double* dtch, double dt_host,
-                          double cfl, cudaStream_t s) {
-  set_dt_kernel<<<1, 1, 0, s>>>(speeds, dtch, dt_host, cfl);
+                          double cfl, cudaStream_t s, int nsolve) {
+  set_dt_kernel<<<(nsolve + 127) / 128, 128, 0, s>>>(speeds, dtch, dt_host, cfl, nsolve);
   return cudaGetLastError();
 }
 
 cudaError_t launch_glm_decay(const AuxArgs& a, const double* dtch, cudaStream_t s) {
   if (a.nblk == 0) return cudaSuccess;
-  if (a.real_bytes == 8) glm_decay_kernel<double><<<a.nblk, 256, 0, s>>>((double*)a.Uw, a.bd, dtch, a.glm_alpha);
-  else glm_decay_kernel<float><<<a.nblk, 256, 0, s>>>((float*)a.Uw, a.bd, dtch, a.glm_alpha);
+  if (a.real_bytes == 8) glm_decay_kernel<double><<<a.nblk, 256, 0, s>>>((double*)a.Uw, a.bd, dtch, a.glm_alpha, a.solve_of);
+  else glm_decay_kernel<float><<<a.nblk, 256, 0, s>>>((float*)a.Uw, a.bd, dtch, a.glm_alpha, a.solve_of);
   return cudaGetLastError();
 }
 

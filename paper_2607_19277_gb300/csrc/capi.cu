@@ -498,6 +498,7 @@ agile_status agile_step(agile_mesh* m, double dt) {
     A.status = m->d_status;
     A.speeds = (last && fuse) ? m->d_speeds : nullptr;
     A.tmap = &m->tmap[st == 0 ? 0 : st];
+    A.solve_of = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (m->timing) {
       CK(m, cudaEventCreate(&e0));
@@ -772,3 +773,386 @@ extern "C" agile_status agile_conserved_sums_noalloc(agile_mesh* m, double* sums
                         m->stream));
   return check_status(m);
 }
+
+// ----------------------------------------------------------------------------------------
+// Batched independent solves (uniform grids): one pool holds the blocks of every solve, the
+// stage kernel updates all of them in one persistent launch per RK stage with each solve's
+// own CFL dt and GLM speed, and a whole step is replayed from one captured CUDA graph.
+// ----------------------------------------------------------------------------------------
+struct agile_batch {
+  agile_config cfg;                 // shared scheme
+  int nsolve = 0;
+  std::vector<agile_config> cfgs;
+  std::vector<HostMesh*> meshes;
+  std::vector<int> offset;          // first block of each solve
+  int nblk = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  agile_allocator alloc{};
+  bool default_alloc = true;
+  int nv = 5, na = 0, nt = 5, rb = 8;
+  void* U[3] = {nullptr, nullptr, nullptr};
+  BlockDesc* d_bd = nullptr;
+  int* d_solve_of = nullptr;
+  int* d_status = nullptr;
+  unsigned long long* d_speeds = nullptr;
+  double* d_dtch = nullptr;
+  CUtensorMap tmap[3];
+  bool speeds_valid = false;
+  int steps_done = 0;
+  cudaGraphExec_t graph = nullptr;
+  long long launches = 0;
+  std::string err;
+};
+
+namespace {
+
+// The batch shares the mesh helpers through a view with the same allocation fields.
+agile_mesh* as_mesh_view(agile_batch* B, agile_mesh* tmp) {
+  tmp->stream = B->stream;
+  tmp->alloc = B->alloc;
+  tmp->default_alloc = B->default_alloc;
+  tmp->nv = B->nv;
+  tmp->na = B->na;
+  tmp->nt = B->nt;
+  tmp->rb = B->rb;
+  tmp->nblk = B->nblk;
+  tmp->cfg = B->cfg;
+  return tmp;
+}
+
+agile_status bfail(agile_batch* B, agile_status s, const std::string& msg) {
+  if (B) B->err = msg;
+  return s;
+}
+
+#define BCK(B, call)                                                                         \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return bfail((B), AGILE_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_));       \
+  } while (0)
+
+AuxArgs batch_aux(agile_batch* B, void* U) {
+  AuxArgs a;
+  a.phys = B->cfg.physics;
+  a.real_bytes = B->rb;
+  a.gamma = B->cfg.gamma;
+  a.cfl = B->cfg.cfl;
+  a.glm_alpha = B->cfg.glm_alpha;
+  a.U = U;
+  a.Uw = U;
+  a.G = nullptr;
+  a.Gw = nullptr;
+  a.FR = nullptr;
+  a.bd = B->d_bd;
+  a.nblk = B->nblk;
+  a.status = B->d_status;
+  a.solve_of = B->d_solve_of;
+  a.nsolve = B->nsolve;
+  return a;
+}
+
+agile_status batch_status(agile_batch* B) {
+  BCK(B, cudaStreamSynchronize(B->stream));
+  int st = 0;
+  BCK(B, cudaMemcpy(&st, B->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) {
+    BCK(B, cudaMemset(B->d_status, 0, sizeof(int)));
+    if (st & ST_ETIMEOUT) return bfail(B, AGILE_ETIMEOUT, "a bounded wait for a TMA plane gave up");
+    if (st & ST_ENOCONV) return bfail(B, AGILE_ENOCONV, "primitive recovery did not converge");
+    return bfail(B, AGILE_EUNPHYS, "non-positive density or pressure on the device");
+  }
+  return AGILE_OK;
+}
+
+agile_status batch_ensure_speeds(agile_batch* B) {
+  if (B->speeds_valid) return AGILE_OK;
+  BCK(B, cudaMemsetAsync(B->d_speeds, 0, 2 * sizeof(unsigned long long) * B->nsolve, B->stream));
+  AuxArgs a = batch_aux(B, B->U[0]);
+  BCK(B, launch_speeds(a, B->d_speeds, B->stream));
+  B->launches++;
+  B->speeds_valid = true;
+  return AGILE_OK;
+}
+
+// Enqueue one full step of every solve (device dt) on the batch stream.
+agile_status batch_enqueue_step(agile_batch* B) {
+  BCK(B, launch_set_dt(B->d_speeds, B->d_dtch, 0.0, B->cfg.cfl, B->stream, B->nsolve));
+  const bool mhd = B->cfg.physics == AGILE_MHD_GLM;
+  if (mhd) {
+    AuxArgs a = batch_aux(B, B->U[0]);
+    BCK(B, launch_glm_decay(a, B->d_dtch, B->stream));
+  }
+  static const double w2[2][2] = {{0.0, 1.0}, {0.5, 0.5}};
+  static const double w3[3][2] = {{0.0, 1.0}, {0.75, 0.25}, {1.0 / 3.0, 2.0 / 3.0}};
+  const int nst = B->cfg.rk;
+  for (int st = 0; st < nst; ++st) {
+    const bool last = st == nst - 1;
+    if (last) BCK(B, cudaMemsetAsync(B->d_speeds, 0, 2 * sizeof(unsigned long long) * B->nsolve, B->stream));
+    StageArgs A;
+    A.Us = st == 0 ? B->U[0] : B->U[st];
+    A.Un = B->U[0];
+    A.Uout = last ? B->U[0] : B->U[st + 1];
+    A.bd = B->d_bd;
+    A.gs = nullptr;
+    A.fr = nullptr;
+    A.dtch = B->d_dtch;
+    A.a = nst == 2 ? w2[st][0] : w3[st][0];
+    A.b = nst == 2 ? w2[st][1] : w3[st][1];
+    A.gamma = B->cfg.gamma;
+    A.glm_alpha = B->cfg.glm_alpha;
+    A.glm_post = (mhd && last) ? 1 : 0;
+    A.nblk = B->nblk;
+    A.status = B->d_status;
+    A.speeds = last ? B->d_speeds : nullptr;
+    A.tmap = &B->tmap[st == 0 ? 0 : st];
+    A.solve_of = B->d_solve_of;
+    cudaError_t e;
+    if (B->cfg.physics == AGILE_HD) e = launch_stage_hd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
+    else if (mhd) e = launch_stage_mhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
+    else e = launch_stage_srhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
+    if (e != cudaSuccess) return bfail(B, AGILE_ECUDA, std::string("stage kernel: ") + cudaGetErrorString(e));
+  }
+  return AGILE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+agile_status agile_batch_create(const agile_config* cfgs, int nsolve, const agile_allocator* alloc,
+                                void* stream, agile_batch** out) {
+  if (!cfgs || !out || nsolve < 1 || nsolve > (1 << 20)) return AGILE_EINVAL;
+  *out = nullptr;
+  const agile_config& c0 = cfgs[0];
+  for (int i = 0; i < nsolve; ++i) {
+    const agile_config& c = cfgs[i];
+    if (c.physics != c0.physics || c.limiter != c0.limiter || c.flux != c0.flux || c.rk != c0.rk ||
+        c.real_bytes != c0.real_bytes || c.gamma != c0.gamma || c.cfl != c0.cfl ||
+        c.glm_alpha != c0.glm_alpha || c.max_level != 1)
+      return AGILE_EINVAL;
+    // validate each configuration like a single mesh (host-side checks only)
+    if (c.physics < 0 || c.physics > 2 || (c.limiter != 0 && c.limiter != 1) || (c.flux != 0 && c.flux != 1) ||
+        (c.rk != 2 && c.rk != 3) || (c.real_bytes != 4 && c.real_bytes != 8) || !(c.gamma > 1.0) ||
+        !(c.cfl > 0.0) || (c.physics == AGILE_SRHD && c.flux != AGILE_TVDLF))
+      return AGILE_EINVAL;
+    for (int d = 0; d < 3; ++d) {
+      if (c.base_blocks[d] < 1 || c.base_blocks[d] > 4096 || !(c.xmax[d] > c.xmin[d])) return AGILE_EINVAL;
+      if ((c.bc[2 * d] == AGILE_PERIODIC) != (c.bc[2 * d + 1] == AGILE_PERIODIC)) return AGILE_EINVAL;
+      for (int s = 0; s < 2; ++s)
+        if (c.bc[2 * d + s] < 0 || c.bc[2 * d + s] > 2) return AGILE_EINVAL;
+    }
+  }
+  agile_batch* B = new agile_batch();
+  B->cfg = c0;
+  B->nsolve = nsolve;
+  B->cfgs.assign(cfgs, cfgs + nsolve);
+  if (alloc && alloc->alloc && alloc->free) {
+    B->alloc = *alloc;
+    B->default_alloc = false;
+  }
+  B->stream = (cudaStream_t)stream;
+  if (!B->stream) {   // graphs cannot be captured on the legacy default stream
+    if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete B;
+      return AGILE_ECUDA;
+    }
+    B->own_stream = true;
+  }
+  B->nv = c0.physics == AGILE_MHD_GLM ? 9 : 5;
+  B->na = c0.physics == AGILE_SRHD ? 2 : 0;
+  B->nt = B->nv + B->na;
+  B->rb = c0.real_bytes;
+  std::vector<BlockDesc> desc;
+  std::vector<int> solve_of;
+  for (int i = 0; i < nsolve; ++i) {
+    HostMesh* hm = new HostMesh(cfgs[i].base_blocks, 1, cfgs[i].bc, cfgs[i].xmin, cfgs[i].xmax);
+    B->meshes.push_back(hm);
+    B->offset.push_back((int)desc.size());
+    std::vector<BlockDesc> d;
+    std::vector<GhostTask> g;
+    std::vector<FixupTask> x;
+    int ns = 0;
+    std::string err;
+    hm->build_descs(&d, &g, &x, &ns, &err);
+    if (!err.empty() || ns != 0) {
+      agile_batch_destroy(B);
+      return AGILE_EINVAL;
+    }
+    for (BlockDesc& bd : d) {
+      for (int f = 0; f < 6; ++f)
+        if (bd.src[f] >= 0) bd.src[f] += B->offset[i];
+      desc.push_back(bd);
+      solve_of.push_back(i);
+    }
+  }
+  B->nblk = (int)desc.size();
+  agile_mesh view;
+  as_mesh_view(B, &view);
+  const size_t pool = (size_t)B->nblk * B->nt * NCELL * B->rb;
+  B->U[0] = dalloc(&view, pool);
+  B->U[1] = dalloc(&view, pool);
+  B->U[2] = c0.rk == 3 ? dalloc(&view, pool) : nullptr;
+  B->d_bd = (BlockDesc*)dalloc(&view, desc.size() * sizeof(BlockDesc));
+  B->d_solve_of = (int*)dalloc(&view, solve_of.size() * sizeof(int));
+  B->d_status = (int*)dalloc(&view, sizeof(int));
+  B->d_speeds = (unsigned long long*)dalloc(&view, 2 * sizeof(unsigned long long) * nsolve);
+  B->d_dtch = (double*)dalloc(&view, 2 * sizeof(double) * nsolve);
+  if (!B->U[0] || !B->U[1] || (c0.rk == 3 && !B->U[2]) || !B->d_bd || !B->d_solve_of || !B->d_status ||
+      !B->d_speeds || !B->d_dtch) {
+    agile_batch_destroy(B);
+    return AGILE_ENOMEM;
+  }
+  if (cudaMemcpyAsync(B->d_bd, desc.data(), desc.size() * sizeof(BlockDesc), cudaMemcpyHostToDevice, B->stream) != cudaSuccess ||
+      cudaMemcpyAsync(B->d_solve_of, solve_of.data(), solve_of.size() * sizeof(int), cudaMemcpyHostToDevice, B->stream) != cudaSuccess ||
+      cudaMemsetAsync(B->d_status, 0, sizeof(int), B->stream) != cudaSuccess ||
+      cudaMemsetAsync(B->U[0], 0, pool, B->stream) != cudaSuccess || cudaStreamSynchronize(B->stream) != cudaSuccess) {
+    agile_batch_destroy(B);
+    return AGILE_ECUDA;
+  }
+  view.nblk = B->nblk;
+  for (int i = 0; i < 3; ++i) {
+    if (make_tmap(&view, B->U[i], &B->tmap[i]) != AGILE_OK) {
+      agile_batch_destroy(B);
+      return AGILE_ECUDA;
+    }
+  }
+  *out = B;
+  return AGILE_OK;
+}
+
+void agile_batch_destroy(agile_batch* B) {
+  if (!B) return;
+  cudaStreamSynchronize(B->stream);
+  if (B->graph) cudaGraphExecDestroy(B->graph);
+  agile_mesh view;
+  as_mesh_view(B, &view);
+  for (int i = 0; i < 3; ++i) dfree(&view, B->U[i]);
+  dfree_t(&view, B->d_bd);
+  dfree_t(&view, B->d_solve_of);
+  dfree_t(&view, B->d_status);
+  dfree_t(&view, B->d_speeds);
+  dfree_t(&view, B->d_dtch);
+  cudaStreamSynchronize(B->stream);
+  for (HostMesh* hm : B->meshes) delete hm;
+  if (B->own_stream) cudaStreamDestroy(B->stream);
+  delete B;
+}
+
+agile_status agile_batch_layout(agile_batch* B, int solve, size_t* nblocks, int* nvar) {
+  if (!B || solve < 0 || solve >= B->nsolve) return AGILE_EINVAL;
+  if (nblocks) *nblocks = B->meshes[solve]->blocks().size();
+  if (nvar) *nvar = B->nv;
+  return AGILE_OK;
+}
+
+agile_status agile_batch_set_state(agile_batch* B, int solve, agile_ic_fn ic, void* user) {
+  if (!B || !ic || solve < 0 || solve >= B->nsolve) return bfail(B, AGILE_EINVAL, "bad argument");
+  agile_mesh view;
+  as_mesh_view(B, &view);
+  view.mesh = B->meshes[solve];
+  view.cfg = B->cfgs[solve];
+  view.ic = ic;
+  view.ic_user = user;
+  view.d_status = B->d_status;
+  std::vector<int> blocks(B->meshes[solve]->blocks().size());
+  for (size_t i = 0; i < blocks.size(); ++i) blocks[i] = B->offset[solve] + (int)i;
+  // apply_ic converts with the block's key from view.mesh: pass local indices through a
+  // pool pointer shifted to this solve's first block
+  std::vector<int> local(blocks.size());
+  for (size_t i = 0; i < local.size(); ++i) local[i] = (int)i;
+  char* base = (char*)B->U[0] + (size_t)B->offset[solve] * B->nt * NCELL * B->rb;
+  view.nblk = (int)local.size();
+  agile_status s = apply_ic(&view, base, local);
+  view.mesh = nullptr;
+  if (s) return bfail(B, s, view.err);
+  B->speeds_valid = false;
+  return batch_status(B);
+}
+
+agile_status agile_batch_step(agile_batch* B) {
+  if (!B) return AGILE_EINVAL;
+  agile_status s = batch_ensure_speeds(B);
+  if (s) return s;
+  if (B->steps_done == 0) {   // first step eagerly: sets kernel attributes outside any capture
+    s = batch_enqueue_step(B);
+    if (s) return s;
+  } else {
+    if (!B->graph) {
+      cudaGraph_t g = nullptr;
+      BCK(B, cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
+      s = batch_enqueue_step(B);
+      cudaGraph_t gg = nullptr;
+      cudaError_t e = cudaStreamEndCapture(B->stream, &gg);
+      if (s) {
+        if (gg) cudaGraphDestroy(gg);
+        return s;
+      }
+      if (e != cudaSuccess) return bfail(B, AGILE_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      g = gg;
+      e = cudaGraphInstantiate(&B->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return bfail(B, AGILE_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    BCK(B, cudaGraphLaunch(B->graph, B->stream));
+  }
+  B->launches += B->cfg.rk + 1 + (B->cfg.physics == AGILE_MHD_GLM ? 1 : 0);
+  B->steps_done++;
+  B->speeds_valid = true;
+  return AGILE_OK;
+}
+
+agile_status agile_batch_cfl_dt(agile_batch* B, double* dt) {
+  if (!B || !dt) return bfail(B, AGILE_EINVAL, "null argument");
+  agile_status s = batch_ensure_speeds(B);
+  if (s) return s;
+  std::vector<unsigned long long> h(2 * (size_t)B->nsolve);
+  BCK(B, cudaMemcpyAsync(h.data(), B->d_speeds, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, B->stream));
+  s = batch_status(B);
+  if (s) return s;
+  for (int i = 0; i < B->nsolve; ++i) {
+    double smax;
+    memcpy(&smax, &h[2 * i], sizeof(double));
+    dt[i] = B->cfg.cfl / smax;
+  }
+  return AGILE_OK;
+}
+
+agile_status agile_batch_get_state(agile_batch* B, int solve, int* level, int* ijk, double* cons) {
+  if (!B || solve < 0 || solve >= B->nsolve) return bfail(B, AGILE_EINVAL, "bad argument");
+  const auto& keys = B->meshes[solve]->blocks();
+  const int n = (int)keys.size();
+  for (int i = 0; i < n; ++i) {
+    if (level) level[i] = keys[i].lev;
+    if (ijk) {
+      ijk[3 * i] = keys[i].x;
+      ijk[3 * i + 1] = keys[i].y;
+      ijk[3 * i + 2] = keys[i].z;
+    }
+  }
+  if (!cons) return batch_status(B);
+  agile_mesh view;
+  as_mesh_view(B, &view);
+  const size_t bytes = (size_t)n * B->nv * NCELL * sizeof(double);
+  double* d = (double*)dalloc(&view, bytes);
+  if (!d) return bfail(B, AGILE_ENOMEM, "device allocation failed");
+  AuxArgs a = batch_aux(B, (char*)B->U[0] + (size_t)B->offset[solve] * B->nt * NCELL * B->rb);
+  a.nblk = n;
+  BCK(B, launch_pack(a, d, nullptr, B->stream));
+  BCK(B, cudaMemcpyAsync(cons, d, bytes, cudaMemcpyDeviceToHost, B->stream));
+  agile_status s = batch_status(B);
+  dfree_t(&view, d);
+  return s;
+}
+
+agile_status agile_batch_sync(agile_batch* B) {
+  if (!B) return AGILE_EINVAL;
+  return batch_status(B);
+}
+
+long long agile_batch_launches(const agile_batch* B) { return B ? B->launches : 0; }
+
+const char* agile_batch_last_error(const agile_batch* B) { return B ? B->err.c_str() : "null batch"; }
+
+}  // extern "C"

@@ -32,8 +32,9 @@ struct StageArgs {
   int glm_post;             // multiply psi of the output by exp(-dt/2 c_h alpha / min dx)
   int nblk;
   int* status;
-  unsigned long long* speeds;   // fused reduction of [max sum_d s_d/dx_d, max s_d] or nullptr
+  unsigned long long* speeds;   // fused reduction of [max sum_d s_d/dx_d, max s_d] per solve, or nullptr
   const void* tmap;             // host CUtensorMap of the pool Us (x, y, z, block*var)
+  const int* solve_of;          // solve index of each block (batched solves), nullptr = one solve
 };
 
 // Conserved + auxiliary values of the cell (x, y, z) of block b in the halo view: the
@@ -290,11 +291,23 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   const R* __restrict__ G = static_cast<const R*>(A.gs);
   R* __restrict__ FR = static_cast<R*>(A.fr);
 
-  const int b = blockIdx.x;
   const int t = threadIdx.x;
   const int tx = t & 15, ty = t >> 4;
   const int warp = t >> 5;
   const int cell2 = ty * 16 + tx;
+  if (t == 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) mbar_init(bar + i, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  int st = 0;
+  // Persistent loop: this CTA updates blocks blockIdx.x, blockIdx.x + gridDim.x, ...; every
+  // block completes 5 phases of each ring barrier, so block jb starts at parity jb & 1.
+  for (int b = blockIdx.x, jb = 0; b < A.nblk; b += gridDim.x, ++jb) {
+  const int sv = A.solve_of ? A.solve_of[b] : 0;
+  const double* dtch = A.dtch + 2 * sv;
+  unsigned long long* speeds = A.speeds ? A.speeds + 2 * sv : nullptr;
   const BlockDesc& bd = A.bd[b];
   int src[6], slot[6];
 #pragma unroll
@@ -302,15 +315,14 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     src[f] = bd.src[f];
     slot[f] = bd.slot[f];
   }
-  const double dt = A.dtch[0];
+  const double dt = dtch[0];
   PhysParamsT<R> pp;
-  pp.set(A.gamma, A.dtch[1]);
+  pp.set(A.gamma, dtch[1]);
   const R idx = R(1.0 / bd.dx[0]), idy = R(1.0 / bd.dx[1]), idz = R(1.0 / bd.dx[2]);
   const R rdt = R(dt);
   const R ra = R(A.a), rb = R(A.b);
   const bool combine = A.a != 0.0;
   const bool glm_post = A.glm_post != 0;
-  int st = 0;
   constexpr uint32_t PLANE_BYTES = (uint32_t)(sizeof(R) * NT * 256);
 
   // plane p (-2 .. 17) -> TMA sequence q = p + 2, ring slot q & 3, phase parity (q >> 2) & 1
@@ -338,7 +350,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     const int q = p + 2;
     R u[NT];
     if (plane_tma(p)) {
-      if (!mbar_wait(bar + (q & 3), (q >> 2) & 1, WAIT_LIMIT)) st |= ST_ETIMEOUT;
+      if (!mbar_wait(bar + (q & 3), ((q >> 2) + jb) & 1, WAIT_LIMIT)) st |= ST_ETIMEOUT;
       const R* r = sRaw + (size_t)(q & 3) * NT * 256 + cell2;
 #pragma unroll
       for (int v = 0; v < NT; ++v) u[v] = r[v * 256];
@@ -415,14 +427,9 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     }
   };
 
-  if (t == 0) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) mbar_init(bar + i, 1);
-    fence_mbar_init();
-  }
   prefetch_halo(0);
-  __syncthreads();
   if (t == 0) {
+    fence_proxy_async();   // the previous block's reads of the ring precede these copies
     for (int p = -2; p <= 1; ++p) issue(p);
   }
   // Prologue: planes -2 .. 1 of this column, then the z-face at -1/2. Ring slots at
@@ -450,7 +457,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   double glm_f = 1.0;
   if (A.glm_post) {
     const double dxm = fmin(fmin(bd.dx[0], bd.dx[1]), bd.dx[2]);
-    glm_f = exp(-0.5 * dt * A.dtch[1] * A.glm_alpha / dxm);
+    glm_f = exp(-0.5 * dt * dtch[1] * A.glm_alpha / dxm);
   }
   const R glm_fr = R(glm_f);
 
@@ -578,7 +585,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       } else {
         auxk[0] = R(0);
       }
-      if (A.speeds) {
+      if (speeds) {
         R ad[NAW];
 #pragma unroll
         for (int i = 0; i < NAW; ++i) ad[i] = auxk[i];
@@ -586,7 +593,9 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       }
     }
   }
-  if (A.speeds) block_max2<256>(ssum, smax, A.speeds);
+  if (speeds) block_max2<256>(ssum, smax, speeds);
+  __syncthreads();       // ring, halo staging and reduction scratch are reused by the next block
+  }
   if (st) atomicOr(A.status, st);
 }
 

@@ -27,6 +27,8 @@ struct AuxArgs {
   const BlockDesc* bd;
   int nblk;
   int* status;
+  const int* solve_of = nullptr;   // solve index per block (batched solves), nullptr = one solve
+  int nsolve = 1;
 };
 
 // Fill ghost slots of coarse-fine faces from U (restriction / limited prolongation).
@@ -36,9 +38,10 @@ cudaError_t launch_fixup(const AuxArgs& a, const FixupTask* tasks, int ntasks, d
                          const double* dtch, cudaStream_t s);
 // Max signal-speed reduction of U into speeds[2] (double bits; caller zeroes them).
 cudaError_t launch_speeds(const AuxArgs& a, unsigned long long* speeds, cudaStream_t s);
-// dtch = {dt, c_h}: dt from the host value or (dt <= 0) cfl / max sum_d s_d / dx_d.
+// dtch[solve] = {dt, c_h}: dt from the host value or (dt <= 0) cfl / max sum_d s_d / dx_d,
+// for each of nsolve solves (speeds[solve][2]).
 cudaError_t launch_set_dt(const unsigned long long* speeds, double* dtch, double dt_host,
-                          double cfl, cudaStream_t s);
+                          double cfl, cudaStream_t s, int nsolve = 1);
 // psi *= exp(-dt/2 c_h alpha / min dx) on every block.
 cudaError_t launch_glm_decay(const AuxArgs& a, const double* dtch, cudaStream_t s);
 // Loehner estimate: emax[nblk] (FP64, no FMA).

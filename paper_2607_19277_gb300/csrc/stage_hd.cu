@@ -15,7 +15,17 @@ static cudaError_t go(const StageArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k<<<a.nblk, 256, smem, s>>>(*static_cast<const CUtensorMap*>(a.tmap), a);
+  // persistent grid: as many CTAs as fit on the GPU at once, each looping over blocks
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int grid = a.nblk < MINB * sms ? a.nblk : MINB * sms;
+  if (grid <= 0) return cudaSuccess;
+  k<<<grid, 256, smem, s>>>(*static_cast<const CUtensorMap*>(a.tmap), a);
   return cudaGetLastError();
 }
 
