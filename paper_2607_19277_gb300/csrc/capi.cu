@@ -36,6 +36,7 @@ struct agile_mesh {
   int* d_status = nullptr;
   unsigned long long* d_speeds = nullptr;
   double* d_dtch = nullptr;
+  int* d_work = nullptr;            // per-stage block counters of the persistent launches
   int* d_vars = nullptr;
   double* d_weights = nullptr;
   bool speeds_valid = false;
@@ -361,9 +362,10 @@ agile_status agile_mesh_create(const agile_config* cfg, const agile_allocator* a
   m->d_status = (int*)dalloc(m, sizeof(int));
   m->d_speeds = (unsigned long long*)dalloc(m, 2 * sizeof(unsigned long long));
   m->d_dtch = (double*)dalloc(m, 2 * sizeof(double));
+  m->d_work = (int*)dalloc(m, 4 * sizeof(int));
   m->d_vars = (int*)dalloc(m, 9 * sizeof(int));
   m->d_weights = (double*)dalloc(m, 9 * sizeof(double));
-  if (!m->U[0] || !m->d_status || !m->d_speeds || !m->d_dtch || !m->d_vars || !m->d_weights) {
+  if (!m->U[0] || !m->d_status || !m->d_speeds || !m->d_dtch || !m->d_work || !m->d_vars || !m->d_weights) {
     agile_mesh_destroy(m);
     return AGILE_ENOMEM;
   }
@@ -394,6 +396,7 @@ void agile_mesh_destroy(agile_mesh* m) {
   dfree_t(m, m->d_status);
   dfree_t(m, m->d_speeds);
   dfree_t(m, m->d_dtch);
+  dfree_t(m, m->d_work);
   dfree_t(m, m->d_vars);
   dfree_t(m, m->d_weights);
   for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
@@ -463,6 +466,7 @@ agile_status agile_step(agile_mesh* m, double dt) {
   agile_status s = ensure_speeds(m);
   if (s) return s;
   CK(m, launch_set_dt(m->d_speeds, m->d_dtch, dt, m->cfg.cfl, m->stream));
+  CK(m, cudaMemsetAsync(m->d_work, 0, 4 * sizeof(int), m->stream));
   m->total_launches++;
   const bool mhd = m->cfg.physics == AGILE_MHD_GLM;
   if (mhd) {
@@ -499,6 +503,7 @@ agile_status agile_step(agile_mesh* m, double dt) {
     A.speeds = (last && fuse) ? m->d_speeds : nullptr;
     A.tmap = &m->tmap[st == 0 ? 0 : st];
     A.solve_of = nullptr;
+    A.work = m->d_work + st;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (m->timing) {
       CK(m, cudaEventCreate(&e0));
@@ -797,6 +802,7 @@ struct agile_batch {
   int* d_status = nullptr;
   unsigned long long* d_speeds = nullptr;
   double* d_dtch = nullptr;
+  int* d_work = nullptr;
   CUtensorMap tmap[3];
   bool speeds_valid = false;
   int steps_done = 0;
@@ -879,6 +885,7 @@ agile_status batch_ensure_speeds(agile_batch* B) {
 // Enqueue one full step of every solve (device dt) on the batch stream.
 agile_status batch_enqueue_step(agile_batch* B) {
   BCK(B, launch_set_dt(B->d_speeds, B->d_dtch, 0.0, B->cfg.cfl, B->stream, B->nsolve));
+  BCK(B, cudaMemsetAsync(B->d_work, 0, 4 * sizeof(int), B->stream));
   const bool mhd = B->cfg.physics == AGILE_MHD_GLM;
   if (mhd) {
     AuxArgs a = batch_aux(B, B->U[0]);
@@ -908,6 +915,7 @@ agile_status batch_enqueue_step(agile_batch* B) {
     A.speeds = last ? B->d_speeds : nullptr;
     A.tmap = &B->tmap[st == 0 ? 0 : st];
     A.solve_of = B->d_solve_of;
+    A.work = B->d_work + st;
     cudaError_t e;
     if (B->cfg.physics == AGILE_HD) e = launch_stage_hd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
     else if (mhd) e = launch_stage_mhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
@@ -999,8 +1007,9 @@ agile_status agile_batch_create(const agile_config* cfgs, int nsolve, const agil
   B->d_status = (int*)dalloc(&view, sizeof(int));
   B->d_speeds = (unsigned long long*)dalloc(&view, 2 * sizeof(unsigned long long) * nsolve);
   B->d_dtch = (double*)dalloc(&view, 2 * sizeof(double) * nsolve);
+  B->d_work = (int*)dalloc(&view, 4 * sizeof(int));
   if (!B->U[0] || !B->U[1] || (c0.rk == 3 && !B->U[2]) || !B->d_bd || !B->d_solve_of || !B->d_status ||
-      !B->d_speeds || !B->d_dtch) {
+      !B->d_speeds || !B->d_dtch || !B->d_work) {
     agile_batch_destroy(B);
     return AGILE_ENOMEM;
   }
@@ -1034,6 +1043,7 @@ void agile_batch_destroy(agile_batch* B) {
   dfree_t(&view, B->d_status);
   dfree_t(&view, B->d_speeds);
   dfree_t(&view, B->d_dtch);
+  dfree_t(&view, B->d_work);
   cudaStreamSynchronize(B->stream);
   for (HostMesh* hm : B->meshes) delete hm;
   if (B->own_stream) cudaStreamDestroy(B->stream);

@@ -35,6 +35,7 @@ struct StageArgs {
   unsigned long long* speeds;   // fused reduction of [max sum_d s_d/dx_d, max s_d] per solve, or nullptr
   const void* tmap;             // host CUtensorMap of the pool Us (x, y, z, block*var)
   const int* solve_of;          // solve index of each block (batched solves), nullptr = one solve
+  int* work;                    // block counter of this launch (zeroed before it), dynamic scheduling
 };
 
 // Conserved + auxiliary values of the cell (x, y, z) of block b in the halo view: the
@@ -302,9 +303,11 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   }
   __syncthreads();
   int st = 0;
-  // Persistent loop: this CTA updates blocks blockIdx.x, blockIdx.x + gridDim.x, ...; every
-  // block completes 5 phases of each ring barrier, so block jb starts at parity jb & 1.
-  for (int b = blockIdx.x, jb = 0; b < A.nblk; b += gridDim.x, ++jb) {
+  // Persistent loop: this CTA starts with block blockIdx.x and then takes the next free block
+  // from the launch's counter; every block completes 5 phases of each ring barrier, so the
+  // CTA's jb-th block starts at parity jb & 1.
+  __shared__ int s_next;
+  for (int b = blockIdx.x, jb = 0; b < A.nblk; ++jb) {
   const int sv = A.solve_of ? A.solve_of[b] : 0;
   const double* dtch = A.dtch + 2 * sv;
   unsigned long long* speeds = A.speeds ? A.speeds + 2 * sv : nullptr;
@@ -594,7 +597,9 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     }
   }
   if (speeds) block_max2<256>(ssum, smax, speeds);
+  if (t == 0) s_next = A.work ? (int)gridDim.x + atomicAdd(A.work, 1) : b + (int)gridDim.x;
   __syncthreads();       // ring, halo staging and reduction scratch are reused by the next block
+  b = s_next;
   }
   if (st) atomicOr(A.status, st);
 }

@@ -156,12 +156,14 @@ def sedov(gamma=5.0 / 3.0, energy=1.0, r0=0.03, rho0=1.0, p0=1e-5, centre=(0.0, 
 
 
 def srhd_shells(seed: int, n_cells: int, n_shells=None, rho_amb=1.0, p_amb=0.01,
-                lorentz_max=10.0):
+                lorentz_max=10.0, smooth=False):
     """SRHD state on [0,1]^3: ambient (rho, p) with 1-3 seeded spherical shells.
 
     Per shell s (draws 8 s .. 8 s + 7 of the stream): centre U[0,1]^3, radius U[0.1, 0.3],
     rho_shell U[1, 10], radial Lorentz factor U[1, lorentz_max]; the shell is 3 cells wide
-    (|r - R| < 1.5 dx) and moves radially outward with four-velocity sqrt(Gamma^2 - 1).
+    and moves radially outward with four-velocity sqrt(Gamma^2 - 1). smooth=False: a top hat
+    |r - R| < 1.5 dx; smooth=True: a Gaussian radial profile exp(-(r - R)^2 / (2 (1.5 dx)^2))
+    of the density excess and of the four-velocity (shells combine by the larger weight).
     """
     if n_shells is None:
         n_shells = 1 + int(uniform01(seed, np.array([1000]))[0] * 3.0)
@@ -179,15 +181,24 @@ def srhd_shells(seed: int, n_cells: int, n_shells=None, rho_amb=1.0, p_amb=0.01,
         prim = np.zeros((5, x.size))
         prim[0] = rho_amb
         prim[4] = p_amb
+        wmax = np.zeros(x.size)
         for sh in shells:
             ddx, ddy, ddz = x - sh["c"][0], y - sh["c"][1], z - sh["c"][2]
             r = np.sqrt(ddx * ddx + ddy * ddy + ddz * ddz)
-            inside = np.abs(r - sh["R"]) < 1.5 * dx
             ur = math.sqrt(sh["lorentz"] ** 2 - 1.0)
             rs = np.where(r > 0, r, 1.0)
-            prim[0] = np.where(inside, sh["rho"], prim[0])
-            for c, d in enumerate((ddx, ddy, ddz)):
-                prim[1 + c] = np.where(inside, ur * d / rs, prim[1 + c])
+            if smooth:
+                w = np.exp(-((r - sh["R"]) ** 2) / (2.0 * (1.5 * dx) ** 2))
+                take = w > wmax
+                wmax = np.where(take, w, wmax)
+                prim[0] = np.where(take, rho_amb + (sh["rho"] - rho_amb) * w, prim[0])
+                for c, d in enumerate((ddx, ddy, ddz)):
+                    prim[1 + c] = np.where(take, w * ur * d / rs, prim[1 + c])
+            else:
+                inside = np.abs(r - sh["R"]) < 1.5 * dx
+                prim[0] = np.where(inside, sh["rho"], prim[0])
+                for c, d in enumerate((ddx, ddy, ddz)):
+                    prim[1 + c] = np.where(inside, ur * d / rs, prim[1 + c])
         return prim
     ic.shells = shells
     return ic

@@ -21,7 +21,9 @@ def _cfg(side, rb, physics, bc=("periodic",) * 6):
 
 def _ic(physics, seed, side):
     if physics == "srhd":
-        return W.srhd_shells(seed, side, lorentz_max=5.0, p_amb=0.1)
+        # Lorentz factors up to 3: thin (3-cell) shells at Gamma ~ 5 turn unphysical within a
+        # step without a floor, in the FP64 oracle as well
+        return W.srhd_shells(seed, side, lorentz_max=3.0, p_amb=0.1)
     return W.random_smooth(9, seed, "mhd")
 
 
@@ -59,8 +61,8 @@ def test_batched_solve_matches_oracle_fp64():
                 base_blocks=(3, 3, 3))
     cfgs = [_cfg(32, 8, "srhd"), agile.make_config(real_bytes=8, **spec)]
     b = agile.Batch(cfgs)
-    ic0 = W.srhd_shells(7, 32, lorentz_max=5.0, p_amb=0.1)
-    ic1 = W.srhd_shells(8, 48, lorentz_max=5.0, p_amb=0.1)
+    ic0 = W.srhd_shells(7, 32, lorentz_max=3.0, p_amb=0.1)
+    ic1 = W.srhd_shells(8, 48, lorentz_max=3.0, p_amb=0.1)
     b.set_state(0, ic0)
     b.set_state(1, ic1)
     o = oracle_solver(spec)
