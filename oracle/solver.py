@@ -42,7 +42,7 @@ RK_STAGES = {
 class Config:
     physics: str = "hd"
     limiter: str = "minmod"        # 'minmod' | 'vanleer'
-    flux: str = "hll"              # 'hll' | 'tvdlf'
+    flux: str = "hll"              # 'hll' | 'tvdlf' | 'hllc' (hd only)
     rk: int = 2
     gamma: float = 5.0 / 3.0
     cfl: float = 0.4
@@ -447,12 +447,43 @@ class Solver:
             c = np.maximum(np.maximum(np.abs(lml), np.abs(lpl)),
                            np.maximum(np.abs(lmr), np.abs(lpr)))
             F = 0.5 * (FL + FR) - 0.5 * c * (UR - UL)
+        elif self.cfg.flux == "hllc":
+            F = self._hllc(PL, PR, UL, UR, FL, FR, np.minimum(lml, lmr), np.maximum(lpl, lpr), d)
         else:
             sl = np.minimum(lml, lmr)
             sr = np.maximum(lpl, lpr)
             mid = (sr * FL - sl * FR + sl * sr * (UR - UL)) / (sr - sl)
             F = np.where(sl >= 0.0, FL, np.where(sr <= 0.0, FR, mid))
         return np.moveaxis(F, -1, _ax(d))
+
+    def _hllc(self, PL, PR, UL, UR, FL, FR, sl, sr, d):
+        """HLLC flux for hydrodynamics (Toro, Spruce & Speares 1994; Toro 2009, ch. 10):
+        the HLL fan with the contact restored. Contact speed
+        S* = (p_R - p_L + rho_L u_L (S_L - u_L) - rho_R u_R (S_R - u_R))
+             / (rho_L (S_L - u_L) - rho_R (S_R - u_R)),
+        star states U*_K = rho_K (S_K - u_K)/(S_K - S*) [1, S* e_d + v_t, E_K/rho_K +
+        (S* - u_K)(S* + p_K / (rho_K (S_K - u_K)))], flux F_K + S_K (U*_K - U_K) on the side
+        of the contact that contains x/t = 0."""
+        if self.phys.name != "hd":
+            raise ValueError("HLLC is available for hydrodynamics only (paper Table 1)")
+        rl, rr = PL[0], PR[0]
+        ul, ur = PL[1 + d], PR[1 + d]
+        pl, pr = PL[4], PR[4]
+        ss = (pr - pl + rl * ul * (sl - ul) - rr * ur * (sr - ur)) / (rl * (sl - ul) - rr * (sr - ur))
+
+        def star(P, U, s):
+            r, u, p = P[0], P[1 + d], P[4]
+            fac = r * (s - u) / (s - ss)
+            Us = np.empty_like(U)
+            Us[0] = fac
+            for i in range(3):
+                Us[1 + i] = fac * P[1 + i]
+            Us[1 + d] = fac * ss
+            Us[4] = fac * (U[4] / r + (ss - u) * (ss + p / (r * (s - u))))
+            return Us
+        FsL = FL + sl * (star(PL, UL, sl) - UL)
+        FsR = FR + sr * (star(PR, UR, sr) - UR)
+        return np.where(sl >= 0.0, FL, np.where(ss >= 0.0, FsL, np.where(sr > 0.0, FsR, FR)))
 
     def _all_fluxes(self, ch):
         fluxes = {}

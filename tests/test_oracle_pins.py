@@ -559,3 +559,47 @@ def test_sedov_octant_shock_radius():
     r_exact = sedov_xi0(5.0 / 3.0) * (energy * tend ** 2 / 1.0) ** 0.2
     assert r_exact > 2.5 * r0
     assert abs(r_shock - r_exact) / r_exact < 0.05, (r_shock, r_exact)
+
+
+# ------------------------------------------------------------------------ HLLC (hd)
+def test_hllc_keeps_stationary_contact_exact_and_hll_smears_it():
+    """An isolated contact (density jump, uniform p, u = 0) is a steady solution; HLLC
+    resolves it exactly, HLL diffuses it (Toro 2009, ch. 10)."""
+    def ic(x, y, z):
+        x = np.asarray(x)
+        return np.stack([np.where(x < 0.5, 1.0, 0.2), 0 * x, 0 * x, 0 * x, 1 + 0 * x])
+    out = {}
+    for flux in ("hllc", "hll"):
+        s = Solver(Config(physics="hd", limiter="minmod", flux=flux, rk=2, base_blocks=(2, 1, 1),
+                          bc=(OUT, OUT, PER, PER, PER, PER)))
+        s.set_state(ic)
+        _, _, c0 = s.get_state()
+        for _ in range(5):
+            s.step()
+        out[flux] = np.abs(s.get_state()[2] - c0).max()
+    assert out["hllc"] < 1e-14
+    assert out["hll"] > 1e-3
+
+
+def test_hllc_sod_matches_exact_riemann():
+    errs = []
+    for nx in (2, 4, 8):
+        s = Solver(Config(physics="hd", limiter="minmod", flux="hllc", rk=2, base_blocks=(nx, 1, 1),
+                          bc=(OUT, OUT, PER, PER, PER, PER)))
+        s.set_state(W.sod_x)
+        run_to(s, 0.1)
+        rho = sod_profile(s, 0)
+        x = (np.arange(rho.size) + 0.5) / rho.size
+        rex, _, _ = riemann_sample(1.0, 0.0, 1.0, 0.125, 0.0, 0.1, 5.0 / 3.0, (x - 0.5) / 0.1)
+        errs.append(np.mean(np.abs(rho - rex)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert errs[-1] < 0.008 and min(orders) >= 0.6, (errs, orders)
+
+
+def test_hllc_consistency_and_uniform_state():
+    s = Solver(Config(physics="hd", limiter="vanleer", flux="hllc", rk=3, base_blocks=(1, 1, 1)))
+    s.set_state(W.uniform_state([1.3, 0.4, -0.7, 0.2, 2.0]))
+    _, _, c0 = s.get_state()
+    s.step()
+    _, _, c1 = s.get_state()
+    assert np.max(np.abs(c1 - c0)) < 1e-14
