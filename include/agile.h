@@ -52,7 +52,7 @@ typedef enum {
 
 enum { AGILE_HD = 0, AGILE_MHD_GLM = 1, AGILE_SRHD = 2 };      /* physics */
 enum { AGILE_MINMOD = 0, AGILE_VANLEER = 1 };                  /* limiter */
-enum { AGILE_TVDLF = 0, AGILE_HLL = 1 };                       /* Riemann flux */
+enum { AGILE_TVDLF = 0, AGILE_HLL = 1, AGILE_HLLC = 2 };        /* Riemann flux */
 enum { AGILE_PERIODIC = 0, AGILE_OUTFLOW = 1, AGILE_REFLECT = 2 }; /* boundaries */
 
 /* Device allocator: alloc(bytes, stream, ctx) returns device memory or NULL;
@@ -66,8 +66,8 @@ typedef struct {
 /* Problem description.
  *  physics        AGILE_HD | AGILE_MHD_GLM | AGILE_SRHD
  *  limiter        slope limiter of the piecewise-linear reconstruction on primitives
- *  flux           AGILE_HLL (hd, mhd) or AGILE_TVDLF (all); srhd supports TVDLF only
- *                 (paper Table 1)
+ *  flux           AGILE_TVDLF (all), AGILE_HLL (hd, mhd), AGILE_HLLC (hd); the
+ *                 solvers per module of paper Table 1
  *  rk             2 or 3: SSPRK2 (Heun) or SSPRK3 (Shu-Osher "threestep")
  *  real_bytes     8 (FP64 stencil) or 4 (FP32 stencil; FP64 kept for the SRHD primitive
  *                 recovery, the CFL reduction and the conserved sums)

@@ -20,7 +20,7 @@ NCELL = 4096
 
 PHYSICS = {"hd": 0, "mhd": 1, "srhd": 2}
 LIMITER = {"minmod": 0, "vanleer": 1}
-FLUX = {"tvdlf": 0, "hll": 1}
+FLUX = {"tvdlf": 0, "hll": 1, "hllc": 2}
 BC = {"periodic": 0, "outflow": 1, "reflect": 2}
 STATUS = {0: "AGILE_OK", 1: "AGILE_EINVAL", 2: "AGILE_ENOMEM", 3: "AGILE_EBUDGET",
           4: "AGILE_ECUDA", 5: "AGILE_ENOCONV", 6: "AGILE_EUNPHYS", 7: "AGILE_ETIMEOUT"}

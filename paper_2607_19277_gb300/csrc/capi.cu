@@ -329,11 +329,12 @@ agile_status agile_mesh_create(const agile_config* cfg, const agile_allocator* a
   if (!cfg || !out) return AGILE_EINVAL;
   *out = nullptr;
   if (cfg->physics < 0 || cfg->physics > 2 || (cfg->limiter != 0 && cfg->limiter != 1) ||
-      (cfg->flux != 0 && cfg->flux != 1) || (cfg->rk != 2 && cfg->rk != 3) ||
+      cfg->flux < 0 || cfg->flux > 2 || (cfg->rk != 2 && cfg->rk != 3) ||
       (cfg->real_bytes != 4 && cfg->real_bytes != 8) || !(cfg->gamma > 1.0) || !(cfg->cfl > 0.0) ||
       cfg->max_level < 1 || cfg->max_level > 12 || cfg->refine_nvars < 0 || cfg->refine_nvars > 9)
     return AGILE_EINVAL;
   if (cfg->physics == AGILE_SRHD && cfg->flux != AGILE_TVDLF) return AGILE_EINVAL;
+  if (cfg->flux == AGILE_HLLC && cfg->physics != AGILE_HD) return AGILE_EINVAL;
   for (int d = 0; d < 3; ++d) {
     if (cfg->base_blocks[d] < 1 || cfg->base_blocks[d] > 4096 || !(cfg->xmax[d] > cfg->xmin[d]))
       return AGILE_EINVAL;
@@ -941,7 +942,8 @@ agile_status agile_batch_create(const agile_config* cfgs, int nsolve, const agil
         c.glm_alpha != c0.glm_alpha || c.max_level != 1)
       return AGILE_EINVAL;
     // validate each configuration like a single mesh (host-side checks only)
-    if (c.physics < 0 || c.physics > 2 || (c.limiter != 0 && c.limiter != 1) || (c.flux != 0 && c.flux != 1) ||
+    if (c.physics < 0 || c.physics > 2 || (c.limiter != 0 && c.limiter != 1) || c.flux < 0 || c.flux > 2 ||
+        (c.flux == AGILE_HLLC && c.physics != AGILE_HD) ||
         (c.rk != 2 && c.rk != 3) || (c.real_bytes != 4 && c.real_bytes != 8) || !(c.gamma > 1.0) ||
         !(c.cfl > 0.0) || (c.physics == AGILE_SRHD && c.flux != AGILE_TVDLF))
       return AGILE_EINVAL;

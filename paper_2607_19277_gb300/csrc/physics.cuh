@@ -17,7 +17,7 @@
 namespace agile {
 
 enum : int { LIM_MINMOD = 0, LIM_VANLEER = 1 };
-enum : int { FLUX_TVDLF = 0, FLUX_HLL = 1 };
+enum : int { FLUX_TVDLF = 0, FLUX_HLL = 1, FLUX_HLLC = 2 };
 enum : int { ST_ENOCONV = 1, ST_EUNPHYS = 2 };
 
 // Equation parameters in the stencil precision R, derived once per CTA (the FP64 copy of
@@ -315,7 +315,35 @@ __device__ __forceinline__ void riemann(R* pl, R* pr, R* f, const PhysParamsT<R>
   R lml, lpl, lmr, lpr;
   P::template lambdas<D>(pl, lml, lpl, pp);
   P::template lambdas<D>(pr, lmr, lpr, pp);
-  if (FLUX == FLUX_TVDLF) {
+  if constexpr (FLUX == FLUX_HLLC) {
+    // HLLC (Toro, Spruce & Speares 1994) for hydrodynamics: the HLL fan with the contact
+    // restored; star states U*_K = rho_K (S_K - u_K)/(S_K - S*) [1, S* e_d + v_t,
+    // E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))], flux F_K + S_K (U*_K - U_K).
+    const R sl = rmin(lml, lmr), sr = rmax(lpl, lpr);
+    const R rl = pl[0], rr = pr[0], vl = pl[1 + D], vr = pr[1 + D];
+    const R ml = rl * (sl - vl), mr = rr * (sr - vr);
+    const R ss = (pr[4] - pl[4] + ml * vl - mr * vr) / (ml - mr);
+    const R fl_ = ml / (sl - ss), fr_ = mr / (sr - ss);
+    R usl[NV], usr[NV];
+    usl[0] = fl_;
+    usr[0] = fr_;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      usl[1 + i] = fl_ * pl[1 + i];
+      usr[1 + i] = fr_ * pr[1 + i];
+    }
+    usl[1 + D] = fl_ * ss;
+    usr[1 + D] = fr_ * ss;
+    usl[4] = fl_ * (ul[4] / rl + (ss - vl) * (ss + pl[4] / ml));
+    usr[4] = fr_ * (ur[4] / rr + (ss - vr) * (ss + pr[4] / mr));
+    const bool left = sl >= R(0), star_l = ss >= R(0), star_r = sr > R(0);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const R fsl = fl[v] + sl * (usl[v] - ul[v]);
+      const R fsr = fr[v] + sr * (usr[v] - ur[v]);
+      f[v] = left ? fl[v] : (star_l ? fsl : (star_r ? fsr : fr[v]));
+    }
+  } else if (FLUX == FLUX_TVDLF) {
     const R c = rmax(rmax(rabs(lml), rabs(lpl)), rmax(rabs(lmr), rabs(lpr)));
 #pragma unroll
     for (int v = 0; v < NV; ++v) f[v] = R(0.5) * (fl[v] + fr[v]) - R(0.5) * c * (ur[v] - ul[v]);

@@ -31,6 +31,8 @@ static cudaError_t go(const StageArgs& a, cudaStream_t s) {
 
 template <typename R>
 static cudaError_t go_r(int lim, int flux, const StageArgs& a, cudaStream_t s) {
+  if (flux == FLUX_HLLC)   // hydrodynamics only (paper Table 1)
+    return lim == LIM_MINMOD ? go<R, LIM_MINMOD, FLUX_HLLC>(a, s) : go<R, LIM_VANLEER, FLUX_HLLC>(a, s);
   if (lim == LIM_MINMOD)
     return flux == FLUX_HLL ? go<R, LIM_MINMOD, FLUX_HLL>(a, s) : go<R, LIM_MINMOD, FLUX_TVDLF>(a, s);
   return flux == FLUX_HLL ? go<R, LIM_VANLEER, FLUX_HLL>(a, s) : go<R, LIM_VANLEER, FLUX_TVDLF>(a, s);

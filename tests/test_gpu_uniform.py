@@ -124,3 +124,29 @@ def test_set_get_state_round_trip_and_sums():
     s = m.conserved_sums()
     assert np.max(np.abs(s - o.conserved_sums())) <= 1e-14 * np.abs(s).max()
     m.close()
+
+
+@pytest.mark.parametrize("rb,tol", [(8, TOL_FP64), (4, 2e-5)])
+def test_hd_hllc_sod_and_smooth(rb, tol):
+    """HLLC (hydrodynamics, paper Table 1) against the oracle on Sod and a smooth state."""
+    for ic, lim in ((W.sod_x, "minmod"), (W.random_smooth(5, 17, "hd"), "vanleer")):
+        spec = dict(physics="hd", limiter=lim, flux="hllc", rk=3, base_blocks=(2, 2, 1),
+                    bc=(OUT, OUT, PER, PER, REF, REF))
+        m, o, g, r, lev, _ = run_both(spec, ic, 4, real_bytes=rb)
+        assert rel_l1(g, r).max() < (tol if ic is not W.sod_x or rb == 8 else 1e-4)
+        m.close()
+
+
+def test_hd_hllc_stationary_contact_exact_on_gpu():
+    def ic(x, y, z):
+        x = np.asarray(x)
+        return np.stack([np.where(x < 0.5, 1.0, 0.2), 0 * x, 0 * x, 0 * x, 1 + 0 * x])
+    spec = dict(physics="hd", limiter="minmod", flux="hllc", rk=2, base_blocks=(2, 1, 1),
+                bc=(OUT, OUT, PER, PER, PER, PER))
+    m = gpu_mesh(spec)
+    m.set_state(ic)
+    _, _, c0 = m.get_state()
+    for _ in range(5):
+        m.step(0.0)
+    assert np.abs(m.get_state()[2] - c0).max() < 1e-14
+    m.close()
