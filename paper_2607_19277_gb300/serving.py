@@ -1,0 +1,207 @@
+"""Request loop for independent solves: continuous admission against a device-memory budget.
+
+Requests (physics, grid side, number of steps, seeded initial condition) arrive over time.
+The loop admits a waiting request as soon as its device pools fit in the budget, keeps the
+pools of every admitted solve resident, and advances all admitted solves together: each
+solve runs on its own CUDA stream, so the stage kernels of different requests overlap on the
+GPU while the host thread only enqueues work. A finished solve's result is read back and its
+memory returns to the budget, which admits the next arrivals. Latency = completion time -
+arrival time; the report gives p50 / p99 latency beside the aggregate zone-updates/s.
+
+Every numerical step runs in libagile.so (agile_step with the on-device CFL dt); this module
+only schedules. A solve's result does not depend on what else is running (the kernels of
+one mesh read and write only that mesh's pools).
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import agile, workloads as W
+
+PHYS = ("hd", "mhd", "srhd")
+
+
+@dataclass
+class Request:
+    rid: int
+    physics: str
+    side: int            # cells per edge (multiple of 16), uniform periodic grid
+    steps: int
+    seed: int
+    arrival: float       # seconds after the start of the loop
+    # filled by the server
+    admitted: float = -1.0
+    finished: float = -1.0
+    result: np.ndarray = None
+
+
+def scheme(physics: str, real_bytes: int, side: int):
+    """The per-physics scheme of the request stream (paper Table 1 solvers)."""
+    bb = (side // 16,) * 3
+    if physics == "hd":
+        return agile.make_config(physics="hd", limiter="vanleer", flux="hllc", rk=3, real_bytes=real_bytes,
+                                 base_blocks=bb)
+    if physics == "mhd":
+        return agile.make_config(physics="mhd", limiter="vanleer", flux="hll", rk=3, real_bytes=real_bytes,
+                                 base_blocks=bb)
+    return agile.make_config(physics="srhd", limiter="minmod", flux="tvdlf", rk=2, gamma=4.0 / 3.0,
+                             real_bytes=real_bytes, base_blocks=bb)
+
+
+def initial_condition(req: Request):
+    if req.physics == "hd":
+        return W.random_smooth(5, req.seed, "hd")
+    if req.physics == "mhd":
+        return W.orszag_tang_3d(req.side, seed=req.seed)
+    return W.srhd_shells(req.seed, req.side, lorentz_max=2.0, p_amb=0.1, smooth=True)
+
+
+def request_stream(n: int, rate: float, sides=(32, 64, 128, 256), steps=(50, 500),
+                   seed: int = W.SEED_BASE + 5):
+    """n requests with Poisson arrivals (mean rate per second; exponential gaps from
+    SplitMix64), physics uniform over hd / mhd / srhd, side uniform over `sides`, steps
+    uniform integer in [steps[0], steps[1]]."""
+    u = W.uniform01(seed, np.arange(4 * n)).reshape(n, 4)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += -math.log(1.0 - u[i, 0]) / rate
+        out.append(Request(rid=i, physics=PHYS[min(2, int(u[i, 1] * 3))],
+                           side=sides[min(len(sides) - 1, int(u[i, 2] * len(sides)))],
+                           steps=steps[0] + min(steps[1] - steps[0], int(u[i, 3] * (steps[1] - steps[0] + 1))),
+                           seed=seed + 1000 + i, arrival=t))
+    return out
+
+
+def pool_bytes(req: Request, real_bytes: int) -> int:
+    """Device bytes a resident solve holds: its state pools (rk + 1 buffers incl. U^n ...
+    one per stage input) plus per-block descriptors and staging, rounded up generously."""
+    nblk = (req.side // 16) ** 3
+    nvar = {"hd": 5, "mhd": 9, "srhd": 7}[req.physics]
+    rk = 2 if req.physics == "srhd" else 3
+    pools = rk * nblk * nvar * 4096 * real_bytes
+    staging = min(256, nblk) * nvar * 4096 * 8      # initial-condition upload chunk
+    return pools + staging + nblk * 512 + (1 << 20)
+
+
+@dataclass
+class Report:
+    requests: list
+    wall_s: float
+    zone_updates: float
+    max_resident_bytes: int
+    max_concurrent: int
+    latencies: list = field(default_factory=list)
+
+    def summary(self):
+        lat = sorted(self.latencies)
+
+        def pct(p):
+            return lat[min(len(lat) - 1, max(0, int(math.ceil(p * len(lat))) - 1))] if lat else None
+        return {"requests": len(self.requests), "wall_s": self.wall_s,
+                "zone_updates_per_s": self.zone_updates / self.wall_s if self.wall_s > 0 else None,
+                "latency_p50_s": pct(0.50), "latency_p99_s": pct(0.99),
+                "max_resident_bytes": self.max_resident_bytes, "max_concurrent": self.max_concurrent}
+
+
+class Server:
+    """Continuous admission of solves against a device-memory budget (bytes)."""
+
+    def __init__(self, budget_bytes: int, real_bytes: int = 4, steps_per_poll: int = 4,
+                 keep_results: bool = False):
+        import torch
+        self.torch = torch
+        self.budget = int(budget_bytes)
+        self.rb = real_bytes
+        self.steps_per_poll = steps_per_poll
+        self.keep = keep_results
+
+    def run(self, requests, time_scale: float = 1.0) -> Report:
+        """Serve `requests` (arrival times scaled by time_scale); returns the report."""
+        torch = self.torch
+        pending = sorted(requests, key=lambda r: r.arrival)
+        waiting = []
+        active = []            # [req, mesh, stream, steps_left, done_event]
+        used = 0
+        max_used = 0
+        max_conc = 0
+        zones = 0.0
+        t0 = time.perf_counter()
+        k = 0
+        while pending or waiting or active:
+            now = time.perf_counter() - t0
+            while k < len(pending) and pending[k].arrival * time_scale <= now:
+                waiting.append(pending[k])
+                k += 1
+            # admit in arrival order while the budget allows (first fit keeps order fair)
+            i = 0
+            while i < len(waiting):
+                r = waiting[i]
+                need = pool_bytes(r, self.rb)
+                if need > self.budget:
+                    raise ValueError("request %d needs %d bytes, more than the budget" % (r.rid, need))
+                if used + need <= self.budget:
+                    stream = torch.cuda.Stream()
+                    with torch.cuda.stream(stream):
+                        mesh = agile.Mesh(scheme(r.physics, self.rb, r.side), stream=stream)
+                        mesh.set_state(initial_condition(r))
+                    r.admitted = time.perf_counter() - t0
+                    active.append([r, mesh, stream, r.steps, None])
+                    used += need
+                    max_used = max(max_used, used)
+                    waiting.pop(i)
+                    continue
+                i += 1
+            max_conc = max(max_conc, len(active))
+            if not active:
+                if k < len(pending):
+                    time.sleep(max(0.0, pending[k].arrival * time_scale - (time.perf_counter() - t0)))
+                continue
+            # enqueue a few steps of every active solve, each on its own stream
+            for a in active:
+                r, mesh, stream, left, ev = a
+                if left > 0:
+                    n = min(self.steps_per_poll, left)
+                    for _ in range(n):
+                        mesh.step(0.0)
+                    a[3] = left - n
+                    if a[3] == 0:
+                        ev = torch.cuda.Event()
+                        ev.record(stream)
+                        a[4] = ev
+            # retire finished solves
+            still = []
+            for a in active:
+                r, mesh, stream, left, ev = a
+                if left == 0 and ev is not None and ev.query():
+                    mesh.sync()
+                    if self.keep:
+                        r.result = mesh.get_state()[2]
+                    r.finished = time.perf_counter() - t0
+                    stages = 2 if r.physics == "srhd" else 3
+                    zones += float(r.side ** 3) * stages * r.steps
+                    mesh.close()
+                    used -= pool_bytes(r, self.rb)
+                else:
+                    still.append(a)
+            active = still
+        wall = time.perf_counter() - t0
+        rep = Report(requests=requests, wall_s=wall, zone_updates=zones, max_resident_bytes=max_used,
+                     max_concurrent=max_conc)
+        rep.latencies = [r.finished - r.arrival * time_scale for r in requests]
+        return rep
+
+
+def run_alone(req: Request, real_bytes: int = 4):
+    """The same request on an idle GPU (reference for the 'same alone and in the mix' check)."""
+    m = agile.Mesh(scheme(req.physics, real_bytes, req.side))
+    m.set_state(initial_condition(req))
+    for _ in range(req.steps):
+        m.step(0.0)
+    out = m.get_state()[2]
+    m.close()
+    return out

@@ -1,0 +1,45 @@
+"""Serving loop: the seeded request stream (CPU) and, on the GPU, continuous admission
+against a memory budget with overlapping solves whose results equal each request run alone
+(bit for bit: a mesh's kernels touch only its own pools)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2607_19277_gb300 import serving
+
+
+def test_request_stream_is_seeded_poisson():
+    reqs = serving.request_stream(4000, rate=50.0)
+    assert reqs == serving.request_stream(4000, rate=50.0) or all(
+        a.arrival == b.arrival for a, b in zip(reqs, serving.request_stream(4000, rate=50.0)))
+    gaps = np.diff([0.0] + [r.arrival for r in reqs])
+    assert abs(gaps.mean() - 1 / 50.0) < 0.05 / 50.0 * 4
+    # exponential gaps: std equals the mean
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.08
+    assert {r.physics for r in reqs} == {"hd", "mhd", "srhd"}
+    assert {r.side for r in reqs} == {32, 64, 128, 256}
+    assert min(r.steps for r in reqs) >= 50 and max(r.steps for r in reqs) <= 500
+
+
+def test_pool_bytes_cover_the_pools():
+    r = serving.Request(rid=0, physics="mhd", side=64, steps=10, seed=1, arrival=0.0)
+    assert serving.pool_bytes(r, 4) >= 3 * 64 * 9 * 4096 * 4
+
+
+@pytest.mark.gpu
+def test_serving_admits_within_budget_overlaps_and_matches_alone():
+    reqs = [serving.Request(rid=i, physics=("hd", "mhd", "srhd")[i % 3], side=(32, 48)[i % 2],
+                            steps=3 + (i % 4), seed=500 + i, arrival=0.002 * i) for i in range(7)]
+    sizes = sorted(serving.pool_bytes(r, 4) for r in reqs)
+    budget = sizes[-1] + sizes[-2] + sizes[-3]       # room for about three at once
+    srv = serving.Server(budget, real_bytes=4, steps_per_poll=1, keep_results=True)
+    rep = srv.run(reqs)
+    s = rep.summary()
+    assert rep.max_resident_bytes <= budget
+    assert rep.max_concurrent >= 2
+    assert s["latency_p99_s"] >= s["latency_p50_s"] > 0
+    for r in reqs:
+        assert r.finished > 0 and r.admitted >= r.arrival - 1e-9
+        alone = serving.run_alone(r, real_bytes=4)
+        assert np.array_equal(r.result, alone), r.rid
