@@ -120,8 +120,9 @@ class Server:
         self.steps_per_poll = steps_per_poll
         self.keep = keep_results
 
-    def run(self, requests, time_scale: float = 1.0) -> Report:
-        """Serve `requests` (arrival times scaled by time_scale); returns the report."""
+    def run(self, requests, time_scale: float = 1.0, max_wall_s: float = 3600.0) -> Report:
+        """Serve `requests` (arrival times scaled by time_scale); returns the report.
+        Raises TimeoutError if the loop runs longer than max_wall_s."""
         torch = self.torch
         pending = sorted(requests, key=lambda r: r.arrival)
         waiting = []
@@ -132,8 +133,12 @@ class Server:
         zones = 0.0
         t0 = time.perf_counter()
         k = 0
-        while pending or waiting or active:
+        while k < len(pending) or waiting or active:
             now = time.perf_counter() - t0
+            if now > max_wall_s:
+                for a in active:
+                    a[1].close()
+                raise TimeoutError("serving loop exceeded %.0f s" % max_wall_s)
             while k < len(pending) and pending[k].arrival * time_scale <= now:
                 waiting.append(pending[k])
                 k += 1

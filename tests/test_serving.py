@@ -34,7 +34,7 @@ def test_serving_admits_within_budget_overlaps_and_matches_alone():
     sizes = sorted(serving.pool_bytes(r, 4) for r in reqs)
     budget = sizes[-1] + sizes[-2] + sizes[-3]       # room for about three at once
     srv = serving.Server(budget, real_bytes=4, steps_per_poll=1, keep_results=True)
-    rep = srv.run(reqs)
+    rep = srv.run(reqs, max_wall_s=120.0)
     s = rep.summary()
     assert rep.max_resident_bytes <= budget
     assert rep.max_concurrent >= 2
@@ -43,3 +43,62 @@ def test_serving_admits_within_budget_overlaps_and_matches_alone():
         assert r.finished > 0 and r.admitted >= r.arrival - 1e-9
         alone = serving.run_alone(r, real_bytes=4)
         assert np.array_equal(r.result, alone), r.rid
+
+
+def test_server_loop_terminates_without_gpu_work(monkeypatch):
+    """The scheduling loop ends when every request is retired (host logic, fake meshes)."""
+    class FakeMesh:
+        def __init__(self, cfg, stream=None):
+            self.steps = 0
+
+        def set_state(self, ic):
+            pass
+
+        def step(self, dt=0.0):
+            self.steps += 1
+
+        def sync(self):
+            pass
+
+        def get_state(self):
+            return None, None, np.zeros(1)
+
+        def close(self):
+            pass
+
+    class FakeEvent:
+        def record(self, stream):
+            pass
+
+        def query(self):
+            return True
+
+    class FakeTorch:
+        class cuda:
+            Event = FakeEvent
+
+            @staticmethod
+            def Stream():
+                return None
+
+            class stream:
+                def __init__(self, s):
+                    pass
+
+                def __enter__(self):
+                    return self
+
+                def __exit__(self, *a):
+                    return False
+
+    monkeypatch.setattr(serving.agile, "Mesh", FakeMesh)
+    reqs = serving.request_stream(20, rate=5000.0, sides=(32, 64), steps=(2, 5))
+    srv = serving.Server.__new__(serving.Server)
+    srv.torch = FakeTorch
+    srv.budget = 3 * max(serving.pool_bytes(r, 4) for r in reqs)
+    srv.rb = 4
+    srv.steps_per_poll = 2
+    srv.keep = False
+    rep = srv.run(reqs, max_wall_s=30.0)
+    assert all(r.finished >= 0 for r in reqs)
+    assert rep.max_resident_bytes <= srv.budget and rep.max_concurrent >= 1
