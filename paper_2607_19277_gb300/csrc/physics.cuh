@@ -229,13 +229,15 @@ struct SrhdPhys {
     if (!(xi > lo && xi < hi)) xi = 0.5 * (lo + hi);
     bool ok = false;
     for (int it = 0; it < 50; ++it) {
-      const double w = s2 / (xi * xi);
-      const double ig2 = 1.0 - w;
-      const double lor = 1.0 / sqrt(ig2);
-      const double rho = D / lor;
+      // per iteration: one reciprocal, one reciprocal square root, one divide
+      const double ixi = 1.0 / xi;
+      const double w = s2 * ixi * ixi;          // v^2
+      const double ig2 = 1.0 - w;               // 1 / Gamma^2
+      const double lor = rsqrt(ig2);            // Gamma
+      const double rho = D * (ig2 * lor);       // D / Gamma
       const double pr = gm * (xi * ig2 - rho);
       const double f = xi - pr - E;
-      const double df = 1.0 - gm * (1.0 + w - D * lor * w / xi);
+      const double df = 1.0 - gm * (1.0 + w - D * lor * w * ixi);
       if (f < 0.0) lo = xi; else hi = xi;
       double xn = xi - f / df;
       if (!(xn >= lo && xn <= hi)) xn = 0.5 * (lo + hi);
@@ -244,11 +246,12 @@ struct SrhdPhys {
       if (conv) { ok = true; break; }
     }
     if (!ok) st |= ST_ENOCONV;
-    const double w = s2 / (xi * xi);
+    const double ixi = 1.0 / xi;
+    const double w = s2 * ixi * ixi;
     const double ig2 = 1.0 - w;
-    const double lor = 1.0 / sqrt(ig2);
-    const double rho = D / lor;
-    const double sc = lor / xi;
+    const double lor = rsqrt(ig2);
+    const double rho = D * (ig2 * lor);
+    const double sc = lor * ixi;
     p[0] = (R)rho;
     p[1] = (R)(mx * sc);
     p[2] = (R)(my * sc);

@@ -204,6 +204,29 @@ def srhd_shells(seed: int, n_cells: int, n_shells=None, rho_amb=1.0, p_amb=0.01,
     return ic
 
 
+def double_kelvin_helmholtz(rho_in=2.0, rho_out=1.0, v0=0.5, p0=2.5, width=0.02, amp=0.01,
+                            seed: int = SEED_BASE + 6):
+    """Doubly periodic shear flow on [0,1]^3: v_x = +v0 outside 0.25 < y < 0.75 and -v0
+    inside (tanh profiles of the given width), density rho_in inside and rho_out outside,
+    uniform pressure, and a small v_y perturbation amp sin(4 pi x) plus a seeded phase per
+    z-plane (a stand-in for the double Kelvin-Helmholtz benchmark of Section 3.1, whose
+    exact setup is not given)."""
+    phase = 2.0 * math.pi * uniform01(seed, np.arange(1))[0]
+
+    def ic(x, y, z):
+        x = np.asarray(x, dtype=np.float64)
+        y = np.asarray(y, dtype=np.float64)
+        z = np.asarray(z, dtype=np.float64)
+        inner = 0.5 * (np.tanh((y - 0.25) / width) - np.tanh((y - 0.75) / width))
+        prim = np.zeros((5, x.size))
+        prim[0] = rho_out + (rho_in - rho_out) * inner
+        prim[1] = v0 * (1.0 - 2.0 * inner)
+        prim[2] = amp * np.sin(4.0 * math.pi * x + phase) * (1.0 + 0.1 * np.sin(2.0 * math.pi * z))
+        prim[4] = p0
+        return prim
+    return ic
+
+
 def uniform_state(prim_values):
     """A spatially uniform state with the given primitive vector."""
     pv = np.asarray(prim_values, dtype=np.float64)
