@@ -405,6 +405,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-paper-scheme", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -500,10 +501,11 @@ def main():
                                            "(Gaussian profile 3 cells wide) Gamma <= 2, TVDLF minmod SSPRK2")
         except Exception as e:   # report, do not lose the headline line
             line["batched"] = {"error": str(e)}
-    try:
-        line["paper_scheme_hd"] = run_paper_scheme()
-    except Exception as e:
-        line["paper_scheme_hd"] = {"error": str(e)}
+    if not args.no_paper_scheme:
+        try:
+            line["paper_scheme_hd"] = run_paper_scheme()
+        except Exception as e:
+            line["paper_scheme_hd"] = {"error": str(e)}
     if not args.no_serving:
         try:
             line["serving"] = run_serving()
