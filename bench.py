@@ -145,6 +145,27 @@ FP32_LANES = 128     # FP32 FMA lanes per SM
 FP64_LANES = 2       # FP64 FMA lanes per SM on GB300 (1.25 TFLOP/s measured at 2.07 GHz)
 
 
+# DRAM bytes (read + write) per stage launch of the FP32 MHD stage kernel on this workload,
+# from one ncu capture of the three stage launches of one SSPRK3 step (1.486, 2.160 and
+# 2.096 GB), averaged; valid only while the kernel sources hash to STAGE_SRC_DIGEST.
+STAGE_TRAFFIC_BYTES = (1.486e9 + 2.160e9 + 2.096e9) / 3
+STAGE_SRC_DIGEST = "dac5dd684bf9b47a"
+STAGE_SRC = ("kernels.cuh", "physics.cuh", "stage_mhd.cu")
+
+
+def stage_traffic():
+    """Measured per-launch DRAM traffic, or None when the kernel changed since the capture."""
+    import hashlib
+    h = hashlib.sha256()
+    try:
+        for f in STAGE_SRC:
+            with open(os.path.join(ROOT, "paper_2607_19277_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    return STAGE_TRAFFIC_BYTES if h.hexdigest()[:16] == STAGE_SRC_DIGEST else None
+
+
 def alu_peak_tflops(lanes, mhz):
     """Peak flop rate from unit counts and the SM clock seen during the run."""
     return SMS * lanes * 2 * mhz * 1e6 / 1e12
@@ -455,6 +476,7 @@ def main():
             torch.distributed.destroy_process_group()
         return
     steps = args.steps
+    traffic = stage_traffic()
     line = {
         "metric": METRIC, "value": s32["value"], "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": args.warmup, "ms_per_step": s32["ms_per_step"], "higher_is_better": True,
@@ -464,14 +486,16 @@ def main():
                    "l2": "state 604 MB (fp32) / 1.2 GB (fp64) per buffer > 129 MB L2, no flush",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "alu", "achieved": s32["tflops"], "peak": s32["peak_alu"],
-                     "unit": "TFLOP/s", "frac": s32["tflops"] / s32["peak_alu"], "traffic": None,
+                     "unit": "TFLOP/s", "frac": s32["tflops"] / s32["peak_alu"], "traffic": traffic,
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read+write, mean of the 3 stages)",
+                     "algorithmic_bytes_per_launch": s32["bytes_per_zone"] * N_SIDE ** 3,
                      "kernel": "stage_kernel<MhdPhys,float,vanleer,hll>",
                      "flops_per_zone_update": MHD_HLL_VL_FLOPS,
                      "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % s32["mhz"],
                      "launch_ms": s32["launch_ms"],
                      "stage_kernel_share_of_step": s32["stage_share"]},
         "hbm_roofline": {"bound": "hbm", "achieved": s32["achieved"], "peak": hbm, "unit": "GB/s",
-                         "frac": s32["achieved"] / hbm,
+                         "frac": s32["achieved"] / hbm, "traffic": traffic,
                          "bytes_per_zone_update": s32["bytes_per_zone"],
                          "peak_kind": peak_kind + " hbm_gbs"},
         "e2e": {"value": s32["e2e"], "unit": UNIT,
