@@ -10,8 +10,10 @@ follows the paper's Section 2.3:
            flux is the HD get_flux of the paper's flux listing (Section 2.3).
   * mhd  : Eqs. 11-13 with GLM (Eq. 14), e = p/(gamma-1) + rho v^2/2 + B^2/2 (units absorb
            4 pi), Section 2.3.3.
-  * srhd : Eqs. 15-19, ideal-gas EOS Eq. 20, con2prim as a 1-D root find in
-           xi = Gamma^2 rho h (Section 2.3.4).
+  * srhd : Eqs. 15-19, con2prim as a 1-D root find in xi = Gamma^2 rho h (Section
+           2.3.4), closed by the ideal-gas enthalpy (Eq. 20) or by the Synge gas (Eq. 21)
+           in Mathews' approximation, which Section 2.3.4 names instead of the Bessel
+           functions: h = 5/2 theta + sqrt(9/4 theta^2 + 1), theta = p / rho.
 """
 from __future__ import annotations
 
@@ -162,7 +164,13 @@ class MHD:
 
 
 class SRHD:
-    """Special-relativistic hydro, U = (D, m, tau), P = (rho, u = Gamma v, p), A = (xi, Gamma)."""
+    """Special-relativistic hydro, U = (D, m, tau), P = (rho, u = Gamma v, p), A = (xi, Gamma).
+
+    eos = "ideal": h = 1 + gamma/(gamma-1) theta (Eq. 20).
+    eos = "synge": Mathews' approximation of the Synge gas (Eq. 21 without the Bessel
+    functions): h = 5/2 theta + sqrt(9/4 theta^2 + 1). It tends to the ideal gas with
+    gamma = 5/3 as theta -> 0 and to gamma = 4/3 as theta -> infinity; gamma is unused.
+    """
 
     name = "srhd"
     nvar = 5
@@ -171,13 +179,35 @@ class SRHD:
     max_iter = 50
     tol = 1e-14
 
-    def __init__(self, gamma: float):
+    def __init__(self, gamma: float, eos: str = "ideal"):
+        if eos not in ("ideal", "synge"):
+            raise ValueError("eos must be 'ideal' or 'synge'")
         self.gamma = float(gamma)
+        self.eos = eos
 
     def enthalpy(self, rho, p):
-        """Ideal-gas specific enthalpy, Eq. 20."""
+        """Specific enthalpy h(rho, p): Eq. 20 (ideal gas) or the approximate Synge gas."""
+        theta = p / rho
+        if self.eos == "synge":
+            return 2.5 * theta + np.sqrt(2.25 * theta * theta + 1.0)
         g = self.gamma
-        return 1.0 + g / (g - 1.0) * p / rho
+        return 1.0 + g / (g - 1.0) * theta
+
+    def theta_of_h(self, h):
+        """Inverse of h(theta) for the approximate Synge gas: (h - 5/2 theta)^2 =
+        9/4 theta^2 + 1 gives 4 theta^2 - 5 h theta + h^2 - 1 = 0; the root with theta = 0
+        at h = 1 is theta = (5 h - sqrt(9 h^2 + 16)) / 8."""
+        return (5.0 * h - np.sqrt(9.0 * h * h + 16.0)) / 8.0
+
+    def sound_speed2(self, rho, p):
+        """Squared sound speed: gamma p / (rho h) (ideal gas); for the approximate Synge
+        gas theta (5 h - 8 theta) / (3 h (h - theta)) (the isentropic derivative dp/de
+        of that enthalpy, as in Mignone & McKinney 2007)."""
+        h = self.enthalpy(rho, p)
+        theta = p / rho
+        if self.eos == "synge":
+            return theta * (5.0 * h - 8.0 * theta) / (3.0 * h * (h - theta))
+        return self.gamma * theta / h
 
     def prim2cons(self, P):
         """Eq. 17 evaluated from the primitives of Eq. 18."""
@@ -199,25 +229,39 @@ class SRHD:
         A[1] = lor
         return A
 
+    def _pressure(self, xi, D, w, lor):
+        """p(xi) and dp/dxi at fixed (D, S), with v^2 = w = S^2/xi^2, Gamma = lor and
+        rho = D / Gamma (so d rho/d xi = D Gamma w / xi, and h = xi / (D Gamma) has
+        dh/dxi = Gamma / D)."""
+        ig2 = 1.0 - w
+        rho = D / lor
+        drho = D * lor * w / xi
+        if self.eos == "synge":
+            h = xi / (D * lor)
+            theta = self.theta_of_h(h)
+            dtheta = (5.0 - 9.0 * h / np.sqrt(9.0 * h * h + 16.0)) / 8.0
+            return rho * theta, theta * drho + dtheta
+        gm = (self.gamma - 1.0) / self.gamma
+        return gm * (xi * ig2 - rho), gm * (1.0 + w - drho)
+
     def cons2prim(self, U, aux=None):
         """Primitive recovery as a root find in xi = Gamma^2 rho h (Section 2.3.4).
 
-        With E = tau + D and S = |m|: v^2 = S^2/xi^2, Gamma = (1 - v^2)^-1/2, rho = D/Gamma
-        and, for the ideal gas, p = (gamma-1)/gamma (xi/Gamma^2 - rho); energy gives
-        f(xi) = xi - p(xi) - E = 0. The root lies in [E, gamma E] (p >= 0 and
-        p <= (gamma-1)/gamma xi). Newton's method with the analytic derivative runs from
-        the stored auxiliary xi (when it lies inside the bracket, else the bracket's
-        midpoint); a step leaving the closed bracket is replaced by bisection. It stops when
+        With E = tau + D and S = |m|: v^2 = S^2/xi^2, Gamma = (1 - v^2)^-1/2, rho = D/Gamma,
+        h = xi / (Gamma^2 rho) and p = p(rho, h) from the EOS; energy gives
+        f(xi) = xi - p(xi) - E = 0. The root lies in [E, k E] with k = gamma for the ideal
+        gas (p <= (gamma-1)/gamma xi) and k = 4/3 for the approximate Synge gas (h >= 4
+        theta, so p <= xi/4). Newton's method with the analytic derivative runs from the
+        stored auxiliary xi (when it lies inside the bracket, else the bracket's midpoint);
+        a step leaving the closed bracket is replaced by bisection. It stops when
         |dxi| <= 1e-14 xi, at most 50 iterations. Returns (P, A) and raises on failure.
         """
-        g = self.gamma
-        gm = (g - 1.0) / g
         D = U[0]
         m = U[1:4]
         S2 = m[0] * m[0] + m[1] * m[1] + m[2] * m[2]
         E = U[4] + D
         lo = E.copy()
-        hi = g * E
+        hi = (4.0 / 3.0 if self.eos == "synge" else self.gamma) * E
         if aux is not None:
             xi = np.where((aux[0] > lo) & (aux[0] < hi), aux[0], 0.5 * (lo + hi))
         else:
@@ -225,12 +269,9 @@ class SRHD:
         done = np.zeros(D.shape, dtype=bool)
         for _ in range(self.max_iter):
             w = S2 / (xi * xi)                   # v^2
-            ig2 = 1.0 - w                        # 1/Gamma^2
-            lor = 1.0 / np.sqrt(ig2)
-            rho = D / lor
-            p = gm * (xi * ig2 - rho)
+            lor = 1.0 / np.sqrt(1.0 - w)
+            p, dp = self._pressure(xi, D, w, lor)
             f = xi - p - E
-            dp = gm * (1.0 + w - D * lor * w / xi)   # dp/dxi
             df = 1.0 - dp
             lo = np.where(f < 0.0, xi, lo)
             hi = np.where(f < 0.0, hi, xi)
@@ -245,13 +286,11 @@ class SRHD:
         if not done.all():
             raise FloatingPointError("srhd con2prim did not converge")
         w = S2 / (xi * xi)
-        ig2 = 1.0 - w
-        lor = 1.0 / np.sqrt(ig2)
-        rho = D / lor
+        lor = 1.0 / np.sqrt(1.0 - w)
         P = np.empty_like(U)
-        P[0] = rho
+        P[0] = D / lor
         P[1:4] = m * (lor / xi)                  # u = Gamma v, v = m / xi
-        P[4] = gm * (xi * ig2 - rho)
+        P[4] = self._pressure(xi, D, w, lor)[0]
         A = np.empty((2,) + U.shape[1:])
         A[0] = xi
         A[1] = lor
@@ -271,17 +310,22 @@ class SRHD:
         return F
 
     def lambdas(self, P, d):
-        """Characteristic speeds along d for an ideal gas (sound speed cs^2 = gamma p/(rho h))."""
+        """Characteristic speeds along d: the relativistic sound-wave speeds of a fluid with
+        velocity v and sound speed cs (cs^2 from the EOS)."""
         rho, u, p = P[0], P[1:4], P[4]
         lor2 = 1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]
         v2 = 1.0 - 1.0 / lor2
         vd = u[d] / np.sqrt(lor2)
-        cs2 = self.gamma * p / (rho * self.enthalpy(rho, p))
+        cs2 = self.sound_speed2(rho, p)
         cs = np.sqrt(cs2)
         den = 1.0 - v2 * cs2
         root = cs * np.sqrt((1.0 - v2) * (1.0 - v2 * cs2 - vd * vd * (1.0 - cs2)))
         return (vd * (1.0 - cs2) - root) / den, (vd * (1.0 - cs2) + root) / den
 
 
-def make_physics(name: str, gamma: float):
-    return {"hd": HD, "mhd": MHD, "srhd": SRHD}[name](gamma)
+def make_physics(name: str, gamma: float, eos: str = "ideal"):
+    if name == "srhd":
+        return SRHD(gamma, eos)
+    if eos != "ideal":
+        raise ValueError("the Synge EOS applies to srhd only")
+    return {"hd": HD, "mhd": MHD}[name](gamma)

@@ -45,6 +45,7 @@ class Config:
     flux: str = "hll"              # 'hll' | 'tvdlf' | 'hllc' (hd only)
     rk: int = 2
     gamma: float = 5.0 / 3.0
+    eos: str = "ideal"             # srhd: 'ideal' (Eq. 20) | 'synge' (approximate Synge gas)
     cfl: float = 0.4
     glm_alpha: float = 0.5
     base_blocks: tuple = (4, 4, 4)
@@ -114,7 +115,7 @@ class Solver:
 
     def __init__(self, cfg: Config):
         self.cfg = cfg
-        self.phys = make_physics(cfg.physics, cfg.gamma)
+        self.phys = make_physics(cfg.physics, cfg.gamma, cfg.eos)
         self.nvar = self.phys.nvar
         self.naux = self.phys.naux
         self.nv = self.nvar + self.naux
