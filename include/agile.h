@@ -54,6 +54,7 @@ enum { AGILE_HD = 0, AGILE_MHD_GLM = 1, AGILE_SRHD = 2 };      /* physics */
 enum { AGILE_MINMOD = 0, AGILE_VANLEER = 1 };                  /* limiter */
 enum { AGILE_TVDLF = 0, AGILE_HLL = 1, AGILE_HLLC = 2 };        /* Riemann flux */
 enum { AGILE_PERIODIC = 0, AGILE_OUTFLOW = 1, AGILE_REFLECT = 2 }; /* boundaries */
+enum { AGILE_EOS_IDEAL = 0, AGILE_EOS_SYNGE = 1 };              /* srhd closure */
 
 /* Device allocator: alloc(bytes, stream, ctx) returns device memory or NULL;
  * free(ptr, stream, ctx) releases it. Both are called only from the calling thread. */
@@ -85,6 +86,10 @@ typedef struct {
  *  derefine_ratio a block may coarsen when its maximum estimate is below
  *                 refine_tol * derefine_ratio
  *  lohner_eps     noise filter epsilon of the estimator (0.01)
+ *  eos            AGILE_EOS_IDEAL: h = 1 + gamma/(gamma-1) p/rho (Eq. 20, every module);
+ *                 AGILE_EOS_SYNGE (srhd only): the Synge gas (Eq. 21) in Mathews'
+ *                 approximation h = 5/2 theta + sqrt(9/4 theta^2 + 1), theta = p/rho
+ *                 (Section 2.3.4); gamma is then unused by the physics
  */
 typedef struct {
   int physics;
@@ -106,6 +111,7 @@ typedef struct {
   double refine_tol;
   double derefine_ratio;
   double lohner_eps;
+  int eos;
 } agile_config;
 
 /* Create a mesh of level-1 blocks (Fig. 1, "init level one") with uninitialised state.

@@ -9,7 +9,7 @@
 namespace agile {
 
 int phys_nvar(int phys) { return phys == PH_MHD ? 9 : 5; }
-int phys_naux(int phys) { return phys == PH_SRHD ? 2 : 0; }
+int phys_naux(int phys) { return phys == PH_SRHD || phys == PH_SRHD_SYNGE ? 2 : 0; }
 
 // ------------------------------------------------------------------------------ helpers
 template <typename R>
@@ -365,7 +365,7 @@ __global__ void prim2cons_kernel(R* __restrict__ U, const double* __restrict__ p
     if constexpr (NA > 0) {
       // xi = Gamma^2 rho h and Gamma from the primitives (Eq. 19)
       const double lor = sqrt(1.0 + p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
-      const double h = 1.0 + gamma / (gamma - 1.0) * p[4] / p[0];
+      const double h = P::enthalpy(p[0], p[4], pp);
       o[(size_t)NV * NCELL] = R(lor * lor * p[0] * h);
       o[(size_t)(NV + 1) * NCELL] = R(lor);
     }
@@ -452,9 +452,12 @@ __global__ void halo_kernel(const R* __restrict__ U, const R* __restrict__ G,
     } else if ((phys) == PH_MHD) {                             \
       if ((rb) == 8) { using R = double; CALL(MhdPhys); }      \
       else { using R = float; CALL(MhdPhys); }                 \
-    } else {                                                   \
+    } else if ((phys) == PH_SRHD) {                            \
       if ((rb) == 8) { using R = double; CALL(SrhdPhys); }     \
       else { using R = float; CALL(SrhdPhys); }                \
+    } else {                                                   \
+      if ((rb) == 8) { using R = double; CALL(SrhdSyngePhys); }\
+      else { using R = float; CALL(SrhdSyngePhys); }           \
     }                                                          \
   } while (0)
 

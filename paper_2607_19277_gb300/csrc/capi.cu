@@ -91,9 +91,14 @@ size_t pool_bytes(const agile_mesh* m, int nblk) {
   return (size_t)nblk * m->nt * NCELL * m->rb;
 }
 
+// Internal physics kind: the srhd module with the Synge EOS has its own device trait.
+int phys_kind(const agile_config& c) {
+  return c.physics == AGILE_SRHD && c.eos == AGILE_EOS_SYNGE ? PH_SRHD_SYNGE : c.physics;
+}
+
 AuxArgs aux_args(agile_mesh* m, void* U) {
   AuxArgs a;
-  a.phys = m->cfg.physics;
+  a.phys = phys_kind(m->cfg);
   a.real_bytes = m->rb;
   a.gamma = m->cfg.gamma;
   a.cfl = m->cfg.cfl;
@@ -335,6 +340,8 @@ agile_status agile_mesh_create(const agile_config* cfg, const agile_allocator* a
     return AGILE_EINVAL;
   if (cfg->physics == AGILE_SRHD && cfg->flux != AGILE_TVDLF) return AGILE_EINVAL;
   if (cfg->flux == AGILE_HLLC && cfg->physics != AGILE_HD) return AGILE_EINVAL;
+  if (cfg->eos != AGILE_EOS_IDEAL && !(cfg->eos == AGILE_EOS_SYNGE && cfg->physics == AGILE_SRHD))
+    return AGILE_EINVAL;
   for (int d = 0; d < 3; ++d) {
     if (cfg->base_blocks[d] < 1 || cfg->base_blocks[d] > 4096 || !(cfg->xmax[d] > cfg->xmin[d]))
       return AGILE_EINVAL;
@@ -514,6 +521,8 @@ agile_status agile_step(agile_mesh* m, double dt) {
     cudaError_t e;
     if (m->cfg.physics == AGILE_HD) e = launch_stage_hd(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
     else if (mhd) e = launch_stage_mhd(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
+    else if (m->cfg.eos == AGILE_EOS_SYNGE)
+      e = launch_stage_srhd_synge(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
     else e = launch_stage_srhd(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
     if (e != cudaSuccess) return fail(m, AGILE_ECUDA, std::string("stage kernel: ") + cudaGetErrorString(e));
     if (m->timing) {
@@ -842,7 +851,7 @@ agile_status bfail(agile_batch* B, agile_status s, const std::string& msg) {
 
 AuxArgs batch_aux(agile_batch* B, void* U) {
   AuxArgs a;
-  a.phys = B->cfg.physics;
+  a.phys = phys_kind(B->cfg);
   a.real_bytes = B->rb;
   a.gamma = B->cfg.gamma;
   a.cfl = B->cfg.cfl;
@@ -920,6 +929,8 @@ agile_status batch_enqueue_step(agile_batch* B) {
     cudaError_t e;
     if (B->cfg.physics == AGILE_HD) e = launch_stage_hd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
     else if (mhd) e = launch_stage_mhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
+    else if (B->cfg.eos == AGILE_EOS_SYNGE)
+      e = launch_stage_srhd_synge(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
     else e = launch_stage_srhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
     if (e != cudaSuccess) return bfail(B, AGILE_ECUDA, std::string("stage kernel: ") + cudaGetErrorString(e));
   }
@@ -939,13 +950,14 @@ agile_status agile_batch_create(const agile_config* cfgs, int nsolve, const agil
     const agile_config& c = cfgs[i];
     if (c.physics != c0.physics || c.limiter != c0.limiter || c.flux != c0.flux || c.rk != c0.rk ||
         c.real_bytes != c0.real_bytes || c.gamma != c0.gamma || c.cfl != c0.cfl ||
-        c.glm_alpha != c0.glm_alpha || c.max_level != 1)
+        c.glm_alpha != c0.glm_alpha || c.eos != c0.eos || c.max_level != 1)
       return AGILE_EINVAL;
     // validate each configuration like a single mesh (host-side checks only)
     if (c.physics < 0 || c.physics > 2 || (c.limiter != 0 && c.limiter != 1) || c.flux < 0 || c.flux > 2 ||
         (c.flux == AGILE_HLLC && c.physics != AGILE_HD) ||
         (c.rk != 2 && c.rk != 3) || (c.real_bytes != 4 && c.real_bytes != 8) || !(c.gamma > 1.0) ||
-        !(c.cfl > 0.0) || (c.physics == AGILE_SRHD && c.flux != AGILE_TVDLF))
+        !(c.cfl > 0.0) || (c.physics == AGILE_SRHD && c.flux != AGILE_TVDLF) ||
+        (c.eos != AGILE_EOS_IDEAL && !(c.eos == AGILE_EOS_SYNGE && c.physics == AGILE_SRHD)))
       return AGILE_EINVAL;
     for (int d = 0; d < 3; ++d) {
       if (c.base_blocks[d] < 1 || c.base_blocks[d] > 4096 || !(c.xmax[d] > c.xmin[d])) return AGILE_EINVAL;

@@ -5,7 +5,8 @@
 // cell-local physics routines, Section 2.3):
 //   HdPhys   : Eqs. 2-4 with e = p/(gamma-1) + rho v^2/2 (Section 2.3.1; HD flux listing)
 //   MhdPhys  : Eqs. 11-13 with GLM (Eq. 14), e = p/(gamma-1) + rho v^2/2 + B^2/2 (Section 2.3.3)
-//   SrhdPhys : Eqs. 15-19 with the ideal-gas enthalpy of Eq. 20 (Section 2.3.4); the
+//   SrhdPhys : Eqs. 15-19 with the ideal-gas enthalpy of Eq. 20 (Section 2.3.4), and
+//   SrhdSyngePhys with the approximate Synge-gas enthalpy (Eq. 21, Mathews' form); the
 //              conserved-to-primitive recovery is a Newton root find in xi = Gamma^2 rho h,
 //              always in FP64.
 // Riemann fluxes: HLL with Davis wave-speed estimates, or TVDLF (Rusanov) with the larger
@@ -206,16 +207,37 @@ struct MhdPhys {
 };
 
 // ------------------------------------------------------------------------------ SRHD
-template <typename R>
-struct SrhdPhys {
+enum : int { EOS_IDEAL = 0, EOS_SYNGE = 1 };
+
+// Closure h(rho, p) of Section 2.3.4: the ideal gas h = 1 + gamma/(gamma-1) theta (Eq. 20)
+// or the Synge gas (Eq. 21) in Mathews' approximation h = 5/2 theta + sqrt(9/4 theta^2 + 1),
+// theta = p / rho, which tends to the ideal gas with gamma = 5/3 (cold) and 4/3 (hot).
+template <typename R, int EOS>
+struct SrhdEos {
+  __device__ static __forceinline__ R enthalpy(R theta, const PhysParamsT<R>& pp) {
+    if constexpr (EOS == EOS_SYNGE) return R(2.5) * theta + rsqrt_(R(2.25) * theta * theta + R(1));
+    else return R(1) + pp.gg1 * theta;
+  }
+  // squared sound speed: gamma theta / h, or theta (5h - 8 theta) / (3h (h - theta)) for the
+  // approximate Synge gas (the isentropic derivative of its enthalpy)
+  __device__ static __forceinline__ R sound_speed2(R theta, R h, const PhysParamsT<R>& pp) {
+    if constexpr (EOS == EOS_SYNGE) return theta * (R(5) * h - R(8) * theta) / (R(3) * h * (h - theta));
+    else return pp.gamma * theta / h;
+  }
+};
+
+template <typename R, int EOS>
+struct SrhdPhysE {
   static constexpr int NV = 5;   // D, m, tau ; primitives rho, u = Gamma v, p
   static constexpr int NA = 2;   // xi = Gamma^2 rho h, Gamma
   static constexpr int BOFF = -1;
+  using Eos = SrhdEos<R, EOS>;
 
-  // Newton root find for f(xi) = xi - p(xi) - (tau + D) = 0 inside the bracket
-  // [E, gamma E]; starts from the stored xi when it lies strictly inside the bracket,
-  // else from the midpoint; a step leaving the closed bracket is replaced by bisection;
-  // stops when |dxi| <= 1e-14 xi; at most 50 iterations. FP64 throughout.
+  // Newton root find for f(xi) = xi - p(xi) - (tau + D) = 0 inside the bracket [E, k E]
+  // (k = gamma for the ideal gas, whose p <= (gamma-1)/gamma xi; k = 4/3 for the approximate
+  // Synge gas, whose h >= 4 theta gives p <= xi/4); starts from the stored xi when it lies
+  // strictly inside the bracket, else from the midpoint; a step leaving the closed bracket
+  // is replaced by bisection; stops when |dxi| <= 1e-14 xi; at most 50 iterations. FP64.
   __device__ static __forceinline__ void cons2prim(const R* u, R* p, R* aux, const PhysParamsT<R>& pp,
                                                    int& st) {
     const double g = pp.gamma_d;
@@ -224,20 +246,33 @@ struct SrhdPhys {
     const double mx = (double)u[1], my = (double)u[2], mz = (double)u[3];
     const double s2 = mx * mx + my * my + mz * mz;
     const double E = (double)u[4] + D;
-    double lo = E, hi = g * E;
+    double lo = E, hi = (EOS == EOS_SYNGE ? 4.0 / 3.0 : g) * E;
+    const double iD = EOS == EOS_SYNGE ? 1.0 / D : 0.0;
     double xi = (double)aux[0];
     if (!(xi > lo && xi < hi)) xi = 0.5 * (lo + hi);
     bool ok = false;
     for (int it = 0; it < 50; ++it) {
-      // per iteration: one reciprocal, one reciprocal square root, one divide
       const double ixi = 1.0 / xi;
       const double w = s2 * ixi * ixi;          // v^2
       const double ig2 = 1.0 - w;               // 1 / Gamma^2
       const double lor = rsqrt(ig2);            // Gamma
       const double rho = D * (ig2 * lor);       // D / Gamma
-      const double pr = gm * (xi * ig2 - rho);
+      const double drho = D * lor * w * ixi;    // d rho / d xi
+      double pr, dp;
+      if constexpr (EOS == EOS_SYNGE) {
+        // h = xi / (D Gamma), theta(h) = (5h - sqrt(9h^2 + 16)) / 8, dh/dxi = Gamma / D
+        const double h = xi * (ig2 * lor) * iD;
+        const double q = 9.0 * h * h + 16.0;
+        const double iq = rsqrt(q);
+        const double th = 0.125 * (5.0 * h - q * iq);
+        pr = rho * th;
+        dp = th * drho + 0.125 * (5.0 - 9.0 * h * iq);
+      } else {
+        pr = gm * (xi * ig2 - rho);
+        dp = gm * (1.0 + w - drho);
+      }
       const double f = xi - pr - E;
-      const double df = 1.0 - gm * (1.0 + w - D * lor * w * ixi);
+      const double df = 1.0 - dp;
       if (f < 0.0) lo = xi; else hi = xi;
       double xn = xi - f / df;
       if (!(xn >= lo && xn <= hi)) xn = 0.5 * (lo + hi);
@@ -256,16 +291,29 @@ struct SrhdPhys {
     p[1] = (R)(mx * sc);
     p[2] = (R)(my * sc);
     p[3] = (R)(mz * sc);
-    const double pr = gm * (xi * ig2 - rho);
+    double pr;
+    if constexpr (EOS == EOS_SYNGE) {
+      const double h = xi * (ig2 * lor) * iD;
+      const double q = 9.0 * h * h + 16.0;
+      pr = rho * (0.125 * (5.0 * h - q * rsqrt(q)));
+    } else {
+      pr = gm * (xi * ig2 - rho);
+    }
     p[4] = (R)pr;
     aux[0] = (R)xi;
     aux[1] = (R)lor;
     if (!(rho > 0.0) || !(pr > 0.0)) st |= ST_EUNPHYS;
   }
 
+  __device__ static __forceinline__ R enthalpy(R rho, R pres, const PhysParamsT<R>& pp) {
+    return Eos::enthalpy(pres / rho, pp);
+  }
+
   __device__ static __forceinline__ void prim2cons(const R* p, R* u, const PhysParamsT<R>& pp) {
     const R lor = rsqrt_(R(1) + p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
-    const R h = R(1) + pp.gg1 * p[4] / p[0];
+    R h;
+    if constexpr (EOS == EOS_SYNGE) h = Eos::enthalpy(p[4] / p[0], pp);
+    else h = R(1) + pp.gg1 * p[4] / p[0];
     const R lr = lor * p[0];
     const R lrh = lr * h;
     u[0] = lr;
@@ -292,8 +340,14 @@ struct SrhdPhys {
     const R lor2 = R(1) + p[1] * p[1] + p[2] * p[2] + p[3] * p[3];
     const R v2 = R(1) - R(1) / lor2;
     const R vd = p[1 + D] / rsqrt_(lor2);
-    const R h = R(1) + pp.gg1 * p[4] / p[0];
-    const R cs2 = pp.gamma * p[4] / (p[0] * h);
+    R cs2;
+    if constexpr (EOS == EOS_SYNGE) {
+      const R th = p[4] / p[0];
+      cs2 = Eos::sound_speed2(th, Eos::enthalpy(th, pp), pp);
+    } else {
+      const R h = R(1) + pp.gg1 * p[4] / p[0];
+      cs2 = pp.gamma * p[4] / (p[0] * h);
+    }
     const R cs = rsqrt_(cs2);
     const R den = R(1) - v2 * cs2;
     const R root = cs * rsqrt_(rmax((R(1) - v2) * (R(1) - v2 * cs2 - vd * vd * (R(1) - cs2)), R(0)));
@@ -304,6 +358,9 @@ struct SrhdPhys {
   template <int D>
   __device__ static __forceinline__ void interface(R*, R*, const PhysParamsT<R>&) {}
 };
+
+template <typename R> using SrhdPhys = SrhdPhysE<R, EOS_IDEAL>;
+template <typename R> using SrhdSyngePhys = SrhdPhysE<R, EOS_SYNGE>;
 
 // Riemann flux at a face from reconstructed primitive states (modified in place).
 template <class P, typename R, int D, int FLUX>

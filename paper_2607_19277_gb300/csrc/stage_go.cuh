@@ -1,0 +1,32 @@
+// Launch of the persistent per-stage update kernel for one physics trait and scheme.
+#pragma once
+#include "kernels.cuh"
+
+namespace agile {
+
+template <template <typename> class PT, typename R, int LIM, int FLUX>
+static cudaError_t stage_go(const StageArgs& a, cudaStream_t s) {
+  constexpr int MINB = sizeof(R) == 4 ? 2 : 1;   // CTAs per SM the register budget targets
+  auto k = stage_kernel<PT, R, LIM, FLUX, MINB>;
+  const size_t smem = stage_smem_bytes<PT, R>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  // persistent grid: as many CTAs as fit on the GPU at once, each looping over blocks
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int grid = a.nblk < MINB * sms ? a.nblk : MINB * sms;
+  if (grid <= 0) return cudaSuccess;
+  k<<<grid, 256, smem, s>>>(*static_cast<const CUtensorMap*>(a.tmap), a);
+  return cudaGetLastError();
+}
+
+}  // namespace agile

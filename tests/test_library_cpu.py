@@ -39,7 +39,8 @@ def test_version(lib):
 
 
 @pytest.mark.parametrize("field,value", [("physics", 7), ("rk", 4), ("real_bytes", 2),
-                                         ("gamma", 1.0), ("max_level", 0), ("limiter", 3)])
+                                         ("gamma", 1.0), ("max_level", 0), ("limiter", 3),
+                                         ("eos", 2)])
 def test_invalid_config_rejected_on_host(lib, field, value):
     from paper_2607_19277_gb300 import agile
     cfg = agile.make_config()
@@ -55,6 +56,8 @@ def test_half_periodic_and_srhd_hll_rejected(lib):
     cfg = agile.make_config(bc=("periodic", "outflow", "periodic", "periodic", "periodic", "periodic"))
     assert lib.agile_mesh_create(C.byref(cfg), None, None, C.byref(out)) == 1
     cfg = agile.make_config(physics="srhd", flux="hll")
+    assert lib.agile_mesh_create(C.byref(cfg), None, None, C.byref(out)) == 1
+    cfg = agile.make_config(physics="hd", eos="synge")    # the Synge EOS is srhd-only
     assert lib.agile_mesh_create(C.byref(cfg), None, None, C.byref(out)) == 1
 
 
