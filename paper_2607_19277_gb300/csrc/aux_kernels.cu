@@ -185,10 +185,10 @@ __global__ void __launch_bounds__(256) speeds_kernel(const R* __restrict__ U,
   using P = PT<R>;
   constexpr int NV = P::NV, NA = P::NA, NT = NV + NA;
   const int b = blockIdx.x;
-  const double dx[3] = {bd[b].dx[0], bd[b].dx[1], bd[b].dx[2]};
+  const R dxr[3] = {R(bd[b].dx[0]), R(bd[b].dx[1]), R(bd[b].dx[2])};
   PhysParamsT<R> pp;
   pp.set(gamma, 0.0);
-  double ssum = 0.0, smax = 0.0;
+  R ssum = R(0), smax = R(0);
   int st = 0;
   const R* base = U + (size_t)b * NT * NCELL;
   for (int c = threadIdx.x; c < NCELL; c += 256) {
@@ -196,9 +196,9 @@ __global__ void __launch_bounds__(256) speeds_kernel(const R* __restrict__ U,
 #pragma unroll
     for (int v = 0; v < NV; ++v) u[v] = base[(size_t)v * NCELL + c];
     if constexpr (NA > 0) aux[0] = base[(size_t)NV * NCELL + c];
-    cell_speeds<PT, R>(u, aux, pp, dx, ssum, smax, st);
+    cell_speeds<PT, R>(u, aux, pp, dxr, ssum, smax, st);
   }
-  block_max2<256>(ssum, smax, speeds + 2 * (solve_of ? solve_of[b] : 0));
+  block_max2<256>((double)ssum, (double)smax, speeds + 2 * (solve_of ? solve_of[b] : 0));
   if (st) atomicOr(status, st);
 }
 

@@ -90,11 +90,12 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long* addr, double 
 }
 
 // Signal speeds of one cell, s_d = max |lambda_+-| along d, evaluated in the stencil
-// precision R (the SRHD primitive recovery inside is FP64 always); the maxima are
-// accumulated in FP64: ssum = max sum_d s_d / dx_d, smax = max_d s_d.
+// precision R (the SRHD primitive recovery inside is FP64 always); the maxima
+// ssum = max sum_d s_d / dx_d and smax = max_d s_d are accumulated in R (a maximum is exact
+// in any precision; the caller widens the result to FP64 once). dxr = dx rounded to R.
 template <template <typename> class PT, typename R>
 __device__ __forceinline__ void cell_speeds(const R* u, R* aux, const PhysParamsT<R>& pp,
-                                            const double* dx, double& ssum, double& smax, int& st) {
+                                            const R* dxr, R& ssum, R& smax, int& st) {
   using P = PT<R>;
   R p[P::NV];
   P::cons2prim(u, p, aux, pp, st);
@@ -105,9 +106,9 @@ __device__ __forceinline__ void cell_speeds(const R* u, R* aux, const PhysParams
   const R s1 = rmax(rabs(lm), rabs(lp));
   P::template lambdas<2>(p, lm, lp, pp);
   const R s2 = rmax(rabs(lm), rabs(lp));
-  smax = fmax(smax, (double)rmax(rmax(s0, s1), s2));
-  const R acc = (s0 / R(dx[0]) + s1 / R(dx[1])) + s2 / R(dx[2]);
-  ssum = fmax(ssum, (double)acc);
+  smax = rmax(smax, rmax(rmax(s0, s1), s2));
+  const R acc = (s0 / dxr[0] + s1 / dxr[1]) + s2 / dxr[2];
+  ssum = rmax(ssum, acc);
 }
 
 template <int NTHREADS>
@@ -307,9 +308,20 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   // from the launch's counter; every block completes 5 phases of each ring barrier, so the
   // CTA's jb-th block starts at parity jb & 1.
   __shared__ int s_next;
+  // Launch constants, and the per-(solve, level) constants of the current block: they are
+  // recomputed only when the block's solve or level differs from the previous block's (a
+  // CTA-uniform test), so the FP64 divisions and the exp stay off the per-block path.
+  PhysParamsT<R> pp;
+  pp.set(A.gamma, 0.0);
+  const R ra = R(A.a), rb = R(A.b);
+  const bool combine = A.a != 0.0;
+  const bool glm_post = A.glm_post != 0;
+  constexpr uint32_t PLANE_BYTES = (uint32_t)(sizeof(R) * NT * 256);
+  int key_sv = -1, key_lev = -1;
+  R idx = R(0), idy = R(0), idz = R(0), rdt = R(0), glm_fr = R(1);
+  R dxr[3] = {R(0), R(0), R(0)};
   for (int b = blockIdx.x, jb = 0; b < A.nblk; ++jb) {
   const int sv = A.solve_of ? A.solve_of[b] : 0;
-  const double* dtch = A.dtch + 2 * sv;
   unsigned long long* speeds = A.speeds ? A.speeds + 2 * sv : nullptr;
   const BlockDesc& bd = A.bd[b];
   int src[6], slot[6];
@@ -318,15 +330,24 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     src[f] = bd.src[f];
     slot[f] = bd.slot[f];
   }
-  const double dt = dtch[0];
-  PhysParamsT<R> pp;
-  pp.set(A.gamma, dtch[1]);
-  const R idx = R(1.0 / bd.dx[0]), idy = R(1.0 / bd.dx[1]), idz = R(1.0 / bd.dx[2]);
-  const R rdt = R(dt);
-  const R ra = R(A.a), rb = R(A.b);
-  const bool combine = A.a != 0.0;
-  const bool glm_post = A.glm_post != 0;
-  constexpr uint32_t PLANE_BYTES = (uint32_t)(sizeof(R) * NT * 256);
+  if (sv != key_sv || bd.level != key_lev) {
+    const double* dtch = A.dtch + 2 * sv;
+    const double dt = dtch[0];
+    pp.set_ch(dtch[1]);
+    idx = R(1.0 / bd.dx[0]);
+    idy = R(1.0 / bd.dx[1]);
+    idz = R(1.0 / bd.dx[2]);
+    rdt = R(dt);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dxr[d] = R(bd.dx[d]);
+    glm_fr = R(1);
+    if (glm_post) {
+      const double dxm = fmin(fmin(bd.dx[0], bd.dx[1]), bd.dx[2]);
+      glm_fr = R(exp(-0.5 * dt * dtch[1] * A.glm_alpha / dxm));
+    }
+    key_sv = sv;
+    key_lev = bd.level;
+  }
 
   // plane p (-2 .. 17) -> TMA sequence q = p + 2, ring slot q & 3, phase parity (q >> 2) & 1
   auto plane_tma = [&](int p) -> bool {   // does plane p come by TMA (else loaded directly)?
@@ -455,14 +476,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     for (int v = 0; v < NV; ++v) FR[((size_t)slot[4] * NV + v) * 256 + cell2] = fzd[v];
   }
 
-  double ssum = 0.0, smax = 0.0;
-  const double dxd[3] = {bd.dx[0], bd.dx[1], bd.dx[2]};
-  double glm_f = 1.0;
-  if (A.glm_post) {
-    const double dxm = fmin(fmin(bd.dx[0], bd.dx[1]), bd.dx[2]);
-    glm_f = exp(-0.5 * dt * dtch[1] * A.glm_alpha / dxm);
-  }
-  const R glm_fr = R(glm_f);
+  R ssum = R(0), smax = R(0);
 
   for (int k = 0; k < NB; ++k) {
     // ---- phase 1
@@ -592,11 +606,11 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
         R ad[NAW];
 #pragma unroll
         for (int i = 0; i < NAW; ++i) ad[i] = auxk[i];
-        cell_speeds<PT, R>(out, ad, pp, dxd, ssum, smax, st);
+        cell_speeds<PT, R>(out, ad, pp, dxr, ssum, smax, st);
       }
     }
   }
-  if (speeds) block_max2<256>(ssum, smax, speeds);
+  if (speeds) block_max2<256>((double)ssum, (double)smax, speeds);
   if (t == 0) s_next = A.work ? (int)gridDim.x + atomicAdd(A.work, 1) : b + (int)gridDim.x;
   __syncthreads();       // ring, halo staging and reduction scratch are reused by the next block
   b = s_next;

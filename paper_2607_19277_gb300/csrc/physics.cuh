@@ -34,6 +34,9 @@ struct PhysParamsT {
     g1 = R(gamma_ - 1.0);
     ig1 = R(1.0 / (gamma_ - 1.0));
     gg1 = R(gamma_ / (gamma_ - 1.0));
+    set_ch(ch_);
+  }
+  __host__ __device__ void set_ch(double ch_) {
     ch = R(ch_);
     ich = ch_ > 0.0 ? R(1.0 / ch_) : R(0);
     ch2 = R(ch_ * ch_);
