@@ -57,18 +57,20 @@ template <typename R> __device__ __forceinline__ R rtiny();
 template <> __device__ __forceinline__ float rtiny<float>() { return 1e-30f; }
 template <> __device__ __forceinline__ double rtiny<double>() { return 1e-300; }
 
-// Slope limiters on the two one-sided differences, written without branches:
-//   minmod(a, b) = (sgn a + sgn b)/2 * min(|a|, |b|)  (0 unless a, b share a sign);
-//   van Leer (1974): 2 max(ab, 0) / (a + b), the denominator nudged by a tiny value of its
-//   own sign so that a = -b gives 0 instead of 0/0 (below half an ulp otherwise).
+// Half of the limited slope, sigma / 2, from the two one-sided differences a and b, written
+// without branches (the final choice is a select):
+//   minmod: sigma = (sgn a + sgn b)/2 min(|a|, |b|)  (0 unless a and b share a sign);
+//   van Leer (1974): sigma = 2ab / (a + b) when ab > 0, else 0. The quotient is formed for
+//   every input and discarded when ab <= 0, where a + b may vanish.
+// Halving is exact, so sigma / 2 equals half the limiter value bit for bit.
 template <typename R, int LIM>
-__device__ __forceinline__ R limit(R a, R b) {
+__device__ __forceinline__ R half_slope(R a, R b) {
   if (LIM == LIM_MINMOD) {
-    return R(0.5) * (rsign(a) + rsign(b)) * rmin(rabs(a), rabs(b));
+    return (R(0.25) * (rsign(a) + rsign(b))) * rmin(rabs(a), rabs(b));
   } else {
     const R ab = a * b;
-    const R den = a + b;
-    return (R(2) * rmax(ab, R(0))) / (den + rsign(den) * rtiny<R>());
+    const R q = ab / (a + b);
+    return ab > R(0) ? q : R(0);
   }
 }
 
@@ -83,7 +85,8 @@ struct HdPhys {
                                                    int& st) {
     const R g1 = pp.g1;
     const R rho = u[0];
-    const R vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
+    const R ir = R(1) / rho;
+    const R vx = u[1] * ir, vy = u[2] * ir, vz = u[3] * ir;
     p[0] = rho;
     p[1] = vx;
     p[2] = vy;
@@ -134,7 +137,8 @@ struct MhdPhys {
                                                    int& st) {
     const R g1 = pp.g1;
     const R rho = u[0];
-    const R vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
+    const R ir = R(1) / rho;
+    const R vx = u[1] * ir, vy = u[2] * ir, vz = u[3] * ir;
     const R b2 = u[5] * u[5] + u[6] * u[6] + u[7] * u[7];
     p[0] = rho;
     p[1] = vx;
@@ -414,8 +418,9 @@ __device__ __forceinline__ void riemann(R* pl, R* pr, R* f, const PhysParamsT<R>
     const R sl = rmin(rmin(lml, lmr), R(0));
     const R sr = rmax(rmax(lpl, lpr), R(0));
     const R inv = R(1) / (sr - sl);
+    const R wl = sr * inv, wr = sl * inv, wd = sl * sr * inv;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) f[v] = (sr * fl[v] - sl * fr[v] + sl * sr * (ur[v] - ul[v])) * inv;
+    for (int v = 0; v < NV; ++v) f[v] = wl * fl[v] - wr * fr[v] + wd * (ur[v] - ul[v]);
   }
 }
 
@@ -426,8 +431,8 @@ __device__ __forceinline__ void plm(const R* a, const R* b, const R* c, const R*
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const R d0 = b[v] - a[v], d1 = c[v] - b[v], d2 = d[v] - c[v];
-    pl[v] = b[v] + R(0.5) * limit<R, LIM>(d0, d1);
-    pr[v] = c[v] - R(0.5) * limit<R, LIM>(d1, d2);
+    pl[v] = b[v] + half_slope<R, LIM>(d0, d1);
+    pr[v] = c[v] - half_slope<R, LIM>(d1, d2);
   }
 }
 
