@@ -23,6 +23,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+from .cooling import Cooling
 from .physics import make_physics
 
 NB = 16          # interior cells per block edge
@@ -58,6 +59,7 @@ class Config:
     refine_tol: float = 0.2
     derefine_ratio: float = 1.0 / 8.0
     lohner_eps: float = 0.01
+    cooling: tuple = None          # (T, Lambda) table: optically thin losses (hd, mhd)
 
 
 def morton3(ix: int, iy: int, iz: int) -> int:
@@ -116,6 +118,11 @@ class Solver:
     def __init__(self, cfg: Config):
         self.cfg = cfg
         self.phys = make_physics(cfg.physics, cfg.gamma, cfg.eos)
+        self.cool = None
+        if cfg.cooling is not None:
+            if cfg.physics not in ("hd", "mhd"):
+                raise ValueError("radiative losses apply to hd and mhd")
+            self.cool = Cooling(cfg.cooling[0], cfg.cooling[1], cfg.gamma)
         self.nvar = self.phys.nvar
         self.naux = self.phys.naux
         self.nv = self.nvar + self.naux
@@ -572,6 +579,12 @@ class Solver:
             dxm = min(self.dx(key[0]))
             blk[(8,) + (slice(G, G + NB),) * 3] *= math.exp(-0.5 * dt * ch * self.cfg.glm_alpha / dxm)
 
+    def _cool(self, dt):
+        """Radiative losses over dt on every leaf interior (exact integration, Section 2.3.1)."""
+        inner = (slice(0, self.nvar),) + (slice(G, G + NB),) * 3
+        for blk in self.leaves.values():
+            blk[inner] = self.cool.apply(self.phys, blk[inner], dt)
+
     def step(self, dt=None, ch=None):
         """One full SSPRK step of every leaf (ghost fill, update and fix-up per stage).
 
@@ -584,6 +597,8 @@ class Solver:
             ch = cmax
         if self.phys.glm:
             self._glm_decay(dt, ch)
+        if self.cool is not None:       # Strang split: half the losses before, half after
+            self._cool(0.5 * dt)
         inner = (slice(G, G + NB),) * 3
         un = {k: b[(slice(0, self.nvar),) + inner].copy() for k, b in self.leaves.items()}
         for a, b in RK_STAGES[self.cfg.rk]:
@@ -603,6 +618,8 @@ class Solver:
                     blk[(slice(self.nvar, self.nv),) + inner] = new_aux[key]
         if self.phys.glm:
             self._glm_decay(dt, ch)
+        if self.cool is not None:
+            self._cool(0.5 * dt)
         self.t += dt
         return dt
 

@@ -267,3 +267,27 @@ def random_smooth(nvar: int, seed: int, kind: str, n_modes: int = 3):
             prim[8] = 0.05 * prim[8]
         return prim
     return ic
+
+
+def skew_normal_cooling(n: int = 256, t_min: float = 1e-2, t_max: float = 1e2, t_peak: float = 0.3,
+                        sigma: float = 3.0, skew: float = 7.0, peak: float = 1.0):
+    """Tabulated optically thin loss function Lambda(T) in code units (T = p / rho): the
+    log-skew-normal shape of the paper's mixing-layer setup,
+        Lambda(T) = 2 A / (sigma T) phi((ln T - mu)/sigma) Phi(skew (ln T - mu)/sigma),
+    with mu chosen so that the maximum sits at T = t_peak and A so that it equals `peak`.
+    Returns (T, Lambda) on n nodes uniformly spaced in ln T over [t_min, t_max].
+    The table is an input: both the oracle and the library take it as given."""
+    def shape(lnt, mu):
+        z = (lnt - mu) / sigma
+        phi = np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
+        big_phi = 0.5 * (1.0 + np.array([math.erf(skew * zi / math.sqrt(2.0)) for zi in np.atleast_1d(z)]))
+        return 2.0 / (sigma * np.exp(lnt)) * phi * big_phi.reshape(np.shape(z))
+
+    # argmax of the shape in ln T moves rigidly with mu: locate it once for mu = 0 on a
+    # fine grid and shift
+    grid = np.linspace(-6.0 * sigma, 6.0 * sigma, 200001)
+    g = shape(grid, 0.0)
+    mu = math.log(t_peak) - grid[int(np.argmax(g))]
+    amp = peak / float(shape(np.array([math.log(t_peak)]), mu)[0])
+    lnt = np.linspace(math.log(t_min), math.log(t_max), n)
+    return np.exp(lnt), amp * shape(lnt, mu)
