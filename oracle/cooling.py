@@ -17,10 +17,18 @@ T_ref = T_{N-1} and the temporal evolution function
     Y(T) = (Lambda_ref / T_ref) * integral_T^T_ref dT' / Lambda(T'),
 
 the ODE integrates to Y(T_new) = Y(T_old) + (Lambda_ref / T_ref) (gamma - 1) rho dt, and
-Y has a closed form and a closed-form inverse on every power-law segment. The
-integral of 1/Lambda over segment k from T_a to T_b is
-    (T_k / Lambda_k) ((T_b/T_k)^(1-alpha) - (T_a/T_k)^(1-alpha)) / (1 - alpha)
-and (T_k / Lambda_k) ln(T_b / T_a) for alpha = 1.
+Y has a closed form and a closed-form inverse on every power-law segment. With
+e = 1 - alpha_k and C_k = (Lambda_ref / T_ref) T_k / Lambda_k, the integral over segment k
+from T to T_{k+1} gives
+
+    Y(T) = Y_{k+1} + C_k (T/T_k)^e ((T_{k+1}/T)^e - 1) / e,
+
+and, with s = (y - Y_{k+1}) / C_k and B_k = (T_{k+1}/T_k)^e, the inverse
+
+    T = T_{k+1} (1 - e s / B_k)^(1/e).
+
+Both are written with expm1 / log1p so that they stay accurate as e -> 0 (alpha -> 1),
+where they tend to the logarithmic forms Y_{k+1} + C_k ln(T_{k+1}/T) and T_{k+1} exp(-s).
 """
 from __future__ import annotations
 
@@ -44,15 +52,25 @@ class Cooling:
         n = T.size
         self.Y = np.zeros(n)
         for k in range(n - 2, -1, -1):
-            self.Y[k] = self.Y[k + 1] + self.Lref / self.Tref * self._seg_integral(k, T[k], T[k + 1])
+            self.Y[k] = self.Y[k + 1] + self._seg_integral(k, T[k], T[k + 1])
+
+    @staticmethod
+    def _em1_over(e, x):
+        """(exp(e x) - 1) / e, and its limit x at e = 0."""
+        return np.expm1(e * x) / e if e != 0.0 else x
+
+    @staticmethod
+    def _l1p_over(e, z):
+        """log(1 - e z) / e, and its limit -z at e = 0."""
+        return np.log1p(-e * z) / e if e != 0.0 else -z
+
+    def _c(self, k):
+        return self.Lref / self.Tref * self.T[k] / self.L[k]
 
     def _seg_integral(self, k, ta, tb):
-        """integral_ta^tb dT / Lambda(T) on the power law of segment k."""
-        a = self.alpha[k]
-        tk, lk = self.T[k], self.L[k]
-        if a == 1.0:
-            return tk / lk * np.log(tb / ta)
-        return tk / lk * ((tb / tk) ** (1.0 - a) - (ta / tk) ** (1.0 - a)) / (1.0 - a)
+        """(Lambda_ref / T_ref) integral_ta^tb dT / Lambda(T) on the power law of segment k."""
+        e = 1.0 - self.alpha[k]
+        return self._c(k) * (ta / self.T[k]) ** e * self._em1_over(e, np.log(tb / ta))
 
     def segment(self, t):
         """Segment index of temperature t: k with T_k <= t < T_{k+1}, clamped to 0..N-2."""
@@ -64,7 +82,7 @@ class Cooling:
         out = np.empty_like(t)
         for kk in np.unique(k):
             m = k == kk
-            out[m] = self.Y[kk + 1] + self.Lref / self.Tref * self._seg_integral(kk, t[m], self.T[kk + 1])
+            out[m] = self.Y[kk + 1] + self._seg_integral(kk, t[m], self.T[kk + 1])
         return out
 
     def t_of_y(self, y):
@@ -80,14 +98,10 @@ class Cooling:
         res = np.empty_like(yr)
         for kk in np.unique(k):
             m = k == kk
-            s = (yr[m] - self.Y[kk + 1]) * self.Tref / self.Lref   # integral from T to T_{k+1}
-            a = self.alpha[kk]
-            tk, lk = self.T[kk], self.L[kk]
-            if a == 1.0:
-                res[m] = self.T[kk + 1] * np.exp(-lk / tk * s)
-            else:
-                base = (self.T[kk + 1] / tk) ** (1.0 - a) - (1.0 - a) * lk / tk * s
-                res[m] = tk * base ** (1.0 / (1.0 - a))
+            e = 1.0 - self.alpha[kk]
+            sk = (yr[m] - self.Y[kk + 1]) / self._c(kk)
+            bk = (self.T[kk + 1] / self.T[kk]) ** e
+            res[m] = self.T[kk + 1] * np.exp(self._l1p_over(e, sk / bk))
         out[rest] = res
         return out
 

@@ -117,3 +117,15 @@ def test_static_state_step_equals_exact_cooling(physics):
     tn = Cooling(T, L, 5.0 / 3.0).cool_temperature(1.3, np.array([0.8]), dt)[0]
     assert np.allclose(p[4] / p[0], tn, rtol=1e-13)
     assert tn < 0.8 * (1 - 1e-4)          # the losses are not negligible at this dt
+
+
+def test_power_law_near_one_is_continuous():
+    """alpha within 1e-10 of 1: the expm1 / log1p forms must reproduce the exponential decay
+    of the alpha = 1 law (a naive (x^e - 1)/e loses about 1e-6 here)."""
+    gamma, rho, t0, t1, l0 = 1.4, 2.5, 1.0, 4.0, 0.3
+    k = (gamma - 1.0) * rho * l0 / t0
+    for a in (1.0 - 1e-10, 1.0 + 1e-10):
+        cool = Cooling([t0, t1], [l0, l0 * (t1 / t0) ** a], gamma)
+        T = np.array([3.9, 2.0])
+        got = cool.cool_temperature(rho, T, 0.1)
+        assert np.allclose(got, T * np.exp(-k * 0.1), rtol=1e-8)
