@@ -7,32 +7,45 @@ CPU-baseline leg are the only users. Shares no code with the CUDA library.
 In code units the sink is de/dt = -rho^2 Lambda(T) with T = p / rho at fixed rho and
 momentum, so the internal energy rho T / (gamma - 1) obeys
 
-    dT/dt = -(gamma - 1) rho Lambda(T).
+    dT/dt = -(gamma - 1) rho Lambda(T),   i.e.   integral_{T_new}^{T} dT' / Lambda(T') = r,
+    r = (gamma - 1) rho dt.
 
 Lambda is given as a table (T_k, Lambda_k), k = 0..N-1, and is a power law between nodes,
 Lambda(T) = Lambda_k (T / T_k)^alpha_k on [T_k, T_{k+1}] (the last segment continues above
-T_{N-1}); there is no loss below T_0, which acts as a floor. With the reference node
-T_ref = T_{N-1} and the temporal evolution function
+T_{N-1}); there is no loss at or below T_0, which is the floor. The integral of 1/Lambda
+has a closed form on each segment, so the exact T_new follows by consuming r segment by
+segment downward from T: with e = 1 - alpha_k,
 
-    Y(T) = (Lambda_ref / T_ref) * integral_T^T_ref dT' / Lambda(T'),
+    integral_{T_k}^{t} dT'/Lambda = (T_k / Lambda_k) expm1(e ln(t / T_k)) / e,
 
-the ODE integrates to Y(T_new) = Y(T_old) + (Lambda_ref / T_ref) (gamma - 1) rho dt, and
-Y has a closed form and a closed-form inverse on every power-law segment. With
-e = 1 - alpha_k and C_k = (Lambda_ref / T_ref) T_k / Lambda_k, the integral over segment k
-from T to T_{k+1} gives
+and inside a segment, below its upper end t with r' of r left,
 
-    Y(T) = Y_{k+1} + C_k (T/T_k)^e ((T_{k+1}/T)^e - 1) / e,
+    T_new = t exp(log1p(-e q) / e),   q = r' Lambda(t) / t
 
-and, with s = (y - Y_{k+1}) / C_k and B_k = (T_{k+1}/T_k)^e, the inverse
-
-    T = T_{k+1} (1 - e s / B_k)^(1/e).
-
-Both are written with expm1 / log1p so that they stay accurate as e -> 0 (alpha -> 1),
-where they tend to the logarithmic forms Y_{k+1} + C_k ln(T_{k+1}/T) and T_{k+1} exp(-s).
+(e -> 0 limits: (T_k/Lambda_k) ln(t/T_k) and t exp(-q)). This is Townsend's exact
+integration with the evolution function referred to each segment's own upper end instead of
+the table's top node: the same integral, but every quantity stays on the scale of the local
+cooling time, so no digits are lost where 1/Lambda near the top of the table dominates.
 """
 from __future__ import annotations
 
 import numpy as np
+
+
+def _em1_over(e, x):
+    """(exp(e x) - 1) / e, and its limit x at e = 0."""
+    e = np.asarray(e, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    safe = np.where(e != 0.0, e, 1.0)
+    return np.where(e != 0.0, np.expm1(e * x) / safe, x)
+
+
+def _l1p_over(e, q):
+    """log(1 - e q) / e, and its limit -q at e = 0."""
+    e = np.asarray(e, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    safe = np.where(e != 0.0, e, 1.0)
+    return np.where(e != 0.0, np.log1p(-e * q) / safe, -q)
 
 
 class Cooling:
@@ -47,74 +60,59 @@ class Cooling:
         self.L = L
         self.g1 = float(gamma) - 1.0
         self.alpha = np.log(L[1:] / L[:-1]) / np.log(T[1:] / T[:-1])
-        self.Tref = T[-1]
-        self.Lref = L[-1]
-        n = T.size
-        self.Y = np.zeros(n)
-        for k in range(n - 2, -1, -1):
-            self.Y[k] = self.Y[k + 1] + self._seg_integral(k, T[k], T[k + 1])
-
-    @staticmethod
-    def _em1_over(e, x):
-        """(exp(e x) - 1) / e, and its limit x at e = 0."""
-        return np.expm1(e * x) / e if e != 0.0 else x
-
-    @staticmethod
-    def _l1p_over(e, z):
-        """log(1 - e z) / e, and its limit -z at e = 0."""
-        return np.log1p(-e * z) / e if e != 0.0 else -z
-
-    def _c(self, k):
-        return self.Lref / self.Tref * self.T[k] / self.L[k]
-
-    def _seg_integral(self, k, ta, tb):
-        """(Lambda_ref / T_ref) integral_ta^tb dT / Lambda(T) on the power law of segment k."""
-        e = 1.0 - self.alpha[k]
-        return self._c(k) * (ta / self.T[k]) ** e * self._em1_over(e, np.log(tb / ta))
+        self.e = 1.0 - self.alpha
+        # integral of 1/Lambda over each whole segment
+        self.W = T[:-1] / L[:-1] * _em1_over(self.e, np.log(T[1:] / T[:-1]))
 
     def segment(self, t):
         """Segment index of temperature t: k with T_k <= t < T_{k+1}, clamped to 0..N-2."""
         k = np.searchsorted(self.T, t, side="right") - 1
         return np.clip(k, 0, self.T.size - 2)
 
-    def y_of_t(self, t):
+    def lam(self, t):
+        """The power-law Lambda(t) (segment of t; the last segment continues above)."""
         k = self.segment(t)
-        out = np.empty_like(t)
-        for kk in np.unique(k):
-            m = k == kk
-            out[m] = self.Y[kk + 1] + self._seg_integral(kk, t[m], self.T[kk + 1])
-        return out
+        return self.L[k] * (t / self.T[k]) ** self.alpha[k]
 
-    def t_of_y(self, y):
-        """Inverse of Y: the temperature whose evolution function is y (T_0 when y >= Y_0)."""
-        out = np.empty_like(y)
-        floor = y >= self.Y[0]
-        out[floor] = self.T[0]
-        rest = ~floor
-        # Y decreases with T: segment k holds Y_{k+1} <= y <= Y_k (last segment above T_ref)
-        k = np.searchsorted(-self.Y, -y[rest], side="left") - 1
-        k = np.clip(k, 0, self.T.size - 2)
-        yr = y[rest]
-        res = np.empty_like(yr)
-        for kk in np.unique(k):
-            m = k == kk
-            e = 1.0 - self.alpha[kk]
-            sk = (yr[m] - self.Y[kk + 1]) / self._c(kk)
-            bk = (self.T[kk + 1] / self.T[kk]) ** e
-            res[m] = self.T[kk + 1] * np.exp(self._l1p_over(e, sk / bk))
-        out[rest] = res
-        return out
+    def integral_below(self, t):
+        """integral from T_k up to t of dT'/Lambda, k the segment of t."""
+        k = self.segment(t)
+        return self.T[k] / self.L[k] * _em1_over(self.e[k], np.log(t / self.T[k]))
 
     def cool_temperature(self, rho, t, dt):
         """Temperature after dt of losses at fixed rho (no change at or below T_0)."""
-        t = np.asarray(t, dtype=np.float64)
-        rho = np.broadcast_to(np.asarray(rho, dtype=np.float64), t.shape)
+        shape = np.shape(t)
+        t = np.asarray(t, dtype=np.float64).ravel()
+        rho = np.broadcast_to(np.asarray(rho, dtype=np.float64), shape).ravel()
         out = t.copy()
-        act = t > self.T[0]
-        if np.any(act):
-            y = self.y_of_t(t[act]) + self.Lref / self.Tref * self.g1 * rho[act] * dt
-            out[act] = np.maximum(self.t_of_y(y), self.T[0])
-        return out
+        act = np.flatnonzero(t > self.T[0])
+        if act.size == 0:
+            return out.reshape(shape)
+        r = self.g1 * rho[act] * dt            # integral of dT/Lambda still to consume
+        top = t[act].copy()                    # upper end of the current partial segment
+        k = self.segment(top)
+        avail = self.integral_below(top)       # integral from T_k up to `top`
+        lam_t = self.lam(top) / top            # Lambda(top) / top
+        res = np.empty(act.size)
+        live = np.ones(act.size, dtype=bool)
+        while np.any(live):
+            inside = live & (r < avail)
+            if np.any(inside):
+                q = r[inside] * lam_t[inside]
+                res[inside] = top[inside] * np.exp(_l1p_over(self.e[k[inside]], q))
+                live &= ~inside
+            down = live & (k == 0)             # every segment consumed: the floor
+            res[down] = self.T[0]
+            live &= ~down
+            if not np.any(live):
+                break
+            r = np.where(live, r - avail, r)
+            k = np.where(live, k - 1, k)
+            top = np.where(live, self.T[k + 1], top)
+            avail = np.where(live, self.W[k], avail)
+            lam_t = np.where(live, self.L[k + 1] / self.T[k + 1], lam_t)
+        out[act] = np.maximum(res, self.T[0])
+        return out.reshape(shape)
 
     def apply(self, phys, U, dt):
         """Losses over dt on conserved HD / MHD states U (nvar, ...): only e changes, by

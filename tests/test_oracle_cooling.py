@@ -7,7 +7,8 @@ Fixed independently of the oracle's own formulas:
     closed form T^(1-a)(t) = T^(1-a)(0) - (1 - a) k t (a != 1) and T(0) exp(-k t) (a = 1);
   * a many-node table: scipy's adaptive ODE integration of dT/dt with Lambda interpolated
     linearly in (ln T, ln Lambda) by this test;
-  * the floor T_0, and the inverse of the evolution function;
+  * the floor T_0, exact composition of two half steps, and the first-order drop in a
+    tiny step resolved to the local cooling time;
   * the conserved update changes only e, by rho (T_new - T) / (gamma - 1);
   * a static uniform state through a full solver step (Strang halves compose exactly).
 """
@@ -63,20 +64,31 @@ def test_table_matches_adaptive_ode_integration():
                                       method="DOP853", rtol=1e-12, atol=1e-14)
             want = max(sol.y[0, -1], T[0])
             got = cool.cool_temperature(rho, np.array([t_start]), dt)[0]
-            assert abs(got - want) <= 1e-9 * want, (t_start, dt, got, want)
+            assert abs(got - want) <= 1e-10 * want, (t_start, dt, got, want)
 
 
-def test_floor_and_inverse():
-    T, L = W.skew_normal_cooling(n=32)
+def test_floor_composition_and_local_precision():
+    T, L = W.skew_normal_cooling(n=32, peak=20.0)
     cool = Cooling(T, L, 5.0 / 3.0)
-    assert np.all(np.diff(cool.Y) < 0)                     # Y decreases with T
-    t = np.exp(np.linspace(np.log(T[0]) + 1e-9, np.log(T[-1]) + 1.0, 500))
-    back = cool.t_of_y(cool.y_of_t(t))
-    assert np.max(np.abs(back / t - 1.0)) < 1e-10
     # a very long step ends exactly on the floor; at or below the floor nothing changes
     assert np.all(cool.cool_temperature(1.0, np.array([0.5, 5.0, 80.0]), 1e9) == T[0])
     low = np.array([T[0], 0.5 * T[0]])
     assert np.array_equal(cool.cool_temperature(1.0, low, 10.0), low)
+    # exact integration composes: two halves equal the whole step
+    t = np.array([0.02, 0.2, 0.31, 1.0, 7.0, 60.0, 140.0])
+    for dt in (1e-4, 1e-2, 0.3):
+        half = cool.cool_temperature(1.2, cool.cool_temperature(1.2, t, 0.5 * dt), 0.5 * dt)
+        full = cool.cool_temperature(1.2, t, dt)
+        assert np.allclose(half, full, rtol=1e-12, atol=0), dt
+    # first order in a tiny step, to the precision of the local cooling time: near the
+    # peak 1/Lambda at the table's top exceeds the local scale by ~1e6
+    lam = np.exp(np.interp(np.log(t), np.log(T), np.log(L)))
+    top = t > T[-1]                                    # the last power law continues
+    slope = np.log(L[-1] / L[-2]) / np.log(T[-1] / T[-2])
+    lam[top] = L[-1] * (t[top] / T[-1]) ** slope
+    dt = 1e-8 * t / ((2.0 / 3.0) * 1.2 * lam)          # dt / t_cool = 1e-8
+    drop = (t - cool.cool_temperature(1.2, t, dt)) / t
+    assert np.max(np.abs(drop / 1e-8 - 1.0)) < 1e-6
 
 
 @pytest.mark.parametrize("phys", [HD(5.0 / 3.0), MHD(5.0 / 3.0)])
