@@ -207,6 +207,21 @@ agile_status agile_conserved_sums(agile_mesh* mesh, double* sums);
  * Synchronises the mesh's stream. Results equal agile_conserved_sums bit for bit. */
 agile_status agile_conserved_sums_noalloc(agile_mesh* mesh, double* sums);
 
+/* Optically thin radiative losses (Section 2.3.1, the -n_e n_H Lambda(T) sink of Eq. 3)
+ * for the hd and mhd modules, in code units de/dt = -rho^2 Lambda(T) with T = p / rho at
+ * fixed rho and momentum, integrated exactly per cell by Townsend's (2009) method for a
+ * Lambda that is a power law between the table's nodes (the last segment continues
+ * above the table; there are no losses at or below T[0], the temperature floor). The
+ * losses are Strang split: half of dt before every agile_step, half after it (the CFL
+ * speeds of the next step come from the state after the losses).
+ *  T, Lambda  host arrays of n nodes, T strictly increasing, T > 0, Lambda > 0, both
+ *             finite; copied (the call synchronises the mesh's stream)
+ *  n          2..4096 nodes; n = 0 switches the losses off
+ * AGILE_EINVAL for srhd or an invalid table (the previous table stays), AGILE_ENOMEM when
+ * the device copy cannot be allocated. Nodes uniform in ln T get an O(1) lookup, others
+ * a binary search. */
+agile_status agile_set_cooling(agile_mesh* mesh, const double* T, const double* Lambda, int n);
+
 /* Maximum Loehner estimate of every leaf (block order) on the current state after a
  * full ghost fill, computed in FP64 without fused multiply-add so that refinement
  * decisions are reproducible bit for bit. Synchronises. */

@@ -30,7 +30,7 @@ STATUS = {0: "AGILE_OK", 1: "AGILE_EINVAL", 2: "AGILE_ENOMEM", 3: "AGILE_EBUDGET
 EXPORTS = ["agile_mesh_create", "agile_mesh_destroy", "agile_set_state", "agile_set_state_blocks",
            "agile_cfl_dt", "agile_max_speeds", "agile_step", "agile_regrid", "agile_regrid_flags", "agile_get_layout",
            "agile_get_state", "agile_get_aux", "agile_conserved_sums",
-           "agile_conserved_sums_noalloc", "agile_estimate",
+           "agile_conserved_sums_noalloc", "agile_set_cooling", "agile_estimate",
            "agile_get_halo", "agile_sync", "agile_set_kernel_timing", "agile_kernel_timing",
            "agile_selftest_bounded_wait", "agile_last_error", "agile_version",
            "agile_batch_create", "agile_batch_destroy", "agile_batch_layout",
@@ -94,6 +94,7 @@ def load(path: str = LIB_PATH):
         "agile_get_aux": (C.c_int, [P, dp]),
         "agile_conserved_sums": (C.c_int, [P, dp]),
         "agile_conserved_sums_noalloc": (C.c_int, [P, dp]),
+        "agile_set_cooling": (C.c_int, [P, dp, dp, C.c_int]),
         "agile_estimate": (C.c_int, [P, dp]),
         "agile_get_halo": (C.c_int, [P, C.c_size_t, dp]),
         "agile_sync": (C.c_int, [P]),
@@ -311,6 +312,17 @@ class Mesh:
         s = np.zeros(self.nvar)
         self._ck(self.lib.agile_conserved_sums_noalloc(self.ptr, _dptr(s)))
         return s
+
+    def set_cooling(self, T=None, Lambda=None):
+        """Radiative losses from the table (T, Lambda) (None switches them off)."""
+        if T is None:
+            self._ck(self.lib.agile_set_cooling(self.ptr, None, None, 0))
+            return
+        t = np.ascontiguousarray(T, dtype=np.float64)
+        lam = np.ascontiguousarray(Lambda, dtype=np.float64)
+        if t.shape != lam.shape or t.ndim != 1:
+            raise ValueError("T and Lambda must be 1-D arrays of the same length")
+        self._ck(self.lib.agile_set_cooling(self.ptr, _dptr(t), _dptr(lam), int(t.size)))
 
     def estimate(self):
         n, _ = self.layout()

@@ -17,7 +17,7 @@ LIB = os.path.join(OUT, "libagile.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 CU_SOURCES = ["stage_hd.cu", "stage_mhd.cu", "stage_srhd.cu", "stage_srhd_synge.cu", "aux_kernels.cu",
-              "capi.cu"]
+              "cooling.cu", "capi.cu"]
 CPP_SOURCES = ["mesh.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE]

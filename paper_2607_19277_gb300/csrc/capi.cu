@@ -47,6 +47,8 @@ struct agile_mesh {
   bool timing = false;
   std::vector<cudaEvent_t> ev;
   long long stage_launches = 0, total_launches = 0;
+  CoolHost cool;                    // radiative-loss table (nseg == 0: no losses)
+  void* d_cool = nullptr;           // its segments in the stencil precision
 };
 
 namespace {
@@ -407,6 +409,7 @@ void agile_mesh_destroy(agile_mesh* m) {
   dfree_t(m, m->d_work);
   dfree_t(m, m->d_vars);
   dfree_t(m, m->d_weights);
+  dfree(m, m->d_cool);
   for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
   cudaStreamSynchronize(m->stream);
   delete m->mesh;
@@ -486,13 +489,20 @@ agile_status agile_step(agile_mesh* m, double dt) {
   static const double w3[3][2] = {{0.0, 1.0}, {0.75, 0.25}, {1.0 / 3.0, 2.0 / 3.0}};
   const int nst = m->cfg.rk;
   const bool fuse = m->nfix == 0;
+  const bool cool = m->cool.nseg > 0;
+  const bool speeds_in_stage = fuse && !cool;   // else the post-step pass reduces them
+  if (cool) {                                   // first Strang half of the losses
+    AuxArgs a = aux_args(m, m->U[0]);
+    CK(m, launch_cooling(a, m->cool, m->d_cool, m->d_dtch, 0.5, nullptr, m->stream));
+    m->total_launches++;
+  }
   for (int st = 0; st < nst; ++st) {
     const bool last = st == nst - 1;
     void* Us = st == 0 ? m->U[0] : m->U[st];
     void* Uo = last ? m->U[0] : m->U[st + 1];
     s = fill_ghosts(m, Us);
     if (s) return s;
-    if (last && fuse) CK(m, cudaMemsetAsync(m->d_speeds, 0, 2 * sizeof(unsigned long long), m->stream));
+    if (last && speeds_in_stage) CK(m, cudaMemsetAsync(m->d_speeds, 0, 2 * sizeof(unsigned long long), m->stream));
     StageArgs A;
     A.Us = Us;
     A.Un = m->U[0];
@@ -508,7 +518,7 @@ agile_status agile_step(agile_mesh* m, double dt) {
     A.glm_post = (mhd && last && fuse) ? 1 : 0;
     A.nblk = m->nblk;
     A.status = m->d_status;
-    A.speeds = (last && fuse) ? m->d_speeds : nullptr;
+    A.speeds = (last && speeds_in_stage) ? m->d_speeds : nullptr;
     A.tmap = &m->tmap[st == 0 ? 0 : st];
     A.solve_of = nullptr;
     A.work = m->d_work + st;
@@ -543,13 +553,45 @@ agile_status agile_step(agile_mesh* m, double dt) {
     CK(m, launch_glm_decay(a, m->d_dtch, m->stream));
     m->total_launches++;
   }
-  if (fuse) {
+  if (cool) {                                   // second half, with the CFL speeds of U^{n+1}
+    CK(m, cudaMemsetAsync(m->d_speeds, 0, 2 * sizeof(unsigned long long), m->stream));
+    AuxArgs a = aux_args(m, m->U[0]);
+    CK(m, launch_cooling(a, m->cool, m->d_cool, m->d_dtch, 0.5, m->d_speeds, m->stream));
+    m->total_launches++;
+    m->speeds_valid = true;
+  } else if (fuse) {
     m->speeds_valid = true;
   } else {
     m->speeds_valid = false;
     s = ensure_speeds(m);
     if (s) return s;
   }
+  return AGILE_OK;
+}
+
+agile_status agile_set_cooling(agile_mesh* m, const double* T, const double* Lambda, int n) {
+  if (!m) return AGILE_EINVAL;
+  if (n == 0) {
+    CK(m, cudaStreamSynchronize(m->stream));
+    dfree(m, m->d_cool);
+    m->d_cool = nullptr;
+    m->cool = CoolHost();
+    return AGILE_OK;
+  }
+  if (m->cfg.physics != AGILE_HD && m->cfg.physics != AGILE_MHD_GLM)
+    return fail(m, AGILE_EINVAL, "radiative losses apply to hd and mhd");
+  CoolHost c;
+  if (build_cool_table(T, Lambda, n, m->cfg.gamma, &c))
+    return fail(m, AGILE_EINVAL, "cooling table: 2..4096 nodes, T increasing, T and Lambda positive and finite");
+  const size_t bytes = c.segd.size() * (size_t)m->rb;
+  void* d = dalloc(m, bytes);
+  if (!d) return fail(m, AGILE_ENOMEM, "device allocation failed");
+  const void* src = m->rb == 8 ? (const void*)c.segd.data() : (const void*)c.segf.data();
+  CK(m, cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, m->stream));
+  CK(m, cudaStreamSynchronize(m->stream));   // the host table is a temporary
+  dfree(m, m->d_cool);
+  m->d_cool = d;
+  m->cool = c;
   return AGILE_OK;
 }
 

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "agile_internal.h"
 
 namespace agile {
@@ -62,6 +64,29 @@ cudaError_t launch_pack(const AuxArgs& a, double* cons, double* aux, cudaStream_
 cudaError_t launch_sums(const AuxArgs& a, double* part, cudaStream_t s);
 // Face-ghost view of one block: out[nt][20][20][20] (NaN at edges / corners).
 cudaError_t launch_halo(const AuxArgs& a, int block, double* out, cudaStream_t s);
+
+// Radiative-loss table (Townsend exact integration, see cooling.cu): per segment
+// [ln T_k, T_k / L_k, e = 1 - alpha_k, W_k = int_{T_k}^{T_{k+1}} dT / Lambda, T_{k+1},
+//  L_{k+1} / T_{k+1}, L_k / T_k, ln T_{k+1}].
+constexpr int COOL_SEG = 8;
+constexpr int COOL_MAX_NODES = 4096;
+struct CoolDev {
+  int nseg = 0;        // segments (nodes - 1); 0 = no losses
+  int uniform = 0;     // nodes uniform in ln T
+  double lnT0 = 0.0, idln = 0.0, T0 = 0.0;
+  double g1 = 0.0;     // gamma - 1: a step consumes (gamma - 1) rho dt of int dT / Lambda
+};
+struct CoolHost : CoolDev {
+  std::vector<double> segd;
+  std::vector<float> segf;
+};
+// Validates the table (2..COOL_MAX_NODES nodes, T increasing, T and Lambda positive and
+// finite) and fills out; returns nonzero when it is invalid.
+int build_cool_table(const double* T, const double* L, int n, double gamma, CoolHost* out);
+// Losses over frac * dt (dt per solve from dtch) on the hd / mhd pool a.Uw; with speeds
+// != nullptr also the CFL speed maxima of the result (caller zeroes them).
+cudaError_t launch_cooling(const AuxArgs& a, const CoolDev& c, const void* seg, const double* dtch,
+                           double frac, unsigned long long* speeds, cudaStream_t s);
 
 int phys_nvar(int phys);
 int phys_naux(int phys);
