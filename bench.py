@@ -324,7 +324,7 @@ def run_paper_scheme(steps=10, warmup=3):
     """The paper's single-device benchmark scheme (Section 3.1): hydrodynamics, LF (TVDLF),
     PLM van Leer, SSPRK3, periodic, 256^3 in 4096 blocks of 16^3, double shear layer
     stand-in for its double Kelvin-Helmholtz setup, FP64 (the paper's precision) and FP32.
-    Paper context (FP64, NVIDIA B200, same grid and block size): 1.552e9 CUPS (Table 5)."""
+    Paper context (FP64, NVIDIA B200, same grid and block size): 1.552e9 CUPS (Table 4, Appendix B)."""
     import torch
     from paper_2607_19277_gb300 import agile, workloads as W
     out = {"workload": "hd tvdlf vanleer ssprk3 periodic 256^3 (4096 x 16^3), double shear layer",

@@ -86,8 +86,8 @@ typedef struct {
  *  derefine_ratio a block may coarsen when its maximum estimate is below
  *                 refine_tol * derefine_ratio
  *  lohner_eps     noise filter epsilon of the estimator (0.01)
- *  eos            AGILE_EOS_IDEAL: h = 1 + gamma/(gamma-1) p/rho (Eq. 20, every module);
- *                 AGILE_EOS_SYNGE (srhd only): the Synge gas (Eq. 21) in Mathews'
+ *  eos            AGILE_EOS_IDEAL: the ideal gas of every module (Eq. 6, Eq. 21 for srhd);
+ *                 AGILE_EOS_SYNGE (srhd only): the Synge gas (Eq. 22) in Mathews'
  *                 approximation h = 5/2 theta + sqrt(9/4 theta^2 + 1), theta = p/rho
  *                 (Section 2.3.4); gamma is then unused by the physics
  */
@@ -207,7 +207,7 @@ agile_status agile_conserved_sums(agile_mesh* mesh, double* sums);
  * Synchronises the mesh's stream. Results equal agile_conserved_sums bit for bit. */
 agile_status agile_conserved_sums_noalloc(agile_mesh* mesh, double* sums);
 
-/* Optically thin radiative losses (Section 2.3.1, the -n_e n_H Lambda(T) sink of Eq. 3)
+/* Optically thin radiative losses (Section 2.3.1, the -n_e n_H Lambda(T) sink of Eq. 4)
  * for the hd and mhd modules, in code units de/dt = -rho^2 Lambda(T) with T = p / rho at
  * fixed rho and momentum, integrated exactly per cell by Townsend's (2009) method for a
  * Lambda that is a power law between the table's nodes (the last segment continues

@@ -1,5 +1,5 @@
 """Oracle: optically thin radiative losses integrated exactly (Townsend 2009), as the paper's
-Section 2.3.1 prescribes for the energy sink -n_e n_H Lambda(T) of Eq. 3.
+Section 2.3.1 prescribes for the energy sink -n_e n_H Lambda(T) of Eq. 4.
 
 TEST INFRASTRUCTURE ONLY (see the package header): tests, the smoke check and the bench's
 CPU-baseline leg are the only users. Shares no code with the CUDA library.

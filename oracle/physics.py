@@ -10,8 +10,8 @@ follows the paper's Section 2.3:
            flux is the HD get_flux of the paper's flux listing (Section 2.3).
   * mhd  : Eqs. 11-13 with GLM (Eq. 14), e = p/(gamma-1) + rho v^2/2 + B^2/2 (units absorb
            4 pi), Section 2.3.3.
-  * srhd : Eqs. 15-19, con2prim as a 1-D root find in xi = Gamma^2 rho h (Section
-           2.3.4), closed by the ideal-gas enthalpy (Eq. 20) or by the Synge gas (Eq. 21)
+  * srhd : Eqs. 15-20, con2prim as a 1-D root find in xi = Gamma^2 rho h (Section
+           2.3.4), closed by the ideal-gas enthalpy (Eq. 21) or by the Synge gas (Eq. 22)
            in Mathews' approximation, which Section 2.3.4 names instead of the Bessel
            functions: h = 5/2 theta + sqrt(9/4 theta^2 + 1), theta = p / rho.
 """
@@ -166,8 +166,8 @@ class MHD:
 class SRHD:
     """Special-relativistic hydro, U = (D, m, tau), P = (rho, u = Gamma v, p), A = (xi, Gamma).
 
-    eos = "ideal": h = 1 + gamma/(gamma-1) theta (Eq. 20).
-    eos = "synge": Mathews' approximation of the Synge gas (Eq. 21 without the Bessel
+    eos = "ideal": h = 1 + gamma/(gamma-1) theta (Eq. 21).
+    eos = "synge": Mathews' approximation of the Synge gas (Eq. 22 without the Bessel
     functions): h = 5/2 theta + sqrt(9/4 theta^2 + 1). It tends to the ideal gas with
     gamma = 5/3 as theta -> 0 and to gamma = 4/3 as theta -> infinity; gamma is unused.
     """
@@ -186,7 +186,7 @@ class SRHD:
         self.eos = eos
 
     def enthalpy(self, rho, p):
-        """Specific enthalpy h(rho, p): Eq. 20 (ideal gas) or the approximate Synge gas."""
+        """Specific enthalpy h(rho, p): Eq. 21 (ideal gas) or the approximate Synge gas."""
         theta = p / rho
         if self.eos == "synge":
             return 2.5 * theta + np.sqrt(2.25 * theta * theta + 1.0)
@@ -210,7 +210,7 @@ class SRHD:
         return self.gamma * theta / h
 
     def prim2cons(self, P):
-        """Eq. 17 evaluated from the primitives of Eq. 18."""
+        """Eq. 18 evaluated from the primitives of Eq. 19."""
         rho, u, p = P[0], P[1:4], P[4]
         lor = np.sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2])
         h = self.enthalpy(rho, p)
@@ -221,7 +221,7 @@ class SRHD:
         return U
 
     def aux_from_prim(self, P):
-        """Auxiliaries of Eq. 19: xi = Gamma^2 rho h and Gamma."""
+        """Auxiliaries of Eq. 20: xi = Gamma^2 rho h and Gamma."""
         rho, u, p = P[0], P[1:4], P[4]
         lor = np.sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2])
         A = np.empty((2,) + P.shape[1:])

@@ -46,7 +46,7 @@ class Config:
     flux: str = "hll"              # 'hll' | 'tvdlf' | 'hllc' (hd only)
     rk: int = 2
     gamma: float = 5.0 / 3.0
-    eos: str = "ideal"             # srhd: 'ideal' (Eq. 20) | 'synge' (approximate Synge gas)
+    eos: str = "ideal"             # srhd: 'ideal' (Eq. 21) | 'synge' (approximate Synge gas)
     cfl: float = 0.4
     glm_alpha: float = 0.5
     base_blocks: tuple = (4, 4, 4)

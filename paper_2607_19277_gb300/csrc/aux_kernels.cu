@@ -363,7 +363,7 @@ __global__ void prim2cons_kernel(R* __restrict__ U, const double* __restrict__ p
 #pragma unroll
     for (int v = 0; v < NV; ++v) o[(size_t)v * NCELL] = R(u[v]);
     if constexpr (NA > 0) {
-      // xi = Gamma^2 rho h and Gamma from the primitives (Eq. 19)
+      // xi = Gamma^2 rho h and Gamma from the primitives (Eq. 20)
       const double lor = sqrt(1.0 + p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
       const double h = P::enthalpy(p[0], p[4], pp);
       o[(size_t)NV * NCELL] = R(lor * lor * p[0] * h);

@@ -1,4 +1,4 @@
-// Optically thin radiative losses (paper Section 2.3.1, energy sink of Eq. 3) integrated
+// Optically thin radiative losses (paper Section 2.3.1, energy sink of Eq. 4) integrated
 // exactly per cell (Townsend 2009): in code units de/dt = -rho^2 Lambda(T), T = p / rho, at
 // fixed rho and momentum, i.e. dT/dt = -(gamma - 1) rho Lambda(T), so a step of dt moves T
 // down to the T_new with  int_{T_new}^{T} dT'/Lambda = r = (gamma - 1) rho dt.

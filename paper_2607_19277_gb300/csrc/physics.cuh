@@ -3,10 +3,10 @@
 // Each trait gives the conserved <-> primitive maps, the physical flux along one axis and
 // the approximate Riemann flux at a face, evaluated per cell in registers (the paper's
 // cell-local physics routines, Section 2.3):
-//   HdPhys   : Eqs. 2-4 with e = p/(gamma-1) + rho v^2/2 (Section 2.3.1; HD flux listing)
+//   HdPhys   : Eqs. 2-4 with e = p/(gamma-1) + rho v^2/2 (Eq. 6; Section 2.3.1; HD flux listing)
 //   MhdPhys  : Eqs. 11-13 with GLM (Eq. 14), e = p/(gamma-1) + rho v^2/2 + B^2/2 (Section 2.3.3)
-//   SrhdPhys : Eqs. 15-19 with the ideal-gas enthalpy of Eq. 20 (Section 2.3.4), and
-//   SrhdSyngePhys with the approximate Synge-gas enthalpy (Eq. 21, Mathews' form); the
+//   SrhdPhys : Eqs. 15-20 with the ideal-gas enthalpy of Eq. 21 (Section 2.3.4), and
+//   SrhdSyngePhys with the approximate Synge-gas enthalpy (Eq. 22, Mathews' form); the
 //              conserved-to-primitive recovery is a Newton root find in xi = Gamma^2 rho h,
 //              always in FP64.
 // Riemann fluxes: HLL with Davis wave-speed estimates, or TVDLF (Rusanov) with the larger
@@ -216,8 +216,8 @@ struct MhdPhys {
 // ------------------------------------------------------------------------------ SRHD
 enum : int { EOS_IDEAL = 0, EOS_SYNGE = 1 };
 
-// Closure h(rho, p) of Section 2.3.4: the ideal gas h = 1 + gamma/(gamma-1) theta (Eq. 20)
-// or the Synge gas (Eq. 21) in Mathews' approximation h = 5/2 theta + sqrt(9/4 theta^2 + 1),
+// Closure h(rho, p) of Section 2.3.4: the ideal gas h = 1 + gamma/(gamma-1) theta (Eq. 21)
+// or the Synge gas (Eq. 22) in Mathews' approximation h = 5/2 theta + sqrt(9/4 theta^2 + 1),
 // theta = p / rho, which tends to the ideal gas with gamma = 5/3 (cold) and 4/3 (hot).
 template <typename R, int EOS>
 struct SrhdEos {

@@ -1,5 +1,5 @@
 """Pins of the oracle's radiative-loss integration (Townsend 2009 exact integration, the
-method Section 2.3.1 names for the sink -n_e n_H Lambda(T) of Eq. 3; code units
+method Section 2.3.1 names for the sink -n_e n_H Lambda(T) of Eq. 4; code units
 de/dt = -rho^2 Lambda(T), T = p / rho).
 
 Fixed independently of the oracle's own formulas:

@@ -1,4 +1,4 @@
-"""Pins of the oracle's approximate Synge-gas EOS for SRHD (Section 2.3.4, Eq. 21 and the
+"""Pins of the oracle's approximate Synge-gas EOS for SRHD (Section 2.3.4, Eq. 22 and the
 Mathews approximation the paper uses instead of the Bessel functions).
 
 What fixes the EOS independently of the oracle's own formulas:
