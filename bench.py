@@ -349,6 +349,40 @@ def run_paper_scheme(steps=10, warmup=3):
     return out
 
 
+def run_cooling(steps=20, warmup=3):
+    """MHD+GLM 256^3 (the headline workload, FP32 stencil) with optically thin radiative
+    losses (Section 2.3.1; log-skew-normal loss table peaked at the Orszag-Tang temperature
+    p / rho = 0.25, cooling time ~0.1 code units), against the same run without losses: the
+    throughput cost of the source term (the paper reports 10.2% for its FFHD case on an
+    H100, Section 4.4)."""
+    import torch
+    from paper_2607_19277_gb300 import agile, workloads as W
+    T, L = W.skew_normal_cooling(n=256, t_min=1e-2, t_max=1e2, t_peak=0.25, peak=1.0)
+    res = {}
+    for name, cool in (("plain", False), ("cooling", True)):
+        m = agile.Mesh(agile.make_config(real_bytes=4, **spec()))
+        if cool:
+            m.set_cooling(T, L)
+        m.set_state(W.orszag_tang_3d(N_SIDE))
+        for _ in range(warmup):
+            m.step(0.0)
+        m.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            m.step(0.0)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = e0.elapsed_time(e1) / steps
+        m.close()
+    zones = float(N_SIDE ** 3) * 3
+    return {"workload": "mhd_glm 256^3 hll vanleer ssprk3 fp32 + radiative losses (256-node table)",
+            "value": zones / (res["cooling"] / 1e3), "unit": UNIT,
+            "ms_per_step": res["cooling"], "ms_per_step_without": res["plain"],
+            "throughput_reduction": 1.0 - res["plain"] / res["cooling"]}
+
+
 def run_serving(nreq=32, rate=50.0, budget_gb=160.0):
     """Serving stream (bounded sample of the configured stream): Poisson arrivals of HD /
     MHD / SRHD solves admitted against the HBM budget, FP32 stencils, then the same stream on
@@ -427,6 +461,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-paper-scheme", action="store_true")
+    ap.add_argument("--no-cooling", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -530,6 +565,11 @@ def main():
             line["paper_scheme_hd"] = run_paper_scheme()
         except Exception as e:
             line["paper_scheme_hd"] = {"error": str(e)}
+    if not args.no_cooling:
+        try:
+            line["cooling_mhd"] = run_cooling()
+        except Exception as e:
+            line["cooling_mhd"] = {"error": str(e)}
     if not args.no_serving:
         try:
             line["serving"] = run_serving()

@@ -215,7 +215,9 @@ agile_status agile_conserved_sums_noalloc(agile_mesh* mesh, double* sums);
  * losses are Strang split: half of dt before every agile_step, half after it (the CFL
  * speeds of the next step come from the state after the losses).
  *  T, Lambda  host arrays of n nodes, T strictly increasing, T > 0, Lambda > 0, both
- *             finite; copied (the call synchronises the mesh's stream)
+ *             finite, and T_k / Lambda_k and the per-segment integrals of 1/Lambda finite
+ *             in the stencil precision (float for real_bytes = 4); copied (the call
+ *             synchronises the mesh's stream)
  *  n          2..4096 nodes; n = 0 switches the losses off
  * AGILE_EINVAL for srhd or an invalid table (the previous table stays), AGILE_ENOMEM when
  * the device copy cannot be allocated. Nodes uniform in ln T get an O(1) lookup, others

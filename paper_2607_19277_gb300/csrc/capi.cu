@@ -581,8 +581,9 @@ agile_status agile_set_cooling(agile_mesh* m, const double* T, const double* Lam
   if (m->cfg.physics != AGILE_HD && m->cfg.physics != AGILE_MHD_GLM)
     return fail(m, AGILE_EINVAL, "radiative losses apply to hd and mhd");
   CoolHost c;
-  if (build_cool_table(T, Lambda, n, m->cfg.gamma, &c))
-    return fail(m, AGILE_EINVAL, "cooling table: 2..4096 nodes, T increasing, T and Lambda positive and finite");
+  if (build_cool_table(T, Lambda, n, m->cfg.gamma, m->rb, &c))
+    return fail(m, AGILE_EINVAL, "cooling table: 2..4096 nodes, T increasing, T and Lambda positive and "
+                                 "finite, segment constants representable in the stencil precision");
   const size_t bytes = c.segd.size() * (size_t)m->rb;
   void* d = dalloc(m, bytes);
   if (!d) return fail(m, AGILE_ENOMEM, "device allocation failed");

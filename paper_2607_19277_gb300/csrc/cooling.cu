@@ -27,7 +27,7 @@ namespace {
 double em1_over(double e, double x) { return e != 0.0 ? std::expm1(e * x) / e : x; }
 }  // namespace
 
-int build_cool_table(const double* T, const double* L, int n, double gamma, CoolHost* out) {
+int build_cool_table(const double* T, const double* L, int n, double gamma, int real_bytes, CoolHost* out) {
   if (n < 2 || n > COOL_MAX_NODES || !T || !L || !out) return 1;
   for (int k = 0; k < n; ++k) {
     if (!(T[k] > 0.0) || !(L[k] > 0.0) || !std::isfinite(T[k]) || !std::isfinite(L[k])) return 1;
@@ -50,12 +50,19 @@ int build_cool_table(const double* T, const double* L, int n, double gamma, Cool
     s[7] = lt1;
   }
   out->segf.resize(out->segd.size());
-  for (size_t i = 0; i < out->segd.size(); ++i) out->segf[i] = (float)out->segd[i];
+  for (size_t i = 0; i < out->segd.size(); ++i) {
+    if (!std::isfinite(out->segd[i])) return 1;
+    out->segf[i] = (float)out->segd[i];
+  }
   // nodes uniform in ln T allow an O(1) segment lookup
   const double l0 = std::log(T[0]), dl = (std::log(T[n - 1]) - l0) / ns;
   bool uni = dl > 0.0;
   for (int k = 1; k < n && uni; ++k)
     uni = std::fabs(std::log(T[k]) - (l0 + k * dl)) <= 1e-9 * dl;
+  if (real_bytes == 4) {   // the FP32 stencil evaluates the table in float: it must fit
+    for (float v : out->segf)
+      if (!std::isfinite(v)) return 1;
+  }
   out->nseg = ns;
   out->uniform = uni ? 1 : 0;
   out->lnT0 = l0;

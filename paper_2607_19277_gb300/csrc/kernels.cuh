@@ -308,6 +308,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   // from the launch's counter; every block completes 5 phases of each ring barrier, so the
   // CTA's jb-th block starts at parity jb & 1.
   __shared__ int s_next;
+  __shared__ int s_src[6], s_slot[6];   // face sources / register slots of the current block
   // Launch constants, and the per-(solve, level) constants of the current block: they are
   // recomputed only when the block's solve or level differs from the previous block's (a
   // CTA-uniform test), so the FP64 divisions and the exp stay off the per-block path.
@@ -320,16 +321,20 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   int key_sv = -1, key_lev = -1;
   R idx = R(0), idy = R(0), idz = R(0), rdt = R(0), glm_fr = R(1);
   R dxr[3] = {R(0), R(0), R(0)};
+  if (t == 0 && blockIdx.x < A.nblk) {
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      s_src[f] = A.bd[blockIdx.x].src[f];
+      s_slot[f] = A.bd[blockIdx.x].slot[f];
+    }
+  }
+  __syncthreads();
+  const int* src = s_src;
+  const int* slot = s_slot;
   for (int b = blockIdx.x, jb = 0; b < A.nblk; ++jb) {
   const int sv = A.solve_of ? A.solve_of[b] : 0;
   unsigned long long* speeds = A.speeds ? A.speeds + 2 * sv : nullptr;
   const BlockDesc& bd = A.bd[b];
-  int src[6], slot[6];
-#pragma unroll
-  for (int f = 0; f < 6; ++f) {
-    src[f] = bd.src[f];
-    slot[f] = bd.slot[f];
-  }
   if (sv != key_sv || bd.level != key_lev) {
     const double* dtch = A.dtch + 2 * sv;
     const double dt = dtch[0];
@@ -397,17 +402,22 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       for (int i = 0; i < NA; ++i) w[(NV + i) * 256] = aux[i];
     }
   };
-  auto zface = [&](int k, R* f) {          // z-face flux at k + 1/2 of this column
-    R a[NV], bq[NV], c[NV], d[NV], pl[NV], pr[NV];
-    const R* r0 = sPr + (size_t)((k - 1) & 3) * NT * 256 + cell2;
+  // z-face flux at k + 1/2 of this column. hz holds half the limited slope of plane k
+  // (from the previous z-face, where plane k was the upper cell) and leaves with that of
+  // plane k + 1, so each plane's z-slope is formed once.
+  auto zface = [&](int k, R* f, R* hz) {
+    R bq[NV], c[NV], d[NV], pl[NV], pr[NV];
     const R* r1 = sPr + (size_t)(k & 3) * NT * 256 + cell2;
     const R* r2 = sPr + (size_t)((k + 1) & 3) * NT * 256 + cell2;
     const R* r3 = sPr + (size_t)((k + 2) & 3) * NT * 256 + cell2;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      a[v] = r0[v * 256]; bq[v] = r1[v * 256]; c[v] = r2[v * 256]; d[v] = r3[v * 256];
+      bq[v] = r1[v * 256]; c[v] = r2[v * 256]; d[v] = r3[v * 256];
+      const R h = half_slope<R, LIM>(c[v] - bq[v], d[v] - c[v]);
+      pl[v] = bq[v] + hz[v];
+      pr[v] = c[v] - h;
+      hz[v] = h;
     }
-    plm<NV, R, LIM>(a, bq, c, d, pl, pr);
     riemann<P, R, 2, FLUX>(pl, pr, f, pp);
   };
   auto xface = [&](int fi, int row, R* f) {  // x-face fi - 1/2 of row `row` in plane buffer
@@ -469,8 +479,15 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   }
   convert_own(0);
   convert_own(1);
-  R fzd[NV], fzu[NV];
-  zface(-1, fzd);
+  R fzd[NV], fzu[NV], hz[NV];
+  {
+    const R* r0 = sPr + (size_t)((-2) & 3) * NT * 256 + cell2;
+    const R* r1 = sPr + (size_t)((-1) & 3) * NT * 256 + cell2;
+    const R* r2 = sPr + (size_t)(0 & 3) * NT * 256 + cell2;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) hz[v] = half_slope<R, LIM>(r1[v * 256] - r0[v * 256], r2[v * 256] - r1[v * 256]);
+  }
+  zface(-1, fzd, hz);
   if (FR && slot[4] >= 0) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) FR[((size_t)slot[4] * NV + v) * 256 + cell2] = fzd[v];
@@ -564,7 +581,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
           for (int v = 0; v < NV; ++v) FR[((size_t)sl * NV + v) * 256 + k * 16 + r] = f[v];
         }
       }
-      zface(k, fzu);
+      zface(k, fzu, hz);
       if (FR && k == NB - 1 && slot[5] >= 0) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) FR[((size_t)slot[5] * NV + v) * 256 + cell2] = fzu[v];
@@ -611,7 +628,18 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     }
   }
   if (speeds) block_max2<256>((double)ssum, (double)smax, speeds);
-  if (t == 0) s_next = A.work ? (int)gridDim.x + atomicAdd(A.work, 1) : b + (int)gridDim.x;
+  if (t == 0) {
+    // every read of this block's face table happened before the last plane's second barrier
+    const int nx = A.work ? (int)gridDim.x + atomicAdd(A.work, 1) : b + (int)gridDim.x;
+    s_next = nx;
+    if (nx < A.nblk) {
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        s_src[f] = A.bd[nx].src[f];
+        s_slot[f] = A.bd[nx].slot[f];
+      }
+    }
+  }
   __syncthreads();       // ring, halo staging and reduction scratch are reused by the next block
   b = s_next;
   }

@@ -81,8 +81,9 @@ struct CoolHost : CoolDev {
   std::vector<float> segf;
 };
 // Validates the table (2..COOL_MAX_NODES nodes, T increasing, T and Lambda positive and
-// finite) and fills out; returns nonzero when it is invalid.
-int build_cool_table(const double* T, const double* L, int n, double gamma, CoolHost* out);
+// finite, every derived segment quantity finite in the stencil precision real_bytes) and
+// fills out; returns nonzero when it is invalid.
+int build_cool_table(const double* T, const double* L, int n, double gamma, int real_bytes, CoolHost* out);
 // Losses over frac * dt (dt per solve from dtch) on the hd / mhd pool a.Uw; with speeds
 // != nullptr also the CFL speed maxima of the result (caller zeroes them).
 cudaError_t launch_cooling(const AuxArgs& a, const CoolDev& c, const void* seg, const double* dtch,

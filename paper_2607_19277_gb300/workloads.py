@@ -290,4 +290,7 @@ def skew_normal_cooling(n: int = 256, t_min: float = 1e-2, t_max: float = 1e2, t
     mu = math.log(t_peak) - grid[int(np.argmax(g))]
     amp = peak / float(shape(np.array([math.log(t_peak)]), mu)[0])
     lnt = np.linspace(math.log(t_min), math.log(t_max), n)
-    return np.exp(lnt), amp * shape(lnt, mu)
+    lam = amp * shape(lnt, mu)
+    if not np.all(lam > 0.0):
+        raise ValueError("the loss function underflows to zero on [t_min, t_max]; raise t_min")
+    return np.exp(lnt), lam
