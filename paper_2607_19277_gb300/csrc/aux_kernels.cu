@@ -3,6 +3,8 @@
 // Loehner estimator, regrid prolongation/restriction, state packing and conserved sums.
 #include <math.h>
 
+#include <type_traits>
+
 #include "kernels.cuh"
 #include "launch.h"
 
@@ -213,16 +215,33 @@ __global__ void set_dt_kernel(const unsigned long long* speeds, double* dtch, do
 }
 
 // ------------------------------------------------------------------------------ GLM source
+// One CTA per block: thread 0 forms the factor in FP64, the CTA scales psi in the stencil
+// precision with 16-byte accesses (psi of a block is 4096 contiguous values).
 template <typename R>
-__global__ void glm_decay_kernel(R* __restrict__ U, const BlockDesc* __restrict__ bd,
-                                 const double* __restrict__ dtch, double alpha,
-                                 const int* __restrict__ solve_of) {
+__global__ void __launch_bounds__(256) glm_decay_kernel(R* __restrict__ U, const BlockDesc* __restrict__ bd,
+                                                         const double* __restrict__ dtch, double alpha,
+                                                         const int* __restrict__ solve_of) {
+  __shared__ R s_f;
   const int b = blockIdx.x;
-  const double* dc = dtch + 2 * (solve_of ? solve_of[b] : 0);
-  const double dxm = fmin(fmin(bd[b].dx[0], bd[b].dx[1]), bd[b].dx[2]);
-  const double f = exp(-0.5 * dc[0] * dc[1] * alpha / dxm);
-  R* psi = U + ((size_t)b * 9 + 8) * NCELL;
-  for (int c = threadIdx.x; c < NCELL; c += blockDim.x) psi[c] = R((double)psi[c] * f);
+  if (threadIdx.x == 0) {
+    const double* dc = dtch + 2 * (solve_of ? solve_of[b] : 0);
+    const double dxm = fmin(fmin(bd[b].dx[0], bd[b].dx[1]), bd[b].dx[2]);
+    s_f = R(exp(-0.5 * dc[0] * dc[1] * alpha / dxm));
+  }
+  __syncthreads();
+  const R f = s_f;
+  using V = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
+  constexpr int PER = 16 / sizeof(R);
+  V* psi = reinterpret_cast<V*>(U + ((size_t)b * 9 + 8) * NCELL);
+  for (int c = threadIdx.x; c < NCELL / PER; c += blockDim.x) {
+    V v = psi[c];
+    if constexpr (sizeof(R) == 4) {
+      v.x *= f; v.y *= f; v.z *= f; v.w *= f;
+    } else {
+      v.x *= f; v.y *= f;
+    }
+    psi[c] = v;
+  }
 }
 
 // ------------------------------------------------------------------------------ estimator
