@@ -394,6 +394,10 @@ def run_serving(nreq=32, rate=50.0, budget_gb=160.0):
         srv = serving.Server(int(budget_gb * 2 ** 30), real_bytes=rb, steps_per_poll=4)
         rep = srv.run(reqs)
         out[name] = rep.summary()
+    # the same stream with requests joining per-physics batches (graph-replayed steps)
+    reqs = serving.request_stream(nreq, rate=rate, sides=(32, 64, 96), steps=(10, 30))
+    rep = serving.BatchedServer(int(budget_gb * 2 ** 30), real_bytes=4, rebuild_every=4).run(reqs)
+    out["fp32_batched"] = rep.summary()
     out["workload"] = ("%d requests, Poisson mean %g/s, physics hd/mhd/srhd, sides 32-96, "
                        "10-30 steps, budget %g GB (bounded sample of the 1000-request stream)"
                        % (nreq, rate, budget_gb))

@@ -281,6 +281,14 @@ agile_status agile_batch_cfl_dt(agile_batch* batch, double* dt);
 /* State of one solve, as agile_get_state. Synchronises. */
 agile_status agile_batch_get_state(agile_batch* batch, int solve, int* level, int* ijk, double* cons);
 
+/* Copy the current state of solve src_solve of batch src into solve dst_solve of batch dst
+ * (device to device; no counterpart in the paper: it lets a request loop rebuild its batch
+ * when solves join or leave without a host round trip). The two solves must have the same
+ * block layout, domain, boundaries, physics, EOS and stencil precision. Waits for the
+ * source batch's stream and the copy (synchronising both); the next step of dst
+ * recomputes its CFL speeds. AGILE_EINVAL when the solves differ. */
+agile_status agile_batch_copy_solve(agile_batch* dst, int dst_solve, agile_batch* src, int src_solve);
+
 /* Wait for the batch stream and return any latched device error. */
 agile_status agile_batch_sync(agile_batch* batch);
 

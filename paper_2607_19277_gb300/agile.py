@@ -34,7 +34,7 @@ EXPORTS = ["agile_mesh_create", "agile_mesh_destroy", "agile_set_state", "agile_
            "agile_get_halo", "agile_sync", "agile_set_kernel_timing", "agile_kernel_timing",
            "agile_selftest_bounded_wait", "agile_last_error", "agile_version",
            "agile_batch_create", "agile_batch_destroy", "agile_batch_layout",
-           "agile_batch_set_state", "agile_batch_step", "agile_batch_cfl_dt",
+           "agile_batch_set_state", "agile_batch_step", "agile_batch_cfl_dt", "agile_batch_copy_solve",
            "agile_batch_get_state", "agile_batch_sync", "agile_batch_launches",
            "agile_batch_last_error"]
 
@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH):
         "agile_batch_step": (C.c_int, [P]),
         "agile_batch_cfl_dt": (C.c_int, [P, dp]),
         "agile_batch_get_state": (C.c_int, [P, C.c_int, ip, ip, dp]),
+        "agile_batch_copy_solve": (C.c_int, [P, C.c_int, P, C.c_int]),
         "agile_batch_sync": (C.c_int, [P]),
         "agile_batch_launches": (C.c_longlong, [P]),
         "agile_batch_last_error": (C.c_char_p, [P]),
@@ -421,6 +422,10 @@ class Batch:
         cons = np.zeros((n, nv, 16, 16, 16))
         self._ck(self.lib.agile_batch_get_state(self.ptr, solve, _iptr(lev), _iptr(ijk), _dptr(cons)))
         return lev, ijk, cons
+
+    def copy_solve(self, solve, src, src_solve):
+        """Device-to-device copy of solve src_solve of Batch src into solve `solve`."""
+        self._ck(self.lib.agile_batch_copy_solve(self.ptr, solve, src.ptr, src_solve))
 
     def sync(self):
         self._ck(self.lib.agile_batch_sync(self.ptr))

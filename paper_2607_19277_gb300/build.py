@@ -21,8 +21,10 @@ CU_SOURCES = ["stage_hd.cu", "stage_mhd.cu", "stage_srhd.cu", "stage_srhd_synge.
 CPP_SOURCES = ["mesh.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
-# The stage kernels' FP32 instantiations use the fast single-precision divide and square
-# root (max 2 ulp); FP64 arithmetic is unaffected by these flags.
+# Every FP32 kernel uses the fast single-precision divide and square root (max 2 ulp) and
+# flushes denormals, so that a quantity formed in two kernels (the CFL speeds fused into the
+# last stage and the standalone speed reduction) has the same bits; FP64 arithmetic is
+# unaffected by these flags.
 FAST_FP32 = ["--prec-div=false", "--prec-sqrt=false", "--ftz=true"]
 
 
@@ -43,6 +45,11 @@ def _stale(obj, deps):
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
+    # objects built with other flags are stale too
+    stamp = os.path.join(OUT, "flags.txt")
+    flags = " ".join(ARCH + NVCC_FLAGS + FAST_FP32)
+    if not os.path.exists(stamp) or open(stamp).read() != flags:
+        force = True
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "agile.h"))
     jobs = []
@@ -52,7 +59,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         o = os.path.join(OUT, src + ".o")
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            extra = FAST_FP32 if src.startswith("stage_") else []
+            extra = FAST_FP32
             jobs.append([nvcc] + ARCH + NVCC_FLAGS + extra + ["-c", s, "-o", o])
     for src in CPP_SOURCES:
         s = os.path.join(CSRC, src)
@@ -74,6 +81,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
         tmp = LIB + ".tmp"
         run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
         os.replace(tmp, LIB)
+        with open(stamp, "w") as f:
+            f.write(flags)
     return LIB
 
 

@@ -1213,6 +1213,28 @@ agile_status agile_batch_get_state(agile_batch* B, int solve, int* level, int* i
   return s;
 }
 
+agile_status agile_batch_copy_solve(agile_batch* dst, int dst_solve, agile_batch* src, int src_solve) {
+  if (!dst || !src || dst_solve < 0 || dst_solve >= dst->nsolve || src_solve < 0 || src_solve >= src->nsolve)
+    return bfail(dst, AGILE_EINVAL, "bad argument");
+  const agile_config& a = dst->cfgs[dst_solve];
+  const agile_config& b = src->cfgs[src_solve];
+  bool same = dst->nt == src->nt && dst->rb == src->rb && a.physics == b.physics && a.eos == b.eos;
+  for (int d = 0; d < 3 && same; ++d)
+    same = a.base_blocks[d] == b.base_blocks[d] && a.xmin[d] == b.xmin[d] && a.xmax[d] == b.xmax[d];
+  for (int f = 0; f < 6 && same; ++f) same = a.bc[f] == b.bc[f];
+  const size_t n = dst->meshes[dst_solve]->blocks().size();
+  if (!same || n != src->meshes[src_solve]->blocks().size())
+    return bfail(dst, AGILE_EINVAL, "solves differ in layout, domain, boundaries or scheme");
+  agile_status s = batch_status(src);     // the source's pending work is complete and error-free
+  if (s) return bfail(dst, s, "source batch: " + src->err);
+  const size_t per = (size_t)dst->nt * NCELL * dst->rb;
+  BCK(dst, cudaMemcpyAsync((char*)dst->U[0] + dst->offset[dst_solve] * per,
+                           (const char*)src->U[0] + src->offset[src_solve] * per, n * per,
+                           cudaMemcpyDeviceToDevice, dst->stream));
+  dst->speeds_valid = false;
+  return batch_status(dst);
+}
+
 agile_status agile_batch_sync(agile_batch* B) {
   if (!B) return AGILE_EINVAL;
   return batch_status(B);

@@ -210,3 +210,130 @@ def run_alone(req: Request, real_bytes: int = 4):
     out = m.get_state()[2]
     m.close()
     return out
+
+
+class BatchedServer:
+    """Requests join a shared batched work list as slots free up.
+
+    The admitted solves of one physics module run in one `agile.Batch` (one persistent
+    launch per RK stage over all of them, every step after the first replayed from a CUDA
+    graph, each solve with its own on-device CFL dt), and the groups of the three modules
+    run on their own streams so that their launches overlap. When solves finish or new ones
+    are admitted, the group's batch is rebuilt: the survivors' states are copied device to
+    device (agile_batch_copy_solve) and the newcomers' initial conditions are loaded. A
+    rebuild happens at most every `rebuild_every` steps of the group (sooner when the group
+    is empty); a solve that reaches its step count is read out at once, so every result is
+    the state after exactly its requested steps, equal to the same request run alone."""
+
+    def __init__(self, budget_bytes: int, real_bytes: int = 4, rebuild_every: int = 4,
+                 keep_results: bool = False):
+        self.budget = int(budget_bytes)
+        self.rb = real_bytes
+        self.rebuild_every = max(1, int(rebuild_every))
+        self.keep = keep_results
+
+    def _rebuild(self, g):
+        """New batch for the group's members: survivors copied, newcomers initialised.
+        Returns the device bytes of the finished solves it drops."""
+        old, old_index = g["batch"], g["index"]
+        freed = sum(pool_bytes(r, self.rb) for r in g["members"] if r.rid in g["done"])
+        members = [r for r in g["members"] if r.rid not in g["done"]] + g["joining"]
+        g["joining"] = []
+        g["members"] = members
+        g["done"] = set()
+        g["since"] = 0
+        if not members:
+            g["batch"], g["index"] = None, {}
+        else:
+            nb = agile.Batch([scheme(r.physics, self.rb, r.side) for r in members])
+            index = {}
+            for i, r in enumerate(members):
+                index[r.rid] = i
+                if old is not None and r.rid in old_index:
+                    nb.copy_solve(i, old, old_index[r.rid])
+                else:
+                    nb.set_state(i, initial_condition(r))
+            g["batch"], g["index"] = nb, index
+        if old is not None:
+            old.close()
+        return freed
+
+    def run(self, requests, time_scale: float = 1.0, max_wall_s: float = 3600.0) -> Report:
+        """Serve `requests`; the budget counts the pools of every solve still held by a batch
+        (a finished solve's pool is released when its batch is rebuilt; during a rebuild the
+        old and the new batch coexist briefly)."""
+        pending = sorted(requests, key=lambda r: r.arrival)
+        waiting = []
+        groups = {p: {"batch": None, "index": {}, "members": [], "joining": [], "done": set(),
+                      "left": {}, "since": 0} for p in PHYS}
+        used = max_used = max_conc = 0
+        zones = 0.0
+        t0 = time.perf_counter()
+        k = 0
+
+        def active():
+            return sum(len(g["members"]) - len(g["done"]) + len(g["joining"]) for g in groups.values())
+
+        def held():
+            return sum(len(g["members"]) + len(g["joining"]) for g in groups.values())
+
+        while k < len(pending) or waiting or held():
+            now = time.perf_counter() - t0
+            if now > max_wall_s:
+                for g in groups.values():
+                    if g["batch"] is not None:
+                        g["batch"].close()
+                raise TimeoutError("serving loop exceeded %.0f s" % max_wall_s)
+            while k < len(pending) and pending[k].arrival * time_scale <= now:
+                waiting.append(pending[k])
+                k += 1
+            i = 0
+            while i < len(waiting):         # admit in arrival order while the budget allows
+                r = waiting[i]
+                need = pool_bytes(r, self.rb)
+                if need > self.budget:
+                    raise ValueError("request %d needs %d bytes, more than the budget" % (r.rid, need))
+                if used + need <= self.budget:
+                    g = groups[r.physics]
+                    g["joining"].append(r)
+                    g["left"][r.rid] = r.steps
+                    r.admitted = time.perf_counter() - t0
+                    used += need
+                    max_used = max(max_used, used)
+                    waiting.pop(i)
+                    continue
+                i += 1
+            max_conc = max(max_conc, active())
+            stepped = False
+            for g in groups.values():
+                live = len(g["members"]) - len(g["done"])
+                if (g["joining"] or g["done"]) and (live == 0 or g["since"] >= self.rebuild_every):
+                    used -= self._rebuild(g)
+                b = g["batch"]
+                if b is None:
+                    continue
+                b.step()
+                g["since"] += 1
+                stepped = True
+                for r in g["members"]:
+                    if r.rid in g["done"]:
+                        continue
+                    g["left"][r.rid] -= 1
+                    if g["left"][r.rid] == 0:
+                        lev, ijk, cons = b.get_state(g["index"][r.rid])
+                        if self.keep:
+                            r.result = cons
+                        r.finished = time.perf_counter() - t0
+                        stages = 2 if r.physics == "srhd" else 3
+                        zones += float(r.side ** 3) * stages * r.steps
+                        g["done"].add(r.rid)
+            if not stepped and not waiting and k < len(pending):
+                time.sleep(max(0.0, pending[k].arrival * time_scale - (time.perf_counter() - t0)))
+        for g in groups.values():
+            if g["batch"] is not None:
+                g["batch"].close()
+        wall = time.perf_counter() - t0
+        rep = Report(requests=requests, wall_s=wall, zone_updates=zones, max_resident_bytes=max_used,
+                     max_concurrent=max_conc)
+        rep.latencies = [r.finished - r.arrival * time_scale for r in requests]
+        return rep

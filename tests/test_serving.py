@@ -102,3 +102,57 @@ def test_server_loop_terminates_without_gpu_work(monkeypatch):
     rep = srv.run(reqs, max_wall_s=30.0)
     assert all(r.finished >= 0 for r in reqs)
     assert rep.max_resident_bytes <= srv.budget and rep.max_concurrent >= 1
+
+
+@pytest.mark.gpu
+def test_batched_serving_matches_alone():
+    """Requests join per-physics batches as slots free up (rebuilds copy the survivors on the
+    device); every result equals the request run alone, bit for bit."""
+    reqs = [serving.Request(rid=i, physics=("hd", "mhd", "srhd")[i % 3], side=(32, 48)[i % 2],
+                            steps=3 + (i % 5), seed=700 + i, arrival=0.001 * i) for i in range(9)]
+    sizes = sorted(serving.pool_bytes(r, 4) for r in reqs)
+    budget = sum(sizes[-4:])                         # room for about four at once
+    srv = serving.BatchedServer(budget, real_bytes=4, rebuild_every=2, keep_results=True)
+    rep = srv.run(reqs, max_wall_s=120.0)
+    assert rep.max_resident_bytes <= budget
+    assert rep.max_concurrent >= 2
+    for r in reqs:
+        assert r.finished > 0 and r.admitted >= r.arrival - 1e-9
+        assert np.array_equal(r.result, serving.run_alone(r, real_bytes=4)), r.rid
+
+
+def test_batched_server_reads_each_solve_at_its_step_count(monkeypatch):
+    """Host logic of the batched loop with a fake batch that counts steps per solve: every
+    request is read out after exactly its requested steps, across rebuilds that copy the
+    survivors, and the budget is respected."""
+    class FakeBatch:
+        live = []
+
+        def __init__(self, cfgs, stream=None):
+            self.n = [0] * len(cfgs)
+            FakeBatch.live.append(self)
+
+        def copy_solve(self, i, src, j):
+            self.n[i] = src.n[j]
+
+        def set_state(self, i, ic):
+            self.n[i] = 0
+
+        def step(self):
+            self.n = [v + 1 for v in self.n]
+
+        def get_state(self, i):
+            return None, None, np.array([self.n[i]])
+
+        def close(self):
+            FakeBatch.live.remove(self)
+
+    monkeypatch.setattr(serving.agile, "Batch", FakeBatch)
+    monkeypatch.setattr(serving, "initial_condition", lambda r: None)
+    reqs = serving.request_stream(30, rate=3000.0, sides=(32, 64), steps=(2, 9))
+    budget = 4 * max(serving.pool_bytes(r, 4) for r in reqs)
+    srv = serving.BatchedServer(budget, real_bytes=4, rebuild_every=3, keep_results=True)
+    rep = srv.run(reqs, max_wall_s=30.0)
+    assert all(r.finished >= 0 and int(r.result[0]) == r.steps for r in reqs)
+    assert rep.max_resident_bytes <= budget
+    assert not FakeBatch.live                          # every batch closed
