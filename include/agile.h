@@ -281,6 +281,19 @@ agile_status agile_batch_cfl_dt(agile_batch* batch, double* dt);
 /* State of one solve, as agile_get_state. Synchronises. */
 agile_status agile_batch_get_state(agile_batch* batch, int solve, int* level, int* ijk, double* cons);
 
+/* Autotuner of the batched stage launches (no counterpart in the paper): times `trials`
+ * launches of the first RK stage (which reads the solution and writes only a stage buffer,
+ * so the solution is not modified) for four launch shapes, the persistent grid at 1 and 2
+ * CTAs per SM, each with blocks taken from an atomic counter or strided by the grid, and
+ * keeps the fastest for every later step (the CUDA graph of a step is captured again).
+ * Results do not depend on the choice: every block's arithmetic is the same.
+ *  trials   1..100 timed launches per shape (after one untimed launch)
+ *  grid     out: CTAs of the chosen shape; dynamic: out, 1 for the atomic counter
+ *  ms       out (may be NULL): mean ms per launch of the shapes in the order (1 CTA/SM,
+ *           counter), (1, strided), (2, counter), (2, strided)
+ * Synchronises the batch's stream. */
+agile_status agile_batch_autotune(agile_batch* batch, int trials, int* grid, int* dynamic, float* ms);
+
 /* Copy the current state of solve src_solve of batch src into solve dst_solve of batch dst
  * (device to device; no counterpart in the paper: it lets a request loop rebuild its batch
  * when solves join or leave without a host round trip). The two solves must have the same

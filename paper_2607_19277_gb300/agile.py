@@ -35,6 +35,7 @@ EXPORTS = ["agile_mesh_create", "agile_mesh_destroy", "agile_set_state", "agile_
            "agile_selftest_bounded_wait", "agile_last_error", "agile_version",
            "agile_batch_create", "agile_batch_destroy", "agile_batch_layout",
            "agile_batch_set_state", "agile_batch_step", "agile_batch_cfl_dt", "agile_batch_copy_solve",
+           "agile_batch_autotune",
            "agile_batch_get_state", "agile_batch_sync", "agile_batch_launches",
            "agile_batch_last_error"]
 
@@ -111,6 +112,7 @@ def load(path: str = LIB_PATH):
         "agile_batch_cfl_dt": (C.c_int, [P, dp]),
         "agile_batch_get_state": (C.c_int, [P, C.c_int, ip, ip, dp]),
         "agile_batch_copy_solve": (C.c_int, [P, C.c_int, P, C.c_int]),
+        "agile_batch_autotune": (C.c_int, [P, C.c_int, ip, ip, C.POINTER(C.c_float)]),
         "agile_batch_sync": (C.c_int, [P]),
         "agile_batch_launches": (C.c_longlong, [P]),
         "agile_batch_last_error": (C.c_char_p, [P]),
@@ -422,6 +424,13 @@ class Batch:
         cons = np.zeros((n, nv, 16, 16, 16))
         self._ck(self.lib.agile_batch_get_state(self.ptr, solve, _iptr(lev), _iptr(ijk), _dptr(cons)))
         return lev, ijk, cons
+
+    def autotune(self, trials=3):
+        """Pick the fastest stage-launch shape; returns (grid, dynamic, ms per shape)."""
+        g, d = C.c_int(), C.c_int()
+        ms = (C.c_float * 4)()
+        self._ck(self.lib.agile_batch_autotune(self.ptr, int(trials), C.byref(g), C.byref(d), ms))
+        return g.value, bool(d.value), list(ms)
 
     def copy_solve(self, solve, src, src_solve):
         """Device-to-device copy of solve src_solve of Batch src into solve `solve`."""

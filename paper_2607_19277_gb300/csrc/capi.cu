@@ -862,6 +862,8 @@ struct agile_batch {
   cudaGraphExec_t graph = nullptr;
   long long launches = 0;
   std::string err;
+  int grid = 0;                     // persistent CTAs of the stage launches (0: default)
+  bool dynamic = true;              // blocks taken from an atomic counter (else strided)
 };
 
 namespace {
@@ -968,7 +970,8 @@ agile_status batch_enqueue_step(agile_batch* B) {
     A.speeds = last ? B->d_speeds : nullptr;
     A.tmap = &B->tmap[st == 0 ? 0 : st];
     A.solve_of = B->d_solve_of;
-    A.work = B->d_work + st;
+    A.work = B->dynamic ? B->d_work + st : nullptr;
+    A.grid = B->grid;
     cudaError_t e;
     if (B->cfg.physics == AGILE_HD) e = launch_stage_hd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
     else if (mhd) e = launch_stage_mhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
@@ -980,9 +983,89 @@ agile_status batch_enqueue_step(agile_batch* B) {
   return AGILE_OK;
 }
 
+// One launch of the first stage (U^n -> the stage-1 buffer; the solution is not modified).
+agile_status batch_stage1(agile_batch* B, int grid, bool dynamic) {
+  if (dynamic) BCK(B, cudaMemsetAsync(B->d_work, 0, sizeof(int), B->stream));
+  StageArgs A;
+  A.Us = B->U[0];
+  A.Un = B->U[0];
+  A.Uout = B->U[1];
+  A.bd = B->d_bd;
+  A.gs = nullptr;
+  A.fr = nullptr;
+  A.dtch = B->d_dtch;
+  A.a = 0.0;
+  A.b = 1.0;
+  A.gamma = B->cfg.gamma;
+  A.glm_alpha = B->cfg.glm_alpha;
+  A.glm_post = 0;
+  A.nblk = B->nblk;
+  A.status = B->d_status;
+  A.speeds = nullptr;
+  A.tmap = &B->tmap[0];
+  A.solve_of = B->d_solve_of;
+  A.work = dynamic ? B->d_work : nullptr;
+  A.grid = grid;
+  cudaError_t e;
+  const bool mhd = B->cfg.physics == AGILE_MHD_GLM;
+  if (B->cfg.physics == AGILE_HD) e = launch_stage_hd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
+  else if (mhd) e = launch_stage_mhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
+  else if (B->cfg.eos == AGILE_EOS_SYNGE)
+    e = launch_stage_srhd_synge(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
+  else e = launch_stage_srhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
+  if (e != cudaSuccess) return bfail(B, AGILE_ECUDA, std::string("stage kernel: ") + cudaGetErrorString(e));
+  return AGILE_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+agile_status agile_batch_autotune(agile_batch* B, int trials, int* grid, int* dynamic, float* ms) {
+  if (!B || trials < 1 || trials > 100) return bfail(B, AGILE_EINVAL, "bad argument");
+  agile_status s = batch_ensure_speeds(B);
+  if (s) return s;
+  BCK(B, launch_set_dt(B->d_speeds, B->d_dtch, 0.0, B->cfg.cfl, B->stream, B->nsolve));
+  int dev = 0, sms = 0;
+  BCK(B, cudaGetDevice(&dev));
+  BCK(B, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grids[2] = {sms, 2 * sms};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  BCK(B, cudaEventCreate(&e0));
+  BCK(B, cudaEventCreate(&e1));
+  float best = 0.0f;
+  int bi = -1;
+  for (int c = 0; c < 4 && !s; ++c) {
+    const int g = grids[c >> 1];
+    const bool dyn = (c & 1) == 0;
+    s = batch_stage1(B, g, dyn);                        // warm-up
+    if (!s) BCK(B, cudaEventRecord(e0, B->stream));
+    for (int t = 0; t < trials && !s; ++t) s = batch_stage1(B, g, dyn);
+    if (s) break;
+    BCK(B, cudaEventRecord(e1, B->stream));
+    BCK(B, cudaEventSynchronize(e1));
+    float t_ms = 0.0f;
+    BCK(B, cudaEventElapsedTime(&t_ms, e0, e1));
+    t_ms /= trials;
+    if (ms) ms[c] = t_ms;
+    if (bi < 0 || t_ms < best) {
+      best = t_ms;
+      bi = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s) return s;
+  B->grid = grids[bi >> 1];
+  B->dynamic = (bi & 1) == 0;
+  if (B->graph) {                     // the next step captures the tuned launches
+    cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+  }
+  if (grid) *grid = B->grid;
+  if (dynamic) *dynamic = B->dynamic ? 1 : 0;
+  return batch_status(B);
+}
 
 agile_status agile_batch_create(const agile_config* cfgs, int nsolve, const agile_allocator* alloc,
                                 void* stream, agile_batch** out) {

@@ -36,6 +36,7 @@ struct StageArgs {
   const void* tmap;             // host CUtensorMap of the pool Us (x, y, z, block*var)
   const int* solve_of;          // solve index of each block (batched solves), nullptr = one solve
   int* work;                    // block counter of this launch (zeroed before it), dynamic scheduling
+  int grid = 0;                 // persistent CTAs of the launch (0: CTAs-per-SM target x SMs)
 };
 
 // Conserved + auxiliary values of the cell (x, y, z) of block b in the halo view: the

@@ -25,11 +25,12 @@ enum : int { ST_ENOCONV = 1, ST_EUNPHYS = 2 };
 // gamma serves the SRHD primitive recovery, which always runs in FP64).
 template <typename R>
 struct PhysParamsT {
-  double gamma_d;
+  double gamma_d, gm_d;    // gamma and (gamma - 1) / gamma in FP64 (SRHD primitive recovery)
   R gamma, g1, ig1, gg1;   // gamma, gamma - 1, 1 / (gamma - 1), gamma / (gamma - 1)
   R ch, ich, ch2;          // GLM cleaning speed c_h = c_max of U^n (MHD), 1 / c_h, c_h^2
   __host__ __device__ void set(double gamma_, double ch_) {
     gamma_d = gamma_;
+    gm_d = (gamma_ - 1.0) / gamma_;
     gamma = R(gamma_);
     g1 = R(gamma_ - 1.0);
     ig1 = R(1.0 / (gamma_ - 1.0));
@@ -240,15 +241,58 @@ struct SrhdPhysE {
   static constexpr int BOFF = -1;
   using Eos = SrhdEos<R, EOS>;
 
+  // The same Newton iteration in FP32, to |dxi| <= 1e-6 xi (at most 12 steps): in the FP32
+  // stencil it moves the starting point of the FP64 iteration close to the root, so that the
+  // FP64 iteration (which alone decides convergence and the result) needs about two steps.
+  // Returns the start unchanged when it does not converge or leaves the bracket.
+  __device__ static __forceinline__ double seed_f32(double xi0, double D, double s2, double E, double lo,
+                                                    double hi, const PhysParamsT<R>& pp) {
+    const float df_ = (float)D, s2f = (float)s2, ef = (float)E, gmf = (float)pp.gm_d;
+    const float idf = EOS == EOS_SYNGE ? 1.0f / df_ : 0.0f;
+    float l = (float)lo, h = (float)hi, x = (float)xi0;
+    for (int it = 0; it < 12; ++it) {
+      const float ixi = 1.0f / x;
+      const float w = s2f * ixi * ixi;
+      const float ig2 = 1.0f - w;
+      const float lor = rsqrtf(ig2);
+      const float rho = df_ * (ig2 * lor);
+      const float drho = df_ * lor * w * ixi;
+      float pr, dp;
+      if constexpr (EOS == EOS_SYNGE) {
+        const float hh = x * (ig2 * lor) * idf;
+        const float q = 9.0f * hh * hh + 16.0f;
+        const float iq = rsqrtf(q);
+        const float th = 0.125f * (5.0f * hh - q * iq);
+        pr = rho * th;
+        dp = th * drho + 0.125f * (5.0f - 9.0f * hh * iq);
+      } else {
+        pr = gmf * (x * ig2 - rho);
+        dp = gmf * (1.0f + w - drho);
+      }
+      const float f = x - pr - ef;
+      if (f < 0.0f) l = x; else h = x;
+      float xn = x - f / (1.0f - dp);
+      if (!(xn >= l && xn <= h)) xn = 0.5f * (l + h);
+      const bool conv = fabsf(xn - x) <= 1e-6f * xn;
+      x = xn;
+      if (conv) {
+        const double xd = (double)x;
+        return (xd > lo && xd < hi) ? xd : xi0;
+      }
+    }
+    return xi0;
+  }
+
   // Newton root find for f(xi) = xi - p(xi) - (tau + D) = 0 inside the bracket [E, k E]
   // (k = gamma for the ideal gas, whose p <= (gamma-1)/gamma xi; k = 4/3 for the approximate
   // Synge gas, whose h >= 4 theta gives p <= xi/4); starts from the stored xi when it lies
-  // strictly inside the bracket, else from the midpoint; a step leaving the closed bracket
-  // is replaced by bisection; stops when |dxi| <= 1e-14 xi; at most 50 iterations. FP64.
+  // strictly inside the bracket, else from the midpoint (in the FP32 stencil first refined by
+  // seed_f32); a step leaving the closed bracket is replaced by bisection; stops when
+  // |dxi| <= 1e-14 xi; at most 50 iterations. FP64.
   __device__ static __forceinline__ void cons2prim(const R* u, R* p, R* aux, const PhysParamsT<R>& pp,
                                                    int& st) {
     const double g = pp.gamma_d;
-    const double gm = (g - 1.0) / g;
+    const double gm = pp.gm_d;
     const double D = (double)u[0];
     const double mx = (double)u[1], my = (double)u[2], mz = (double)u[3];
     const double s2 = mx * mx + my * my + mz * mz;
@@ -257,6 +301,7 @@ struct SrhdPhysE {
     const double iD = EOS == EOS_SYNGE ? 1.0 / D : 0.0;
     double xi = (double)aux[0];
     if (!(xi > lo && xi < hi)) xi = 0.5 * (lo + hi);
+    if constexpr (sizeof(R) == 4) xi = seed_f32(xi, D, s2, E, lo, hi, pp);
     bool ok = false;
     for (int it = 0; it < 50; ++it) {
       const double ixi = 1.0 / xi;

@@ -23,7 +23,8 @@ static cudaError_t stage_go(const StageArgs& a, cudaStream_t s) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
   }
-  const int grid = a.nblk < MINB * sms ? a.nblk : MINB * sms;
+  int grid = a.grid > 0 ? a.grid : MINB * sms;   // a tuned persistent grid, else the default
+  if (grid > a.nblk) grid = a.nblk;
   if (grid <= 0) return cudaSuccess;
   k<<<grid, 256, smem, s>>>(*static_cast<const CUtensorMap*>(a.tmap), a);
   return cudaGetLastError();

@@ -75,3 +75,34 @@ def test_batched_solve_matches_oracle_fp64():
     _, _, r = o.get_state()
     assert rel_l1(g, r).max() < TOL_FP64
     b.close()
+
+
+@pytest.mark.parametrize("physics", ["srhd", "mhd"])
+def test_autotune_keeps_results_and_picks_a_shape(physics):
+    """The autotuner times four launch shapes without touching the solution; the tuned
+    batch (re-captured graph) gives the same results bit for bit."""
+    sides = [32, 48, 64]
+    cfgs = [_cfg(s, 4, physics) for s in sides]
+    a, b = agile.Batch(cfgs), agile.Batch(cfgs)
+    for i, s in enumerate(sides):
+        a.set_state(i, _ic(physics, 200 + i, s))
+        b.set_state(i, _ic(physics, 200 + i, s))
+    a.step()
+    b.step()
+    a.step()                  # graph captured before tuning, replaced after it
+    b.step()
+    before = [a.get_state(i)[2] for i in range(len(sides))]
+    grid, dynamic, ms = a.autotune(trials=2)
+    after = [a.get_state(i)[2] for i in range(len(sides))]
+    assert all(np.array_equal(x, y) for x, y in zip(after, before))
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert grid in (sms, 2 * sms) and all(t > 0 for t in ms)
+    assert min(ms) == ms[(0 if grid == sms else 2) + (0 if dynamic else 1)]
+    for _ in range(3):
+        a.step()
+        b.step()
+    for i in range(len(sides)):
+        assert np.array_equal(a.get_state(i)[2], b.get_state(i)[2]), i
+    a.close()
+    b.close()
