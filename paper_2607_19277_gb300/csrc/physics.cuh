@@ -288,7 +288,7 @@ struct SrhdPhysE {
   // Synge gas, whose h >= 4 theta gives p <= xi/4); starts from the stored xi when it lies
   // strictly inside the bracket, else from the midpoint (in the FP32 stencil first refined by
   // seed_f32); a step leaving the closed bracket is replaced by bisection; stops when
-  // |dxi| <= 1e-14 xi; at most 50 iterations. FP64.
+  // |dxi| <= tol xi (below); at most 50 iterations. FP64.
   __device__ static __forceinline__ void cons2prim(const R* u, R* p, R* aux, const PhysParamsT<R>& pp,
                                                    int& st) {
     const double g = pp.gamma_d;
@@ -302,6 +302,10 @@ struct SrhdPhysE {
     double xi = (double)aux[0];
     if (!(xi > lo && xi < hi)) xi = 0.5 * (lo + hi);
     if constexpr (sizeof(R) == 4) xi = seed_f32(xi, D, s2, E, lo, hi, pp);
+    // FP64 stencil: |dxi| <= 1e-14 xi. FP32 stencil: |dxi| <= 1e-6 xi; Newton converges
+    // quadratically, so the iterate after such a step is within about (1e-6)^2 relative
+    // (times a factor that grows like Gamma^3), far below the FP32 rounding of the output.
+    constexpr double tol = sizeof(R) == 4 ? 1e-6 : 1e-14;
     bool ok = false;
     for (int it = 0; it < 50; ++it) {
       const double ixi = 1.0 / xi;
@@ -328,7 +332,7 @@ struct SrhdPhysE {
       if (f < 0.0) lo = xi; else hi = xi;
       double xn = xi - f / df;
       if (!(xn >= lo && xn <= hi)) xn = 0.5 * (lo + hi);
-      const bool conv = fabs(xn - xi) <= 1e-14 * xn;
+      const bool conv = fabs(xn - xi) <= tol * xn;
       xi = xn;
       if (conv) { ok = true; break; }
     }
