@@ -115,12 +115,13 @@ class Cooling:
         return out.reshape(shape)
 
     def apply(self, phys, U, dt):
-        """Losses over dt on conserved HD / MHD states U (nvar, ...): only e changes, by
-        rho (T_new - T) / (gamma - 1)."""
+        """Losses over dt on conserved HD / MHD / FFHD states U (nvar, ...): only e
+        changes, by rho (T_new - T) / (gamma - 1)."""
         P, _ = phys.cons2prim(U)
+        ie = 2 if phys.name == "ffhd" else 4      # index of e in U and of p in P
         rho = P[0]
-        t = P[4] / rho
+        t = P[ie] / rho
         tn = self.cool_temperature(rho, t, dt)
         out = U.copy()
-        out[4] = U[4] - rho * (t - tn) / self.g1
+        out[ie] = U[ie] - rho * (t - tn) / self.g1
         return out

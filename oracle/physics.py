@@ -14,6 +14,7 @@ follows the paper's Section 2.3:
            2.3.4), closed by the ideal-gas enthalpy (Eq. 21) or by the Synge gas (Eq. 22)
            in Mathews' approximation, which Section 2.3.4 names instead of the Bessel
            functions: h = 5/2 theta + sqrt(9/4 theta^2 + 1), theta = p / rho.
+  * ffhd : Section 2.3.2, Eqs. 7-9 (frozen-field hydrodynamics along a frozen unit field).
 """
 from __future__ import annotations
 
@@ -323,9 +324,92 @@ class SRHD:
         return (vd * (1.0 - cs2) - root) / den, (vd * (1.0 - cs2) + root) / den
 
 
+class FFHD:
+    """Frozen-field hydrodynamics (Section 2.3.2, Eqs. 7-9 without gravity, heating and the
+    heat flux): U = (rho, m_par = rho v_par, e = p/(gamma-1) + rho v_par^2 / 2) moving along
+    a frozen unit field b = B/|B| that is carried as three more variables (b_x, b_y, b_z)
+    which are never updated. P = (rho, v_par, p, b).
+
+    Discretisation (the paper gives the equations only):
+      * b is not reconstructed: the face value of b_d is the mean of the two cells' b_d;
+      * the flux along d is b_d,face (rho v, rho v^2 + p, (e + p) v) for the two face
+        states (TVDLF, the module's solver in Table 1); the b variables carry the flux
+        b_d,face along d (and 0 along the other axes), so the divergence of their fluxes
+        is the discrete div b of the same face values;
+      * the source p div b of the m_par equation (Eq. 8) uses that discrete div b and the
+        cell pressure, so a state at rest with uniform p stays at rest in any field;
+      * reflecting walls negate b_n (v_n = v_par b_n then changes sign), not m_par.
+    """
+
+    name = "ffhd"
+    nvar = 6
+    naux = 0
+    glm = False
+    nrec = 3            # variables that are reconstructed (the rest is taken cell-constant)
+    frozen_from = 3     # variables from this index on are never updated
+
+    def __init__(self, gamma: float):
+        self.gamma = float(gamma)
+
+    def cons2prim(self, U, aux=None):
+        g = self.gamma
+        P = np.empty_like(U)
+        rho = U[0]
+        v = U[1] / rho
+        P[0] = rho
+        P[1] = v
+        P[2] = (g - 1.0) * (U[2] - 0.5 * rho * v * v)
+        P[3:6] = U[3:6]
+        return P, None
+
+    def prim2cons(self, P):
+        g = self.gamma
+        U = np.empty_like(P)
+        U[0] = P[0]
+        U[1] = P[0] * P[1]
+        U[2] = P[2] / (g - 1.0) + 0.5 * P[0] * P[1] * P[1]
+        U[3:6] = P[3:6]
+        return U
+
+    def interface(self, PL, PR, d):
+        """Both face states carry the mean of the two cells' b_d."""
+        bf = 0.5 * (PL[3 + d] + PR[3 + d])
+        PL = PL.copy()
+        PR = PR.copy()
+        PL[3 + d] = bf
+        PR[3 + d] = bf
+        return PL, PR
+
+    def flux(self, P, U, d):
+        rho, v, p, b = P[0], P[1], P[2], P[3 + d]
+        F = np.zeros_like(P)
+        F[0] = rho * v * b
+        F[1] = (rho * v * v + p) * b
+        F[2] = (U[2] + p) * v * b
+        F[3 + d] = b
+        return F
+
+    def lambdas(self, P, d):
+        """Signal speeds along d: (v_par -+ c_s) b_d (the speeds along the field projected)."""
+        c = np.sqrt(self.gamma * P[2] / P[0])
+        b = P[3 + d]
+        a = P[1] * b
+        w = c * np.abs(b)
+        return a - w, a + w
+
+    def source(self, Pc, L):
+        """Adds p div b to the m_par equation; L[3..5] holds -d_d b_face,d."""
+        L = L.copy()
+        L[1] = L[1] - Pc[2] * ((L[3] + L[4]) + L[5])
+        return L
+
+    def reflect_vars(self, d):
+        return [3 + d]
+
+
 def make_physics(name: str, gamma: float, eos: str = "ideal"):
     if name == "srhd":
         return SRHD(gamma, eos)
     if eos != "ideal":
         raise ValueError("the Synge EOS applies to srhd only")
-    return {"hd": HD, "mhd": MHD}[name](gamma)
+    return {"hd": HD, "mhd": MHD, "ffhd": FFHD}[name](gamma)

@@ -118,10 +118,12 @@ class Solver:
     def __init__(self, cfg: Config):
         self.cfg = cfg
         self.phys = make_physics(cfg.physics, cfg.gamma, cfg.eos)
+        if cfg.physics == "ffhd" and cfg.max_level != 1:
+            raise ValueError("ffhd runs on uniform meshes (max_level 1)")
         self.cool = None
         if cfg.cooling is not None:
-            if cfg.physics not in ("hd", "mhd"):
-                raise ValueError("radiative losses apply to hd and mhd")
+            if cfg.physics not in ("hd", "mhd", "ffhd"):
+                raise ValueError("radiative losses apply to hd, mhd and ffhd")
             self.cool = Cooling(cfg.cooling[0], cfg.cooling[1], cfg.gamma)
         self.nvar = self.phys.nvar
         self.naux = self.phys.naux
@@ -295,6 +297,10 @@ class Solver:
                 dst[d] = slice(G + NB + layer, G + NB + layer + 1)   # 16, 17
                 src[d] = slice(G + NB - 1 - layer, G + NB - layer)   # 15, 14
             blk[_S(dst)] = blk[_S(src)]
+            if hasattr(self.phys, "reflect_vars"):
+                for v in self.phys.reflect_vars(d):
+                    blk[(v,) + _S(dst)[1:]] *= -1.0
+                continue
             blk[(1 + d,) + _S(dst)[1:]] *= -1.0
             if self.phys.name == "mhd":
                 blk[(5 + d,) + _S(dst)[1:]] *= -1.0
@@ -437,10 +443,14 @@ class Solver:
         dl = Pd[..., 1:NT - 1] - Pd[..., 0:NT - 2]
         dr = Pd[..., 2:NT] - Pd[..., 1:NT - 1]
         sig = lim(dl, dr)                                # cells 1..18
+        nrec = getattr(phys, "nrec", phys.nvar)
+        sig[nrec:] = 0.0                                 # cell-constant variables (ffhd b)
         PL = Pd[..., 1:NT - 2] + 0.5 * sig[..., 0:NT - 3]
         PR = Pd[..., 2:NT - 1] - 0.5 * sig[..., 1:NT - 2]
         if phys.glm:
             PL, PR = phys.glm_interface(PL, PR, d, ch)
+        if hasattr(phys, "interface"):
+            PL, PR = phys.interface(PL, PR, d)
         UL = phys.prim2cons(PL)
         UR = phys.prim2cons(PR)
         if phys.glm:
@@ -462,6 +472,9 @@ class Solver:
             sr = np.maximum(lpl, lpr)
             mid = (sr * FL - sl * FR + sl * sr * (UR - UL)) / (sr - sl)
             F = np.where(sl >= 0.0, FL, np.where(sr <= 0.0, FR, mid))
+        if hasattr(phys, "frozen_from"):
+            # frozen variables: their exact flux (equal on both sides), no dissipation
+            F[phys.frozen_from:] = FL[phys.frozen_from:]
         return np.moveaxis(F, -1, _ax(d))
 
     def _hllc(self, PL, PR, UL, UR, FL, FR, sl, sr, d):
@@ -496,10 +509,13 @@ class Solver:
     def _all_fluxes(self, ch):
         fluxes = {}
         new_aux = {}
+        self._pcell = {}
         for key, blk in self.leaves.items():
             P, A = self._prims(blk)
             if A is not None:
                 new_aux[key] = A[(slice(None),) + (slice(G, G + NB),) * 3]
+            if hasattr(self.phys, "source"):
+                self._pcell[key] = P[(slice(None),) + (slice(G, G + NB),) * 3]
             dxl = self.dx(key[0])
             fluxes[key] = [self._face_fluxes(P, d, dxl, ch) for d in range(3)]
         return fluxes, new_aux
@@ -608,9 +624,14 @@ class Solver:
             new = {}
             for key, blk in self.leaves.items():
                 us = blk[(slice(0, self.nvar),) + inner]
-                upd = us + dt * self._rhs(fluxes, key)
+                rhs = self._rhs(fluxes, key)
+                if hasattr(self.phys, "source"):
+                    rhs = self.phys.source(self._pcell[key], rhs)
+                upd = us + dt * rhs
                 if a != 0.0:
                     upd = a * un[key] + b * upd
+                if hasattr(self.phys, "frozen_from"):
+                    upd[self.phys.frozen_from:] = us[self.phys.frozen_from:]
                 new[key] = upd
             for key, blk in self.leaves.items():
                 blk[(slice(0, self.nvar),) + inner] = new[key]
