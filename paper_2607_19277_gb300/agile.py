@@ -18,7 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libagile.so")
 NCELL = 4096
 
-PHYSICS = {"hd": 0, "mhd": 1, "srhd": 2}
+PHYSICS = {"hd": 0, "mhd": 1, "srhd": 2, "ffhd": 3}
+NVAR = {0: 5, 1: 9, 2: 5, 3: 6}
 EOS = {"ideal": 0, "synge": 1}
 LIMITER = {"minmod": 0, "vanleer": 1}
 FLUX = {"tvdlf": 0, "hll": 1, "hllc": 2}
@@ -223,7 +224,7 @@ class Mesh:
             self._alloc = _TorchAllocator(torch.cuda.current_device()) if use_torch_allocator else None
             alloc_struct = self._alloc.struct if self._alloc else None
         self.ptr = agile_mesh_create(cfg, alloc_struct, int(stream.cuda_stream))
-        self.nvar = 9 if cfg.physics == 1 else 5
+        self.nvar = NVAR[cfg.physics]
         self.naux = 2 if cfg.physics == 2 else 0
         self._ic = None
 
@@ -379,7 +380,7 @@ class Batch:
                                          C.byref(out))
         _check(self.lib, None, st)
         self.ptr = out
-        self.nvar = 9 if self.cfgs[0].physics == 1 else 5
+        self.nvar = NVAR[self.cfgs[0].physics]
         self._ics = {}
 
     def _ck(self, st):

@@ -10,7 +10,7 @@
 
 namespace agile {
 
-int phys_nvar(int phys) { return phys == PH_MHD ? 9 : 5; }
+int phys_nvar(int phys) { return phys == PH_MHD ? 9 : (phys == PH_FFHD ? 6 : 5); }
 int phys_naux(int phys) { return phys == PH_SRHD || phys == PH_SRHD_SYNGE ? 2 : 0; }
 
 // ------------------------------------------------------------------------------ helpers
@@ -474,6 +474,9 @@ __global__ void halo_kernel(const R* __restrict__ U, const R* __restrict__ G,
     } else if ((phys) == PH_SRHD) {                            \
       if ((rb) == 8) { using R = double; CALL(SrhdPhys); }     \
       else { using R = float; CALL(SrhdPhys); }                \
+    } else if ((phys) == PH_FFHD) {                            \
+      if ((rb) == 8) { using R = double; CALL(FfhdPhys); }     \
+      else { using R = float; CALL(FfhdPhys); }                \
     } else {                                                   \
       if ((rb) == 8) { using R = double; CALL(SrhdSyngePhys); }\
       else { using R = float; CALL(SrhdSyngePhys); }           \

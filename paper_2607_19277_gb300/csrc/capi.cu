@@ -95,7 +95,27 @@ size_t pool_bytes(const agile_mesh* m, int nblk) {
 
 // Internal physics kind: the srhd module with the Synge EOS has its own device trait.
 int phys_kind(const agile_config& c) {
+  if (c.physics == AGILE_FFHD) return PH_FFHD;
   return c.physics == AGILE_SRHD && c.eos == AGILE_EOS_SYNGE ? PH_SRHD_SYNGE : c.physics;
+}
+
+int cfg_nvar(const agile_config& c) {
+  return c.physics == AGILE_MHD_GLM ? 9 : (c.physics == AGILE_FFHD ? 6 : 5);
+}
+
+// Scheme restrictions shared by meshes and batches: the solvers per module of paper
+// Table 1 (TVDLF for srhd and ffhd, HLLC for hd), the Synge EOS for srhd only, ffhd on
+// uniform meshes.
+bool scheme_ok(const agile_config& c) {
+  if (c.physics < 0 || c.physics > 3 || (c.limiter != 0 && c.limiter != 1) || c.flux < 0 || c.flux > 2 ||
+      (c.rk != 2 && c.rk != 3) || (c.real_bytes != 4 && c.real_bytes != 8) || !(c.gamma > 1.0) ||
+      !(c.cfl > 0.0))
+    return false;
+  if ((c.physics == AGILE_SRHD || c.physics == AGILE_FFHD) && c.flux != AGILE_TVDLF) return false;
+  if (c.flux == AGILE_HLLC && c.physics != AGILE_HD) return false;
+  if (c.eos != AGILE_EOS_IDEAL && !(c.eos == AGILE_EOS_SYNGE && c.physics == AGILE_SRHD)) return false;
+  if (c.physics == AGILE_FFHD && c.max_level != 1) return false;
+  return true;
 }
 
 AuxArgs aux_args(agile_mesh* m, void* U) {
@@ -335,14 +355,8 @@ agile_status agile_mesh_create(const agile_config* cfg, const agile_allocator* a
                                agile_mesh** out) {
   if (!cfg || !out) return AGILE_EINVAL;
   *out = nullptr;
-  if (cfg->physics < 0 || cfg->physics > 2 || (cfg->limiter != 0 && cfg->limiter != 1) ||
-      cfg->flux < 0 || cfg->flux > 2 || (cfg->rk != 2 && cfg->rk != 3) ||
-      (cfg->real_bytes != 4 && cfg->real_bytes != 8) || !(cfg->gamma > 1.0) || !(cfg->cfl > 0.0) ||
-      cfg->max_level < 1 || cfg->max_level > 12 || cfg->refine_nvars < 0 || cfg->refine_nvars > 9)
-    return AGILE_EINVAL;
-  if (cfg->physics == AGILE_SRHD && cfg->flux != AGILE_TVDLF) return AGILE_EINVAL;
-  if (cfg->flux == AGILE_HLLC && cfg->physics != AGILE_HD) return AGILE_EINVAL;
-  if (cfg->eos != AGILE_EOS_IDEAL && !(cfg->eos == AGILE_EOS_SYNGE && cfg->physics == AGILE_SRHD))
+  if (!scheme_ok(*cfg) || cfg->max_level < 1 || cfg->max_level > 12 || cfg->refine_nvars < 0 ||
+      cfg->refine_nvars > 9)
     return AGILE_EINVAL;
   for (int d = 0; d < 3; ++d) {
     if (cfg->base_blocks[d] < 1 || cfg->base_blocks[d] > 4096 || !(cfg->xmax[d] > cfg->xmin[d]))
@@ -352,7 +366,7 @@ agile_status agile_mesh_create(const agile_config* cfg, const agile_allocator* a
     for (int s = 0; s < 2; ++s)
       if (cfg->bc[2 * d + s] < 0 || cfg->bc[2 * d + s] > 2) return AGILE_EINVAL;
   }
-  const int nvar = cfg->physics == AGILE_MHD_GLM ? 9 : 5;
+  const int nvar = cfg_nvar(*cfg);
   for (int i = 0; i < cfg->refine_nvars; ++i)
     if (cfg->refine_vars[i] < 0 || cfg->refine_vars[i] >= nvar) return AGILE_EINVAL;
   agile_mesh* m = new agile_mesh();
@@ -533,6 +547,7 @@ agile_status agile_step(agile_mesh* m, double dt) {
     else if (mhd) e = launch_stage_mhd(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
     else if (m->cfg.eos == AGILE_EOS_SYNGE)
       e = launch_stage_srhd_synge(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
+    else if (m->cfg.physics == AGILE_FFHD) e = launch_stage_ffhd(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
     else e = launch_stage_srhd(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
     if (e != cudaSuccess) return fail(m, AGILE_ECUDA, std::string("stage kernel: ") + cudaGetErrorString(e));
     if (m->timing) {
@@ -578,8 +593,8 @@ agile_status agile_set_cooling(agile_mesh* m, const double* T, const double* Lam
     m->cool = CoolHost();
     return AGILE_OK;
   }
-  if (m->cfg.physics != AGILE_HD && m->cfg.physics != AGILE_MHD_GLM)
-    return fail(m, AGILE_EINVAL, "radiative losses apply to hd and mhd");
+  if (m->cfg.physics != AGILE_HD && m->cfg.physics != AGILE_MHD_GLM && m->cfg.physics != AGILE_FFHD)
+    return fail(m, AGILE_EINVAL, "radiative losses apply to hd, mhd and ffhd");
   CoolHost c;
   if (build_cool_table(T, Lambda, n, m->cfg.gamma, m->rb, &c))
     return fail(m, AGILE_EINVAL, "cooling table: 2..4096 nodes, T increasing, T and Lambda positive and "
@@ -977,6 +992,7 @@ agile_status batch_enqueue_step(agile_batch* B) {
     else if (mhd) e = launch_stage_mhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
     else if (B->cfg.eos == AGILE_EOS_SYNGE)
       e = launch_stage_srhd_synge(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
+    else if (B->cfg.physics == AGILE_FFHD) e = launch_stage_ffhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
     else e = launch_stage_srhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
     if (e != cudaSuccess) return bfail(B, AGILE_ECUDA, std::string("stage kernel: ") + cudaGetErrorString(e));
   }
@@ -1012,6 +1028,7 @@ agile_status batch_stage1(agile_batch* B, int grid, bool dynamic) {
   else if (mhd) e = launch_stage_mhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
   else if (B->cfg.eos == AGILE_EOS_SYNGE)
     e = launch_stage_srhd_synge(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
+  else if (B->cfg.physics == AGILE_FFHD) e = launch_stage_ffhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
   else e = launch_stage_srhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
   if (e != cudaSuccess) return bfail(B, AGILE_ECUDA, std::string("stage kernel: ") + cudaGetErrorString(e));
   return AGILE_OK;
@@ -1079,12 +1096,7 @@ agile_status agile_batch_create(const agile_config* cfgs, int nsolve, const agil
         c.glm_alpha != c0.glm_alpha || c.eos != c0.eos || c.max_level != 1)
       return AGILE_EINVAL;
     // validate each configuration like a single mesh (host-side checks only)
-    if (c.physics < 0 || c.physics > 2 || (c.limiter != 0 && c.limiter != 1) || c.flux < 0 || c.flux > 2 ||
-        (c.flux == AGILE_HLLC && c.physics != AGILE_HD) ||
-        (c.rk != 2 && c.rk != 3) || (c.real_bytes != 4 && c.real_bytes != 8) || !(c.gamma > 1.0) ||
-        !(c.cfl > 0.0) || (c.physics == AGILE_SRHD && c.flux != AGILE_TVDLF) ||
-        (c.eos != AGILE_EOS_IDEAL && !(c.eos == AGILE_EOS_SYNGE && c.physics == AGILE_SRHD)))
-      return AGILE_EINVAL;
+    if (!scheme_ok(c)) return AGILE_EINVAL;
     for (int d = 0; d < 3; ++d) {
       if (c.base_blocks[d] < 1 || c.base_blocks[d] > 4096 || !(c.xmax[d] > c.xmin[d])) return AGILE_EINVAL;
       if ((c.bc[2 * d] == AGILE_PERIODIC) != (c.bc[2 * d + 1] == AGILE_PERIODIC)) return AGILE_EINVAL;
@@ -1108,7 +1120,7 @@ agile_status agile_batch_create(const agile_config* cfgs, int nsolve, const agil
     }
     B->own_stream = true;
   }
-  B->nv = c0.physics == AGILE_MHD_GLM ? 9 : 5;
+  B->nv = cfg_nvar(c0);
   B->na = c0.physics == AGILE_SRHD ? 2 : 0;
   B->nt = B->nv + B->na;
   B->rb = c0.real_bytes;

@@ -160,11 +160,12 @@ __global__ void __launch_bounds__(256) cooling_kernel(R* __restrict__ U, const B
     for (int v = 0; v < NV; ++v) u[v] = base[(size_t)v * NCELL + i];
     R p[NV], aux[1] = {R(0)};
     P::cons2prim(u, p, aux, pp, st);
+    constexpr int IE = P::IE;   // energy in U, pressure in P
     const R rho = p[0];
-    const R T = p[4] / rho;
+    const R T = p[IE] / rho;
     const R tn = cool_temperature<R>(rho, T, dt, c, seg);
-    u[4] = u[4] - rho * (T - tn) * ig1;
-    base[(size_t)4 * NCELL + i] = u[4];
+    u[IE] = u[IE] - rho * (T - tn) * ig1;
+    base[(size_t)IE * NCELL + i] = u[IE];
     if (speeds) cell_speeds<PT, R>(u, aux, pp, dxr, ssum, smax, st);
   }
   if (speeds) block_max2<256>((double)ssum, (double)smax, speeds + 2 * sv);
@@ -182,6 +183,9 @@ cudaError_t launch_cooling(const AuxArgs& a, const CoolDev& c, const void* seg, 
   } else if (a.phys == PH_MHD) {
     if (a.real_bytes == 8) { using R = double; CALL(MhdPhys); }
     else { using R = float; CALL(MhdPhys); }
+  } else if (a.phys == PH_FFHD) {
+    if (a.real_bytes == 8) { using R = double; CALL(FfhdPhys); }
+    else { using R = float; CALL(FfhdPhys); }
   } else {
     return cudaErrorInvalidValue;
   }

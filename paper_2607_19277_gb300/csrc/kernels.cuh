@@ -67,7 +67,7 @@ __device__ __forceinline__ void load_cell(const R* __restrict__ U, const R* __re
       const R* p = U + (size_t)blk * NT * NCELL + q[2] * 256 + q[1] * 16 + q[0];
 #pragma unroll
       for (int v = 0; v < NT; ++v) u[v] = p[(size_t)v * NCELL];
-      u[1 + d] = -u[1 + d];
+      if (P::IV >= 0) u[P::IV + d] = -u[P::IV + d];
       if (P::BOFF >= 0) u[P::BOFF + d] = -u[P::BOFF + d];
       return;
     } else {
@@ -237,9 +237,11 @@ __device__ __forceinline__ const R* cell_addr(const R* __restrict__ U, const R* 
 // x/y component swap used to evaluate a y-face with the x-face solver.
 template <class P, typename R>
 __device__ __forceinline__ void swap_xy(R* v, bool yd) {
-  const R a = v[1], c = v[2];
-  v[1] = yd ? c : a;
-  v[2] = yd ? a : c;
+  if constexpr (P::IV >= 0) {
+    const R a = v[P::IV], c = v[P::IV + 1];
+    v[P::IV] = yd ? c : a;
+    v[P::IV + 1] = yd ? a : c;
+  }
   if constexpr (P::BOFF >= 0) {
     const R e = v[P::BOFF], g = v[P::BOFF + 1];
     v[P::BOFF] = yd ? g : e;
@@ -414,7 +416,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       bq[v] = r1[v * 256]; c[v] = r2[v * 256]; d[v] = r3[v * 256];
-      const R h = half_slope<R, LIM>(c[v] - bq[v], d[v] - c[v]);
+      const R h = v < P::NREC ? half_slope<R, LIM>(c[v] - bq[v], d[v] - c[v]) : R(0);
       pl[v] = bq[v] + hz[v];
       pr[v] = c[v] - h;
       hz[v] = h;
@@ -428,7 +430,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       const R* r = sC + v * 400 + (row + 2) * 20 + fi;
       a[v] = r[0]; bq[v] = r[1]; c[v] = r[2]; d[v] = r[3];
     }
-    plm<NV, R, LIM>(a, bq, c, d, pl, pr);
+    plm<NV, R, LIM, P::NREC>(a, bq, c, d, pl, pr);
     riemann<P, R, 0, FLUX>(pl, pr, f, pp);
   };
   auto yface = [&](int fj, int col, R* f) {  // y-face fj - 1/2 of column `col`
@@ -438,7 +440,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       const R* r = sC + v * 400 + fj * 20 + col + 2;
       a[v] = r[0]; bq[v] = r[20]; c[v] = r[40]; d[v] = r[60];
     }
-    plm<NV, R, LIM>(a, bq, c, d, pl, pr);
+    plm<NV, R, LIM, P::NREC>(a, bq, c, d, pl, pr);
     riemann<P, R, 1, FLUX>(pl, pr, f, pp);
   };
 
@@ -486,7 +488,8 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     const R* r1 = sPr + (size_t)((-1) & 3) * NT * 256 + cell2;
     const R* r2 = sPr + (size_t)(0 & 3) * NT * 256 + cell2;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) hz[v] = half_slope<R, LIM>(r1[v * 256] - r0[v * 256], r2[v * 256] - r1[v * 256]);
+    for (int v = 0; v < NV; ++v)
+      hz[v] = v < P::NREC ? half_slope<R, LIM>(r1[v * 256] - r0[v * 256], r2[v * 256] - r1[v * 256]) : R(0);
   }
   zface(-1, fzd, hz);
   if (FR && slot[4] >= 0) {
@@ -515,7 +518,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
 #pragma unroll
         for (int v = 0; v < NT; ++v) u[v] = sHalo[v * 128 + h];
         if (nd >= 0) {
-          u[1 + nd] = -u[1 + nd];
+          if (P::IV >= 0) u[P::IV + nd] = -u[P::IV + nd];
           if (P::BOFF >= 0) u[P::BOFF + nd] = -u[P::BOFF + nd];
         }
         if constexpr (NA > 0) {
@@ -569,7 +572,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
         swap_xy<P, R>(bq, yd);
         swap_xy<P, R>(c, yd);
         swap_xy<P, R>(d, yd);
-        plm<NV, R, LIM>(a, bq, c, d, pl, pr);
+        plm<NV, R, LIM, P::NREC>(a, bq, c, d, pl, pr);
         riemann<P, R, 0, FLUX>(pl, pr, f, pp);
         swap_xy<P, R>(f, yd);
         const int fs = yd ? 1 : 0;
@@ -595,18 +598,45 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       const size_t base = (size_t)b * NT * NCELL + cell;
       const R* raw = sRaw + (size_t)((k + 2) & 3) * NT * 256 + cell2;
       R out[NV];
+      if constexpr (P::SOURCE) {
+        // all flux divergences first: the source needs those of other variables
+        R L[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const R lx = (sFx[v * 272 + ty * 17 + tx + 1] - sFx[v * 272 + ty * 17 + tx]) * idx;
-        const R ly = (sFy[v * 272 + (ty + 1) * 16 + tx] - sFy[v * 272 + ty * 16 + tx]) * idy;
-        const R lz = (fzu[v] - fzd[v]) * idz;
-        const R L = -((lx + ly) + lz);
-        R val = raw[v * 256] + rdt * L;
-        if (combine) val = ra * Un[base + (size_t)v * NCELL] + rb * val;
-        out[v] = val;
-        fzd[v] = fzu[v];
+        for (int v = 0; v < NV; ++v) {
+          const R lx = (sFx[v * 272 + ty * 17 + tx + 1] - sFx[v * 272 + ty * 17 + tx]) * idx;
+          const R ly = (sFy[v * 272 + (ty + 1) * 16 + tx] - sFy[v * 272 + ty * 16 + tx]) * idy;
+          const R lz = (fzu[v] - fzd[v]) * idz;
+          L[v] = -((lx + ly) + lz);
+          fzd[v] = fzu[v];
+        }
+        R pc[NV];
+        const R* pk = sPr + (size_t)(k & 3) * NT * 256 + cell2;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) pc[v] = pk[v * 256];
+        P::source(L, pc);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          R val = raw[v * 256];
+          if (v < P::FROZEN) {
+            val = val + rdt * L[v];
+            if (combine) val = ra * Un[base + (size_t)v * NCELL] + rb * val;
+          }
+          out[v] = val;
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const R lx = (sFx[v * 272 + ty * 17 + tx + 1] - sFx[v * 272 + ty * 17 + tx]) * idx;
+          const R ly = (sFy[v * 272 + (ty + 1) * 16 + tx] - sFy[v * 272 + ty * 16 + tx]) * idy;
+          const R lz = (fzu[v] - fzd[v]) * idz;
+          const R L = -((lx + ly) + lz);
+          R val = raw[v * 256] + rdt * L;
+          if (combine) val = ra * Un[base + (size_t)v * NCELL] + rb * val;
+          out[v] = val;
+          fzd[v] = fzu[v];
+        }
       }
-      if (P::BOFF >= 0 && glm_post) out[NV - 1] = out[NV - 1] * glm_fr;
+      if (P::GLM && glm_post) out[NV - 1] = out[NV - 1] * glm_fr;
 #pragma unroll
       for (int v = 0; v < NV; ++v) Uo[base + (size_t)v * NCELL] = out[v];
       R auxk[NAW];

@@ -81,6 +81,12 @@ struct HdPhys {
   static constexpr int NV = 5;   // rho, m, e
   static constexpr int NA = 0;
   static constexpr int BOFF = -1;  // no magnetic field
+  static constexpr int IV = 1;     // first velocity / momentum component
+  static constexpr int NREC = NV;  // reconstructed variables
+  static constexpr int FROZEN = NV;  // variables from this index on are never updated
+  static constexpr int IE = 4;     // energy in U, pressure in P
+  static constexpr bool SOURCE = false;
+  static constexpr bool GLM = false;
 
   __device__ static __forceinline__ void cons2prim(const R* u, R* p, R*, const PhysParamsT<R>& pp,
                                                    int& st) {
@@ -133,6 +139,12 @@ struct MhdPhys {
   static constexpr int NV = 9;   // rho, m, e, B, psi
   static constexpr int NA = 0;
   static constexpr int BOFF = 5;   // B_x is variable 5
+  static constexpr int IV = 1;
+  static constexpr int NREC = NV;
+  static constexpr int FROZEN = NV;
+  static constexpr int IE = 4;
+  static constexpr bool SOURCE = false;
+  static constexpr bool GLM = true;
 
   __device__ static __forceinline__ void cons2prim(const R* u, R* p, R*, const PhysParamsT<R>& pp,
                                                    int& st) {
@@ -239,6 +251,12 @@ struct SrhdPhysE {
   static constexpr int NV = 5;   // D, m, tau ; primitives rho, u = Gamma v, p
   static constexpr int NA = 2;   // xi = Gamma^2 rho h, Gamma
   static constexpr int BOFF = -1;
+  static constexpr int IV = 1;
+  static constexpr int NREC = NV;
+  static constexpr int FROZEN = NV;
+  static constexpr int IE = 4;
+  static constexpr bool SOURCE = false;
+  static constexpr bool GLM = false;
   using Eos = SrhdEos<R, EOS>;
 
   // The same Newton iteration in FP32, to |dxi| <= 1e-6 xi (at most 12 steps): in the FP32
@@ -418,6 +436,83 @@ struct SrhdPhysE {
 template <typename R> using SrhdPhys = SrhdPhysE<R, EOS_IDEAL>;
 template <typename R> using SrhdSyngePhys = SrhdPhysE<R, EOS_SYNGE>;
 
+// ------------------------------------------------------------------------------ FFHD
+// Frozen-field hydrodynamics (Section 2.3.2, Eqs. 7-9): U = (rho, m_par, e, b), P = (rho,
+// v_par, p, b) with b the frozen unit field, never updated and not reconstructed (cell
+// values; the face value of b_d is the mean of the two cells'). The flux along d is
+// b_d (rho v, rho v^2 + p, (e + p) v) and b_d for the variable b_d (0 for the other two), so
+// the flux divergence of the b variables is -div b of the same face values; the source
+// p div b of the m_par equation is added from it. TVDLF only (paper Table 1).
+template <typename R>
+struct FfhdPhys {
+  static constexpr int NV = 6;
+  static constexpr int NA = 0;
+  static constexpr int BOFF = 3;     // b: swapped with the x/y trick, b_n negated at walls
+  static constexpr int IV = -1;      // no vector velocity
+  static constexpr int NREC = 3;
+  static constexpr int FROZEN = 3;
+  static constexpr int IE = 2;
+  static constexpr bool SOURCE = true;
+  static constexpr bool GLM = false;
+
+  __device__ static __forceinline__ void cons2prim(const R* u, R* p, R*, const PhysParamsT<R>& pp,
+                                                   int& st) {
+    const R rho = u[0];
+    const R v = u[1] * (R(1) / rho);
+    p[0] = rho;
+    p[1] = v;
+    p[2] = pp.g1 * (u[2] - R(0.5) * rho * v * v);
+    p[3] = u[3];
+    p[4] = u[4];
+    p[5] = u[5];
+    st |= (!(rho > R(0)) | !(p[2] > R(0))) ? ST_EUNPHYS : 0;
+  }
+
+  __device__ static __forceinline__ void prim2cons(const R* p, R* u, const PhysParamsT<R>& pp) {
+    u[0] = p[0];
+    u[1] = p[0] * p[1];
+    u[2] = p[2] * pp.ig1 + R(0.5) * p[0] * p[1] * p[1];
+    u[3] = p[3];
+    u[4] = p[4];
+    u[5] = p[5];
+  }
+
+  template <int D>
+  __device__ static __forceinline__ void flux(const R* p, const R* u, R* f, const PhysParamsT<R>&) {
+    const R b = p[3 + D];
+    const R vb = p[1] * b;
+    f[0] = u[0] * vb;
+    f[1] = u[1] * vb + p[2] * b;
+    f[2] = (u[2] + p[2]) * vb;
+    f[3] = R(0);
+    f[4] = R(0);
+    f[5] = R(0);
+    f[3 + D] = b;
+  }
+
+  template <int D>
+  __device__ static __forceinline__ void lambdas(const R* p, R& lm, R& lp, const PhysParamsT<R>& pp) {
+    const R c = rsqrt_(pp.gamma * p[2] / p[0]);
+    const R b = p[3 + D];
+    const R a = p[1] * b;
+    const R w = c * rabs(b);
+    lm = a - w;
+    lp = a + w;
+  }
+
+  template <int D>
+  __device__ static __forceinline__ void interface(R* pl, R* pr, const PhysParamsT<R>&) {
+    const R bf = R(0.5) * (pl[3 + D] + pr[3 + D]);
+    pl[3 + D] = bf;
+    pr[3 + D] = bf;
+  }
+
+  // L holds -div F of every variable: L[3..5] sum to -div b; adds p div b to m_par.
+  __device__ static __forceinline__ void source(R* L, const R* pcell) {
+    L[1] = L[1] - pcell[2] * ((L[3] + L[4]) + L[5]);
+  }
+};
+
 // Riemann flux at a face from reconstructed primitive states (modified in place).
 template <class P, typename R, int D, int FLUX>
 __device__ __forceinline__ void riemann(R* pl, R* pr, R* f, const PhysParamsT<R>& pp) {
@@ -462,7 +557,10 @@ __device__ __forceinline__ void riemann(R* pl, R* pr, R* f, const PhysParamsT<R>
   } else if (FLUX == FLUX_TVDLF) {
     const R c = rmax(rmax(rabs(lml), rabs(lpl)), rmax(rabs(lmr), rabs(lpr)));
 #pragma unroll
-    for (int v = 0; v < NV; ++v) f[v] = R(0.5) * (fl[v] + fr[v]) - R(0.5) * c * (ur[v] - ul[v]);
+    for (int v = 0; v < NV; ++v) {
+      if (v >= P::FROZEN) f[v] = fl[v];   // frozen variables: exact flux, no dissipation
+      else f[v] = R(0.5) * (fl[v] + fr[v]) - R(0.5) * c * (ur[v] - ul[v]);
+    }
   } else {
     const R sl = rmin(rmin(lml, lmr), R(0));
     const R sr = rmax(rmax(lpl, lpr), R(0));
@@ -475,13 +573,18 @@ __device__ __forceinline__ void riemann(R* pl, R* pr, R* f, const PhysParamsT<R>
 
 // PLM face states: pl = P_i + phi_i / 2, pr = P_{i+1} - phi_{i+1} / 2 from the four cells
 // i-1, i, i+1, i+2 around face i+1/2.
-template <int NV, typename R, int LIM>
+template <int NV, typename R, int LIM, int NREC = NV>
 __device__ __forceinline__ void plm(const R* a, const R* b, const R* c, const R* d, R* pl, R* pr) {
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const R d0 = b[v] - a[v], d1 = c[v] - b[v], d2 = d[v] - c[v];
-    pl[v] = b[v] + half_slope<R, LIM>(d0, d1);
-    pr[v] = c[v] - half_slope<R, LIM>(d1, d2);
+    if (v < NREC) {
+      const R d0 = b[v] - a[v], d1 = c[v] - b[v], d2 = d[v] - c[v];
+      pl[v] = b[v] + half_slope<R, LIM>(d0, d1);
+      pr[v] = c[v] - half_slope<R, LIM>(d1, d2);
+    } else {                 // not reconstructed: the cell values
+      pl[v] = b[v];
+      pr[v] = c[v];
+    }
   }
 }
 

@@ -59,6 +59,10 @@ def test_half_periodic_and_srhd_hll_rejected(lib):
     assert lib.agile_mesh_create(C.byref(cfg), None, None, C.byref(out)) == 1
     cfg = agile.make_config(physics="hd", eos="synge")    # the Synge EOS is srhd-only
     assert lib.agile_mesh_create(C.byref(cfg), None, None, C.byref(out)) == 1
+    cfg = agile.make_config(physics="ffhd", flux="hll")    # ffhd: TVDLF only
+    assert lib.agile_mesh_create(C.byref(cfg), None, None, C.byref(out)) == 1
+    cfg = agile.make_config(physics="ffhd", flux="tvdlf", max_level=2)   # ffhd: uniform meshes
+    assert lib.agile_mesh_create(C.byref(cfg), None, None, C.byref(out)) == 1
 
 
 def test_allocator_failure_returns_enomem(lib):
