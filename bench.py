@@ -388,6 +388,49 @@ def run_cooling(steps=20, warmup=3):
             "throughput_reduction": 1.0 - res["plain"] / res["cooling"]}
 
 
+def run_ffhd(steps=20, warmup=3):
+    """Frozen-field hydrodynamics (Section 2.3.2) on a periodic 256^3 grid of 16^3 blocks
+    in a sheared frozen field, TVDLF, van Leer, SSPRK3, FP32 stencil, without and with the
+    radiative losses (the paper compares these configurations for its FFHD case on an H100,
+    Section 4.4; it reports relative costs, not this grid)."""
+    import torch
+    from paper_2607_19277_gb300 import agile, workloads as W
+    T, L = W.skew_normal_cooling(n=256, t_min=1e-2, t_max=1e2, t_peak=1.0, peak=0.5)
+
+    def ic(x, y, z):
+        th = 0.7 * np.sin(2 * math.pi * x) + 0.5 * np.cos(2 * math.pi * (y + z))
+        p = np.zeros((6,) + np.shape(x))
+        p[0] = 1.0 + 0.3 * np.sin(2 * math.pi * (x + 2 * y)) * np.cos(2 * math.pi * z)
+        p[1] = 0.4 * np.cos(2 * math.pi * (x - y))
+        p[2] = 1.0 + 0.2 * np.sin(2 * math.pi * (y + z))
+        p[3] = np.cos(th) * np.cos(0.3 * th)
+        p[4] = np.sin(th) * np.cos(0.3 * th)
+        p[5] = np.sin(0.3 * th)
+        return p
+    out = {"workload": "ffhd 256^3 (4096 x 16^3) sheared frozen field, tvdlf vanleer ssprk3, fp32"}
+    for name, cool in (("plain", False), ("losses", True)):
+        m = agile.Mesh(agile.make_config(physics="ffhd", limiter="vanleer", flux="tvdlf", rk=3, real_bytes=4,
+                                         base_blocks=(N_SIDE // 16,) * 3))
+        if cool:
+            m.set_cooling(T, L)
+        m.set_state(ic)
+        for _ in range(warmup):
+            m.step(0.0)
+        m.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            m.step(0.0)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        m.close()
+        out[name] = {"value": float(N_SIDE ** 3) * 3 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms}
+    out["throughput_reduction_with_losses"] = 1.0 - out["plain"]["ms_per_step"] / out["losses"]["ms_per_step"]
+    return out
+
+
 def run_serving(nreq=32, rate=50.0, budget_gb=160.0):
     """Serving stream (bounded sample of the configured stream): Poisson arrivals of HD /
     MHD / SRHD solves admitted against the HBM budget, FP32 stencils, then the same stream on
@@ -471,6 +514,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-paper-scheme", action="store_true")
     ap.add_argument("--no-cooling", action="store_true")
+    ap.add_argument("--no-ffhd", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -579,6 +623,11 @@ def main():
             line["cooling_mhd"] = run_cooling()
         except Exception as e:
             line["cooling_mhd"] = {"error": str(e)}
+    if not args.no_ffhd:
+        try:
+            line["ffhd"] = run_ffhd()
+        except Exception as e:
+            line["ffhd"] = {"error": str(e)}
     if not args.no_serving:
         try:
             line["serving"] = run_serving()
