@@ -300,7 +300,8 @@ def run_batched(steps, warmup, nsolve=256, fp64_solves=8):
            "kernel_launches_in_timed_region": launches,
            "autotune": {"grid": tuned[0], "dynamic_blocks": tuned[1],
                         "stage1_ms": {"1/SM,counter": tuned[2][0], "1/SM,strided": tuned[2][1],
-                                      "2/SM,counter": tuned[2][2], "2/SM,strided": tuned[2][3]}}}
+                                      "2/SM,counter": tuned[2][2], "2/SM,strided": tuned[2][3],
+                                      "3/SM,counter": tuned[2][4], "3/SM,strided": tuned[2][5]}}}
     # plain FP64 per-solve path: each solve its own mesh, solved one after the other
     z64 = 0
     t64 = 0.0
@@ -395,7 +396,7 @@ def run_ffhd(steps=20, warmup=3):
     Section 4.4; it reports relative costs, not this grid)."""
     import torch
     from paper_2607_19277_gb300 import agile, workloads as W
-    T, L = W.skew_normal_cooling(n=256, t_min=1e-2, t_max=1e2, t_peak=1.0, peak=0.5)
+    T, L = W.skew_normal_cooling(n=256, t_min=5e-2, t_max=1e2, t_peak=1.0, peak=0.5)
 
     def ic(x, y, z):
         th = 0.7 * np.sin(2 * math.pi * x) + 0.5 * np.cos(2 * math.pi * (y + z))

@@ -286,14 +286,15 @@ agile_status agile_batch_get_state(agile_batch* batch, int solve, int* level, in
 
 /* Autotuner of the batched stage launches (no counterpart in the paper): times `trials`
  * launches of the first RK stage (which reads the solution and writes only a stage buffer,
- * so the solution is not modified) for four launch shapes, the persistent grid at 1 and 2
+ * so the solution is not modified) for six launch shapes, the persistent grid at 1, 2 and 3
  * CTAs per SM, each with blocks taken from an atomic counter or strided by the grid, and
  * keeps the fastest for every later step (the CUDA graph of a step is captured again).
  * Results do not depend on the choice: every block's arithmetic is the same.
  *  trials   1..100 timed launches per shape (after one untimed launch)
  *  grid     out: CTAs of the chosen shape; dynamic: out, 1 for the atomic counter
- *  ms       out (may be NULL): mean ms per launch of the shapes in the order (1 CTA/SM,
- *           counter), (1, strided), (2, counter), (2, strided)
+ *  ms       out (may be NULL, else 6 floats): mean ms per launch of the shapes in the
+ *           order (1 CTA/SM, counter), (1, strided), (2, counter), (2, strided), (3,
+ *           counter), (3, strided)
  * Synchronises the batch's stream. */
 agile_status agile_batch_autotune(agile_batch* batch, int trials, int* grid, int* dynamic, float* ms);
 

@@ -429,7 +429,7 @@ class Batch:
     def autotune(self, trials=3):
         """Pick the fastest stage-launch shape; returns (grid, dynamic, ms per shape)."""
         g, d = C.c_int(), C.c_int()
-        ms = (C.c_float * 4)()
+        ms = (C.c_float * 6)()      # the library writes six values
         self._ck(self.lib.agile_batch_autotune(self.ptr, int(trials), C.byref(g), C.byref(d), ms))
         return g.value, bool(d.value), list(ms)
 

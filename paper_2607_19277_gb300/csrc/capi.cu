@@ -1046,13 +1046,13 @@ agile_status agile_batch_autotune(agile_batch* B, int trials, int* grid, int* dy
   int dev = 0, sms = 0;
   BCK(B, cudaGetDevice(&dev));
   BCK(B, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int grids[2] = {sms, 2 * sms};
+  const int grids[3] = {sms, 2 * sms, 3 * sms};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   BCK(B, cudaEventCreate(&e0));
   BCK(B, cudaEventCreate(&e1));
   float best = 0.0f;
   int bi = -1;
-  for (int c = 0; c < 4 && !s; ++c) {
+  for (int c = 0; c < 6 && !s; ++c) {
     const int g = grids[c >> 1];
     const bool dyn = (c & 1) == 0;
     s = batch_stage1(B, g, dyn);                        // warm-up

@@ -6,9 +6,12 @@ namespace agile {
 
 template <template <typename> class PT, typename R, int LIM, int FLUX>
 static cudaError_t stage_go(const StageArgs& a, cudaStream_t s) {
-  constexpr int MINB = sizeof(R) == 4 ? 2 : 1;   // CTAs per SM the register budget targets
+  // CTAs per SM the register budget targets: 1 in FP64; in FP32 3 when three CTAs' shared
+  // memory fits an SM (233472 bytes, 1 KB reserved per CTA), else 2
+  constexpr size_t SMEM = stage_smem_bytes<PT, R>();
+  constexpr int MINB = sizeof(R) == 8 ? 1 : (3 * (SMEM + 1024) <= 233472 ? 3 : 2);
   auto k = stage_kernel<PT, R, LIM, FLUX, MINB>;
-  const size_t smem = stage_smem_bytes<PT, R>();
+  const size_t smem = SMEM;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -97,8 +97,8 @@ def test_autotune_keeps_results_and_picks_a_shape(physics):
     assert all(np.array_equal(x, y) for x, y in zip(after, before))
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    assert grid in (sms, 2 * sms) and all(t > 0 for t in ms)
-    assert min(ms) == ms[(0 if grid == sms else 2) + (0 if dynamic else 1)]
+    assert grid in (sms, 2 * sms, 3 * sms) and len(ms) == 6 and all(t > 0 for t in ms)
+    assert min(ms) == ms[2 * (grid // sms - 1) + (0 if dynamic else 1)]
     for _ in range(3):
         a.step()
         b.step()
