@@ -250,6 +250,11 @@ __device__ __forceinline__ void swap_xy(R* v, bool yd) {
 }
 
 constexpr uint32_t WAIT_LIMIT = 1u << 22;   // ~0.1 s of polling per wait at most
+
+// Slot of plane p (-2 .. 17) in the primitive ring. The ring is thread-private (every thread
+// reads and writes only its own column), holds the three planes a z-face needs, and plane p
+// + 3 takes the slot of plane p.
+__device__ __forceinline__ int pslot(int p) { return (p + 3) % 3; }
 constexpr int ST_ETIMEOUT = 4;
 
 template <template <typename> class PT, typename R>
@@ -257,8 +262,8 @@ struct StageSmem {
   static constexpr int NV = PT<R>::NV, NT = PT<R>::NV + PT<R>::NA;
   static constexpr size_t bars = 128;                                  // 4 mbarriers (+pad)
   static constexpr size_t raw = bars;                                  // [4][NT][256]
-  static constexpr size_t prim = raw + sizeof(R) * 4 * NT * 256;       // [4][NT][256]
-  static constexpr size_t cur = prim + sizeof(R) * 4 * NT * 256;       // [NV][20][20]
+  static constexpr size_t prim = raw + sizeof(R) * 4 * NT * 256;       // [3][NT][256]
+  static constexpr size_t cur = prim + sizeof(R) * 3 * NT * 256;       // [NV][20][20]
   static constexpr size_t fx = cur + sizeof(R) * NV * 400;             // [NV][16][17]
   static constexpr size_t fy = fx + sizeof(R) * NV * 272;              // [NV][17][16]
   static constexpr size_t halo = fy + sizeof(R) * NV * 272;            // [NT][128] raw halo
@@ -397,7 +402,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       aux[0] = R(0);
     }
     P::cons2prim(u, pr, aux, pp, st);
-    R* w = sPr + (size_t)(p & 3) * NT * 256 + cell2;
+    R* w = sPr + (size_t)pslot(p) * NT * 256 + cell2;
 #pragma unroll
     for (int v = 0; v < NV; ++v) w[v * 256] = pr[v];
     if constexpr (NA > 0) {
@@ -410,9 +415,9 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   // plane k + 1, so each plane's z-slope is formed once.
   auto zface = [&](int k, R* f, R* hz) {
     R bq[NV], c[NV], d[NV], pl[NV], pr[NV];
-    const R* r1 = sPr + (size_t)(k & 3) * NT * 256 + cell2;
-    const R* r2 = sPr + (size_t)((k + 1) & 3) * NT * 256 + cell2;
-    const R* r3 = sPr + (size_t)((k + 2) & 3) * NT * 256 + cell2;
+    const R* r1 = sPr + (size_t)pslot(k) * NT * 256 + cell2;
+    const R* r2 = sPr + (size_t)pslot(k + 1) * NT * 256 + cell2;
+    const R* r3 = sPr + (size_t)pslot(k + 2) * NT * 256 + cell2;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       bq[v] = r1[v * 256]; c[v] = r2[v * 256]; d[v] = r3[v * 256];
@@ -481,16 +486,16 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     issue(3);
   }
   convert_own(0);
-  convert_own(1);
   R fzd[NV], fzu[NV], hz[NV];
-  {
-    const R* r0 = sPr + (size_t)((-2) & 3) * NT * 256 + cell2;
-    const R* r1 = sPr + (size_t)((-1) & 3) * NT * 256 + cell2;
-    const R* r2 = sPr + (size_t)(0 & 3) * NT * 256 + cell2;
+  {  // z-slope of plane 0 from planes -1, 0 and 1 ... before plane 1 takes plane -2's slot
+    const R* r0 = sPr + (size_t)pslot(-2) * NT * 256 + cell2;
+    const R* r1 = sPr + (size_t)pslot(-1) * NT * 256 + cell2;
+    const R* r2 = sPr + (size_t)pslot(0) * NT * 256 + cell2;
 #pragma unroll
     for (int v = 0; v < NV; ++v)
       hz[v] = v < P::NREC ? half_slope<R, LIM>(r1[v * 256] - r0[v * 256], r2[v * 256] - r1[v * 256]) : R(0);
   }
+  convert_own(1);
   zface(-1, fzd, hz);
   if (FR && slot[4] >= 0) {
 #pragma unroll
@@ -503,7 +508,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     // ---- phase 1
     if (k + 2 <= NB + 1) convert_own(k + 2);
     {
-      const R* r = sPr + (size_t)(k & 3) * NT * 256 + cell2;
+      const R* r = sPr + (size_t)pslot(k) * NT * 256 + cell2;
 #pragma unroll
       for (int v = 0; v < NV; ++v) sC[v * 400 + (ty + 2) * 20 + tx + 2] = r[v * 256];
     }
@@ -610,7 +615,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
           fzd[v] = fzu[v];
         }
         R pc[NV];
-        const R* pk = sPr + (size_t)(k & 3) * NT * 256 + cell2;
+        const R* pk = sPr + (size_t)pslot(k) * NT * 256 + cell2;
 #pragma unroll
         for (int v = 0; v < NV; ++v) pc[v] = pk[v * 256];
         P::source(L, pc);
@@ -641,7 +646,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       for (int v = 0; v < NV; ++v) Uo[base + (size_t)v * NCELL] = out[v];
       R auxk[NAW];
       if constexpr (NA > 0) {
-        const R* pa = sPr + (size_t)(k & 3) * NT * 256 + cell2;
+        const R* pa = sPr + (size_t)pslot(k) * NT * 256 + cell2;
 #pragma unroll
         for (int i = 0; i < NA; ++i) {
           auxk[i] = pa[(NV + i) * 256];
