@@ -284,6 +284,19 @@ agile_status agile_batch_cfl_dt(agile_batch* batch, double* dt);
 /* State of one solve, as agile_get_state. Synchronises. */
 agile_status agile_batch_get_state(agile_batch* batch, int solve, int* level, int* ijk, double* cons);
 
+/* Refinement of one solve of a batch (Fig. 2 regrid, as agile_regrid / agile_regrid_flags for
+ * a mesh): the Loehner estimate of its blocks after a ghost fill of the batch decides the
+ * flags (agile_batch_regrid), or the caller gives one flag per block of the solve (-1
+ * coarsen, 0 keep, 1 refine; agile_batch_regrid_flags). The batch's pools are laid out
+ * again (the other solves' blocks are copied on the device), its descriptor tables rebuilt
+ * and the next step's CUDA graph captured again. init != 0 re-applies the initial condition
+ * given to agile_batch_set_state to the blocks a refinement creates. Ghost fill of the
+ * coarse-fine faces, the flux fix-up and their launches join every batched step from then
+ * on (solves with max_level = 1 never refine). Synchronises. */
+agile_status agile_batch_regrid(agile_batch* batch, int solve, int init, int* n_refined, int* n_coarsened);
+agile_status agile_batch_regrid_flags(agile_batch* batch, int solve, const int* flags, int init,
+                                      int* n_refined, int* n_coarsened);
+
 /* Autotuner of the batched stage launches (no counterpart in the paper): times `trials`
  * launches of the first RK stage (which reads the solution and writes only a stage buffer,
  * so the solution is not modified) for six launch shapes, the persistent grid at 1, 2 and 3
@@ -301,7 +314,7 @@ agile_status agile_batch_autotune(agile_batch* batch, int trials, int* grid, int
 /* Copy the current state of solve src_solve of batch src into solve dst_solve of batch dst
  * (device to device; no counterpart in the paper: it lets a request loop rebuild its batch
  * when solves join or leave without a host round trip). The two solves must have the same
- * block layout, domain, boundaries, physics, EOS and stencil precision. Waits for the
+ * blocks (refinement included), domain, boundaries, physics, EOS and stencil precision. Waits for the
  * source batch's stream and the copy (synchronising both); the next step of dst
  * recomputes its CFL speeds. AGILE_EINVAL when the solves differ. */
 agile_status agile_batch_copy_solve(agile_batch* dst, int dst_solve, agile_batch* src, int src_solve);

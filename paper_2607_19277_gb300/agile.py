@@ -36,7 +36,7 @@ EXPORTS = ["agile_mesh_create", "agile_mesh_destroy", "agile_set_state", "agile_
            "agile_selftest_bounded_wait", "agile_last_error", "agile_version",
            "agile_batch_create", "agile_batch_destroy", "agile_batch_layout",
            "agile_batch_set_state", "agile_batch_step", "agile_batch_cfl_dt", "agile_batch_copy_solve",
-           "agile_batch_autotune",
+           "agile_batch_autotune", "agile_batch_regrid", "agile_batch_regrid_flags",
            "agile_batch_get_state", "agile_batch_sync", "agile_batch_launches",
            "agile_batch_last_error"]
 
@@ -114,6 +114,8 @@ def load(path: str = LIB_PATH):
         "agile_batch_get_state": (C.c_int, [P, C.c_int, ip, ip, dp]),
         "agile_batch_copy_solve": (C.c_int, [P, C.c_int, P, C.c_int]),
         "agile_batch_autotune": (C.c_int, [P, C.c_int, ip, ip, C.POINTER(C.c_float)]),
+        "agile_batch_regrid": (C.c_int, [P, C.c_int, C.c_int, ip, ip]),
+        "agile_batch_regrid_flags": (C.c_int, [P, C.c_int, ip, C.c_int, ip, ip]),
         "agile_batch_sync": (C.c_int, [P]),
         "agile_batch_launches": (C.c_longlong, [P]),
         "agile_batch_last_error": (C.c_char_p, [P]),
@@ -425,6 +427,18 @@ class Batch:
         cons = np.zeros((n, nv, 16, 16, 16))
         self._ck(self.lib.agile_batch_get_state(self.ptr, solve, _iptr(lev), _iptr(ijk), _dptr(cons)))
         return lev, ijk, cons
+
+    def regrid(self, solve, init=False):
+        """Estimate-driven refinement of one solve; returns (n_refined, n_coarsened)."""
+        nr, nc = C.c_int(), C.c_int()
+        self._ck(self.lib.agile_batch_regrid(self.ptr, solve, int(init), C.byref(nr), C.byref(nc)))
+        return nr.value, nc.value
+
+    def regrid_flags(self, solve, flags, init=False):
+        f = np.ascontiguousarray(flags, dtype=np.int32)
+        nr, nc = C.c_int(), C.c_int()
+        self._ck(self.lib.agile_batch_regrid_flags(self.ptr, solve, _iptr(f), int(init), C.byref(nr), C.byref(nc)))
+        return nr.value, nc.value
 
     def autotune(self, trials=3):
         """Pick the fastest stage-launch shape; returns (grid, dynamic, ms per shape)."""

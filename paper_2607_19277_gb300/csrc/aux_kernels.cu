@@ -148,8 +148,10 @@ template <typename R, int NV, int NT>
 __global__ void __launch_bounds__(256) fixup_kernel(R* __restrict__ U, const R* __restrict__ FR,
                                                      const BlockDesc* __restrict__ bd,
                                                      const FixupTask* __restrict__ tasks, double b,
-                                                     const double* __restrict__ dtch) {
+                                                     const double* __restrict__ dtch,
+                                                     const int* __restrict__ solve_of) {
   const FixupTask& tk = tasks[blockIdx.x];
+  const double dt = dtch[2 * (solve_of ? solve_of[tk.blk] : 0)];   // the block's solve
   const int t1 = threadIdx.x & 15, t2 = threadIdx.x >> 4;
   for (int j = 0; j < tk.nface; ++j) {
     const int face = tk.face[j];
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(256) fixup_kernel(R* __restrict__ U, const R* 
     const size_t cell = (size_t)q[2] * 256 + q[1] * 16 + q[0];
     const int sf = tk.slot_f[j][(t1 >> 3) + 2 * (t2 >> 3)];
     const int a0 = 2 * (t1 & 7), b0 = 2 * (t2 & 7);
-    const R w = R(b * dtch[0] / bd[tk.blk].dx[d]) * (s ? R(1) : R(-1));
+    const R w = R(b * dt / bd[tk.blk].dx[d]) * (s ? R(1) : R(-1));
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const R fc = FR[((size_t)tk.slot_c[j] * NV + v) * 256 + t2 * 16 + t1];
@@ -495,14 +497,15 @@ cudaError_t launch_fixup(const AuxArgs& a, const FixupTask* tasks, int ntasks, d
                          const double* dtch, cudaStream_t s) {
   if (ntasks == 0) return cudaSuccess;
   const int nv = phys_nvar(a.phys), nt = nv + phys_naux(a.phys);
+  if (nv == 6) return cudaErrorInvalidValue;   // ffhd runs on uniform meshes only
   if (a.real_bytes == 8) {
-    if (nv == 9) fixup_kernel<double, 9, 9><<<ntasks, 256, 0, s>>>((double*)a.Uw, (const double*)a.FR, a.bd, tasks, b, dtch);
-    else if (nt == 5) fixup_kernel<double, 5, 5><<<ntasks, 256, 0, s>>>((double*)a.Uw, (const double*)a.FR, a.bd, tasks, b, dtch);
-    else fixup_kernel<double, 5, 7><<<ntasks, 256, 0, s>>>((double*)a.Uw, (const double*)a.FR, a.bd, tasks, b, dtch);
+    if (nv == 9) fixup_kernel<double, 9, 9><<<ntasks, 256, 0, s>>>((double*)a.Uw, (const double*)a.FR, a.bd, tasks, b, dtch, a.solve_of);
+    else if (nt == 5) fixup_kernel<double, 5, 5><<<ntasks, 256, 0, s>>>((double*)a.Uw, (const double*)a.FR, a.bd, tasks, b, dtch, a.solve_of);
+    else fixup_kernel<double, 5, 7><<<ntasks, 256, 0, s>>>((double*)a.Uw, (const double*)a.FR, a.bd, tasks, b, dtch, a.solve_of);
   } else {
-    if (nv == 9) fixup_kernel<float, 9, 9><<<ntasks, 256, 0, s>>>((float*)a.Uw, (const float*)a.FR, a.bd, tasks, b, dtch);
-    else if (nt == 5) fixup_kernel<float, 5, 5><<<ntasks, 256, 0, s>>>((float*)a.Uw, (const float*)a.FR, a.bd, tasks, b, dtch);
-    else fixup_kernel<float, 5, 7><<<ntasks, 256, 0, s>>>((float*)a.Uw, (const float*)a.FR, a.bd, tasks, b, dtch);
+    if (nv == 9) fixup_kernel<float, 9, 9><<<ntasks, 256, 0, s>>>((float*)a.Uw, (const float*)a.FR, a.bd, tasks, b, dtch, a.solve_of);
+    else if (nt == 5) fixup_kernel<float, 5, 5><<<ntasks, 256, 0, s>>>((float*)a.Uw, (const float*)a.FR, a.bd, tasks, b, dtch, a.solve_of);
+    else fixup_kernel<float, 5, 7><<<ntasks, 256, 0, s>>>((float*)a.Uw, (const float*)a.FR, a.bd, tasks, b, dtch, a.solve_of);
   }
   return cudaGetLastError();
 }

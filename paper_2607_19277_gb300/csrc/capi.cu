@@ -879,6 +879,14 @@ struct agile_batch {
   std::string err;
   int grid = 0;                     // persistent CTAs of the stage launches (0: default)
   bool dynamic = true;              // blocks taken from an atomic counter (else strided)
+  // refinement: ghost slots, flux registers and their tasks of all solves (indices offset)
+  void* G = nullptr;
+  void* FR = nullptr;
+  GhostTask* d_ghosts = nullptr;
+  FixupTask* d_fix = nullptr;
+  int nghost = 0, nfix = 0, nslots = 0;
+  std::vector<agile_ic_fn> ics;     // initial conditions, re-applied to blocks a regrid creates
+  std::vector<void*> ic_users;
 };
 
 namespace {
@@ -918,15 +926,206 @@ AuxArgs batch_aux(agile_batch* B, void* U) {
   a.glm_alpha = B->cfg.glm_alpha;
   a.U = U;
   a.Uw = U;
-  a.G = nullptr;
-  a.Gw = nullptr;
-  a.FR = nullptr;
+  a.G = B->G;
+  a.Gw = B->G;
+  a.FR = B->FR;
   a.bd = B->d_bd;
   a.nblk = B->nblk;
   a.status = B->d_status;
   a.solve_of = B->d_solve_of;
   a.nsolve = B->nsolve;
   return a;
+}
+
+agile_status batch_status(agile_batch* B);
+
+// Descriptor tables of all solves concatenated: block indices offset by the solve's first
+// block, ghost-slot / flux-register indices by its first slot. Every index is checked against
+// the new sizes before anything is uploaded. Reallocates everything except U[0], whose
+// blocks the caller has already laid out in this order.
+agile_status batch_rebuild(agile_batch* B) {
+  std::vector<BlockDesc> desc;
+  std::vector<GhostTask> ghosts;
+  std::vector<FixupTask> fix;
+  std::vector<int> solve_of;
+  B->offset.clear();
+  int slots = 0;
+  for (int i = 0; i < B->nsolve; ++i) {
+    std::vector<BlockDesc> d;
+    std::vector<GhostTask> g;
+    std::vector<FixupTask> x;
+    int ns = 0;
+    std::string err;
+    B->meshes[i]->build_descs(&d, &g, &x, &ns, &err);
+    if (!err.empty()) return bfail(B, AGILE_EINVAL, err);
+    const int O = (int)desc.size(), S = slots;
+    B->offset.push_back(O);
+    for (BlockDesc& bd : d) {
+      for (int f = 0; f < 6; ++f) {
+        if (bd.src[f] >= 0) bd.src[f] += O;
+        else if (bd.src[f] <= SRC_SLOT0) bd.src[f] = SRC_SLOT0 - (SRC_SLOT0 - bd.src[f] + S);
+        if (bd.slot[f] >= 0) bd.slot[f] += S;
+        for (int q = 0; q < 4; ++q)
+          if (bd.nbr[f][q] >= 0) bd.nbr[f][q] += O;
+      }
+      desc.push_back(bd);
+      solve_of.push_back(i);
+    }
+    for (GhostTask& t : g) {
+      t.blk += O;
+      t.slot += S;
+      for (int q = 0; q < 4; ++q)
+        if (t.nbr[q] >= 0) t.nbr[q] += O;
+      ghosts.push_back(t);
+    }
+    for (FixupTask& t : x) {
+      t.blk += O;
+      for (int j = 0; j < t.nface; ++j) {
+        t.slot_c[j] += S;
+        for (int q = 0; q < 4; ++q) t.slot_f[j][q] += S;
+      }
+      fix.push_back(t);
+    }
+    slots += ns;
+  }
+  const int nblk = (int)desc.size();
+  auto blk_ok = [&](int v) { return v >= 0 && v < nblk; };
+  auto slot_ok = [&](int v) { return v >= 0 && v < slots; };
+  for (const BlockDesc& bd : desc)
+    for (int f = 0; f < 6; ++f) {
+      if (bd.src[f] >= 0 && !blk_ok(bd.src[f])) return bfail(B, AGILE_EINVAL, "block table out of range");
+      if (bd.src[f] <= SRC_SLOT0 && !slot_ok(SRC_SLOT0 - bd.src[f])) return bfail(B, AGILE_EINVAL, "slot out of range");
+      if (bd.slot[f] >= slots) return bfail(B, AGILE_EINVAL, "slot out of range");
+      for (int q = 0; q < 4; ++q)
+        if (bd.nbr[f][q] >= nblk) return bfail(B, AGILE_EINVAL, "neighbour out of range");
+    }
+  for (const GhostTask& t : ghosts) {
+    if (!blk_ok(t.blk) || !slot_ok(t.slot)) return bfail(B, AGILE_EINVAL, "ghost task out of range");
+    for (int q = 0; q < 4; ++q)
+      if (t.nbr[q] >= nblk) return bfail(B, AGILE_EINVAL, "ghost task out of range");
+  }
+  for (const FixupTask& t : fix) {
+    if (!blk_ok(t.blk)) return bfail(B, AGILE_EINVAL, "fix-up task out of range");
+    for (int j = 0; j < t.nface; ++j) {
+      if (!slot_ok(t.slot_c[j])) return bfail(B, AGILE_EINVAL, "fix-up task out of range");
+      for (int q = 0; q < 4; ++q)
+        if (!slot_ok(t.slot_f[j][q])) return bfail(B, AGILE_EINVAL, "fix-up task out of range");
+    }
+  }
+  agile_mesh view;
+  as_mesh_view(B, &view);
+  dfree_t(&view, B->d_bd);
+  dfree_t(&view, B->d_solve_of);
+  dfree_t(&view, B->d_ghosts);
+  dfree_t(&view, B->d_fix);
+  dfree(&view, B->G);
+  dfree(&view, B->FR);
+  dfree(&view, B->U[1]);
+  dfree(&view, B->U[2]);
+  B->nblk = nblk;
+  view.nblk = nblk;
+  const size_t pool = (size_t)nblk * B->nt * NCELL * B->rb;
+  B->U[1] = dalloc(&view, pool);
+  B->U[2] = B->cfg.rk == 3 ? dalloc(&view, pool) : nullptr;
+  B->d_bd = (BlockDesc*)dalloc(&view, desc.size() * sizeof(BlockDesc));
+  B->d_solve_of = (int*)dalloc(&view, solve_of.size() * sizeof(int));
+  if (!ghosts.empty()) B->d_ghosts = (GhostTask*)dalloc(&view, ghosts.size() * sizeof(GhostTask));
+  if (!fix.empty()) B->d_fix = (FixupTask*)dalloc(&view, fix.size() * sizeof(FixupTask));
+  if (slots) {
+    B->G = dalloc(&view, (size_t)slots * B->nt * 512 * B->rb);
+    B->FR = dalloc(&view, (size_t)slots * B->nv * 256 * B->rb);
+  }
+  if (!B->U[1] || (B->cfg.rk == 3 && !B->U[2]) || !B->d_bd || !B->d_solve_of ||
+      (!ghosts.empty() && !B->d_ghosts) || (!fix.empty() && !B->d_fix) || (slots && (!B->G || !B->FR)))
+    return bfail(B, AGILE_ENOMEM, "device allocation failed");
+  BCK(B, cudaMemcpyAsync(B->d_bd, desc.data(), desc.size() * sizeof(BlockDesc), cudaMemcpyHostToDevice, B->stream));
+  BCK(B, cudaMemcpyAsync(B->d_solve_of, solve_of.data(), solve_of.size() * sizeof(int), cudaMemcpyHostToDevice, B->stream));
+  if (!ghosts.empty())
+    BCK(B, cudaMemcpyAsync(B->d_ghosts, ghosts.data(), ghosts.size() * sizeof(GhostTask), cudaMemcpyHostToDevice, B->stream));
+  if (!fix.empty())
+    BCK(B, cudaMemcpyAsync(B->d_fix, fix.data(), fix.size() * sizeof(FixupTask), cudaMemcpyHostToDevice, B->stream));
+  B->nghost = (int)ghosts.size();
+  B->nfix = (int)fix.size();
+  B->nslots = slots;
+  BCK(B, cudaStreamSynchronize(B->stream));   // host tables go out of scope
+  for (int i = 0; i < 3; ++i) {
+    if (make_tmap(&view, B->U[i], &B->tmap[i]) != AGILE_OK) return bfail(B, AGILE_ECUDA, "tensor map");
+  }
+  if (B->graph) {                   // the captured step refers to the old tables
+    cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+  }
+  B->steps_done = 0;
+  B->speeds_valid = false;
+  return AGILE_OK;
+}
+
+// Regrid one solve with the given flags: the other solves' blocks are copied to their new
+// places, the solve's new blocks come from the regrid kernel (copy / prolong / restrict),
+// then the tables are rebuilt; blocks a refinement creates get the initial condition again
+// when init is set.
+agile_status batch_regrid(agile_batch* B, int solve, const std::vector<int>& flags, int init, int* nr,
+                          int* nc) {
+  HostMesh* hm = B->meshes[solve];
+  RegridPlan plan = hm->plan(flags);
+  if (nr) *nr = plan.n_refined;
+  if (nc) *nc = plan.n_coarsened;
+  if (plan.n_refined == 0 && plan.n_coarsened == 0) return AGILE_OK;
+  agile_mesh view;
+  as_mesh_view(B, &view);
+  AuxArgs a = batch_aux(B, B->U[0]);
+  if (B->nghost) BCK(B, launch_ghosts(a, B->d_ghosts, B->nghost, B->stream));
+  const size_t per = (size_t)B->nt * NCELL * B->rb;
+  std::vector<int> count(B->nsolve);
+  for (int j = 0; j < B->nsolve; ++j) count[j] = (int)B->meshes[j]->blocks().size();
+  const int nnew_i = (int)plan.blocks.size();
+  long long total = 0;
+  std::vector<long long> noff(B->nsolve);
+  for (int j = 0; j < B->nsolve; ++j) {
+    noff[j] = total;
+    total += j == solve ? nnew_i : count[j];
+  }
+  void* Unew = dalloc(&view, (size_t)total * per);
+  std::vector<RegridSrc> src = plan.src;
+  for (RegridSrc& r : src) {
+    const int nsrc = r.mode == 2 ? 8 : 1;
+    for (int q = 0; q < nsrc; ++q) {
+      if (r.src[q] < 0 || r.src[q] >= count[solve]) {
+        dfree(&view, Unew);
+        return bfail(B, AGILE_EINVAL, "regrid source out of range");
+      }
+      r.src[q] += B->offset[solve];
+    }
+  }
+  RegridSrc* d_src = (RegridSrc*)dalloc(&view, src.size() * sizeof(RegridSrc));
+  if (!Unew || !d_src) return bfail(B, AGILE_ENOMEM, "device allocation failed");
+  for (int j = 0; j < B->nsolve; ++j)
+    if (j != solve && count[j])
+      BCK(B, cudaMemcpyAsync((char*)Unew + noff[j] * per, (const char*)B->U[0] + (size_t)B->offset[j] * per,
+                             (size_t)count[j] * per, cudaMemcpyDeviceToDevice, B->stream));
+  BCK(B, cudaMemcpyAsync(d_src, src.data(), src.size() * sizeof(RegridSrc), cudaMemcpyHostToDevice, B->stream));
+  BCK(B, launch_regrid(a, (char*)Unew + noff[solve] * per, d_src, nnew_i, B->stream));
+  BCK(B, cudaStreamSynchronize(B->stream));
+  dfree_t(&view, d_src);
+  dfree(&view, B->U[0]);
+  B->U[0] = Unew;
+  hm->apply(plan);
+  agile_status st = batch_rebuild(B);
+  if (st) return st;
+  if (init && B->ics[solve]) {
+    agile_mesh v2;
+    as_mesh_view(B, &v2);
+    v2.mesh = hm;
+    v2.cfg = B->cfgs[solve];
+    v2.ic = B->ics[solve];
+    v2.ic_user = B->ic_users[solve];
+    v2.d_status = B->d_status;
+    v2.nblk = nnew_i;
+    st = apply_ic(&v2, (char*)B->U[0] + (size_t)B->offset[solve] * per, plan.created);
+    v2.mesh = nullptr;
+    if (st) return bfail(B, st, v2.err);
+  }
+  return batch_status(B);
 }
 
 agile_status batch_status(agile_batch* B) {
@@ -964,25 +1163,31 @@ agile_status batch_enqueue_step(agile_batch* B) {
   static const double w2[2][2] = {{0.0, 1.0}, {0.5, 0.5}};
   static const double w3[3][2] = {{0.0, 1.0}, {0.75, 0.25}, {1.0 / 3.0, 2.0 / 3.0}};
   const int nst = B->cfg.rk;
+  const bool fuse = B->nfix == 0;     // no flux fix-up: GLM half and CFL speeds in the last stage
   for (int st = 0; st < nst; ++st) {
     const bool last = st == nst - 1;
+    void* Us = st == 0 ? B->U[0] : B->U[st];
+    if (B->nghost) {
+      AuxArgs ga = batch_aux(B, Us);
+      BCK(B, launch_ghosts(ga, B->d_ghosts, B->nghost, B->stream));
+    }
     if (last) BCK(B, cudaMemsetAsync(B->d_speeds, 0, 2 * sizeof(unsigned long long) * B->nsolve, B->stream));
     StageArgs A;
-    A.Us = st == 0 ? B->U[0] : B->U[st];
+    A.Us = Us;
     A.Un = B->U[0];
     A.Uout = last ? B->U[0] : B->U[st + 1];
     A.bd = B->d_bd;
-    A.gs = nullptr;
-    A.fr = nullptr;
+    A.gs = B->G;
+    A.fr = B->nfix ? B->FR : nullptr;
     A.dtch = B->d_dtch;
     A.a = nst == 2 ? w2[st][0] : w3[st][0];
     A.b = nst == 2 ? w2[st][1] : w3[st][1];
     A.gamma = B->cfg.gamma;
     A.glm_alpha = B->cfg.glm_alpha;
-    A.glm_post = (mhd && last) ? 1 : 0;
+    A.glm_post = (mhd && last && fuse) ? 1 : 0;
     A.nblk = B->nblk;
     A.status = B->d_status;
-    A.speeds = last ? B->d_speeds : nullptr;
+    A.speeds = (last && fuse) ? B->d_speeds : nullptr;
     A.tmap = &B->tmap[st == 0 ? 0 : st];
     A.solve_of = B->d_solve_of;
     A.work = B->dynamic ? B->d_work + st : nullptr;
@@ -995,6 +1200,15 @@ agile_status batch_enqueue_step(agile_batch* B) {
     else if (B->cfg.physics == AGILE_FFHD) e = launch_stage_ffhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
     else e = launch_stage_srhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
     if (e != cudaSuccess) return bfail(B, AGILE_ECUDA, std::string("stage kernel: ") + cudaGetErrorString(e));
+    if (B->nfix) {
+      AuxArgs fa = batch_aux(B, A.Uout);
+      BCK(B, launch_fixup(fa, B->d_fix, B->nfix, A.b, B->d_dtch, B->stream));
+    }
+  }
+  if (!fuse) {                        // after the last fix-up: GLM half, then the CFL speeds
+    AuxArgs a = batch_aux(B, B->U[0]);
+    if (mhd) BCK(B, launch_glm_decay(a, B->d_dtch, B->stream));
+    BCK(B, launch_speeds(a, B->d_speeds, B->stream));
   }
   return AGILE_OK;
 }
@@ -1093,7 +1307,8 @@ agile_status agile_batch_create(const agile_config* cfgs, int nsolve, const agil
     const agile_config& c = cfgs[i];
     if (c.physics != c0.physics || c.limiter != c0.limiter || c.flux != c0.flux || c.rk != c0.rk ||
         c.real_bytes != c0.real_bytes || c.gamma != c0.gamma || c.cfl != c0.cfl ||
-        c.glm_alpha != c0.glm_alpha || c.eos != c0.eos || c.max_level != 1)
+        c.glm_alpha != c0.glm_alpha || c.eos != c0.eos || c.max_level < 1 || c.max_level > 12 ||
+        c.refine_nvars < 0 || c.refine_nvars > 9)
       return AGILE_EINVAL;
     // validate each configuration like a single mesh (host-side checks only)
     if (!scheme_ok(c)) return AGILE_EINVAL;
@@ -1124,60 +1339,36 @@ agile_status agile_batch_create(const agile_config* cfgs, int nsolve, const agil
   B->na = c0.physics == AGILE_SRHD ? 2 : 0;
   B->nt = B->nv + B->na;
   B->rb = c0.real_bytes;
-  std::vector<BlockDesc> desc;
-  std::vector<int> solve_of;
+  B->ics.assign(nsolve, nullptr);
+  B->ic_users.assign(nsolve, nullptr);
+  int nblk = 0;
   for (int i = 0; i < nsolve; ++i) {
-    HostMesh* hm = new HostMesh(cfgs[i].base_blocks, 1, cfgs[i].bc, cfgs[i].xmin, cfgs[i].xmax);
+    HostMesh* hm = new HostMesh(cfgs[i].base_blocks, cfgs[i].max_level, cfgs[i].bc, cfgs[i].xmin, cfgs[i].xmax);
     B->meshes.push_back(hm);
-    B->offset.push_back((int)desc.size());
-    std::vector<BlockDesc> d;
-    std::vector<GhostTask> g;
-    std::vector<FixupTask> x;
-    int ns = 0;
-    std::string err;
-    hm->build_descs(&d, &g, &x, &ns, &err);
-    if (!err.empty() || ns != 0) {
-      agile_batch_destroy(B);
-      return AGILE_EINVAL;
-    }
-    for (BlockDesc& bd : d) {
-      for (int f = 0; f < 6; ++f)
-        if (bd.src[f] >= 0) bd.src[f] += B->offset[i];
-      desc.push_back(bd);
-      solve_of.push_back(i);
-    }
+    nblk += (int)hm->blocks().size();
   }
-  B->nblk = (int)desc.size();
   agile_mesh view;
   as_mesh_view(B, &view);
-  const size_t pool = (size_t)B->nblk * B->nt * NCELL * B->rb;
+  view.nblk = nblk;
+  const size_t pool = (size_t)nblk * B->nt * NCELL * B->rb;
   B->U[0] = dalloc(&view, pool);
-  B->U[1] = dalloc(&view, pool);
-  B->U[2] = c0.rk == 3 ? dalloc(&view, pool) : nullptr;
-  B->d_bd = (BlockDesc*)dalloc(&view, desc.size() * sizeof(BlockDesc));
-  B->d_solve_of = (int*)dalloc(&view, solve_of.size() * sizeof(int));
   B->d_status = (int*)dalloc(&view, sizeof(int));
   B->d_speeds = (unsigned long long*)dalloc(&view, 2 * sizeof(unsigned long long) * nsolve);
   B->d_dtch = (double*)dalloc(&view, 2 * sizeof(double) * nsolve);
   B->d_work = (int*)dalloc(&view, 4 * sizeof(int));
-  if (!B->U[0] || !B->U[1] || (c0.rk == 3 && !B->U[2]) || !B->d_bd || !B->d_solve_of || !B->d_status ||
-      !B->d_speeds || !B->d_dtch || !B->d_work) {
+  if (!B->U[0] || !B->d_status || !B->d_speeds || !B->d_dtch || !B->d_work) {
     agile_batch_destroy(B);
     return AGILE_ENOMEM;
   }
-  if (cudaMemcpyAsync(B->d_bd, desc.data(), desc.size() * sizeof(BlockDesc), cudaMemcpyHostToDevice, B->stream) != cudaSuccess ||
-      cudaMemcpyAsync(B->d_solve_of, solve_of.data(), solve_of.size() * sizeof(int), cudaMemcpyHostToDevice, B->stream) != cudaSuccess ||
-      cudaMemsetAsync(B->d_status, 0, sizeof(int), B->stream) != cudaSuccess ||
-      cudaMemsetAsync(B->U[0], 0, pool, B->stream) != cudaSuccess || cudaStreamSynchronize(B->stream) != cudaSuccess) {
+  if (cudaMemsetAsync(B->d_status, 0, sizeof(int), B->stream) != cudaSuccess ||
+      cudaMemsetAsync(B->U[0], 0, pool, B->stream) != cudaSuccess) {
     agile_batch_destroy(B);
     return AGILE_ECUDA;
   }
-  view.nblk = B->nblk;
-  for (int i = 0; i < 3; ++i) {
-    if (make_tmap(&view, B->U[i], &B->tmap[i]) != AGILE_OK) {
-      agile_batch_destroy(B);
-      return AGILE_ECUDA;
-    }
+  const agile_status st = batch_rebuild(B);
+  if (st) {
+    agile_batch_destroy(B);
+    return st;
   }
   *out = B;
   return AGILE_OK;
@@ -1196,6 +1387,10 @@ void agile_batch_destroy(agile_batch* B) {
   dfree_t(&view, B->d_speeds);
   dfree_t(&view, B->d_dtch);
   dfree_t(&view, B->d_work);
+  dfree_t(&view, B->d_ghosts);
+  dfree_t(&view, B->d_fix);
+  dfree(&view, B->G);
+  dfree(&view, B->FR);
   cudaStreamSynchronize(B->stream);
   for (HostMesh* hm : B->meshes) delete hm;
   if (B->own_stream) cudaStreamDestroy(B->stream);
@@ -1229,6 +1424,8 @@ agile_status agile_batch_set_state(agile_batch* B, int solve, agile_ic_fn ic, vo
   agile_status s = apply_ic(&view, base, local);
   view.mesh = nullptr;
   if (s) return bfail(B, s, view.err);
+  B->ics[solve] = ic;
+  B->ic_users[solve] = user;
   B->speeds_valid = false;
   return batch_status(B);
 }
@@ -1259,7 +1456,8 @@ agile_status agile_batch_step(agile_batch* B) {
     }
     BCK(B, cudaGraphLaunch(B->graph, B->stream));
   }
-  B->launches += B->cfg.rk + 1 + (B->cfg.physics == AGILE_MHD_GLM ? 1 : 0);
+  B->launches += B->cfg.rk + 1 + (B->cfg.physics == AGILE_MHD_GLM ? 1 : 0) +
+                 (B->nghost ? B->cfg.rk : 0) + (B->nfix ? B->cfg.rk + 1 + (B->cfg.physics == AGILE_MHD_GLM ? 1 : 0) : 0);
   B->steps_done++;
   B->speeds_valid = true;
   return AGILE_OK;
@@ -1308,6 +1506,46 @@ agile_status agile_batch_get_state(agile_batch* B, int solve, int* level, int* i
   return s;
 }
 
+agile_status agile_batch_regrid_flags(agile_batch* B, int solve, const int* flags, int init, int* nr, int* nc) {
+  if (!B || !flags || solve < 0 || solve >= B->nsolve) return bfail(B, AGILE_EINVAL, "bad argument");
+  const int n = (int)B->meshes[solve]->blocks().size();
+  std::vector<int> f(flags, flags + n);
+  return batch_regrid(B, solve, f, init, nr, nc);
+}
+
+agile_status agile_batch_regrid(agile_batch* B, int solve, int init, int* nr, int* nc) {
+  if (!B || solve < 0 || solve >= B->nsolve) return bfail(B, AGILE_EINVAL, "bad argument");
+  if (nr) *nr = 0;
+  if (nc) *nc = 0;
+  const agile_config& c = B->cfgs[solve];
+  if (c.max_level == 1) return AGILE_OK;
+  agile_mesh view;
+  as_mesh_view(B, &view);
+  AuxArgs a = batch_aux(B, B->U[0]);
+  if (B->nghost) BCK(B, launch_ghosts(a, B->d_ghosts, B->nghost, B->stream));
+  int* d_vars = (int*)dalloc(&view, 9 * sizeof(int));
+  double* d_w = (double*)dalloc(&view, 9 * sizeof(double));
+  double* d_e = (double*)dalloc(&view, (size_t)B->nblk * sizeof(double));
+  if (!d_vars || !d_w || !d_e) return bfail(B, AGILE_ENOMEM, "device allocation failed");
+  BCK(B, cudaMemcpyAsync(d_vars, c.refine_vars, 9 * sizeof(int), cudaMemcpyHostToDevice, B->stream));
+  BCK(B, cudaMemcpyAsync(d_w, c.refine_weights, 9 * sizeof(double), cudaMemcpyHostToDevice, B->stream));
+  BCK(B, launch_estimate(a, d_vars, d_w, c.refine_nvars, c.lohner_eps, d_e, B->stream));
+  const int n = (int)B->meshes[solve]->blocks().size();
+  std::vector<double> emax(n);
+  BCK(B, cudaMemcpyAsync(emax.data(), d_e + B->offset[solve], n * sizeof(double), cudaMemcpyDeviceToHost, B->stream));
+  BCK(B, cudaStreamSynchronize(B->stream));
+  dfree_t(&view, d_vars);
+  dfree_t(&view, d_w);
+  dfree_t(&view, d_e);
+  std::vector<int> flags(n, 0);
+  const auto& keys = B->meshes[solve]->blocks();
+  for (int i = 0; i < n; ++i) {
+    if (emax[i] > c.refine_tol && keys[i].lev < c.max_level) flags[i] = 1;
+    else if (emax[i] < c.refine_tol * c.derefine_ratio && keys[i].lev > 1) flags[i] = -1;
+  }
+  return batch_regrid(B, solve, flags, init, nr, nc);
+}
+
 agile_status agile_batch_copy_solve(agile_batch* dst, int dst_solve, agile_batch* src, int src_solve) {
   if (!dst || !src || dst_solve < 0 || dst_solve >= dst->nsolve || src_solve < 0 || src_solve >= src->nsolve)
     return bfail(dst, AGILE_EINVAL, "bad argument");
@@ -1317,9 +1555,13 @@ agile_status agile_batch_copy_solve(agile_batch* dst, int dst_solve, agile_batch
   for (int d = 0; d < 3 && same; ++d)
     same = a.base_blocks[d] == b.base_blocks[d] && a.xmin[d] == b.xmin[d] && a.xmax[d] == b.xmax[d];
   for (int f = 0; f < 6 && same; ++f) same = a.bc[f] == b.bc[f];
-  const size_t n = dst->meshes[dst_solve]->blocks().size();
-  if (!same || n != src->meshes[src_solve]->blocks().size())
-    return bfail(dst, AGILE_EINVAL, "solves differ in layout, domain, boundaries or scheme");
+  const auto& kd = dst->meshes[dst_solve]->blocks();
+  const auto& ks = src->meshes[src_solve]->blocks();
+  const size_t n = kd.size();
+  if (same && n == ks.size())
+    for (size_t i = 0; i < n && same; ++i)
+      same = kd[i].lev == ks[i].lev && kd[i].x == ks[i].x && kd[i].y == ks[i].y && kd[i].z == ks[i].z;
+  if (!same) return bfail(dst, AGILE_EINVAL, "solves differ in blocks, domain, boundaries or scheme");
   agile_status s = batch_status(src);     // the source's pending work is complete and error-free
   if (s) return bfail(dst, s, "source batch: " + src->err);
   const size_t per = (size_t)dst->nt * NCELL * dst->rb;
