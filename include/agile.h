@@ -284,11 +284,12 @@ agile_status agile_batch_cfl_dt(agile_batch* batch, double* dt);
 /* State of one solve, as agile_get_state. Synchronises. */
 agile_status agile_batch_get_state(agile_batch* batch, int solve, int* level, int* ijk, double* cons);
 
-/* Refinement of one solve of a batch (Fig. 2 regrid, as agile_regrid / agile_regrid_flags for
- * a mesh): the Loehner estimate of its blocks after a ghost fill of the batch decides the
- * flags (agile_batch_regrid), or the caller gives one flag per block of the solve (-1
- * coarsen, 0 keep, 1 refine; agile_batch_regrid_flags). The batch's pools are laid out
- * again (the other solves' blocks are copied on the device), its descriptor tables rebuilt
+/* Refinement of the solves of a batch (Fig. 2 regrid, as agile_regrid / agile_regrid_flags
+ * for a mesh): the Loehner estimate after a ghost fill of the batch decides the flags of one
+ * solve, or of every solve at once with solve = -1 (agile_batch_regrid; the counts returned
+ * are summed over the solves), or the caller gives one flag per block of one solve (-1
+ * coarsen, 0 keep, 1 refine; agile_batch_regrid_flags). The batch's pools are laid out once
+ * more (the unchanged solves' blocks are copied on the device), its descriptor tables rebuilt
  * and the next step's CUDA graph captured again. init != 0 re-applies the initial condition
  * given to agile_batch_set_state to the blocks a refinement creates. Ghost fill of the
  * coarse-fine faces, the flux fix-up and their launches join every batched step from then

@@ -428,8 +428,9 @@ class Batch:
         self._ck(self.lib.agile_batch_get_state(self.ptr, solve, _iptr(lev), _iptr(ijk), _dptr(cons)))
         return lev, ijk, cons
 
-    def regrid(self, solve, init=False):
-        """Estimate-driven refinement of one solve; returns (n_refined, n_coarsened)."""
+    def regrid(self, solve=-1, init=False):
+        """Estimate-driven refinement of one solve (every solve for -1, with one new layout of
+        the pools); returns (n_refined, n_coarsened)."""
         nr, nc = C.c_int(), C.c_int()
         self._ck(self.lib.agile_batch_regrid(self.ptr, solve, int(init), C.byref(nr), C.byref(nc)))
         return nr.value, nc.value

@@ -1060,72 +1060,140 @@ agile_status batch_rebuild(agile_batch* B) {
   return AGILE_OK;
 }
 
-// Regrid one solve with the given flags: the other solves' blocks are copied to their new
-// places, the solve's new blocks come from the regrid kernel (copy / prolong / restrict),
-// then the tables are rebuilt; blocks a refinement creates get the initial condition again
-// when init is set.
-agile_status batch_regrid(agile_batch* B, int solve, const std::vector<int>& flags, int init, int* nr,
-                          int* nc) {
-  HostMesh* hm = B->meshes[solve];
-  RegridPlan plan = hm->plan(flags);
-  if (nr) *nr = plan.n_refined;
-  if (nc) *nc = plan.n_coarsened;
-  if (plan.n_refined == 0 && plan.n_coarsened == 0) return AGILE_OK;
+// Regrid the solves whose plan changes anything (plans[j] for solve j; unchanged solves are
+// copied to their new places), with one new layout of the pools and one rebuild of the
+// tables; blocks a refinement creates get the initial condition again when init is set.
+agile_status batch_apply_plans(agile_batch* B, std::vector<RegridPlan>& plans, int init) {
+  std::vector<char> changed(B->nsolve, 0);
+  bool any = false;
+  for (int j = 0; j < B->nsolve; ++j) {
+    changed[j] = plans[j].n_refined != 0 || plans[j].n_coarsened != 0;
+    any = any || changed[j];
+  }
+  if (!any) return AGILE_OK;
   agile_mesh view;
   as_mesh_view(B, &view);
   AuxArgs a = batch_aux(B, B->U[0]);
   if (B->nghost) BCK(B, launch_ghosts(a, B->d_ghosts, B->nghost, B->stream));
   const size_t per = (size_t)B->nt * NCELL * B->rb;
-  std::vector<int> count(B->nsolve);
-  for (int j = 0; j < B->nsolve; ++j) count[j] = (int)B->meshes[j]->blocks().size();
-  const int nnew_i = (int)plan.blocks.size();
-  long long total = 0;
+  std::vector<int> count(B->nsolve), ncount(B->nsolve);
   std::vector<long long> noff(B->nsolve);
+  long long total = 0;
   for (int j = 0; j < B->nsolve; ++j) {
+    count[j] = (int)B->meshes[j]->blocks().size();
+    ncount[j] = changed[j] ? (int)plans[j].blocks.size() : count[j];
     noff[j] = total;
-    total += j == solve ? nnew_i : count[j];
+    total += ncount[j];
   }
-  void* Unew = dalloc(&view, (size_t)total * per);
-  std::vector<RegridSrc> src = plan.src;
-  for (RegridSrc& r : src) {
-    const int nsrc = r.mode == 2 ? 8 : 1;
-    for (int q = 0; q < nsrc; ++q) {
-      if (r.src[q] < 0 || r.src[q] >= count[solve]) {
-        dfree(&view, Unew);
-        return bfail(B, AGILE_EINVAL, "regrid source out of range");
+  // one list of regrid sources over all changed solves, indices global in the old pool
+  std::vector<RegridSrc> src;
+  std::vector<int> first(B->nsolve, -1);
+  for (int j = 0; j < B->nsolve; ++j) {
+    if (!changed[j]) continue;
+    first[j] = (int)src.size();
+    for (RegridSrc r : plans[j].src) {
+      const int nsrc = r.mode == 2 ? 8 : 1;
+      for (int q = 0; q < nsrc; ++q) {
+        if (r.src[q] < 0 || r.src[q] >= count[j]) return bfail(B, AGILE_EINVAL, "regrid source out of range");
+        r.src[q] += B->offset[j];
       }
-      r.src[q] += B->offset[solve];
+      src.push_back(r);
     }
   }
+  void* Unew = dalloc(&view, (size_t)total * per);
   RegridSrc* d_src = (RegridSrc*)dalloc(&view, src.size() * sizeof(RegridSrc));
   if (!Unew || !d_src) return bfail(B, AGILE_ENOMEM, "device allocation failed");
-  for (int j = 0; j < B->nsolve; ++j)
-    if (j != solve && count[j])
+  BCK(B, cudaMemcpyAsync(d_src, src.data(), src.size() * sizeof(RegridSrc), cudaMemcpyHostToDevice, B->stream));
+  for (int j = 0; j < B->nsolve; ++j) {
+    if (changed[j]) {
+      BCK(B, launch_regrid(a, (char*)Unew + noff[j] * per, d_src + first[j], ncount[j], B->stream));
+    } else if (count[j]) {
       BCK(B, cudaMemcpyAsync((char*)Unew + noff[j] * per, (const char*)B->U[0] + (size_t)B->offset[j] * per,
                              (size_t)count[j] * per, cudaMemcpyDeviceToDevice, B->stream));
-  BCK(B, cudaMemcpyAsync(d_src, src.data(), src.size() * sizeof(RegridSrc), cudaMemcpyHostToDevice, B->stream));
-  BCK(B, launch_regrid(a, (char*)Unew + noff[solve] * per, d_src, nnew_i, B->stream));
+    }
+  }
   BCK(B, cudaStreamSynchronize(B->stream));
   dfree_t(&view, d_src);
   dfree(&view, B->U[0]);
   B->U[0] = Unew;
-  hm->apply(plan);
+  for (int j = 0; j < B->nsolve; ++j)
+    if (changed[j]) B->meshes[j]->apply(plans[j]);
   agile_status st = batch_rebuild(B);
   if (st) return st;
-  if (init && B->ics[solve]) {
+  for (int j = 0; j < B->nsolve && init; ++j) {
+    if (!changed[j] || !B->ics[j] || plans[j].created.empty()) continue;
     agile_mesh v2;
     as_mesh_view(B, &v2);
-    v2.mesh = hm;
-    v2.cfg = B->cfgs[solve];
-    v2.ic = B->ics[solve];
-    v2.ic_user = B->ic_users[solve];
+    v2.mesh = B->meshes[j];
+    v2.cfg = B->cfgs[j];
+    v2.ic = B->ics[j];
+    v2.ic_user = B->ic_users[j];
     v2.d_status = B->d_status;
-    v2.nblk = nnew_i;
-    st = apply_ic(&v2, (char*)B->U[0] + (size_t)B->offset[solve] * per, plan.created);
+    v2.nblk = ncount[j];
+    st = apply_ic(&v2, (char*)B->U[0] + (size_t)B->offset[j] * per, plans[j].created);
     v2.mesh = nullptr;
     if (st) return bfail(B, st, v2.err);
   }
   return batch_status(B);
+}
+
+// Regrid one solve with the given flags (the others unchanged).
+agile_status batch_regrid(agile_batch* B, int solve, const std::vector<int>& flags, int init, int* nr,
+                          int* nc) {
+  std::vector<RegridPlan> plans(B->nsolve);
+  plans[solve] = B->meshes[solve]->plan(flags);
+  if (nr) *nr = plans[solve].n_refined;
+  if (nc) *nc = plans[solve].n_coarsened;
+  return batch_apply_plans(B, plans, init);
+}
+
+// Loehner flags of every solve from one estimate over the batch (after a ghost fill).
+agile_status batch_flags(agile_batch* B, std::vector<std::vector<int>>* flags) {
+  agile_mesh view;
+  as_mesh_view(B, &view);
+  AuxArgs a = batch_aux(B, B->U[0]);
+  if (B->nghost) BCK(B, launch_ghosts(a, B->d_ghosts, B->nghost, B->stream));
+  const agile_config& c0 = B->cfgs[0];
+  int* d_vars = (int*)dalloc(&view, 9 * sizeof(int));
+  double* d_w = (double*)dalloc(&view, 9 * sizeof(double));
+  double* d_e = (double*)dalloc(&view, (size_t)B->nblk * sizeof(double));
+  if (!d_vars || !d_w || !d_e) return bfail(B, AGILE_ENOMEM, "device allocation failed");
+  std::vector<double> emax(B->nblk);
+  flags->assign(B->nsolve, std::vector<int>());
+  // the estimator's variables and weights may differ per solve: one pass per distinct set
+  std::vector<char> done(B->nsolve, 0);
+  for (int j = 0; j < B->nsolve; ++j) {
+    if (done[j]) continue;
+    const agile_config& c = B->cfgs[j];
+    BCK(B, cudaMemcpyAsync(d_vars, c.refine_vars, 9 * sizeof(int), cudaMemcpyHostToDevice, B->stream));
+    BCK(B, cudaMemcpyAsync(d_w, c.refine_weights, 9 * sizeof(double), cudaMemcpyHostToDevice, B->stream));
+    BCK(B, launch_estimate(a, d_vars, d_w, c.refine_nvars, c.lohner_eps, d_e, B->stream));
+    BCK(B, cudaMemcpyAsync(emax.data(), d_e, B->nblk * sizeof(double), cudaMemcpyDeviceToHost, B->stream));
+    BCK(B, cudaStreamSynchronize(B->stream));
+    for (int i = j; i < B->nsolve; ++i) {
+      const agile_config& ci = B->cfgs[i];
+      if (done[i] || ci.refine_nvars != c.refine_nvars || ci.lohner_eps != c.lohner_eps ||
+          memcmp(ci.refine_vars, c.refine_vars, sizeof(c.refine_vars)) != 0 ||
+          memcmp(ci.refine_weights, c.refine_weights, sizeof(c.refine_weights)) != 0)
+        continue;
+      done[i] = 1;
+      const auto& keys = B->meshes[i]->blocks();
+      const int n = (int)keys.size();
+      std::vector<int>& f = (*flags)[i];
+      f.assign(n, 0);
+      if (ci.max_level == 1) continue;
+      for (int q = 0; q < n; ++q) {
+        const double e = emax[B->offset[i] + q];
+        if (e > ci.refine_tol && keys[q].lev < ci.max_level) f[q] = 1;
+        else if (e < ci.refine_tol * ci.derefine_ratio && keys[q].lev > 1) f[q] = -1;
+      }
+    }
+  }
+  (void)c0;
+  dfree_t(&view, d_vars);
+  dfree_t(&view, d_w);
+  dfree_t(&view, d_e);
+  return AGILE_OK;
 }
 
 agile_status batch_status(agile_batch* B) {
@@ -1514,36 +1582,21 @@ agile_status agile_batch_regrid_flags(agile_batch* B, int solve, const int* flag
 }
 
 agile_status agile_batch_regrid(agile_batch* B, int solve, int init, int* nr, int* nc) {
-  if (!B || solve < 0 || solve >= B->nsolve) return bfail(B, AGILE_EINVAL, "bad argument");
-  if (nr) *nr = 0;
-  if (nc) *nc = 0;
-  const agile_config& c = B->cfgs[solve];
-  if (c.max_level == 1) return AGILE_OK;
-  agile_mesh view;
-  as_mesh_view(B, &view);
-  AuxArgs a = batch_aux(B, B->U[0]);
-  if (B->nghost) BCK(B, launch_ghosts(a, B->d_ghosts, B->nghost, B->stream));
-  int* d_vars = (int*)dalloc(&view, 9 * sizeof(int));
-  double* d_w = (double*)dalloc(&view, 9 * sizeof(double));
-  double* d_e = (double*)dalloc(&view, (size_t)B->nblk * sizeof(double));
-  if (!d_vars || !d_w || !d_e) return bfail(B, AGILE_ENOMEM, "device allocation failed");
-  BCK(B, cudaMemcpyAsync(d_vars, c.refine_vars, 9 * sizeof(int), cudaMemcpyHostToDevice, B->stream));
-  BCK(B, cudaMemcpyAsync(d_w, c.refine_weights, 9 * sizeof(double), cudaMemcpyHostToDevice, B->stream));
-  BCK(B, launch_estimate(a, d_vars, d_w, c.refine_nvars, c.lohner_eps, d_e, B->stream));
-  const int n = (int)B->meshes[solve]->blocks().size();
-  std::vector<double> emax(n);
-  BCK(B, cudaMemcpyAsync(emax.data(), d_e + B->offset[solve], n * sizeof(double), cudaMemcpyDeviceToHost, B->stream));
-  BCK(B, cudaStreamSynchronize(B->stream));
-  dfree_t(&view, d_vars);
-  dfree_t(&view, d_w);
-  dfree_t(&view, d_e);
-  std::vector<int> flags(n, 0);
-  const auto& keys = B->meshes[solve]->blocks();
-  for (int i = 0; i < n; ++i) {
-    if (emax[i] > c.refine_tol && keys[i].lev < c.max_level) flags[i] = 1;
-    else if (emax[i] < c.refine_tol * c.derefine_ratio && keys[i].lev > 1) flags[i] = -1;
+  if (!B || solve < -1 || solve >= B->nsolve) return bfail(B, AGILE_EINVAL, "bad argument");
+  std::vector<std::vector<int>> flags;
+  agile_status s = batch_flags(B, &flags);
+  if (s) return s;
+  std::vector<RegridPlan> plans(B->nsolve);
+  int tr = 0, tc = 0;
+  for (int j = 0; j < B->nsolve; ++j) {
+    if (solve >= 0 && j != solve) continue;
+    plans[j] = B->meshes[j]->plan(flags[j]);
+    tr += plans[j].n_refined;
+    tc += plans[j].n_coarsened;
   }
-  return batch_regrid(B, solve, flags, init, nr, nc);
+  if (nr) *nr = tr;
+  if (nc) *nc = tc;
+  return batch_apply_plans(B, plans, init);
 }
 
 agile_status agile_batch_copy_solve(agile_batch* dst, int dst_solve, agile_batch* src, int src_solve) {
