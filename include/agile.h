@@ -192,7 +192,10 @@ agile_status agile_get_state(agile_mesh* mesh, int* level, int* ijk, double* con
 agile_status agile_get_aux(agile_mesh* mesh, double* aux);
 
 /* Volume integrals of the conserved variables over the leaves (FP64 sums of
- * U * cell volume; the paper's high-cadence mass/energy log, Section 4.1). Synchronises. */
+ * U * cell volume; the paper's high-cadence mass/energy log, Section 4.1): per block on the
+ * device (FP32 pools: each thread's values added in FP32 with the exact error of every
+ * addition kept, then FP64), then a deterministic compensated (Neumaier) total over the
+ * blocks on the device; only the nvar totals come back. Synchronises. */
 agile_status agile_conserved_sums(agile_mesh* mesh, double* sums);
 
 /* Conserved sums like agile_conserved_sums, for callers that cannot allocate device memory

@@ -419,27 +419,55 @@ __global__ void pack_kernel(const R* __restrict__ U, double* __restrict__ cons, 
   }
 }
 
+// Per-block volume integrals of the conserved variables, all variables in one pass. FP64
+// pools add in FP64. FP32 pools add each thread's 16 values in FP32 with the exact error of
+// every addition kept (Knuth's TwoSum: s = a + b, e = (a - (s - (s - a))) + (b - (s - a)),
+// so s + e = a + b exactly), an FP32 pair whose sum carries about 48 significant bits, then
+// in FP64: the FP64 units of the GPU add 64 times slower than its FP32 units.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) sums_kernel(const R* __restrict__ U, const BlockDesc* __restrict__ bd,
                                                     double* __restrict__ part, int nv, int na) {
   const int b = blockIdx.x;
   const int nt = nv + na;
   const double dv = bd[b].dx[0] * bd[b].dx[1] * bd[b].dx[2];
-  __shared__ double red[8];
+  __shared__ double red[8][16];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int v = 0; v < nv; ++v) {
     const R* p = U + ((size_t)b * nt + v) * NCELL;
-    double s = 0.0;
-    for (int c = threadIdx.x; c < NCELL; c += 256) s += (double)p[c];
+    double s;
+    if constexpr (sizeof(R) == 4) {
+      const float4* q = reinterpret_cast<const float4*>(p);
+      float hi = 0.0f, lo = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float4 x = q[threadIdx.x + 256 * i];
+        two_sum_acc(hi, lo, x.x);
+        two_sum_acc(hi, lo, x.y);
+        two_sum_acc(hi, lo, x.z);
+        two_sum_acc(hi, lo, x.w);
+      }
+      s = (double)hi + (double)lo;
+    } else {
+      s = 0.0;
+      for (int c = threadIdx.x; c < NCELL; c += 256) s += (double)p[c];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int i = 0; i < 8; ++i) t += red[i];
-      part[(size_t)b * nv + v] = t * dv;
-    }
-    __syncthreads();
+    if (lane == 0) red[w][v] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += red[i][threadIdx.x];
+    part[(size_t)b * nv + threadIdx.x] = t * dv;
   }
 }
 

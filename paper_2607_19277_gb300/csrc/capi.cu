@@ -17,6 +17,9 @@
 
 using namespace agile;
 
+// Deterministic compensated total of per-block sums (defined with the conserved-sum calls).
+__global__ void sums_total_kernel(const double* part, int nblk, int nv, double* totals);
+
 struct agile_mesh {
   agile_config cfg;
   cudaStream_t stream = nullptr;
@@ -698,28 +701,18 @@ agile_status agile_get_aux(agile_mesh* m, double* aux) {
 
 agile_status agile_conserved_sums(agile_mesh* m, double* sums) {
   if (!m || !sums) return fail(m, AGILE_EINVAL, "null argument");
-  std::vector<double> part((size_t)m->nblk * m->nv);
-  double* d = (double*)dalloc(m, part.size() * sizeof(double));
+  const size_t np = (size_t)m->nblk * m->nv;
+  double* d = (double*)dalloc(m, (np + 16) * sizeof(double));
   if (!d) return fail(m, AGILE_ENOMEM, "device allocation failed");
   AuxArgs a = aux_args(m, m->U[0]);
   CK(m, launch_sums(a, d, m->stream));
-  m->total_launches++;
-  CK(m, cudaMemcpyAsync(part.data(), d, part.size() * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  sums_total_kernel<<<1, 256, 0, m->stream>>>(d, m->nblk, m->nv, d + np);
+  CK(m, cudaGetLastError());
+  m->total_launches += 2;
+  CK(m, cudaMemcpyAsync(sums, d + np, m->nv * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
   agile_status s = check_status(m);
   dfree_t(m, d);
-  if (s) return s;
-  for (int v = 0; v < m->nv; ++v) {
-    double sum = 0.0, comp = 0.0;   // Neumaier compensated sum over blocks
-    for (int b = 0; b < m->nblk; ++b) {
-      const double x = part[(size_t)b * m->nv + v];
-      const double t = sum + x;
-      if (fabs(sum) >= fabs(x)) comp += (sum - t) + x;
-      else comp += (x - t) + sum;
-      sum = t;
-    }
-    sums[v] = sum + comp;
-  }
-  return AGILE_OK;
+  return s;
 }
 
 agile_status agile_get_halo(agile_mesh* m, size_t block, double* out) {
@@ -810,23 +803,43 @@ cudaError_t noalloc_scratch(double** out) {
   return cudaSuccess;
 }
 
-// Totals over blocks in block order with Neumaier compensation, one thread per variable:
-// the same order and operations as the host-side sum of agile_conserved_sums.
-__global__ void noalloc_total_kernel(const double* part, int nblk, int nv, double* totals) {
-  const int v = threadIdx.x;
-  if (v >= nv) return;
-  double sum = 0.0, comp = 0.0;
-  for (int b = 0; b < nblk; ++b) {
-    const double x = part[(size_t)b * nv + v];
-    const double t = __dadd_rn(sum, x);
-    if (fabs(sum) >= fabs(x)) comp = __dadd_rn(comp, __dadd_rn(__dsub_rn(sum, t), x));
-    else comp = __dadd_rn(comp, __dadd_rn(__dsub_rn(x, t), sum));
-    sum = t;
-  }
-  totals[v] = __dadd_rn(sum, comp);
-}
-
 }  // namespace
+
+// Totals over the per-block sums: thread i of one CTA of 256 sums blocks i, i + 256, ... with
+// Neumaier compensation, then the 256 (sum, compensation) pairs merge in a fixed tree whose
+// every addition keeps its exact error (TwoSum). Deterministic; agile_conserved_sums and
+// agile_conserved_sums_noalloc both use it, so their results agree bit for bit.
+__global__ void __launch_bounds__(256) sums_total_kernel(const double* part, int nblk, int nv,
+                                                         double* totals) {
+  __shared__ double ss[256], sc[256];
+  const int t = threadIdx.x;
+  for (int v = 0; v < nv; ++v) {
+    double sum = 0.0, comp = 0.0;
+    for (int b = t; b < nblk; b += 256) {
+      const double x = part[(size_t)b * nv + v];
+      const double u = __dadd_rn(sum, x);
+      if (fabs(sum) >= fabs(x)) comp = __dadd_rn(comp, __dadd_rn(__dsub_rn(sum, u), x));
+      else comp = __dadd_rn(comp, __dadd_rn(__dsub_rn(x, u), sum));
+      sum = u;
+    }
+    ss[t] = sum;
+    sc[t] = comp;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if (t < w) {
+        const double x = ss[t], y = ss[t + w];
+        const double u = __dadd_rn(x, y);
+        const double yy = __dsub_rn(u, x);
+        const double e = __dadd_rn(__dsub_rn(x, __dsub_rn(u, yy)), __dsub_rn(y, yy));
+        ss[t] = u;
+        sc[t] = __dadd_rn(__dadd_rn(sc[t], sc[t + w]), e);
+      }
+      __syncthreads();
+    }
+    if (t == 0) totals[v] = __dadd_rn(ss[0], sc[0]);
+    __syncthreads();
+  }
+}
 
 extern "C" agile_status agile_conserved_sums_noalloc(agile_mesh* m, double* sums) {
   if (!m || !sums) return fail(m, AGILE_EINVAL, "null argument");
@@ -839,7 +852,7 @@ extern "C" agile_status agile_conserved_sums_noalloc(agile_mesh* m, double* sums
   CK(m, noalloc_scratch(&scratch));
   AuxArgs a = aux_args(m, m->U[0]);
   CK(m, launch_sums(a, scratch, m->stream));
-  noalloc_total_kernel<<<1, 32, 0, m->stream>>>(scratch, m->nblk, m->nv, scratch + NOALLOC_TOTALS);
+  sums_total_kernel<<<1, 256, 0, m->stream>>>(scratch, m->nblk, m->nv, scratch + NOALLOC_TOTALS);
   CK(m, cudaGetLastError());
   m->total_launches += 2;
   CK(m, cudaMemcpyAsync(sums, scratch + NOALLOC_TOTALS, m->nv * sizeof(double), cudaMemcpyDeviceToHost,
