@@ -252,19 +252,21 @@ agile_status agile_kernel_timing(agile_mesh* mesh, double* stage_ms, long long* 
                                  long long* total_launches);
 
 /* ---------------------------------------------------------------------------------------
- * Batched independent solves. Several uniform-grid problems that share one scheme
- * (physics, limiter, flux, rk, real_bytes, gamma, cfl, glm_alpha) but differ in size, box
- * and boundaries advance together: one pool holds the blocks of all solves, every RK stage
- * is one persistent launch of the update kernel over all of them (each block with its
- * solve's CFL dt and GLM speed), and from the second step on a whole step is replayed from
- * a captured CUDA graph (dt stays on the device). Each solve's result is the same as when
+ * Batched independent solves. Several problems that share one scheme (physics, limiter,
+ * flux, rk, real_bytes, gamma, cfl, glm_alpha, eos) but differ in size, box, boundaries and
+ * refinement advance together: one pool holds the blocks of all levels of all solves, every
+ * RK stage is one persistent launch of the update kernel over all of them (each block with
+ * its solve's CFL dt and GLM speed), the coarse-fine ghost fill and flux fix-up of all
+ * solves share one launch each, and from the second step after a (re)layout a whole step is
+ * replayed from a captured CUDA graph (dt stays on the device). Each solve's result is the same as when
  * it runs alone as an agile_mesh (same kernels, same per-block arithmetic).
  * The paper runs one problem per job; batching is this library's serving form of the
  * same per-block update (macro-kernel of Section 2.1.3, time loop of Fig. 2 per solve).
  * --------------------------------------------------------------------------------------- */
 typedef struct agile_batch agile_batch;
 
-/* Create nsolve solves from cfgs[nsolve] (max_level must be 1). alloc as for meshes;
+/* Create nsolve solves from cfgs[nsolve], each with its level-1 blocks (refine with
+ * agile_batch_regrid). alloc as for meshes;
  * cuda_stream NULL makes the batch create its own non-blocking stream (graphs cannot be
  * captured on the legacy default stream). Errors: AGILE_EINVAL, AGILE_ENOMEM, AGILE_ECUDA. */
 agile_status agile_batch_create(const agile_config* cfgs, int nsolve, const agile_allocator* alloc,

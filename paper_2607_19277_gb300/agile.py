@@ -366,8 +366,9 @@ def _ic_callback(ic, nvar):
 
 
 class Batch:
-    """Independent uniform-grid solves advanced together (one launch per RK stage over all
-    of them, each step replayed from a CUDA graph)."""
+    """Independent solves advanced together (one launch per RK stage over the blocks of all
+    levels of all of them, each step replayed from a CUDA graph); refined per solve or all
+    at once with regrid / regrid_flags."""
 
     def __init__(self, cfgs, stream=None, use_torch_allocator=True):
         import torch

@@ -861,9 +861,10 @@ extern "C" agile_status agile_conserved_sums_noalloc(agile_mesh* m, double* sums
 }
 
 // ----------------------------------------------------------------------------------------
-// Batched independent solves (uniform grids): one pool holds the blocks of every solve, the
+// Batched independent solves: one pool holds the blocks of all levels of every solve, the
 // stage kernel updates all of them in one persistent launch per RK stage with each solve's
-// own CFL dt and GLM speed, and a whole step is replayed from one captured CUDA graph.
+// own CFL dt and GLM speed, ghost fill and flux fix-up of all solves share launches, and a
+// whole step is replayed from one captured CUDA graph.
 // ----------------------------------------------------------------------------------------
 struct agile_batch {
   agile_config cfg;                 // shared scheme

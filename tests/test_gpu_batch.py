@@ -79,7 +79,7 @@ def test_batched_solve_matches_oracle_fp64():
 
 @pytest.mark.parametrize("physics", ["srhd", "mhd"])
 def test_autotune_keeps_results_and_picks_a_shape(physics):
-    """The autotuner times four launch shapes without touching the solution; the tuned
+    """The autotuner times six launch shapes without touching the solution; the tuned
     batch (re-captured graph) gives the same results bit for bit."""
     sides = [32, 48, 64]
     cfgs = [_cfg(s, 4, physics) for s in sides]
