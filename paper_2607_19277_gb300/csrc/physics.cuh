@@ -54,6 +54,26 @@ __device__ __forceinline__ float rsqrt_(float a) { return sqrtf(a); }
 __device__ __forceinline__ double rsqrt_(double a) { return sqrt(a); }
 __device__ __forceinline__ float rsign(float a) { return copysignf(1.0f, a); }
 __device__ __forceinline__ double rsign(double a) { return copysign(1.0, a); }
+// Reciprocal and quotient in the stencil precision. FP32: the build's fast single-precision
+// divide. FP64: the hardware reciprocal estimate (PTX rcp.approx.ftz.f64) refined by one
+// third-order Newton-Raphson step: with e = 1 - s r0, r1 = r0 (1 + e + e^2) is the series of
+// r0 / (s r0) = r0 / (1 - e) truncated after e^2, so its relative error is e^3, far below
+// 2^-53 for the estimate's error. The product a r1 lies within 1 ulp of the rounded quotient
+// a / s (4 FP64 operations against about twice as many for the IEEE divide, which the FP64
+// units of this GPU make the costly part of the stencil). Valid for normal, finite s with
+// |s| < 2^1022; every divisor below is a density, a sum of two same-sign slopes, a signal-
+// speed interval or a Newton derivative (a zero or non-finite one yields NaN, as the IEEE
+// quotient's use would).
+__device__ __forceinline__ double rcp64(double s) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(s));
+  const double e = fma(-s, r, 1.0);
+  return fma(r, fma(e, e, e), r);
+}
+__device__ __forceinline__ float rrcp(float s) { return 1.0f / s; }
+__device__ __forceinline__ double rrcp(double s) { return rcp64(s); }
+__device__ __forceinline__ float rdiv(float a, float s) { return a / s; }
+__device__ __forceinline__ double rdiv(double a, double s) { return a * rcp64(s); }
 template <typename R> __device__ __forceinline__ R rtiny();
 template <> __device__ __forceinline__ float rtiny<float>() { return 1e-30f; }
 template <> __device__ __forceinline__ double rtiny<double>() { return 1e-300; }
@@ -70,7 +90,7 @@ __device__ __forceinline__ R half_slope(R a, R b) {
     return (R(0.25) * (rsign(a) + rsign(b))) * rmin(rabs(a), rabs(b));
   } else {
     const R ab = a * b;
-    const R q = ab / (a + b);
+    const R q = rdiv(ab, a + b);
     return ab > R(0) ? q : R(0);
   }
 }
@@ -92,7 +112,7 @@ struct HdPhys {
                                                    int& st) {
     const R g1 = pp.g1;
     const R rho = u[0];
-    const R ir = R(1) / rho;
+    const R ir = rrcp(rho);
     const R vx = u[1] * ir, vy = u[2] * ir, vz = u[3] * ir;
     p[0] = rho;
     p[1] = vx;
@@ -124,7 +144,7 @@ struct HdPhys {
 
   template <int D>
   __device__ static __forceinline__ void lambdas(const R* p, R& lm, R& lp, const PhysParamsT<R>& pp) {
-    const R c = rsqrt_(pp.gamma * p[4] / p[0]);
+    const R c = rsqrt_(rdiv(pp.gamma * p[4], p[0]));
     lm = p[1 + D] - c;
     lp = p[1 + D] + c;
   }
@@ -150,7 +170,7 @@ struct MhdPhys {
                                                    int& st) {
     const R g1 = pp.g1;
     const R rho = u[0];
-    const R ir = R(1) / rho;
+    const R ir = rrcp(rho);
     const R vx = u[1] * ir, vy = u[2] * ir, vz = u[3] * ir;
     const R b2 = u[5] * u[5] + u[6] * u[6] + u[7] * u[7];
     p[0] = rho;
@@ -199,7 +219,7 @@ struct MhdPhys {
 
   template <int D>
   __device__ static __forceinline__ void lambdas(const R* p, R& lm, R& lp, const PhysParamsT<R>& pp) {
-    const R ir = R(1) / p[0];
+    const R ir = rrcp(p[0]);
     const R a2 = pp.gamma * p[4] * ir;
     const R b2 = (p[5] * p[5] + p[6] * p[6] + p[7] * p[7]) * ir;
     const R bd2 = p[5 + D] * p[5 + D] * ir;
@@ -241,8 +261,8 @@ struct SrhdEos {
   // squared sound speed: gamma theta / h, or theta (5h - 8 theta) / (3h (h - theta)) for the
   // approximate Synge gas (the isentropic derivative of its enthalpy)
   __device__ static __forceinline__ R sound_speed2(R theta, R h, const PhysParamsT<R>& pp) {
-    if constexpr (EOS == EOS_SYNGE) return theta * (R(5) * h - R(8) * theta) / (R(3) * h * (h - theta));
-    else return pp.gamma * theta / h;
+    if constexpr (EOS == EOS_SYNGE) return rdiv(theta * (R(5) * h - R(8) * theta), R(3) * h * (h - theta));
+    else return rdiv(pp.gamma * theta, h);
   }
 };
 
@@ -316,7 +336,7 @@ struct SrhdPhysE {
     const double s2 = mx * mx + my * my + mz * mz;
     const double E = (double)u[4] + D;
     double lo = E, hi = (EOS == EOS_SYNGE ? 4.0 / 3.0 : g) * E;
-    const double iD = EOS == EOS_SYNGE ? 1.0 / D : 0.0;
+    const double iD = EOS == EOS_SYNGE ? rcp64(D) : 0.0;
     double xi = (double)aux[0];
     if (!(xi > lo && xi < hi)) xi = 0.5 * (lo + hi);
     if constexpr (sizeof(R) == 4) xi = seed_f32(xi, D, s2, E, lo, hi, pp);
@@ -326,7 +346,7 @@ struct SrhdPhysE {
     constexpr double tol = sizeof(R) == 4 ? 1e-6 : 1e-14;
     bool ok = false;
     for (int it = 0; it < 50; ++it) {
-      const double ixi = 1.0 / xi;
+      const double ixi = rcp64(xi);
       const double w = s2 * ixi * ixi;          // v^2
       const double ig2 = 1.0 - w;               // 1 / Gamma^2
       const double lor = rsqrt(ig2);            // Gamma
@@ -348,14 +368,14 @@ struct SrhdPhysE {
       const double f = xi - pr - E;
       const double df = 1.0 - dp;
       if (f < 0.0) lo = xi; else hi = xi;
-      double xn = xi - f / df;
+      double xn = xi - f * rcp64(df);
       if (!(xn >= lo && xn <= hi)) xn = 0.5 * (lo + hi);
       const bool conv = fabs(xn - xi) <= tol * xn;
       xi = xn;
       if (conv) { ok = true; break; }
     }
     if (!ok) st |= ST_ENOCONV;
-    const double ixi = 1.0 / xi;
+    const double ixi = rcp64(xi);
     const double w = s2 * ixi * ixi;
     const double ig2 = 1.0 - w;
     const double lor = rsqrt(ig2);
@@ -380,14 +400,14 @@ struct SrhdPhysE {
   }
 
   __device__ static __forceinline__ R enthalpy(R rho, R pres, const PhysParamsT<R>& pp) {
-    return Eos::enthalpy(pres / rho, pp);
+    return Eos::enthalpy(rdiv(pres, rho), pp);
   }
 
   __device__ static __forceinline__ void prim2cons(const R* p, R* u, const PhysParamsT<R>& pp) {
     const R lor = rsqrt_(R(1) + p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
     R h;
-    if constexpr (EOS == EOS_SYNGE) h = Eos::enthalpy(p[4] / p[0], pp);
-    else h = R(1) + pp.gg1 * p[4] / p[0];
+    if constexpr (EOS == EOS_SYNGE) h = Eos::enthalpy(rdiv(p[4], p[0]), pp);
+    else h = R(1) + rdiv(pp.gg1 * p[4], p[0]);
     const R lr = lor * p[0];
     const R lrh = lr * h;
     u[0] = lr;
@@ -400,7 +420,7 @@ struct SrhdPhysE {
   template <int D>
   __device__ static __forceinline__ void flux(const R* p, const R* u, R* f, const PhysParamsT<R>&) {
     const R lor = rsqrt_(R(1) + p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
-    const R vd = p[1 + D] / lor;
+    const R vd = rdiv(p[1 + D], lor);
     f[0] = u[0] * vd;
     f[1] = u[1] * vd;
     f[2] = u[2] * vd;
@@ -412,21 +432,22 @@ struct SrhdPhysE {
   template <int D>
   __device__ static __forceinline__ void lambdas(const R* p, R& lm, R& lp, const PhysParamsT<R>& pp) {
     const R lor2 = R(1) + p[1] * p[1] + p[2] * p[2] + p[3] * p[3];
-    const R v2 = R(1) - R(1) / lor2;
-    const R vd = p[1 + D] / rsqrt_(lor2);
+    const R v2 = R(1) - rrcp(lor2);
+    const R vd = rdiv(p[1 + D], rsqrt_(lor2));
     R cs2;
     if constexpr (EOS == EOS_SYNGE) {
-      const R th = p[4] / p[0];
+      const R th = rdiv(p[4], p[0]);
       cs2 = Eos::sound_speed2(th, Eos::enthalpy(th, pp), pp);
     } else {
-      const R h = R(1) + pp.gg1 * p[4] / p[0];
-      cs2 = pp.gamma * p[4] / (p[0] * h);
+      const R h = R(1) + rdiv(pp.gg1 * p[4], p[0]);
+      cs2 = rdiv(pp.gamma * p[4], p[0] * h);
     }
     const R cs = rsqrt_(cs2);
     const R den = R(1) - v2 * cs2;
     const R root = cs * rsqrt_(rmax((R(1) - v2) * (R(1) - v2 * cs2 - vd * vd * (R(1) - cs2)), R(0)));
-    lm = (vd * (R(1) - cs2) - root) / den;
-    lp = (vd * (R(1) - cs2) + root) / den;
+    const R iden = rrcp(den);
+    lm = (vd * (R(1) - cs2) - root) * iden;
+    lp = (vd * (R(1) - cs2) + root) * iden;
   }
 
   template <int D>
@@ -458,7 +479,7 @@ struct FfhdPhys {
   __device__ static __forceinline__ void cons2prim(const R* u, R* p, R*, const PhysParamsT<R>& pp,
                                                    int& st) {
     const R rho = u[0];
-    const R v = u[1] * (R(1) / rho);
+    const R v = u[1] * rrcp(rho);
     p[0] = rho;
     p[1] = v;
     p[2] = pp.g1 * (u[2] - R(0.5) * rho * v * v);
@@ -492,7 +513,7 @@ struct FfhdPhys {
 
   template <int D>
   __device__ static __forceinline__ void lambdas(const R* p, R& lm, R& lp, const PhysParamsT<R>& pp) {
-    const R c = rsqrt_(pp.gamma * p[2] / p[0]);
+    const R c = rsqrt_(rdiv(pp.gamma * p[2], p[0]));
     const R b = p[3 + D];
     const R a = p[1] * b;
     const R w = c * rabs(b);
@@ -533,8 +554,8 @@ __device__ __forceinline__ void riemann(R* pl, R* pr, R* f, const PhysParamsT<R>
     const R sl = rmin(lml, lmr), sr = rmax(lpl, lpr);
     const R rl = pl[0], rr = pr[0], vl = pl[1 + D], vr = pr[1 + D];
     const R ml = rl * (sl - vl), mr = rr * (sr - vr);
-    const R ss = (pr[4] - pl[4] + ml * vl - mr * vr) / (ml - mr);
-    const R fl_ = ml / (sl - ss), fr_ = mr / (sr - ss);
+    const R ss = rdiv(pr[4] - pl[4] + ml * vl - mr * vr, ml - mr);
+    const R fl_ = rdiv(ml, sl - ss), fr_ = rdiv(mr, sr - ss);
     R usl[NV], usr[NV];
     usl[0] = fl_;
     usr[0] = fr_;
@@ -545,8 +566,8 @@ __device__ __forceinline__ void riemann(R* pl, R* pr, R* f, const PhysParamsT<R>
     }
     usl[1 + D] = fl_ * ss;
     usr[1 + D] = fr_ * ss;
-    usl[4] = fl_ * (ul[4] / rl + (ss - vl) * (ss + pl[4] / ml));
-    usr[4] = fr_ * (ur[4] / rr + (ss - vr) * (ss + pr[4] / mr));
+    usl[4] = fl_ * (rdiv(ul[4], rl) + (ss - vl) * (ss + rdiv(pl[4], ml)));
+    usr[4] = fr_ * (rdiv(ur[4], rr) + (ss - vr) * (ss + rdiv(pr[4], mr)));
     const bool left = sl >= R(0), star_l = ss >= R(0), star_r = sr > R(0);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -564,7 +585,7 @@ __device__ __forceinline__ void riemann(R* pl, R* pr, R* f, const PhysParamsT<R>
   } else {
     const R sl = rmin(rmin(lml, lmr), R(0));
     const R sr = rmax(rmax(lpl, lpr), R(0));
-    const R inv = R(1) / (sr - sl);
+    const R inv = rrcp(sr - sl);
     const R wl = sr * inv, wr = sl * inv, wd = sl * sr * inv;
 #pragma unroll
     for (int v = 0; v < NV; ++v) f[v] = wl * fl[v] - wr * fr[v] + wd * (ur[v] - ul[v]);
