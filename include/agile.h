@@ -342,6 +342,17 @@ const char* agile_batch_last_error(const agile_batch* batch);
  * stays usable. Synchronises `stream` (a cudaStream_t, NULL for the default stream). */
 agile_status agile_selftest_bounded_wait(void* stream, unsigned int limit, int* timed_out);
 
+/* Accuracy check of the FP64 stencil's quotient: every FP64 division of the stencil
+ * (limiter, primitive recovery, signal speeds, HLL/HLLC weights, the SRHD Newton iteration)
+ * is a * r with r the hardware reciprocal estimate of s refined by one third-order
+ * Newton-Raphson step. Evaluates that quotient and the IEEE quotient a / s on the device for
+ * the n pairs of the HOST arrays s and a (1 <= n <= 2^26; every |s| normal and below 2^1022,
+ * every a finite, else AGILE_EINVAL) and returns the largest distance in units of the last
+ * place of the IEEE result (*max_ulps, 0 when all agree) and the largest relative difference
+ * (*max_rel). Synchronises `stream` (a cudaStream_t, NULL for the default stream). */
+agile_status agile_selftest_rcp64(const double* s, const double* a, size_t n, void* stream, double* max_ulps,
+                                  double* max_rel);
+
 /* Message of the last failed call on this mesh (static storage owned by the mesh). */
 const char* agile_last_error(const agile_mesh* mesh);
 

@@ -33,7 +33,7 @@ EXPORTS = ["agile_mesh_create", "agile_mesh_destroy", "agile_set_state", "agile_
            "agile_get_state", "agile_get_aux", "agile_conserved_sums",
            "agile_conserved_sums_noalloc", "agile_set_cooling", "agile_estimate",
            "agile_get_halo", "agile_sync", "agile_set_kernel_timing", "agile_kernel_timing",
-           "agile_selftest_bounded_wait", "agile_last_error", "agile_version",
+           "agile_selftest_bounded_wait", "agile_selftest_rcp64", "agile_last_error", "agile_version",
            "agile_batch_create", "agile_batch_destroy", "agile_batch_layout",
            "agile_batch_set_state", "agile_batch_step", "agile_batch_cfl_dt", "agile_batch_copy_solve",
            "agile_batch_autotune", "agile_batch_regrid", "agile_batch_regrid_flags",
@@ -103,6 +103,7 @@ def load(path: str = LIB_PATH):
         "agile_set_kernel_timing": (C.c_int, [P, C.c_int]),
         "agile_kernel_timing": (C.c_int, [P, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
         "agile_selftest_bounded_wait": (C.c_int, [P, C.c_uint, ip]),
+        "agile_selftest_rcp64": (C.c_int, [dp, dp, C.c_size_t, P, dp, dp]),
         "agile_last_error": (C.c_char_p, [P]),
         "agile_version": (C.c_char_p, []),
         "agile_batch_create": (C.c_int, [C.POINTER(agile_config), C.c_int, C.POINTER(agile_allocator), P, C.POINTER(P)]),
@@ -189,6 +190,21 @@ class _TorchAllocator:
         self.c_alloc = ALLOC_FN(alloc)
         self.c_free = FREE_FN(free)
         self.struct = agile_allocator(self.c_alloc, self.c_free, None)
+
+
+def check_rcp64(s, a):
+    """Largest distance, in units of the last place of the IEEE quotient, and largest relative
+    difference between the FP64 stencil's quotient of a by s (Newton-refined reciprocal
+    estimate) and a / s, both formed on the device (agile_selftest_rcp64)."""
+    lib = load()
+    s = np.ascontiguousarray(s, dtype=np.float64).ravel()
+    a = np.ascontiguousarray(a, dtype=np.float64).ravel()
+    if s.shape != a.shape:
+        raise ValueError("s and a differ in size")
+    mu, mr = C.c_double(-1.0), C.c_double(-1.0)
+    st = lib.agile_selftest_rcp64(_dptr(s), _dptr(a), s.size, None, C.byref(mu), C.byref(mr))
+    _check(lib, None, st)
+    return mu.value, mr.value
 
 
 def _check(lib, mesh_ptr, st):

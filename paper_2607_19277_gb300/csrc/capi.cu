@@ -2,10 +2,14 @@
 // (paper Fig. 2), regrid (Figs. 1-2), state transfer and diagnostics.
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <float.h>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <cmath>
+#include <cstring>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -331,9 +335,61 @@ __global__ void selftest_wait_kernel(uint32_t limit, int* out) {
     out[0] = mbar_wait(&bar, 0, limit) ? 0 : 1;
   }
 }
+
+// Accuracy of the FP64 stencil quotient rdiv(a, s) against the IEEE quotient: per element the
+// distance in units of the last place of the IEEE result (measured towards rdiv's result),
+// maxima over all elements as non-negative doubles through their ordered bit patterns.
+__global__ void selftest_rcp64_kernel(const double* __restrict__ s, const double* __restrict__ a, size_t n,
+                                      unsigned long long* out) {
+  double mu = 0.0, mr = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double q0 = __ddiv_rn(a[i], s[i]);
+    const double q1 = rdiv(a[i], s[i]);
+    if (q1 != q0) {
+      const double step = fabs(nextafter(q0, q1) - q0);
+      mu = fmax(mu, fabs(q1 - q0) / step);
+      mr = fmax(mr, fabs(q1 - q0) / fabs(q0));
+    }
+  }
+  atomicMax(out, (unsigned long long)__double_as_longlong(mu));
+  atomicMax(out + 1, (unsigned long long)__double_as_longlong(mr));
+}
 }  // namespace
 
 extern "C" {
+
+agile_status agile_selftest_rcp64(const double* s, const double* a, size_t n, void* stream, double* max_ulps,
+                                  double* max_rel) {
+  if (!s || !a || !max_ulps || !max_rel || n == 0 || n > ((size_t)1 << 26)) return AGILE_EINVAL;
+  for (size_t i = 0; i < n; ++i) {
+    const double v = std::fabs(s[i]);
+    if (!(v >= DBL_MIN && v < std::ldexp(1.0, 1022)) || !std::isfinite(a[i])) return AGILE_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  double *ds = nullptr, *da = nullptr;
+  unsigned long long* dout = nullptr;
+  cudaError_t e = cudaMallocAsync(&ds, n * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&da, n * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&dout, 2 * sizeof(unsigned long long), st);
+  unsigned long long h[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ds, s, n * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(da, a, n * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dout, 0, 2 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) {
+    const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, 4096);
+    selftest_rcp64_kernel<<<grid, 256, 0, st>>>(ds, da, n, dout);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, dout, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (ds) cudaFreeAsync(ds, st);
+  if (da) cudaFreeAsync(da, st);
+  if (dout) cudaFreeAsync(dout, st);
+  if (e != cudaSuccess) return AGILE_ECUDA;
+  std::memcpy(max_ulps, &h[0], sizeof(double));
+  std::memcpy(max_rel, &h[1], sizeof(double));
+  return AGILE_OK;
+}
 
 const char* agile_version(void) { return "agile-gb300 1.0 (sm_103a)"; }
 

@@ -93,3 +93,16 @@ def test_binding_refuses_missing_library(tmp_path):
             agile.load(str(tmp_path / "missing.so"))
     finally:
         agile._lib = saved
+
+
+@pytest.mark.parametrize("bad", [0.0, 5e-324, float("inf"), float("nan"), 2.0 ** 1022])
+def test_rcp64_selftest_rejects_divisors_outside_its_range(lib, bad):
+    """The quotient check validates its divisors on the host (zero, subnormal, infinite, NaN,
+    or |s| >= 2^1022 are outside the documented range) before any device work."""
+    import numpy as np
+    from paper_2607_19277_gb300 import agile
+    s = np.array([1.0, bad, 3.0])
+    a = np.ones(3)
+    with pytest.raises(agile.AgileError) as e:
+        agile.check_rcp64(s, a)
+    assert e.value.status == 1
