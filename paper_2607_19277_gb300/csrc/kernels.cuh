@@ -264,7 +264,7 @@ struct StageSmem {
   static constexpr size_t raw = bars;                                  // [4][NT][256]
   static constexpr size_t prim = raw + sizeof(R) * 4 * NT * 256;       // [3][NT][256]
   static constexpr size_t cur = prim + sizeof(R) * 3 * NT * 256;       // [NV][20][20]
-  static constexpr size_t fx = cur + sizeof(R) * NV * 400;             // [NV][16][17]
+  static constexpr size_t fx = cur + sizeof(R) * NV * 400;             // [NV][16 x 16 + 16]
   static constexpr size_t fy = fx + sizeof(R) * NV * 272;              // [NV][17][16]
   static constexpr size_t halo = fy + sizeof(R) * NV * 272;            // [NT][128] raw halo
   static constexpr size_t total = halo + sizeof(R) * NT * 128;
@@ -305,6 +305,13 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   const int tx = t & 15, ty = t >> 4;
   const int warp = t >> 5;
   const int cell2 = ty * 16 + tx;
+  // Faces of the x/y pass: column fc of row fr, the two half-warps of warp w on rows
+  // (w & 3) + 8 (w >> 2) and 4 rows further, which the 20-wide plane rows put 16 banks apart
+  // (the four-cell stencil loads are free of bank conflicts).
+  const int fc = tx;
+  const int fr = (warp & 3) + 8 * (warp >> 2) + 4 * ((t >> 4) & 1);
+  // x-face fluxes: [NV][16 rows][16] for faces 0..15 of each row, then [NV][16] for face 16
+  const int fxr = tx < 15 ? cell2 + 1 : 256 + ty;   // this cell's right x-face
   if (t == 0) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) mbar_init(bar + i, 1);
@@ -546,19 +553,19 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     if (k + 1 < NB) prefetch_halo(k + 1);   // the other half of the CTA; sHalo is free now
     {
       R f[NV];
-      xface(tx, ty, f);
+      xface(fc, fr, f);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) sFx[v * 272 + ty * 17 + tx] = f[v];
-      if (FR && tx == 0 && slot[0] >= 0) {
+      for (int v = 0; v < NV; ++v) sFx[v * 272 + fr * 16 + fc] = f[v];
+      if (FR && fc == 0 && slot[0] >= 0) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) FR[((size_t)slot[0] * NV + v) * 256 + k * 16 + ty] = f[v];
+        for (int v = 0; v < NV; ++v) FR[((size_t)slot[0] * NV + v) * 256 + k * 16 + fr] = f[v];
       }
-      yface(ty, tx, f);
+      yface(fr, fc, f);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) sFy[v * 272 + ty * 16 + tx] = f[v];
-      if (FR && ty == 0 && slot[2] >= 0) {
+      for (int v = 0; v < NV; ++v) sFy[v * 272 + fr * 16 + fc] = f[v];
+      if (FR && fr == 0 && slot[2] >= 0) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) FR[((size_t)slot[2] * NV + v) * 256 + k * 16 + tx] = f[v];
+        for (int v = 0; v < NV; ++v) FR[((size_t)slot[2] * NV + v) * 256 + k * 16 + fc] = f[v];
       }
       if (warp == (k & 7)) {      // the 32 block-boundary faces, one warp per plane in turn
         // lanes 0-15: x-face 16 - 1/2 of row r; lanes 16-31: y-face 16 - 1/2 of column r,
@@ -581,7 +588,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
         riemann<P, R, 0, FLUX>(pl, pr, f, pp);
         swap_xy<P, R>(f, yd);
         const int fs = yd ? 1 : 0;
-        R* dstp = yd ? sFy + 16 * 16 + r : sFx + r * 17 + 16;
+        R* dstp = yd ? sFy + 16 * 16 + r : sFx + 256 + r;
 #pragma unroll
         for (int v = 0; v < NV; ++v) dstp[v * 272] = f[v];
         const int sl = slot[1 + 2 * fs];
@@ -608,7 +615,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
         R L[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const R lx = (sFx[v * 272 + ty * 17 + tx + 1] - sFx[v * 272 + ty * 17 + tx]) * idx;
+          const R lx = (sFx[v * 272 + fxr] - sFx[v * 272 + cell2]) * idx;
           const R ly = (sFy[v * 272 + (ty + 1) * 16 + tx] - sFy[v * 272 + ty * 16 + tx]) * idy;
           const R lz = (fzu[v] - fzd[v]) * idz;
           L[v] = -((lx + ly) + lz);
@@ -631,7 +638,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       } else {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const R lx = (sFx[v * 272 + ty * 17 + tx + 1] - sFx[v * 272 + ty * 17 + tx]) * idx;
+          const R lx = (sFx[v * 272 + fxr] - sFx[v * 272 + cell2]) * idx;
           const R ly = (sFy[v * 272 + (ty + 1) * 16 + tx] - sFy[v * 272 + ty * 16 + tx]) * idy;
           const R lz = (fzu[v] - fzd[v]) * idz;
           const R L = -((lx + ly) + lz);
