@@ -146,11 +146,11 @@ FP64_LANES = 2       # FP64 FMA lanes per SM on GB300 (1.25 TFLOP/s measured at 
 
 
 # DRAM bytes (read + write) per stage launch of the FP32 MHD stage kernel on this workload,
-# from one ncu capture of the three stage launches of one SSPRK3 step (1.443, 2.105 and
-# 2.044 GB), averaged; valid only while the kernel sources hash to STAGE_SRC_DIGEST.
-STAGE_TRAFFIC_BYTES = (1.4427e9 + 2.1051e9 + 2.0437e9) / 3
-STAGE_SRC_DIGEST = "de0fdc77e35a5d52"
-STAGE_SRC = ("kernels.cuh", "physics.cuh", "stage_go.cuh", "stage_mhd.cu")
+# from one ncu capture of the three stage launches of one SSPRK3 step (1.446, 2.108 and
+# 2.047 GB), averaged; valid only while the kernel sources hash to STAGE_SRC_DIGEST.
+STAGE_TRAFFIC_BYTES = (1.4462e9 + 2.1080e9 + 2.0474e9) / 3
+STAGE_SRC_DIGEST = "b78ece870c8079ce"
+STAGE_SRC = ("kernels.cuh", "pair.cuh", "physics.cuh", "stage_go.cuh", "stage_mhd.cu")
 
 
 def stage_traffic():

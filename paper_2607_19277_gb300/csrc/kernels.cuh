@@ -14,6 +14,7 @@
 #include <stdint.h>
 
 #include "agile_internal.h"
+#include "pair.cuh"
 #include "physics.cuh"
 
 namespace agile {
@@ -249,6 +250,16 @@ __device__ __forceinline__ void swap_xy(R* v, bool yd) {
   }
 }
 
+// Variable that takes slot v when the x and y vector components are exchanged.
+template <class P>
+__host__ __device__ constexpr int swapv(int v) {
+  return (P::IV >= 0 && v == P::IV)          ? P::IV + 1
+         : (P::IV >= 0 && v == P::IV + 1)    ? P::IV
+         : (P::BOFF >= 0 && v == P::BOFF)     ? P::BOFF + 1
+         : (P::BOFF >= 0 && v == P::BOFF + 1) ? P::BOFF
+                                              : v;
+}
+
 constexpr uint32_t WAIT_LIMIT = 1u << 22;   // ~0.1 s of polling per wait at most
 
 // Slot of plane p (-2 .. 17) in the primitive ring. The ring is thread-private (every thread
@@ -285,6 +296,8 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   using P = PT<R>;
   using S = StageSmem<PT, R>;
   constexpr int NV = P::NV, NA = P::NA, NT = NV + NA;
+  // FP32 HD / MHD with HLL or TVDLF: x- and y-faces solved as packed pairs
+  constexpr bool PAIRED = sizeof(R) == 4 && PairPhys<P>::OK && (FLUX == FLUX_HLL || FLUX == FLUX_TVDLF);
   constexpr int NAW = NA > 0 ? NA : 1;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
@@ -553,19 +566,51 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     if (k + 1 < NB) prefetch_halo(k + 1);   // the other half of the CTA; sHalo is free now
     {
       R f[NV];
-      xface(fc, fr, f);
+      if constexpr (PAIRED) {
+        // the x-face fc - 1/2 of row fr and the y-face fr - 1/2 of column fc as one pair, the
+        // y-face's states with x and y components exchanged
+        f2 a[NV], bq[NV], c[NV], d[NV], pl[NV], pr[NV], fp[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) sFx[v * 272 + fr * 16 + fc] = f[v];
-      if (FR && fc == 0 && slot[0] >= 0) {
+        for (int v = 0; v < NV; ++v) {
+          const R* rx = sC + v * 400 + (fr + 2) * 20 + fc;
+          const R* ry = sC + swapv<P>(v) * 400 + fr * 20 + fc + 2;
+          a[v] = f2_of(rx[0], ry[0]);
+          bq[v] = f2_of(rx[1], ry[20]);
+          c[v] = f2_of(rx[2], ry[40]);
+          d[v] = f2_of(rx[3], ry[60]);
+        }
+        plm2<NV, LIM>(a, bq, c, d, pl, pr);
+        riemann2<P, FLUX>(pl, pr, fp, PairK(pp));
+        R fy[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) FR[((size_t)slot[0] * NV + v) * 256 + k * 16 + fr] = f[v];
-      }
-      yface(fr, fc, f);
+        for (int v = 0; v < NV; ++v) {
+          f2_split(fp[v], f[v], fy[v]);
+          sFx[v * 272 + fr * 16 + fc] = f[v];
+          sFy[swapv<P>(v) * 272 + fr * 16 + fc] = fy[v];
+        }
+        if (FR && fc == 0 && slot[0] >= 0) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) sFy[v * 272 + fr * 16 + fc] = f[v];
-      if (FR && fr == 0 && slot[2] >= 0) {
+          for (int v = 0; v < NV; ++v) FR[((size_t)slot[0] * NV + v) * 256 + k * 16 + fr] = f[v];
+        }
+        if (FR && fr == 0 && slot[2] >= 0) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) FR[((size_t)slot[2] * NV + v) * 256 + k * 16 + fc] = f[v];
+          for (int v = 0; v < NV; ++v) FR[((size_t)slot[2] * NV + swapv<P>(v)) * 256 + k * 16 + fc] = fy[v];
+        }
+      } else {
+        xface(fc, fr, f);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sFx[v * 272 + fr * 16 + fc] = f[v];
+        if (FR && fc == 0 && slot[0] >= 0) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) FR[((size_t)slot[0] * NV + v) * 256 + k * 16 + fr] = f[v];
+        }
+        yface(fr, fc, f);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sFy[v * 272 + fr * 16 + fc] = f[v];
+        if (FR && fr == 0 && slot[2] >= 0) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) FR[((size_t)slot[2] * NV + v) * 256 + k * 16 + fc] = f[v];
+        }
       }
       if (warp == (k & 7)) {      // the 32 block-boundary faces, one warp per plane in turn
         // lanes 0-15: x-face 16 - 1/2 of row r; lanes 16-31: y-face 16 - 1/2 of column r,
