@@ -146,10 +146,10 @@ FP64_LANES = 2       # FP64 FMA lanes per SM on GB300 (1.25 TFLOP/s measured at 
 
 
 # DRAM bytes (read + write) per stage launch of the FP32 MHD stage kernel on this workload,
-# from one ncu capture of the three stage launches of one SSPRK3 step (1.446, 2.108 and
-# 2.047 GB), averaged; valid only while the kernel sources hash to STAGE_SRC_DIGEST.
-STAGE_TRAFFIC_BYTES = (1.4462e9 + 2.1080e9 + 2.0474e9) / 3
-STAGE_SRC_DIGEST = "b78ece870c8079ce"
+# from one ncu capture of the three stage launches of one SSPRK3 step (1.446, 2.109 and
+# 2.050 GB), averaged; valid only while the kernel sources hash to STAGE_SRC_DIGEST.
+STAGE_TRAFFIC_BYTES = (1.4462e9 + 2.1091e9 + 2.0499e9) / 3
+STAGE_SRC_DIGEST = "1e0b4e4d7a3ffbee"
 STAGE_SRC = ("kernels.cuh", "pair.cuh", "physics.cuh", "stage_go.cuh", "stage_mhd.cu")
 
 

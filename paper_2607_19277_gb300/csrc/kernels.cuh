@@ -446,7 +446,8 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       pr[v] = c[v] - h;
       hz[v] = h;
     }
-    riemann<P, R, 2, FLUX>(pl, pr, f, pp);
+    if constexpr (PAIRED) riemann_z_lr<P, FLUX>(pl, pr, f, pp);
+    else riemann<P, R, 2, FLUX>(pl, pr, f, pp);
   };
   auto xface = [&](int fi, int row, R* f) {  // x-face fi - 1/2 of row `row` in plane buffer
     R a[NV], bq[NV], c[NV], d[NV], pl[NV], pr[NV];

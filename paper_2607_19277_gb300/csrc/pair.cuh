@@ -130,6 +130,8 @@ template <>
 struct PairPhys<HdPhys<float>> {
   static constexpr bool OK = true;
   static constexpr int NV = 5;
+  // variable in slot v when the z axis takes the place of the x axis
+  __host__ __device__ static constexpr int zrot(int v) { return v == 1 ? 3 : v == 3 ? 1 : v; }
   __device__ static __forceinline__ void interface(f2*, f2*, const PairK&) {}
   __device__ static __forceinline__ void prim2cons(const f2* p, f2* u, const PairK& k) {
     const f2 v2 = fma2(p[3], p[3], fma2(p[2], p[2], p[1] * p[1]));
@@ -158,6 +160,9 @@ template <>
 struct PairPhys<MhdPhys<float>> {
   static constexpr bool OK = true;
   static constexpr int NV = 9;
+  __host__ __device__ static constexpr int zrot(int v) {
+    return v == 1 ? 3 : v == 3 ? 1 : v == 5 ? 7 : v == 7 ? 5 : v;
+  }
   // GLM face values B_x* and psi* (the scalar interface<0>)
   __device__ static __forceinline__ void interface(f2* pl, f2* pr, const PairK& k) {
     const f2 bl = pl[5], br = pr[5], sl = pl[8], sr = pr[8];
@@ -235,6 +240,47 @@ __device__ __forceinline__ void riemann2(f2* pl, f2* pr, f2* f, const PairK& k) 
     const f2 wl = sr * inv, nwr = (k.zero - sl) * inv, wd = sl * sr * inv;
 #pragma unroll
     for (int v = 0; v < NV; ++v) f[v] = fma2(wd, ur[v] - ul[v], fma2(wl, fl[v], nwr * fr[v]));
+  }
+}
+
+// z-face flux of one face with its left and right states as the pair: the states rotated so
+// that z takes the place of x, the primitive-to-conserved map, physical fluxes and signal
+// speeds of both sides in packed instructions, the HLL / TVDLF combination of the two halves
+// at the end. pl and pr are the scalar face states (modified by the GLM face values).
+template <class P, int FLUX>
+__device__ __forceinline__ void riemann_z_lr(float* pl, float* pr, float* f, const PhysParamsT<float>& pp) {
+  using Q = PairPhys<P>;
+  constexpr int NV = Q::NV;
+  P::template interface<2>(pl, pr, pp);
+  const PairK k(pp);
+  f2 q[NV], u[NV], fq[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) q[v] = f2_of(pl[Q::zrot(v)], pr[Q::zrot(v)]);
+  Q::prim2cons(q, u, k);
+  Q::flux(q, u, fq, k);
+  f2 lm, lp;
+  Q::lambdas(q, lm, lp, k);
+  float lml, lmr, lpl, lpr;
+  f2_split(lm, lml, lmr);
+  f2_split(lp, lpl, lpr);
+  f2 w, dw;   // F = w.x fl + w.y fr + dw.x ul + dw.y ur
+  if constexpr (FLUX == FLUX_TVDLF) {
+    const float c = fmaxf(fmaxf(fabsf(lml), fabsf(lpl)), fmaxf(fabsf(lmr), fabsf(lpr)));
+    w = k.half;
+    dw = f2_of(0.5f * c, -0.5f * c);
+  } else {
+    const float sl = fminf(fminf(lml, lmr), 0.0f);
+    const float sr = fmaxf(fmaxf(lpl, lpr), 0.0f);
+    const float inv = 1.0f / (sr - sl);
+    const float wd = sl * sr * inv;
+    w = f2_of(sr * inv, -(sl * inv));
+    dw = f2_of(-wd, wd);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    float a, b;
+    f2_split(fma2(w, fq[v], dw * u[v]), a, b);
+    f[Q::zrot(v)] = a + b;
   }
 }
 
