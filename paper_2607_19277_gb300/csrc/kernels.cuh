@@ -565,6 +565,14 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       issue(k + 3);   // slot (k+1)&3: plane k-1's raw data, read by its update before this barrier
     }
     if (k + 1 < NB) prefetch_halo(k + 1);   // the other half of the CTA; sHalo is free now
+    // U^n of cell (tx, ty, k) for the stage combine, loaded now so that the face work of
+    // this phase covers its latency
+    R unk[NV];
+    if (combine) {
+      const R* pn = Un + (size_t)b * NT * NCELL + (size_t)k * 256 + cell2;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) unk[v] = __ldg(pn + (size_t)v * NCELL);
+    }
     {
       R f[NV];
       if constexpr (PAIRED) {
@@ -677,7 +685,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
           R val = raw[v * 256];
           if (v < P::FROZEN) {
             val = val + rdt * L[v];
-            if (combine) val = ra * Un[base + (size_t)v * NCELL] + rb * val;
+            if (combine) val = ra * unk[v] + rb * val;
           }
           out[v] = val;
         }
@@ -689,7 +697,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
           const R lz = (fzu[v] - fzd[v]) * idz;
           const R L = -((lx + ly) + lz);
           R val = raw[v * 256] + rdt * L;
-          if (combine) val = ra * Un[base + (size_t)v * NCELL] + rb * val;
+          if (combine) val = ra * unk[v] + rb * val;
           out[v] = val;
           fzd[v] = fzu[v];
         }
