@@ -118,7 +118,7 @@ class Cooling:
         """Losses over dt on conserved HD / MHD / FFHD states U (nvar, ...): only e
         changes, by rho (T_new - T) / (gamma - 1)."""
         P, _ = phys.cons2prim(U)
-        ie = 2 if phys.name == "ffhd" else 4      # index of e in U and of p in P
+        ie = 2 if phys.name in ("ffhd", "ffhd_htc") else 4      # index of e in U and of p in P
         rho = P[0]
         t = P[ie] / rho
         tn = self.cool_temperature(rho, t, dt)

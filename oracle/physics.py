@@ -407,9 +407,108 @@ class FFHD:
         return [3 + d]
 
 
-def make_physics(name: str, gamma: float, eos: str = "ideal"):
+class FFHDHTC(FFHD):
+    """Frozen-field hydrodynamics with hyperbolic field-aligned thermal conduction (Section
+    2.3.2, Eqs. 7-10 without gravity and heating): U = (rho, m_par, e, q_par, b_x, b_y, b_z),
+    P = (rho, v_par, p, q_par, b). The heat flux q_par relaxes towards kappa_par b.grad T
+    (Eq. 10) and carries energy along the field: the energy flux is ((e + p) v_par - q_par) b
+    (Eq. 9).
+
+    Readings (the paper gives the equations and the relaxation time only):
+      * q_par is reconstructed like rho, v_par and p (PLM); Eq. 10 has no divergence term, so
+        q_par has no face flux of its own and no numerical dissipation;
+      * the target kappa_par b.grad T uses T = p / rho (code units), kappa_par = kappa0
+        T^(5/2) and grad T by central differences of the stage state across the cell's face
+        neighbours, b the cell's frozen field;
+      * tau = max(4 dt, tau_reduced) with tau_reduced = 0, i.e. tau = 4 dt; the relaxation
+        -(q_par - kappa_par b.grad T) / tau is a source of every RK stage;
+      * the signal speeds (and so the CFL step) are those of FFHD.
+    """
+
+    name = "ffhd_htc"
+    nvar = 7
+    naux = 0
+    glm = False
+    nrec = 4
+    frozen_from = 4
+    noflux = 3          # q_par: no face flux
+
+    def __init__(self, gamma: float, kappa0: float):
+        self.gamma = float(gamma)
+        self.kappa0 = float(kappa0)
+
+    def cons2prim(self, U, aux=None):
+        g = self.gamma
+        P = np.empty_like(U)
+        rho = U[0]
+        v = U[1] / rho
+        P[0] = rho
+        P[1] = v
+        P[2] = (g - 1.0) * (U[2] - 0.5 * rho * v * v)
+        P[3:7] = U[3:7]
+        return P, None
+
+    def prim2cons(self, P):
+        g = self.gamma
+        U = np.empty_like(P)
+        U[0] = P[0]
+        U[1] = P[0] * P[1]
+        U[2] = P[2] / (g - 1.0) + 0.5 * P[0] * P[1] * P[1]
+        U[3:7] = P[3:7]
+        return U
+
+    def interface(self, PL, PR, d):
+        bf = 0.5 * (PL[4 + d] + PR[4 + d])
+        PL = PL.copy()
+        PR = PR.copy()
+        PL[4 + d] = bf
+        PR[4 + d] = bf
+        return PL, PR
+
+    def flux(self, P, U, d):
+        rho, v, p, q, b = P[0], P[1], P[2], P[3], P[4 + d]
+        F = np.zeros_like(P)
+        F[0] = rho * v * b
+        F[1] = (rho * v * v + p) * b
+        F[2] = ((U[2] + p) * v - q) * b
+        F[4 + d] = b
+        return F
+
+    def lambdas(self, P, d):
+        c = np.sqrt(self.gamma * P[2] / P[0])
+        b = P[4 + d]
+        a = P[1] * b
+        w = c * np.abs(b)
+        return a - w, a + w
+
+    def source(self, Pc, L):
+        """p div b for m_par; L[4..6] holds -d_d b_face,d. (The q_par relaxation needs the
+        time step and is added by the solver from htc_target.)"""
+        L = L.copy()
+        L[1] = L[1] - Pc[2] * ((L[4] + L[5]) + L[6])
+        return L
+
+    def htc_target(self, P, dx):
+        """kappa0 T^(5/2) b.grad T on the 16^3 interior of a block whose primitives P carry
+        two ghost layers (face neighbours filled); central differences per axis."""
+        T = P[2] / P[0]
+        i = slice(2, 18)
+        Tc = T[i, i, i]
+        grad = ((T[i, i, 3:19] - T[i, i, 1:17]) / (2.0 * dx[0]),
+                (T[i, 3:19, i] - T[i, 1:17, i]) / (2.0 * dx[1]),
+                (T[3:19, i, i] - T[1:17, i, i]) / (2.0 * dx[2]))
+        bgrad = P[4][i, i, i] * grad[0] + P[5][i, i, i] * grad[1] + P[6][i, i, i] * grad[2]
+        return self.kappa0 * Tc * Tc * np.sqrt(Tc) * bgrad
+
+    def reflect_vars(self, d):
+        return [4 + d]
+
+
+def make_physics(name: str, gamma: float, eos: str = "ideal", kappa0: float = 0.0):
     if name == "srhd":
         return SRHD(gamma, eos)
     if eos != "ideal":
         raise ValueError("the Synge EOS applies to srhd only")
+    if name == "ffhd_htc":
+        return FFHDHTC(gamma, kappa0)
     return {"hd": HD, "mhd": MHD, "ffhd": FFHD}[name](gamma)

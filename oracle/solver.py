@@ -60,6 +60,7 @@ class Config:
     derefine_ratio: float = 1.0 / 8.0
     lohner_eps: float = 0.01
     cooling: tuple = None          # (T, Lambda) table: optically thin losses (hd, mhd)
+    htc_kappa0: float = 0.0        # ffhd_htc: kappa_par = htc_kappa0 T^(5/2)
 
 
 def morton3(ix: int, iy: int, iz: int) -> int:
@@ -117,12 +118,12 @@ class Solver:
 
     def __init__(self, cfg: Config):
         self.cfg = cfg
-        self.phys = make_physics(cfg.physics, cfg.gamma, cfg.eos)
-        if cfg.physics == "ffhd" and cfg.max_level != 1:
+        self.phys = make_physics(cfg.physics, cfg.gamma, cfg.eos, cfg.htc_kappa0)
+        if cfg.physics in ("ffhd", "ffhd_htc") and cfg.max_level != 1:
             raise ValueError("ffhd runs on uniform meshes (max_level 1)")
         self.cool = None
         if cfg.cooling is not None:
-            if cfg.physics not in ("hd", "mhd", "ffhd"):
+            if cfg.physics not in ("hd", "mhd", "ffhd", "ffhd_htc"):
                 raise ValueError("radiative losses apply to hd, mhd and ffhd")
             self.cool = Cooling(cfg.cooling[0], cfg.cooling[1], cfg.gamma)
         self.nvar = self.phys.nvar
@@ -475,6 +476,8 @@ class Solver:
         if hasattr(phys, "frozen_from"):
             # frozen variables: their exact flux (equal on both sides), no dissipation
             F[phys.frozen_from:] = FL[phys.frozen_from:]
+        if hasattr(phys, "noflux"):
+            F[phys.noflux] = 0.0                         # a variable without a flux term
         return np.moveaxis(F, -1, _ax(d))
 
     def _hllc(self, PL, PR, UL, UR, FL, FR, sl, sr, d):
@@ -510,6 +513,7 @@ class Solver:
         fluxes = {}
         new_aux = {}
         self._pcell = {}
+        self._htc = {}
         for key, blk in self.leaves.items():
             P, A = self._prims(blk)
             if A is not None:
@@ -517,6 +521,8 @@ class Solver:
             if hasattr(self.phys, "source"):
                 self._pcell[key] = P[(slice(None),) + (slice(G, G + NB),) * 3]
             dxl = self.dx(key[0])
+            if hasattr(self.phys, "htc_target"):
+                self._htc[key] = self.phys.htc_target(P, dxl)
             fluxes[key] = [self._face_fluxes(P, d, dxl, ch) for d in range(3)]
         return fluxes, new_aux
 
@@ -627,6 +633,9 @@ class Solver:
                 rhs = self._rhs(fluxes, key)
                 if hasattr(self.phys, "source"):
                     rhs = self.phys.source(self._pcell[key], rhs)
+                if hasattr(self.phys, "htc_target"):
+                    # relaxation of q_par towards its target over tau = 4 dt (Eq. 10)
+                    rhs[3] = -(us[3] - self._htc[key]) / (4.0 * dt)
                 upd = us + dt * rhs
                 if a != 0.0:
                     upd = a * un[key] + b * upd
