@@ -50,7 +50,7 @@ typedef enum {
   AGILE_ETIMEOUT = 7    /* a bounded device wait gave up */
 } agile_status;
 
-enum { AGILE_HD = 0, AGILE_MHD_GLM = 1, AGILE_SRHD = 2, AGILE_FFHD = 3 };  /* physics */
+enum { AGILE_HD = 0, AGILE_MHD_GLM = 1, AGILE_SRHD = 2, AGILE_FFHD = 3, AGILE_FFHD_HTC = 4 };  /* physics */
 enum { AGILE_MINMOD = 0, AGILE_VANLEER = 1 };                  /* limiter */
 enum { AGILE_TVDLF = 0, AGILE_HLL = 1, AGILE_HLLC = 2 };        /* Riemann flux */
 enum { AGILE_PERIODIC = 0, AGILE_OUTFLOW = 1, AGILE_REFLECT = 2 }; /* boundaries */
@@ -68,7 +68,10 @@ typedef struct {
  *  physics        AGILE_HD | AGILE_MHD_GLM | AGILE_SRHD | AGILE_FFHD (frozen-field
  *                 hydrodynamics, Section 2.3.2: U = (rho, m_par, e, b_x, b_y, b_z) with the
  *                 frozen unit field b set by the initial condition and never updated;
- *                 uniform meshes, TVDLF)
+ *                 uniform meshes, TVDLF) | AGILE_FFHD_HTC (the same with hyperbolic
+ *                 field-aligned thermal conduction, Eqs. 9-10: U = (rho, m_par, e, q_par,
+ *                 b_x, b_y, b_z); q_par relaxes towards htc_kappa0 T^(5/2) b.grad T, T =
+ *                 p / rho, over tau = 4 dt and carries energy as -q_par b)
  *  limiter        slope limiter of the piecewise-linear reconstruction on primitives
  *  flux           AGILE_TVDLF (all), AGILE_HLL (hd, mhd), AGILE_HLLC (hd); the
  *                 solvers per module of paper Table 1
@@ -93,6 +96,7 @@ typedef struct {
  *                 AGILE_EOS_SYNGE (srhd only): the Synge gas (Eq. 22) in Mathews'
  *                 approximation h = 5/2 theta + sqrt(9/4 theta^2 + 1), theta = p/rho
  *                 (Section 2.3.4); gamma is then unused by the physics
+ *  htc_kappa0     AGILE_FFHD_HTC: conduction coefficient kappa0 >= 0 (ignored otherwise)
  */
 typedef struct {
   int physics;
@@ -115,6 +119,7 @@ typedef struct {
   double derefine_ratio;
   double lohner_eps;
   int eos;
+  double htc_kappa0;
 } agile_config;
 
 /* Create a mesh of level-1 blocks (Fig. 1, "init level one") with uninitialised state.
@@ -266,7 +271,9 @@ agile_status agile_kernel_timing(agile_mesh* mesh, double* stage_ms, long long* 
 typedef struct agile_batch agile_batch;
 
 /* Create nsolve solves from cfgs[nsolve], each with its level-1 blocks (refine with
- * agile_batch_regrid). alloc as for meshes;
+ * agile_batch_regrid). The solves share physics, limiter, flux, rk, real_bytes, gamma, cfl,
+ * glm_alpha, eos and htc_kappa0 (AGILE_EINVAL otherwise); grids, boundaries and refinement
+ * settings are per solve. alloc as for meshes;
  * cuda_stream NULL makes the batch create its own non-blocking stream (graphs cannot be
  * captured on the legacy default stream). Errors: AGILE_EINVAL, AGILE_ENOMEM, AGILE_ECUDA. */
 agile_status agile_batch_create(const agile_config* cfgs, int nsolve, const agile_allocator* alloc,

@@ -18,8 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libagile.so")
 NCELL = 4096
 
-PHYSICS = {"hd": 0, "mhd": 1, "srhd": 2, "ffhd": 3}
-NVAR = {0: 5, 1: 9, 2: 5, 3: 6}
+PHYSICS = {"hd": 0, "mhd": 1, "srhd": 2, "ffhd": 3, "ffhd_htc": 4}
+NVAR = {0: 5, 1: 9, 2: 5, 3: 6, 4: 7}
 EOS = {"ideal": 0, "synge": 1}
 LIMITER = {"minmod": 0, "vanleer": 1}
 FLUX = {"tvdlf": 0, "hll": 1, "hllc": 2}
@@ -48,7 +48,8 @@ class agile_config(C.Structure):
                 ("xmax", C.c_double * 3), ("bc", C.c_int * 6), ("max_level", C.c_int),
                 ("refine_nvars", C.c_int), ("refine_vars", C.c_int * 9),
                 ("refine_weights", C.c_double * 9), ("refine_tol", C.c_double),
-                ("derefine_ratio", C.c_double), ("lohner_eps", C.c_double), ("eos", C.c_int)]
+                ("derefine_ratio", C.c_double), ("lohner_eps", C.c_double), ("eos", C.c_int),
+                ("htc_kappa0", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -133,7 +134,7 @@ def make_config(physics="hd", limiter="minmod", flux="hll", rk=2, real_bytes=8, 
                 cfl=0.4, glm_alpha=0.5, base_blocks=(4, 4, 4), xmin=(0.0, 0.0, 0.0),
                 xmax=(1.0, 1.0, 1.0), bc=("periodic",) * 6, max_level=1, refine_vars=(0,),
                 refine_weights=(1.0,), refine_tol=0.2, derefine_ratio=1.0 / 8.0,
-                lohner_eps=0.01, eos="ideal") -> agile_config:
+                lohner_eps=0.01, eos="ideal", htc_kappa0=0.0) -> agile_config:
     c = agile_config()
     c.physics = PHYSICS[physics]
     c.limiter = LIMITER[limiter]
@@ -158,6 +159,7 @@ def make_config(physics="hd", limiter="minmod", flux="hll", rk=2, real_bytes=8, 
     c.derefine_ratio = derefine_ratio
     c.lohner_eps = lohner_eps
     c.eos = EOS[eos] if isinstance(eos, str) else eos
+    c.htc_kappa0 = htc_kappa0
     return c
 
 

@@ -21,7 +21,7 @@ constexpr int NFACE = 6;          // faces: -x, +x, -y, +y, -z, +z
 
 enum FaceKind : int { FK_SAME = 0, FK_BC = 1, FK_COARSER = 2, FK_FINER = 3 };
 enum BcKind : int { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECT = 2 };
-enum PhysKind : int { PH_HD = 0, PH_MHD = 1, PH_SRHD = 2, PH_SRHD_SYNGE = 3, PH_FFHD = 4 };
+enum PhysKind : int { PH_HD = 0, PH_MHD = 1, PH_SRHD = 2, PH_SRHD_SYNGE = 3, PH_FFHD = 4, PH_FFHD_HTC = 5 };
 
 // src encoding: >= 0 same-level neighbour block; SRC_OUTFLOW / SRC_REFLECT physical
 // boundary; <= SRC_SLOT0 ghost slot (SRC_SLOT0 - slot).

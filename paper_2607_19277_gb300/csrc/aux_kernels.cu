@@ -10,7 +10,9 @@
 
 namespace agile {
 
-int phys_nvar(int phys) { return phys == PH_MHD ? 9 : (phys == PH_FFHD ? 6 : 5); }
+int phys_nvar(int phys) {
+  return phys == PH_MHD ? 9 : (phys == PH_FFHD ? 6 : (phys == PH_FFHD_HTC ? 7 : 5));
+}
 int phys_naux(int phys) { return phys == PH_SRHD || phys == PH_SRHD_SYNGE ? 2 : 0; }
 
 // ------------------------------------------------------------------------------ helpers
@@ -507,6 +509,9 @@ __global__ void halo_kernel(const R* __restrict__ U, const R* __restrict__ G,
     } else if ((phys) == PH_FFHD) {                            \
       if ((rb) == 8) { using R = double; CALL(FfhdPhys); }     \
       else { using R = float; CALL(FfhdPhys); }                \
+    } else if ((phys) == PH_FFHD_HTC) {                        \
+      if ((rb) == 8) { using R = double; CALL(FfhdHtcPhys); }  \
+      else { using R = float; CALL(FfhdHtcPhys); }             \
     } else {                                                   \
       if ((rb) == 8) { using R = double; CALL(SrhdSyngePhys); }\
       else { using R = float; CALL(SrhdSyngePhys); }           \

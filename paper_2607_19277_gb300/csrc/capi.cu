@@ -103,25 +103,28 @@ size_t pool_bytes(const agile_mesh* m, int nblk) {
 // Internal physics kind: the srhd module with the Synge EOS has its own device trait.
 int phys_kind(const agile_config& c) {
   if (c.physics == AGILE_FFHD) return PH_FFHD;
+  if (c.physics == AGILE_FFHD_HTC) return PH_FFHD_HTC;
   return c.physics == AGILE_SRHD && c.eos == AGILE_EOS_SYNGE ? PH_SRHD_SYNGE : c.physics;
 }
 
 int cfg_nvar(const agile_config& c) {
-  return c.physics == AGILE_MHD_GLM ? 9 : (c.physics == AGILE_FFHD ? 6 : 5);
+  return c.physics == AGILE_MHD_GLM ? 9 : (c.physics == AGILE_FFHD ? 6 : (c.physics == AGILE_FFHD_HTC ? 7 : 5));
 }
 
 // Scheme restrictions shared by meshes and batches: the solvers per module of paper
 // Table 1 (TVDLF for srhd and ffhd, HLLC for hd), the Synge EOS for srhd only, ffhd on
-// uniform meshes.
+// uniform meshes, a finite non-negative conduction coefficient.
 bool scheme_ok(const agile_config& c) {
-  if (c.physics < 0 || c.physics > 3 || (c.limiter != 0 && c.limiter != 1) || c.flux < 0 || c.flux > 2 ||
+  const bool ffhd = c.physics == AGILE_FFHD || c.physics == AGILE_FFHD_HTC;
+  if (c.physics < 0 || c.physics > 4 || (c.limiter != 0 && c.limiter != 1) || c.flux < 0 || c.flux > 2 ||
       (c.rk != 2 && c.rk != 3) || (c.real_bytes != 4 && c.real_bytes != 8) || !(c.gamma > 1.0) ||
       !(c.cfl > 0.0))
     return false;
-  if ((c.physics == AGILE_SRHD || c.physics == AGILE_FFHD) && c.flux != AGILE_TVDLF) return false;
+  if ((c.physics == AGILE_SRHD || ffhd) && c.flux != AGILE_TVDLF) return false;
   if (c.flux == AGILE_HLLC && c.physics != AGILE_HD) return false;
   if (c.eos != AGILE_EOS_IDEAL && !(c.eos == AGILE_EOS_SYNGE && c.physics == AGILE_SRHD)) return false;
-  if (c.physics == AGILE_FFHD && c.max_level != 1) return false;
+  if (ffhd && c.max_level != 1) return false;
+  if (c.physics == AGILE_FFHD_HTC && !(c.htc_kappa0 >= 0.0 && c.htc_kappa0 < 1e300)) return false;
   return true;
 }
 
@@ -588,6 +591,7 @@ agile_status agile_step(agile_mesh* m, double dt) {
     A.b = nst == 2 ? w2[st][1] : w3[st][1];
     A.gamma = m->cfg.gamma;
     A.glm_alpha = m->cfg.glm_alpha;
+    A.htc_kappa0 = m->cfg.htc_kappa0;
     A.glm_post = (mhd && last && fuse) ? 1 : 0;
     A.nblk = m->nblk;
     A.status = m->d_status;
@@ -607,6 +611,8 @@ agile_status agile_step(agile_mesh* m, double dt) {
     else if (m->cfg.eos == AGILE_EOS_SYNGE)
       e = launch_stage_srhd_synge(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
     else if (m->cfg.physics == AGILE_FFHD) e = launch_stage_ffhd(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
+    else if (m->cfg.physics == AGILE_FFHD_HTC)
+      e = launch_stage_ffhd_htc(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
     else e = launch_stage_srhd(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
     if (e != cudaSuccess) return fail(m, AGILE_ECUDA, std::string("stage kernel: ") + cudaGetErrorString(e));
     if (m->timing) {
@@ -652,7 +658,8 @@ agile_status agile_set_cooling(agile_mesh* m, const double* T, const double* Lam
     m->cool = CoolHost();
     return AGILE_OK;
   }
-  if (m->cfg.physics != AGILE_HD && m->cfg.physics != AGILE_MHD_GLM && m->cfg.physics != AGILE_FFHD)
+  if (m->cfg.physics != AGILE_HD && m->cfg.physics != AGILE_MHD_GLM && m->cfg.physics != AGILE_FFHD &&
+      m->cfg.physics != AGILE_FFHD_HTC)
     return fail(m, AGILE_EINVAL, "radiative losses apply to hd, mhd and ffhd");
   CoolHost c;
   if (build_cool_table(T, Lambda, n, m->cfg.gamma, m->rb, &c))
@@ -1322,6 +1329,8 @@ agile_status batch_enqueue_step(agile_batch* B) {
     A.b = nst == 2 ? w2[st][1] : w3[st][1];
     A.gamma = B->cfg.gamma;
     A.glm_alpha = B->cfg.glm_alpha;
+  A.htc_kappa0 = B->cfg.htc_kappa0;
+    A.htc_kappa0 = B->cfg.htc_kappa0;
     A.glm_post = (mhd && last && fuse) ? 1 : 0;
     A.nblk = B->nblk;
     A.status = B->d_status;
@@ -1336,6 +1345,8 @@ agile_status batch_enqueue_step(agile_batch* B) {
     else if (B->cfg.eos == AGILE_EOS_SYNGE)
       e = launch_stage_srhd_synge(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
     else if (B->cfg.physics == AGILE_FFHD) e = launch_stage_ffhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
+  else if (B->cfg.physics == AGILE_FFHD_HTC)
+    e = launch_stage_ffhd_htc(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
     else e = launch_stage_srhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
     if (e != cudaSuccess) return bfail(B, AGILE_ECUDA, std::string("stage kernel: ") + cudaGetErrorString(e));
     if (B->nfix) {
@@ -1366,6 +1377,7 @@ agile_status batch_stage1(agile_batch* B, int grid, bool dynamic) {
   A.b = 1.0;
   A.gamma = B->cfg.gamma;
   A.glm_alpha = B->cfg.glm_alpha;
+  A.htc_kappa0 = B->cfg.htc_kappa0;
   A.glm_post = 0;
   A.nblk = B->nblk;
   A.status = B->d_status;
@@ -1381,6 +1393,8 @@ agile_status batch_stage1(agile_batch* B, int grid, bool dynamic) {
   else if (B->cfg.eos == AGILE_EOS_SYNGE)
     e = launch_stage_srhd_synge(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
   else if (B->cfg.physics == AGILE_FFHD) e = launch_stage_ffhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
+  else if (B->cfg.physics == AGILE_FFHD_HTC)
+    e = launch_stage_ffhd_htc(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
   else e = launch_stage_srhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
   if (e != cudaSuccess) return bfail(B, AGILE_ECUDA, std::string("stage kernel: ") + cudaGetErrorString(e));
   return AGILE_OK;
@@ -1445,7 +1459,8 @@ agile_status agile_batch_create(const agile_config* cfgs, int nsolve, const agil
     const agile_config& c = cfgs[i];
     if (c.physics != c0.physics || c.limiter != c0.limiter || c.flux != c0.flux || c.rk != c0.rk ||
         c.real_bytes != c0.real_bytes || c.gamma != c0.gamma || c.cfl != c0.cfl ||
-        c.glm_alpha != c0.glm_alpha || c.eos != c0.eos || c.max_level < 1 || c.max_level > 12 ||
+        c.glm_alpha != c0.glm_alpha || c.eos != c0.eos || c.htc_kappa0 != c0.htc_kappa0 || c.max_level < 1 ||
+        c.max_level > 12 ||
         c.refine_nvars < 0 || c.refine_nvars > 9)
       return AGILE_EINVAL;
     // validate each configuration like a single mesh (host-side checks only)

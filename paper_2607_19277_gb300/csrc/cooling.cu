@@ -186,6 +186,9 @@ cudaError_t launch_cooling(const AuxArgs& a, const CoolDev& c, const void* seg, 
   } else if (a.phys == PH_FFHD) {
     if (a.real_bytes == 8) { using R = double; CALL(FfhdPhys); }
     else { using R = float; CALL(FfhdPhys); }
+  } else if (a.phys == PH_FFHD_HTC) {
+    if (a.real_bytes == 8) { using R = double; CALL(FfhdHtcPhys); }
+    else { using R = float; CALL(FfhdHtcPhys); }
   } else {
     return cudaErrorInvalidValue;
   }

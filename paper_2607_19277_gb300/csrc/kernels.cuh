@@ -38,6 +38,7 @@ struct StageArgs {
   const int* solve_of;          // solve index of each block (batched solves), nullptr = one solve
   int* work;                    // block counter of this launch (zeroed before it), dynamic scheduling
   int grid = 0;                 // persistent CTAs of the launch (0: CTAs-per-SM target x SMs)
+  double htc_kappa0 = 0.0;      // ffhd with conduction: kappa_par = htc_kappa0 T^(5/2)
 };
 
 // Conserved + auxiliary values of the cell (x, y, z) of block b in the halo view: the
@@ -348,6 +349,8 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   constexpr uint32_t PLANE_BYTES = (uint32_t)(sizeof(R) * NT * 256);
   int key_sv = -1, key_lev = -1;
   R idx = R(0), idy = R(0), idz = R(0), rdt = R(0), glm_fr = R(1);
+  R rq4 = R(0);                        // 1 / tau = 1 / (4 dt) of the conduction relaxation
+  const R kap0 = R(A.htc_kappa0);
   R dxr[3] = {R(0), R(0), R(0)};
   if (t == 0 && blockIdx.x < A.nblk) {
 #pragma unroll
@@ -371,6 +374,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     idy = R(1.0 / bd.dx[1]);
     idz = R(1.0 / bd.dx[2]);
     rdt = R(dt);
+    if constexpr (P::QV >= 0) rq4 = R(0.25 / dt);
 #pragma unroll
     for (int d = 0; d < 3; ++d) dxr[d] = R(bd.dx[d]);
     glm_fr = R(1);
@@ -525,8 +529,13 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
 
   R ssum = R(0), smax = R(0);
 
+  R Tkm1 = R(0);   // conduction: T = p / rho of this column at plane k - 1
   for (int k = 0; k < NB; ++k) {
     // ---- phase 1
+    if constexpr (P::QV >= 0) {   // plane k - 1 leaves the primitive ring now
+      const R* r = sPr + (size_t)pslot(k - 1) * NT * 256 + cell2;
+      Tkm1 = rdiv(r[P::IE * 256], r[0]);
+    }
     if (k + 2 <= NB + 1) convert_own(k + 2);
     {
       const R* r = sPr + (size_t)pslot(k) * NT * 256 + cell2;
@@ -565,6 +574,21 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       issue(k + 3);   // slot (k+1)&3: plane k-1's raw data, read by its update before this barrier
     }
     if (k + 1 < NB) prefetch_halo(k + 1);   // the other half of the CTA; sHalo is free now
+    // conduction target kappa0 T^(5/2) b.grad T of cell (tx, ty, k) (Eq. 10): central
+    // differences of T = p / rho over the face neighbours (x, y from the plane buffer, z
+    // from the ring and the carried plane k - 1), b of the cell
+    R htc_g = R(0);
+    if constexpr (P::QV >= 0) {
+      const R* C = sC + (ty + 2) * 20 + tx + 2;
+      auto T_at = [&](int o) { return rdiv(C[P::IE * 400 + o], C[o]); };
+      const R* rp = sPr + (size_t)pslot(k + 1) * NT * 256 + cell2;
+      const R Tc = T_at(0);
+      const R gx = (T_at(1) - T_at(-1)) * (R(0.5) * idx);
+      const R gy = (T_at(20) - T_at(-20)) * (R(0.5) * idy);
+      const R gz = (rdiv(rp[P::IE * 256], rp[0]) - Tkm1) * (R(0.5) * idz);
+      const R bgrad = (C[P::BOFF * 400] * gx + C[(P::BOFF + 1) * 400] * gy) + C[(P::BOFF + 2) * 400] * gz;
+      htc_g = kap0 * (Tc * Tc * rsqrt_(Tc)) * bgrad;
+    }
     // U^n of cell (tx, ty, k) for the stage combine, loaded now so that the face work of
     // this phase covers its latency
     R unk[NV];
@@ -680,6 +704,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
 #pragma unroll
         for (int v = 0; v < NV; ++v) pc[v] = pk[v * 256];
         P::source(L, pc);
+        if constexpr (P::QV >= 0) L[P::QV] = (htc_g - pc[P::QV]) * rq4;   // -(q - target) / tau
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           R val = raw[v * 256];

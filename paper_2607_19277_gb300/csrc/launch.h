@@ -16,6 +16,7 @@ cudaError_t launch_stage_mhd(int real_bytes, int lim, int flux, const StageArgs&
 cudaError_t launch_stage_srhd(int real_bytes, int lim, int flux, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_stage_srhd_synge(int real_bytes, int lim, int flux, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_stage_ffhd(int real_bytes, int lim, int flux, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_stage_ffhd_htc(int real_bytes, int lim, int flux, const StageArgs& a, cudaStream_t s);
 
 struct AuxArgs {
   int phys;                 // PhysKind (PH_SRHD_SYNGE for srhd with the Synge EOS)

@@ -104,6 +104,7 @@ struct HdPhys {
   static constexpr int IV = 1;     // first velocity / momentum component
   static constexpr int NREC = NV;  // reconstructed variables
   static constexpr int FROZEN = NV;  // variables from this index on are never updated
+  static constexpr int QV = -1;      // a variable with no face flux (source-only), or -1
   static constexpr int IE = 4;     // energy in U, pressure in P
   static constexpr bool SOURCE = false;
   static constexpr bool GLM = false;
@@ -162,6 +163,7 @@ struct MhdPhys {
   static constexpr int IV = 1;
   static constexpr int NREC = NV;
   static constexpr int FROZEN = NV;
+  static constexpr int QV = -1;
   static constexpr int IE = 4;
   static constexpr bool SOURCE = false;
   static constexpr bool GLM = true;
@@ -274,6 +276,7 @@ struct SrhdPhysE {
   static constexpr int IV = 1;
   static constexpr int NREC = NV;
   static constexpr int FROZEN = NV;
+  static constexpr int QV = -1;
   static constexpr int IE = 4;
   static constexpr bool SOURCE = false;
   static constexpr bool GLM = false;
@@ -464,14 +467,19 @@ template <typename R> using SrhdSyngePhys = SrhdPhysE<R, EOS_SYNGE>;
 // b_d (rho v, rho v^2 + p, (e + p) v) and b_d for the variable b_d (0 for the other two), so
 // the flux divergence of the b variables is -div b of the same face values; the source
 // p div b of the m_par equation is added from it. TVDLF only (paper Table 1).
-template <typename R>
-struct FfhdPhys {
-  static constexpr int NV = 6;
+// With hyperbolic thermal conduction (HTC, Eqs. 9-10): U = (rho, m_par, e, q_par, b); q_par
+// is reconstructed, has no face flux of its own (no dissipation either) and enters the
+// energy flux as -q_par b_d; its relaxation towards kappa0 T^(5/2) b.grad T over tau = 4 dt
+// is the stage kernel's source term for it.
+template <typename R, bool HTC>
+struct FfhdPhysT {
+  static constexpr int NV = HTC ? 7 : 6;
   static constexpr int NA = 0;
-  static constexpr int BOFF = 3;     // b: swapped with the x/y trick, b_n negated at walls
-  static constexpr int IV = -1;      // no vector velocity
-  static constexpr int NREC = 3;
-  static constexpr int FROZEN = 3;
+  static constexpr int BOFF = HTC ? 4 : 3;   // b: swapped with the x/y trick, b_n negated at walls
+  static constexpr int IV = -1;              // no vector velocity
+  static constexpr int NREC = HTC ? 4 : 3;
+  static constexpr int FROZEN = BOFF;
+  static constexpr int QV = HTC ? 3 : -1;
   static constexpr int IE = 2;
   static constexpr bool SOURCE = true;
   static constexpr bool GLM = false;
@@ -483,9 +491,8 @@ struct FfhdPhys {
     p[0] = rho;
     p[1] = v;
     p[2] = pp.g1 * (u[2] - R(0.5) * rho * v * v);
-    p[3] = u[3];
-    p[4] = u[4];
-    p[5] = u[5];
+#pragma unroll
+    for (int i = 3; i < NV; ++i) p[i] = u[i];
     st |= (!(rho > R(0)) | !(p[2] > R(0))) ? ST_EUNPHYS : 0;
   }
 
@@ -493,28 +500,27 @@ struct FfhdPhys {
     u[0] = p[0];
     u[1] = p[0] * p[1];
     u[2] = p[2] * pp.ig1 + R(0.5) * p[0] * p[1] * p[1];
-    u[3] = p[3];
-    u[4] = p[4];
-    u[5] = p[5];
+#pragma unroll
+    for (int i = 3; i < NV; ++i) u[i] = p[i];
   }
 
   template <int D>
   __device__ static __forceinline__ void flux(const R* p, const R* u, R* f, const PhysParamsT<R>&) {
-    const R b = p[3 + D];
+    const R b = p[BOFF + D];
     const R vb = p[1] * b;
     f[0] = u[0] * vb;
     f[1] = u[1] * vb + p[2] * b;
-    f[2] = (u[2] + p[2]) * vb;
-    f[3] = R(0);
-    f[4] = R(0);
-    f[5] = R(0);
-    f[3 + D] = b;
+    if constexpr (HTC) f[2] = (u[2] + p[2]) * vb - p[3] * b;
+    else f[2] = (u[2] + p[2]) * vb;
+#pragma unroll
+    for (int i = 3; i < NV; ++i) f[i] = R(0);
+    f[BOFF + D] = b;
   }
 
   template <int D>
   __device__ static __forceinline__ void lambdas(const R* p, R& lm, R& lp, const PhysParamsT<R>& pp) {
     const R c = rsqrt_(rdiv(pp.gamma * p[2], p[0]));
-    const R b = p[3 + D];
+    const R b = p[BOFF + D];
     const R a = p[1] * b;
     const R w = c * rabs(b);
     lm = a - w;
@@ -523,16 +529,18 @@ struct FfhdPhys {
 
   template <int D>
   __device__ static __forceinline__ void interface(R* pl, R* pr, const PhysParamsT<R>&) {
-    const R bf = R(0.5) * (pl[3 + D] + pr[3 + D]);
-    pl[3 + D] = bf;
-    pr[3 + D] = bf;
+    const R bf = R(0.5) * (pl[BOFF + D] + pr[BOFF + D]);
+    pl[BOFF + D] = bf;
+    pr[BOFF + D] = bf;
   }
 
-  // L holds -div F of every variable: L[3..5] sum to -div b; adds p div b to m_par.
+  // L holds -div F of every variable: L[BOFF..BOFF+2] sum to -div b; adds p div b to m_par.
   __device__ static __forceinline__ void source(R* L, const R* pcell) {
-    L[1] = L[1] - pcell[2] * ((L[3] + L[4]) + L[5]);
+    L[1] = L[1] - pcell[2] * ((L[BOFF] + L[BOFF + 1]) + L[BOFF + 2]);
   }
 };
+template <typename R> using FfhdPhys = FfhdPhysT<R, false>;
+template <typename R> using FfhdHtcPhys = FfhdPhysT<R, true>;
 
 // Riemann flux at a face from reconstructed primitive states (modified in place).
 template <class P, typename R, int D, int FLUX>
@@ -580,6 +588,7 @@ __device__ __forceinline__ void riemann(R* pl, R* pr, R* f, const PhysParamsT<R>
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       if (v >= P::FROZEN) f[v] = fl[v];   // frozen variables: exact flux, no dissipation
+      else if (v == P::QV) f[v] = R(0);   // no flux term at all
       else f[v] = R(0.5) * (fl[v] + fr[v]) - R(0.5) * c * (ur[v] - ul[v]);
     }
   } else {

@@ -106,3 +106,14 @@ def test_rcp64_selftest_rejects_divisors_outside_its_range(lib, bad):
     with pytest.raises(agile.AgileError) as e:
         agile.check_rcp64(s, a)
     assert e.value.status == 1
+
+
+def test_conduction_config_checked_on_host(lib):
+    """ffhd with conduction: TVDLF only, uniform meshes, a finite kappa0 >= 0."""
+    from paper_2607_19277_gb300 import agile
+    out = C.c_void_p()
+    for kw in (dict(flux="hll"), dict(max_level=2), dict(htc_kappa0=-1.0), dict(htc_kappa0=float("nan"))):
+        args = dict(physics="ffhd_htc", flux="tvdlf", htc_kappa0=0.1)
+        args.update(kw)
+        cfg = agile.make_config(**args)
+        assert lib.agile_mesh_create(C.byref(cfg), None, None, C.byref(out)) == 1, kw
