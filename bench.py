@@ -146,10 +146,10 @@ FP64_LANES = 2       # FP64 FMA lanes per SM on GB300 (1.25 TFLOP/s measured at 
 
 
 # DRAM bytes (read + write) per stage launch of the FP32 MHD stage kernel on this workload,
-# from one ncu capture of the three stage launches of one SSPRK3 step (1.446, 2.109 and
-# 2.050 GB), averaged; valid only while the kernel sources hash to STAGE_SRC_DIGEST.
-STAGE_TRAFFIC_BYTES = (1.4462e9 + 2.1091e9 + 2.0499e9) / 3
-STAGE_SRC_DIGEST = "1e0b4e4d7a3ffbee"
+# from one ncu capture of the three stage launches of one SSPRK3 step (1.443, 2.109 and
+# 2.051 GB), averaged; valid only while the kernel sources hash to STAGE_SRC_DIGEST.
+STAGE_TRAFFIC_BYTES = (1.4427e9 + 2.1088e9 + 2.0514e9) / 3
+STAGE_SRC_DIGEST = "9dfbd0feef2b23e5"
 STAGE_SRC = ("kernels.cuh", "pair.cuh", "physics.cuh", "stage_go.cuh", "stage_mhd.cu")
 
 
@@ -451,32 +451,40 @@ def run_batched_amr(nsolve=16, steps=20, regrid_every=10):
     return out
 
 
-def run_ffhd(steps=20, warmup=3):
+def run_ffhd(steps=20, warmup=3, kappa0=1e-3):
     """Frozen-field hydrodynamics (Section 2.3.2) on a periodic 256^3 grid of 16^3 blocks
-    in a sheared frozen field, TVDLF, van Leer, SSPRK3, FP32 stencil, without and with the
-    radiative losses (the paper compares these configurations for its FFHD case on an H100,
-    Section 4.4; it reports relative costs, not this grid)."""
+    in a sheared frozen field, TVDLF, van Leer, SSPRK3, FP32 stencil: without source terms,
+    with radiative losses, with hyperbolic thermal conduction (kappa0 T^(5/2), tau = 4 dt) and
+    with both (the paper compares these four configurations for its FFHD case on an H100 and
+    reports 10.2%, 21.8% and 29.4% lower throughput for losses, conduction and both, Section
+    4.4; it reports relative costs, not this grid)."""
     import torch
     from paper_2607_19277_gb300 import agile, workloads as W
     T, L = W.skew_normal_cooling(n=256, t_min=5e-2, t_max=1e2, t_peak=1.0, peak=0.5)
 
-    def ic(x, y, z):
-        th = 0.7 * np.sin(2 * math.pi * x) + 0.5 * np.cos(2 * math.pi * (y + z))
-        p = np.zeros((6,) + np.shape(x))
-        p[0] = 1.0 + 0.3 * np.sin(2 * math.pi * (x + 2 * y)) * np.cos(2 * math.pi * z)
-        p[1] = 0.4 * np.cos(2 * math.pi * (x - y))
-        p[2] = 1.0 + 0.2 * np.sin(2 * math.pi * (y + z))
-        p[3] = np.cos(th) * np.cos(0.3 * th)
-        p[4] = np.sin(th) * np.cos(0.3 * th)
-        p[5] = np.sin(0.3 * th)
-        return p
-    out = {"workload": "ffhd 256^3 (4096 x 16^3) sheared frozen field, tvdlf vanleer ssprk3, fp32"}
-    for name, cool in (("plain", False), ("losses", True)):
-        m = agile.Mesh(agile.make_config(physics="ffhd", limiter="vanleer", flux="tvdlf", rk=3, real_bytes=4,
+    def ic(nv):
+        def f(x, y, z):
+            th = 0.7 * np.sin(2 * math.pi * x) + 0.5 * np.cos(2 * math.pi * (y + z))
+            p = np.zeros((nv,) + np.shape(x))
+            p[0] = 1.0 + 0.3 * np.sin(2 * math.pi * (x + 2 * y)) * np.cos(2 * math.pi * z)
+            p[1] = 0.4 * np.cos(2 * math.pi * (x - y))
+            p[2] = 1.0 + 0.2 * np.sin(2 * math.pi * (y + z))
+            o = nv - 3                      # the frozen field follows q_par when present
+            p[o] = np.cos(th) * np.cos(0.3 * th)
+            p[o + 1] = np.sin(th) * np.cos(0.3 * th)
+            p[o + 2] = np.sin(0.3 * th)
+            return p
+        return f
+    out = {"workload": "ffhd 256^3 (4096 x 16^3) sheared frozen field, tvdlf vanleer ssprk3, fp32; "
+                       "conduction kappa0 = %g" % kappa0}
+    for name, cool, htc in (("plain", False, False), ("losses", True, False), ("conduction", False, True),
+                            ("both", True, True)):
+        m = agile.Mesh(agile.make_config(physics="ffhd_htc" if htc else "ffhd", htc_kappa0=kappa0 if htc else 0.0,
+                                         limiter="vanleer", flux="tvdlf", rk=3, real_bytes=4,
                                          base_blocks=(N_SIDE // 16,) * 3))
         if cool:
             m.set_cooling(T, L)
-        m.set_state(ic)
+        m.set_state(ic(7 if htc else 6))
         for _ in range(warmup):
             m.step(0.0)
         m.sync()
@@ -490,7 +498,9 @@ def run_ffhd(steps=20, warmup=3):
         ms = e0.elapsed_time(e1) / steps
         m.close()
         out[name] = {"value": float(N_SIDE ** 3) * 3 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms}
-    out["throughput_reduction_with_losses"] = 1.0 - out["plain"]["ms_per_step"] / out["losses"]["ms_per_step"]
+    for name in ("losses", "conduction", "both"):
+        out["throughput_reduction_" + name] = 1.0 - out["plain"]["ms_per_step"] / out[name]["ms_per_step"]
+    out["paper_h100_reduction"] = {"losses": 0.102, "conduction": 0.218, "both": 0.294}
     return out
 
 
