@@ -148,6 +148,16 @@ agile_status agile_set_state(agile_mesh* mesh, agile_ic_fn ic, void* user);
  * primitive recovery starts from the bracket midpoint). */
 agile_status agile_set_state_blocks(agile_mesh* mesh, const double* cons, size_t nblk);
 
+/* Initial state from primitive values on the host (Fig. 1, the values an agile_ic_fn
+ * returns, evaluated by the caller): prim[nblk][nvar][16][16][16], FP64, the blocks in the
+ * mesh's block order (see Conventions; after creation the level-1 blocks in Morton order),
+ * nvar primitives per cell: hd 5 (rho, v, p), mhd 9 (rho, v, p, B, psi), srhd 5 (rho,
+ * u = Gamma v, p), ffhd 6 (rho, v_par, p, b), ffhd_htc 7 (rho, v_par, p, q_par, b).
+ * Converted to conserved variables on the device. nblk must equal the mesh's block count
+ * (AGILE_EINVAL otherwise). No callback is kept: agile_regrid(init=1) then has nothing to
+ * re-evaluate new blocks with and fills them by prolongation like init=0. */
+agile_status agile_set_state_prims(agile_mesh* mesh, const double* prim, size_t nblk);
+
 /* Global CFL time step of the current state ("Set dt", Fig. 2):
  * dt = cfl / max over leaf cells of sum_d (|v_d| + c_d) / dx_d, with c_d the sound speed
  * (hd), the fast magnetosonic speed along d (mhd) or the largest |characteristic speed|
@@ -285,6 +295,9 @@ agile_status agile_batch_layout(agile_batch* batch, int solve, size_t* nblocks, 
 
 /* Initial condition of one solve (as agile_set_state). Synchronises. */
 agile_status agile_batch_set_state(agile_batch* batch, int solve, agile_ic_fn ic, void* user);
+
+/* agile_set_state_prims for solve `solve` of a batch (its blocks in the solve's order). */
+agile_status agile_batch_set_state_prims(agile_batch* batch, int solve, const double* prim, size_t nblk);
 
 /* One full SSPRK step of every solve with its own on-device CFL dt (as agile_step(dt <= 0)).
  * The first call runs eagerly; later calls launch one captured CUDA graph. Asynchronous. */

@@ -29,6 +29,7 @@ STATUS = {0: "AGILE_OK", 1: "AGILE_EINVAL", 2: "AGILE_ENOMEM", 3: "AGILE_EBUDGET
 
 # Symbols declared in include/agile.h (checked by the CPU test suite).
 EXPORTS = ["agile_mesh_create", "agile_mesh_destroy", "agile_set_state", "agile_set_state_blocks",
+           "agile_set_state_prims", "agile_batch_set_state_prims",
            "agile_cfl_dt", "agile_max_speeds", "agile_step", "agile_regrid", "agile_regrid_flags", "agile_get_layout",
            "agile_get_state", "agile_get_aux", "agile_conserved_sums",
            "agile_conserved_sums_noalloc", "agile_set_cooling", "agile_estimate",
@@ -87,6 +88,8 @@ def load(path: str = LIB_PATH):
         "agile_mesh_destroy": (None, [P]),
         "agile_set_state": (C.c_int, [P, IC_FN, P]),
         "agile_set_state_blocks": (C.c_int, [P, dp, C.c_size_t]),
+        "agile_set_state_prims": (C.c_int, [P, dp, C.c_size_t]),
+        "agile_batch_set_state_prims": (C.c_int, [P, C.c_int, dp, C.c_size_t]),
         "agile_cfl_dt": (C.c_int, [P, dp]),
         "agile_max_speeds": (C.c_int, [P, dp, dp]),
         "agile_step": (C.c_int, [P, C.c_double]),
@@ -281,6 +284,13 @@ class Mesh:
         cons = np.ascontiguousarray(cons, dtype=np.float64)
         self._ck(self.lib.agile_set_state_blocks(self.ptr, _dptr(cons), cons.shape[0]))
 
+    def set_state_prims(self, prim):
+        """Primitive values prim[nblk, nvar, 16, 16, 16] in the mesh's block order (see
+        level1_cell_centres), converted to conserved variables on the device."""
+        prim = np.ascontiguousarray(prim, dtype=np.float64)
+        self._ic = None
+        self._ck(self.lib.agile_set_state_prims(self.ptr, _dptr(prim), prim.shape[0]))
+
     def cfl_dt(self) -> float:
         dt = C.c_double()
         self._ck(self.lib.agile_cfl_dt(self.ptr, C.byref(dt)))
@@ -373,6 +383,50 @@ class Mesh:
         return ms.value, n.value, tot.value
 
 
+def morton3(i, j, k):
+    """Morton (Z-order) key of integer block coordinates, x in the lowest bit of each triple
+    (the library's block order within a level); numpy arrays or ints."""
+    i, j, k = (np.asarray(a, dtype=np.int64) for a in (i, j, k))
+    key = np.zeros(np.broadcast(i, j, k).shape, dtype=np.int64)
+    for b in range(21):
+        key |= ((i >> b) & 1) << (3 * b)
+        key |= ((j >> b) & 1) << (3 * b + 1)
+        key |= ((k >> b) & 1) << (3 * b + 2)
+    return key
+
+
+def level1_cell_centres(cfg: agile_config):
+    """Cell centres (x, y, z), each of shape (nblk, 16, 16, 16), of a mesh of level-1 blocks
+    in the library's block order (Morton order of the block coordinates) with cells [z][y][x],
+    computed as the library computes them, so that ic(x, y, z) here gives the primitives
+    agile_set_state would ask the callback for."""
+    nb = [int(cfg.base_blocks[d]) for d in range(3)]
+    bk, bj, bi = np.meshgrid(np.arange(nb[2]), np.arange(nb[1]), np.arange(nb[0]), indexing="ij")
+    bi, bj, bk = bi.ravel(), bj.ravel(), bk.ravel()
+    order = np.argsort(morton3(bi, bj, bk), kind="stable")
+    bi, bj, bk = bi[order], bj[order], bk[order]
+    c = np.arange(16)
+    out = []
+    for d, bb in enumerate((bi, bj, bk)):
+        dx = (cfg.xmax[d] - cfg.xmin[d]) / (float(nb[d]) * 16 * 1.0)
+        idx = (bb[:, None] * 16 + c[None, :]).astype(np.float64) + 0.5      # (nblk, 16)
+        v = cfg.xmin[d] + idx * dx
+        shape = [len(bb), 1, 1, 1]
+        shape[3 - d] = 16
+        out.append(np.broadcast_to(v.reshape(shape), (len(bb), 16, 16, 16)))
+    return out[0], out[1], out[2]
+
+
+def prims_of(ic, cfg: agile_config):
+    """ic evaluated once at every cell centre of a level-1 mesh: prim[nblk, nvar, 16, 16, 16]
+    in block order (the argument of Mesh.set_state_prims)."""
+    x, y, z = level1_cell_centres(cfg)
+    nblk = x.shape[0]
+    p = np.asarray(ic(x.ravel(), y.ravel(), z.ravel()), dtype=np.float64)
+    nvar = p.shape[0]
+    return np.ascontiguousarray(p.reshape(nvar, nblk, 16, 16, 16).transpose(1, 0, 2, 3, 4))
+
+
 def _ic_callback(ic, nvar):
     def cb(x, y, z, n, prim, user):
         xs = np.ctypeslib.as_array(x, shape=(n,)).copy()
@@ -430,6 +484,11 @@ class Batch:
         cb = _ic_callback(ic, self.nvar)
         self._ics[solve] = cb
         self._ck(self.lib.agile_batch_set_state(self.ptr, solve, cb, None))
+
+    def set_state_prims(self, solve, prim):
+        prim = np.ascontiguousarray(prim, dtype=np.float64)
+        self._ics.pop(solve, None)
+        self._ck(self.lib.agile_batch_set_state_prims(self.ptr, solve, _dptr(prim), prim.shape[0]))
 
     def step(self):
         self._ck(self.lib.agile_batch_step(self.ptr))

@@ -250,7 +250,10 @@ agile_status fill_ghosts(agile_mesh* m, void* U) {
 
 // Evaluate the initial condition on the listed blocks (host callback, then prim -> cons on
 // the device), in chunks to bound host and device staging.
-agile_status apply_ic(agile_mesh* m, void* U, const std::vector<int>& blocks) {
+// Initial state of the listed blocks: primitives from the mesh's callback at the cell centres,
+// or (prim_src non-null) from the host array prim_src[i][nv][16^3] for the i-th listed
+// block; converted to conserved variables on the device.
+agile_status apply_ic(agile_mesh* m, void* U, const std::vector<int>& blocks, const double* prim_src = nullptr) {
   const int chunk = 256;
   std::vector<double> prim((size_t)chunk * m->nv * NCELL);
   std::vector<double> xs(NCELL), ys(NCELL), zs(NCELL);
@@ -260,7 +263,7 @@ agile_status apply_ic(agile_mesh* m, void* U, const std::vector<int>& blocks) {
   const auto& keys = m->mesh->blocks();
   for (size_t c0 = 0; c0 < blocks.size(); c0 += chunk) {
     const int n = (int)std::min(blocks.size() - c0, (size_t)chunk);
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < n && !prim_src; ++i) {
       const Key& k = keys[blocks[c0 + i]];
       const double dx = m->mesh->dx(k.lev, 0), dy = m->mesh->dx(k.lev, 1), dz = m->mesh->dx(k.lev, 2);
       for (int z = 0; z < NB; ++z)
@@ -273,7 +276,8 @@ agile_status apply_ic(agile_mesh* m, void* U, const std::vector<int>& blocks) {
           }
       m->ic(xs.data(), ys.data(), zs.data(), NCELL, prim.data() + (size_t)i * m->nv * NCELL, m->ic_user);
     }
-    CK(m, cudaMemcpyAsync(d_prim, prim.data(), (size_t)n * m->nv * NCELL * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+    const double* src = prim_src ? prim_src + c0 * m->nv * NCELL : prim.data();
+    CK(m, cudaMemcpyAsync(d_prim, src, (size_t)n * m->nv * NCELL * sizeof(double), cudaMemcpyHostToDevice, m->stream));
     CK(m, cudaMemcpyAsync(d_blocks, blocks.data() + c0, n * sizeof(int), cudaMemcpyHostToDevice, m->stream));
     AuxArgs a = aux_args(m, U);
     CK(m, launch_prim2cons(a, d_prim, d_blocks, n, m->stream));
@@ -518,6 +522,19 @@ agile_status agile_set_state_blocks(agile_mesh* m, const double* cons, size_t nb
   dfree_t(m, d);
   m->speeds_valid = false;
   return AGILE_OK;
+}
+
+agile_status agile_set_state_prims(agile_mesh* m, const double* prim, size_t nblk) {
+  if (!m || !prim) return fail(m, AGILE_EINVAL, "null argument");
+  if ((int)nblk != m->nblk) return fail(m, AGILE_EINVAL, "block count does not match the mesh");
+  std::vector<int> all(nblk);
+  for (size_t i = 0; i < nblk; ++i) all[i] = (int)i;
+  m->ic = nullptr;      // no callback for later regrid(init=1) re-evaluation
+  m->ic_user = nullptr;
+  agile_status s = apply_ic(m, m->U[0], all, prim);
+  if (s) return s;
+  m->speeds_valid = false;
+  return check_status(m);
 }
 
 agile_status agile_cfl_dt(agile_mesh* m, double* dt_out) {
@@ -1579,6 +1596,29 @@ agile_status agile_batch_set_state(agile_batch* B, int solve, agile_ic_fn ic, vo
   if (s) return bfail(B, s, view.err);
   B->ics[solve] = ic;
   B->ic_users[solve] = user;
+  B->speeds_valid = false;
+  return batch_status(B);
+}
+
+agile_status agile_batch_set_state_prims(agile_batch* B, int solve, const double* prim, size_t nblk) {
+  if (!B || !prim || solve < 0 || solve >= B->nsolve) return bfail(B, AGILE_EINVAL, "bad argument");
+  if (nblk != B->meshes[solve]->blocks().size()) return bfail(B, AGILE_EINVAL, "block count does not match the solve");
+  agile_mesh view;
+  as_mesh_view(B, &view);
+  view.mesh = B->meshes[solve];
+  view.cfg = B->cfgs[solve];
+  view.ic = nullptr;
+  view.ic_user = nullptr;
+  view.d_status = B->d_status;
+  std::vector<int> local(nblk);
+  for (size_t i = 0; i < nblk; ++i) local[i] = (int)i;
+  char* base = (char*)B->U[0] + (size_t)B->offset[solve] * B->nt * NCELL * B->rb;
+  view.nblk = (int)nblk;
+  agile_status s = apply_ic(&view, base, local, prim);
+  view.mesh = nullptr;
+  if (s) return bfail(B, s, view.err);
+  B->ics[solve] = nullptr;
+  B->ic_users[solve] = nullptr;
   B->speeds_valid = false;
   return batch_status(B);
 }

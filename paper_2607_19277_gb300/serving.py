@@ -4,9 +4,13 @@ Requests (physics, grid side, number of steps, seeded initial condition) arrive 
 The loop admits a waiting request as soon as its device pools fit in the budget, keeps the
 pools of every admitted solve resident, and advances all admitted solves together: each
 solve runs on its own CUDA stream, so the stage kernels of different requests overlap on the
-GPU while the host thread only enqueues work. A finished solve's result is read back and its
-memory returns to the budget, which admits the next arrivals. Latency = completion time -
-arrival time; the report gives p50 / p99 latency beside the aggregate zone-updates/s.
+GPU while the host thread only enqueues work. A request's initial condition is evaluated on
+the host by a pool of worker threads as soon as it arrives (numpy releases the interpreter
+lock in its array arithmetic), so that admission only uploads the primitives
+(agile_set_state_prims) and the loop thread keeps the GPU fed. A finished solve's result is
+read back and its memory returns to the budget, which admits the next arrivals. Latency =
+completion time - arrival time; the report gives p50 / p99 latency beside the aggregate
+zone-updates/s.
 
 Every numerical step runs in libagile.so (agile_step with the on-device CFL dt); this module
 only schedules. A solve's result does not depend on what else is running (the kernels of
@@ -16,6 +20,7 @@ from __future__ import annotations
 
 import math
 import time
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -77,6 +82,39 @@ def request_stream(n: int, rate: float, sides=(32, 64, 128, 256), steps=(50, 500
     return out
 
 
+def prepare(req: Request, real_bytes: int):
+    """Primitives of the request's initial condition at every cell, in block order."""
+    return agile.prims_of(initial_condition(req), scheme(req.physics, real_bytes, req.side))
+
+
+class _Preparer:
+    """Initial conditions evaluated ahead by worker threads, at most `limit` held at once."""
+
+    def __init__(self, workers: int, limit: int, real_bytes: int):
+        self.pool = ThreadPoolExecutor(max_workers=max(1, workers))
+        self.limit = max(1, limit)
+        self.rb = real_bytes
+        self.futs = {}
+
+    def feed(self, waiting):
+        """Starts the preparation of the earliest waiting requests up to the limit."""
+        for r in waiting:
+            if len(self.futs) >= self.limit:
+                break
+            if r.rid not in self.futs:
+                self.futs[r.rid] = self.pool.submit(prepare, r, self.rb)
+
+    def ready(self, r) -> bool:
+        f = self.futs.get(r.rid)
+        return f is not None and f.done()
+
+    def take(self, r):
+        return self.futs.pop(r.rid).result()
+
+    def close(self):
+        self.pool.shutdown(wait=True)
+
+
 def pool_bytes(req: Request, real_bytes: int) -> int:
     """Device bytes a resident solve holds: its state pools (rk + 1 buffers incl. U^n ...
     one per stage input) plus per-block descriptors and staging, rounded up generously."""
@@ -112,13 +150,15 @@ class Server:
     """Continuous admission of solves against a device-memory budget (bytes)."""
 
     def __init__(self, budget_bytes: int, real_bytes: int = 4, steps_per_poll: int = 4,
-                 keep_results: bool = False):
+                 keep_results: bool = False, prepare_workers: int = 8, max_prepared: int = 16):
         import torch
         self.torch = torch
         self.budget = int(budget_bytes)
         self.rb = real_bytes
         self.steps_per_poll = steps_per_poll
         self.keep = keep_results
+        self.workers = prepare_workers
+        self.max_prepared = max_prepared
 
     def run(self, requests, time_scale: float = 1.0, max_wall_s: float = 3600.0) -> Report:
         """Serve `requests` (arrival times scaled by time_scale); returns the report.
@@ -127,6 +167,14 @@ class Server:
         pending = sorted(requests, key=lambda r: r.arrival)
         waiting = []
         active = []            # [req, mesh, stream, steps_left, done_event]
+        prep = _Preparer(self.workers, self.max_prepared, self.rb)
+        try:
+            return self._loop(pending, waiting, active, prep, requests, time_scale, max_wall_s)
+        finally:
+            prep.close()
+
+    def _loop(self, pending, waiting, active, prep, requests, time_scale, max_wall_s):
+        torch = self.torch
         used = 0
         max_used = 0
         max_conc = 0
@@ -142,18 +190,21 @@ class Server:
             while k < len(pending) and pending[k].arrival * time_scale <= now:
                 waiting.append(pending[k])
                 k += 1
-            # admit in arrival order while the budget allows (first fit keeps order fair)
+            prep.feed(waiting)
+            # admit in arrival order among the prepared requests while the budget allows
             i = 0
             while i < len(waiting):
                 r = waiting[i]
                 need = pool_bytes(r, self.rb)
                 if need > self.budget:
                     raise ValueError("request %d needs %d bytes, more than the budget" % (r.rid, need))
-                if used + need <= self.budget:
+                if used + need <= self.budget and prep.ready(r):
+                    prims = prep.take(r)
                     stream = torch.cuda.Stream()
                     with torch.cuda.stream(stream):
                         mesh = agile.Mesh(scheme(r.physics, self.rb, r.side), stream=stream)
-                        mesh.set_state(initial_condition(r))
+                        mesh.set_state_prims(prims)
+                    del prims
                     r.admitted = time.perf_counter() - t0
                     active.append([r, mesh, stream, r.steps, None])
                     used += need
@@ -163,7 +214,9 @@ class Server:
                 i += 1
             max_conc = max(max_conc, len(active))
             if not active:
-                if k < len(pending):
+                if waiting:
+                    time.sleep(0.0005)         # preparations in flight
+                elif k < len(pending):
                     time.sleep(max(0.0, pending[k].arrival * time_scale - (time.perf_counter() - t0)))
                 continue
             # enqueue a few steps of every active solve, each on its own stream
@@ -223,14 +276,18 @@ class BatchedServer:
     device (agile_batch_copy_solve) and the newcomers' initial conditions are loaded. A
     rebuild happens at most every `rebuild_every` steps of the group (sooner when the group
     is empty); a solve that reaches its step count is read out at once, so every result is
-    the state after exactly its requested steps, equal to the same request run alone."""
+    the state after exactly its requested steps, equal to the same request run alone.
+    Initial conditions are prepared ahead by worker threads as for Server."""
 
     def __init__(self, budget_bytes: int, real_bytes: int = 4, rebuild_every: int = 4,
-                 keep_results: bool = False):
+                 keep_results: bool = False, prepare_workers: int = 8, max_prepared: int = 16):
         self.budget = int(budget_bytes)
         self.rb = real_bytes
         self.rebuild_every = max(1, int(rebuild_every))
         self.keep = keep_results
+        self.workers = prepare_workers
+        self.max_prepared = max_prepared
+        self._prims = {}
 
     def _rebuild(self, g):
         """New batch for the group's members: survivors copied, newcomers initialised.
@@ -252,7 +309,7 @@ class BatchedServer:
                 if old is not None and r.rid in old_index:
                     nb.copy_solve(i, old, old_index[r.rid])
                 else:
-                    nb.set_state(i, initial_condition(r))
+                    nb.set_state_prims(i, self._prims.pop(r.rid))
             g["batch"], g["index"] = nb, index
         if old is not None:
             old.close()
@@ -262,6 +319,14 @@ class BatchedServer:
         """Serve `requests`; the budget counts the pools of every solve still held by a batch
         (a finished solve's pool is released when its batch is rebuilt; during a rebuild the
         old and the new batch coexist briefly)."""
+        prep = _Preparer(self.workers, self.max_prepared, self.rb)
+        try:
+            return self._loop(requests, time_scale, max_wall_s, prep)
+        finally:
+            prep.close()
+            self._prims.clear()
+
+    def _loop(self, requests, time_scale, max_wall_s, prep):
         pending = sorted(requests, key=lambda r: r.arrival)
         waiting = []
         groups = {p: {"batch": None, "index": {}, "members": [], "joining": [], "done": set(),
@@ -287,13 +352,15 @@ class BatchedServer:
             while k < len(pending) and pending[k].arrival * time_scale <= now:
                 waiting.append(pending[k])
                 k += 1
+            prep.feed(waiting)
             i = 0
-            while i < len(waiting):         # admit in arrival order while the budget allows
+            while i < len(waiting):         # admit prepared requests in arrival order while the budget allows
                 r = waiting[i]
                 need = pool_bytes(r, self.rb)
                 if need > self.budget:
                     raise ValueError("request %d needs %d bytes, more than the budget" % (r.rid, need))
-                if used + need <= self.budget:
+                if used + need <= self.budget and prep.ready(r):
+                    self._prims[r.rid] = prep.take(r)
                     g = groups[r.physics]
                     g["joining"].append(r)
                     g["left"][r.rid] = r.steps
@@ -327,8 +394,11 @@ class BatchedServer:
                         stages = 2 if r.physics == "srhd" else 3
                         zones += float(r.side ** 3) * stages * r.steps
                         g["done"].add(r.rid)
-            if not stepped and not waiting and k < len(pending):
-                time.sleep(max(0.0, pending[k].arrival * time_scale - (time.perf_counter() - t0)))
+            if not stepped:
+                if waiting:
+                    time.sleep(0.0005)         # preparations in flight
+                elif k < len(pending):
+                    time.sleep(max(0.0, pending[k].arrival * time_scale - (time.perf_counter() - t0)))
         for g in groups.values():
             if g["batch"] is not None:
                 g["batch"].close()

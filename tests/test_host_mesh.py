@@ -113,3 +113,23 @@ def test_host_mesh_matches_oracle_tree(shim, seed, base, bc):
         assert nslots == n_cf
     finally:
         shim.shim_destroy(h)
+
+
+@pytest.mark.parametrize("base", [(3, 2, 4), (4, 4, 4), (1, 5, 2)])
+def test_level1_cell_centres_follow_the_host_block_order(shim, base):
+    """The binding's cell centres for set_state_prims follow the library's block order (the
+    host octree's level-1 blocks) and its centre formula."""
+    from paper_2607_19277_gb300 import agile
+    h = shim.shim_create((C.c_int * 3)(*base), 1, (C.c_int * 6)(*([0] * 6)))
+    blocks = _host_blocks(shim, h)
+    shim.shim_destroy(h)
+    cfg = agile.make_config(base_blocks=base, xmin=(-0.3, 0.1, 2.0), xmax=(0.7, 0.9, 5.0))
+    x, y, z = agile.level1_cell_centres(cfg)
+    assert x.shape == (len(blocks), 16, 16, 16)
+    for b, (lev, i, j, k) in enumerate(blocks):
+        assert lev == 1
+        for arr, d, bc in ((x, 0, i), (y, 1, j), (z, 2, k)):
+            dx = (cfg.xmax[d] - cfg.xmin[d]) / (float(base[d]) * 16 * 1.0)
+            ref = cfg.xmin[d] + (np.arange(bc * 16, bc * 16 + 16, dtype=np.float64) + 0.5) * dx
+            line = {0: arr[b, 3, 5, :], 1: arr[b, 3, :, 5], 2: arr[b, :, 3, 5]}[d]
+            assert np.array_equal(line, ref), (b, d)

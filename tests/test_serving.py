@@ -54,6 +54,9 @@ def test_server_loop_terminates_without_gpu_work(monkeypatch):
         def set_state(self, ic):
             pass
 
+        def set_state_prims(self, prim):
+            pass
+
         def step(self, dt=0.0):
             self.steps += 1
 
@@ -92,6 +95,7 @@ def test_server_loop_terminates_without_gpu_work(monkeypatch):
                     return False
 
     monkeypatch.setattr(serving.agile, "Mesh", FakeMesh)
+    monkeypatch.setattr(serving, "prepare", lambda r, rb: np.zeros(1))
     reqs = serving.request_stream(20, rate=5000.0, sides=(32, 64), steps=(2, 5))
     srv = serving.Server.__new__(serving.Server)
     srv.torch = FakeTorch
@@ -99,6 +103,8 @@ def test_server_loop_terminates_without_gpu_work(monkeypatch):
     srv.rb = 4
     srv.steps_per_poll = 2
     srv.keep = False
+    srv.workers = 2
+    srv.max_prepared = 3
     rep = srv.run(reqs, max_wall_s=30.0)
     assert all(r.finished >= 0 for r in reqs)
     assert rep.max_resident_bytes <= srv.budget and rep.max_concurrent >= 1
@@ -138,6 +144,9 @@ def test_batched_server_reads_each_solve_at_its_step_count(monkeypatch):
         def set_state(self, i, ic):
             self.n[i] = 0
 
+        def set_state_prims(self, i, prim):
+            self.n[i] = 0
+
         def step(self):
             self.n = [v + 1 for v in self.n]
 
@@ -149,6 +158,7 @@ def test_batched_server_reads_each_solve_at_its_step_count(monkeypatch):
 
     monkeypatch.setattr(serving.agile, "Batch", FakeBatch)
     monkeypatch.setattr(serving, "initial_condition", lambda r: None)
+    monkeypatch.setattr(serving, "prepare", lambda r, rb: np.zeros(1))
     reqs = serving.request_stream(30, rate=3000.0, sides=(32, 64), steps=(2, 9))
     budget = 4 * max(serving.pool_bytes(r, 4) for r in reqs)
     srv = serving.BatchedServer(budget, real_bytes=4, rebuild_every=3, keep_results=True)
