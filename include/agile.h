@@ -210,7 +210,10 @@ agile_status agile_get_aux(agile_mesh* mesh, double* aux);
  * U * cell volume; the paper's high-cadence mass/energy log, Section 4.1): per block on the
  * device (FP32 pools: each thread's values added in FP32 with the exact error of every
  * addition kept, then FP64), then a deterministic compensated (Neumaier) total over the
- * blocks on the device; only the nvar totals come back. Synchronises. */
+ * blocks on the device; only the nvar totals come back. The device scratch (nblk x nvar + 16
+ * doubles) is allocated at the first call, kept by the mesh for later calls (a diagnostic
+ * read every step allocates nothing after the first), grown when the mesh grows and freed
+ * with the mesh. Synchronises. */
 agile_status agile_conserved_sums(agile_mesh* mesh, double* sums);
 
 /* Conserved sums like agile_conserved_sums, for callers that cannot allocate device memory

@@ -56,6 +56,8 @@ struct agile_mesh {
   long long stage_launches = 0, total_launches = 0;
   CoolHost cool;                    // radiative-loss table (nseg == 0: no losses)
   void* d_cool = nullptr;           // its segments in the stencil precision
+  double* d_sums = nullptr;         // per-block sums and totals of agile_conserved_sums (kept)
+  size_t d_sums_cap = 0;            // its capacity in doubles
 };
 
 namespace {
@@ -487,6 +489,7 @@ void agile_mesh_destroy(agile_mesh* m) {
   dfree_t(m, m->d_speeds);
   dfree_t(m, m->d_dtch);
   dfree_t(m, m->d_work);
+  dfree_t(m, m->d_sums);
   dfree_t(m, m->d_vars);
   dfree_t(m, m->d_weights);
   dfree(m, m->d_cool);
@@ -782,17 +785,21 @@ agile_status agile_get_aux(agile_mesh* m, double* aux) {
 agile_status agile_conserved_sums(agile_mesh* m, double* sums) {
   if (!m || !sums) return fail(m, AGILE_EINVAL, "null argument");
   const size_t np = (size_t)m->nblk * m->nv;
-  double* d = (double*)dalloc(m, (np + 16) * sizeof(double));
-  if (!d) return fail(m, AGILE_ENOMEM, "device allocation failed");
+  if (m->d_sums_cap < np + 16) {     // the scratch is kept between calls (a diagnostic per step)
+    dfree_t(m, m->d_sums);
+    m->d_sums_cap = 0;
+    m->d_sums = (double*)dalloc(m, (np + 16) * sizeof(double));
+    if (!m->d_sums) return fail(m, AGILE_ENOMEM, "device allocation failed");
+    m->d_sums_cap = np + 16;
+  }
+  double* d = m->d_sums;
   AuxArgs a = aux_args(m, m->U[0]);
   CK(m, launch_sums(a, d, m->stream));
-  sums_total_kernel<<<1, 256, 0, m->stream>>>(d, m->nblk, m->nv, d + np);
+  sums_total_kernel<<<m->nv, 256, 0, m->stream>>>(d, m->nblk, m->nv, d + np);
   CK(m, cudaGetLastError());
   m->total_launches += 2;
   CK(m, cudaMemcpyAsync(sums, d + np, m->nv * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
-  agile_status s = check_status(m);
-  dfree_t(m, d);
-  return s;
+  return check_status(m);
 }
 
 agile_status agile_get_halo(agile_mesh* m, size_t block, double* out) {
@@ -885,15 +892,17 @@ cudaError_t noalloc_scratch(double** out) {
 
 }  // namespace
 
-// Totals over the per-block sums: thread i of one CTA of 256 sums blocks i, i + 256, ... with
-// Neumaier compensation, then the 256 (sum, compensation) pairs merge in a fixed tree whose
-// every addition keeps its exact error (TwoSum). Deterministic; agile_conserved_sums and
-// agile_conserved_sums_noalloc both use it, so their results agree bit for bit.
+// Totals over the per-block sums, one CTA of 256 threads per variable (launched with nv CTAs):
+// thread i sums blocks i, i + 256, ... with Neumaier compensation, then the 256 (sum,
+// compensation) pairs merge in a fixed tree whose every addition keeps its exact error
+// (TwoSum). Deterministic; agile_conserved_sums and agile_conserved_sums_noalloc both use it,
+// so their results agree bit for bit.
 __global__ void __launch_bounds__(256) sums_total_kernel(const double* part, int nblk, int nv,
                                                          double* totals) {
   __shared__ double ss[256], sc[256];
   const int t = threadIdx.x;
-  for (int v = 0; v < nv; ++v) {
+  {
+    const int v = blockIdx.x;
     double sum = 0.0, comp = 0.0;
     for (int b = t; b < nblk; b += 256) {
       const double x = part[(size_t)b * nv + v];
@@ -917,7 +926,6 @@ __global__ void __launch_bounds__(256) sums_total_kernel(const double* part, int
       __syncthreads();
     }
     if (t == 0) totals[v] = __dadd_rn(ss[0], sc[0]);
-    __syncthreads();
   }
 }
 
@@ -932,7 +940,7 @@ extern "C" agile_status agile_conserved_sums_noalloc(agile_mesh* m, double* sums
   CK(m, noalloc_scratch(&scratch));
   AuxArgs a = aux_args(m, m->U[0]);
   CK(m, launch_sums(a, scratch, m->stream));
-  sums_total_kernel<<<1, 256, 0, m->stream>>>(scratch, m->nblk, m->nv, scratch + NOALLOC_TOTALS);
+  sums_total_kernel<<<m->nv, 256, 0, m->stream>>>(scratch, m->nblk, m->nv, scratch + NOALLOC_TOTALS);
   CK(m, cudaGetLastError());
   m->total_launches += 2;
   CK(m, cudaMemcpyAsync(sums, scratch + NOALLOC_TOTALS, m->nv * sizeof(double), cudaMemcpyDeviceToHost,
