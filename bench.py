@@ -171,6 +171,17 @@ def alu_peak_tflops(lanes, mhz):
     return SMS * lanes * 2 * mhz * 1e6 / 1e12
 
 
+def ghost_inflated_bytes_per_zone(nvar, w, rk):
+    """Bytes per zone-update of a storage scheme with 20^3 ghost-cell block arrays (the paper's
+    layout, Section 3.1): the algorithmic bytes plus, per stage, the halo part of the stage
+    input read (8000 / 4096 - 1 of the interior), the ghost-cell writes of the fill (3904 /
+    4096) and the reads that fill them (as many). This build reads same-level halos in place
+    and writes no ghost cells on uniform grids; the figure says what a ghost-copy
+    implementation must move for the same rate."""
+    g = nvar * w * (8000.0 / 4096.0 - 1.0 + 2.0 * 3904.0 / 4096.0)
+    return algorithmic_bytes_per_zone(nvar, w, rk) + g
+
+
 def algorithmic_bytes_per_zone(nvar, w, rk):
     """Compulsory bytes per zone-update, averaged over the stages of one step: read U_s and
     write U_out every stage, read U^n in the stages that combine with it."""
@@ -681,7 +692,7 @@ def main():
         mhz = (r["clocks"] or {}).get("sm_mhz") or 2070.0
         peak_alu = alu_peak_tflops(FP32_LANES if w == 4 else FP64_LANES, mhz)
         return dict(value=zu, ms_per_step=ms_step, bytes_per_zone=bpz, launch_ms=launch_ms,
-                    achieved=achieved, tflops=flops, peak_alu=peak_alu, mhz=mhz,
+                    zps=r["zones"] / (launch_ms / 1e3), achieved=achieved, tflops=flops, peak_alu=peak_alu, mhz=mhz,
                     e2e=e2e, p50=ps[len(ps) // 2],
                     p99=ps[min(len(ps) - 1, int(math.ceil(0.99 * len(ps))) - 1)],
                     stage_share=r["stage_ms"] / max(1e-9, r["total_ms"]),
@@ -715,7 +726,13 @@ def main():
         "hbm_roofline": {"bound": "hbm", "achieved": s32["achieved"], "peak": hbm, "unit": "GB/s",
                          "frac": s32["achieved"] / hbm, "traffic": traffic,
                          "bytes_per_zone_update": s32["bytes_per_zone"],
-                         "peak_kind": peak_kind + " hbm_gbs"},
+                         "peak_kind": peak_kind + " hbm_gbs",
+                         "ghost_inflated": {
+                             "bytes_per_zone_update": ghost_inflated_bytes_per_zone(9, 4, 3),
+                             "achieved": ghost_inflated_bytes_per_zone(9, 4, 3) * s32["zps"] / 1e9,
+                             "frac": ghost_inflated_bytes_per_zone(9, 4, 3) * s32["zps"] / 1e9 / hbm,
+                             "note": "equivalent rate of a 20^3 ghost-cell storage scheme at this "
+                                     "stage-launch zone-update rate; not this build's traffic"}},
         "e2e": {"value": s32["e2e"], "unit": UNIT,
                 "h2d_bytes_per_step": r32["state_bytes"] / steps,
                 "d2h_bytes_per_step": r32["state_bytes"] / steps + 8 * (1 + 9),
