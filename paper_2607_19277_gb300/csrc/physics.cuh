@@ -27,6 +27,7 @@ template <typename R>
 struct PhysParamsT {
   double gamma_d, gm_d;    // gamma and (gamma - 1) / gamma in FP64 (SRHD primitive recovery)
   R gamma, g1, ig1, gg1;   // gamma, gamma - 1, 1 / (gamma - 1), gamma / (gamma - 1)
+  R gmr;                   // (gamma - 1) / gamma in the stencil precision
   R ch, ich, ch2;          // GLM cleaning speed c_h = c_max of U^n (MHD), 1 / c_h, c_h^2
   __host__ __device__ void set(double gamma_, double ch_) {
     gamma_d = gamma_;
@@ -35,6 +36,7 @@ struct PhysParamsT {
     g1 = R(gamma_ - 1.0);
     ig1 = R(1.0 / (gamma_ - 1.0));
     gg1 = R(gamma_ / (gamma_ - 1.0));
+    gmr = R(gm_d);
     set_ch(ch_);
   }
   __host__ __device__ void set_ch(double ch_) {
@@ -284,13 +286,13 @@ struct SrhdPhysE {
 
   // The same Newton iteration in FP32, to |dxi| <= 1e-6 xi (at most 12 steps): in the FP32
   // stencil it moves the starting point of the FP64 iteration close to the root, so that the
-  // FP64 iteration (which alone decides convergence and the result) needs about two steps.
-  // Returns the start unchanged when it does not converge or leaves the bracket.
-  __device__ static __forceinline__ double seed_f32(double xi0, double D, double s2, double E, double lo,
-                                                    double hi, const PhysParamsT<R>& pp) {
-    const float df_ = (float)D, s2f = (float)s2, ef = (float)E, gmf = (float)pp.gm_d;
+  // FP64 iteration (which alone decides convergence and the result) needs about one step.
+  // Returns the start unchanged when it does not converge (the caller checks the bracket).
+  __device__ static __forceinline__ double seed_f32(float x, float df_, float s2f, float ef, float l, float h,
+                                                    const PhysParamsT<R>& pp) {
+    const float gmf = (float)pp.gmr;
     const float idf = EOS == EOS_SYNGE ? 1.0f / df_ : 0.0f;
-    float l = (float)lo, h = (float)hi, x = (float)xi0;
+    const float x0 = x;
     for (int it = 0; it < 12; ++it) {
       const float ixi = 1.0f / x;
       const float w = s2f * ixi * ixi;
@@ -316,12 +318,9 @@ struct SrhdPhysE {
       if (!(xn >= l && xn <= h)) xn = 0.5f * (l + h);
       const bool conv = fabsf(xn - x) <= 1e-6f * xn;
       x = xn;
-      if (conv) {
-        const double xd = (double)x;
-        return (xd > lo && xd < hi) ? xd : xi0;
-      }
+      if (conv) return (double)x;
     }
-    return xi0;
+    return (double)x0;
   }
 
   // Newton root find for f(xi) = xi - p(xi) - (tau + D) = 0 inside the bracket [E, k E]
@@ -340,22 +339,36 @@ struct SrhdPhysE {
     const double E = (double)u[4] + D;
     double lo = E, hi = (EOS == EOS_SYNGE ? 4.0 / 3.0 : g) * E;
     const double iD = EOS == EOS_SYNGE ? rcp64(D) : 0.0;
-    double xi = (double)aux[0];
+    double xi;
+    if constexpr (sizeof(R) == 4) {
+      // the FP32 start from the FP32 inputs (no FP64 -> FP32 conversions), in the bracket
+      // [E, k E] formed in FP32; the result lands in the FP64 bracket or the FP64 midpoint
+      // is taken
+      const float ef = u[4] + u[0];
+      const float lof = ef, hif = (EOS == EOS_SYNGE ? 4.0f / 3.0f : (float)pp.gamma) * ef;
+      float x0 = aux[0];
+      if (!(x0 > lof && x0 < hif)) x0 = 0.5f * (lof + hif);
+      const float s2f = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+      xi = seed_f32(x0, u[0], s2f, ef, lof, hif, pp);
+    } else {
+      xi = (double)aux[0];
+    }
     if (!(xi > lo && xi < hi)) xi = 0.5 * (lo + hi);
-    if constexpr (sizeof(R) == 4) xi = seed_f32(xi, D, s2, E, lo, hi, pp);
     // FP64 stencil: |dxi| <= 1e-14 xi. FP32 stencil: |dxi| <= 1e-6 xi; Newton converges
     // quadratically, so the iterate after such a step is within about (1e-6)^2 relative
     // (times a factor that grows like Gamma^3), far below the FP32 rounding of the output.
     constexpr double tol = sizeof(R) == 4 ? 1e-6 : 1e-14;
     bool ok = false;
+    // quantities of the last iteration, evaluated at its starting point xs
+    double xs = xi, ixi = 1.0, w = 0.0, lor = 1.0, rho = 0.0, drho = 0.0, pr = 0.0, dp = 0.0;
     for (int it = 0; it < 50; ++it) {
-      const double ixi = rcp64(xi);
-      const double w = s2 * ixi * ixi;          // v^2
+      xs = xi;
+      ixi = rcp64(xi);
+      w = s2 * ixi * ixi;                       // v^2
       const double ig2 = 1.0 - w;               // 1 / Gamma^2
-      const double lor = rsqrt(ig2);            // Gamma
-      const double rho = D * (ig2 * lor);       // D / Gamma
-      const double drho = D * lor * w * ixi;    // d rho / d xi
-      double pr, dp;
+      lor = rsqrt(ig2);                         // Gamma
+      rho = D * (ig2 * lor);                    // D / Gamma
+      drho = D * lor * w * ixi;                 // d rho / d xi
       if constexpr (EOS == EOS_SYNGE) {
         // h = xi / (D Gamma), theta(h) = (5h - sqrt(9h^2 + 16)) / 8, dh/dxi = Gamma / D
         const double h = xi * (ig2 * lor) * iD;
@@ -378,24 +391,30 @@ struct SrhdPhysE {
       if (conv) { ok = true; break; }
     }
     if (!ok) st |= ST_ENOCONV;
-    const double ixi = rcp64(xi);
-    const double w = s2 * ixi * ixi;
-    const double ig2 = 1.0 - w;
-    const double lor = rsqrt(ig2);
-    const double rho = D * (ig2 * lor);
-    const double sc = lor * ixi;
-    p[0] = (R)rho;
-    p[1] = (R)(mx * sc);
-    p[2] = (R)(my * sc);
-    p[3] = (R)(mz * sc);
-    double pr;
-    if constexpr (EOS == EOS_SYNGE) {
-      const double h = xi * (ig2 * lor) * iD;
-      const double q = 9.0 * h * h + 16.0;
-      pr = rho * (0.125 * (5.0 * h - q * rsqrt(q)));
+    // The primitives at the converged xi from those of the last iterate xs by first-order
+    // Taylor steps (the derivatives are the iteration's own): |xi - xs| <= tol xi, so the
+    // neglected second-order terms are of relative size tol^2 (1e-28 in the FP64 stencil,
+    // 1e-12 in the FP32 one), far below the rounding of the result.
+    const double dx = xi - xs;
+    const double ixn = fma(-ixi * ixi, dx, ixi);                    // d(1/xi) = -dx / xi^2
+    const double lorn = fma(-(lor * lor * lor) * (w * ixi), dx, lor);   // dGamma/dxi = -Gamma^3 v^2 / xi
+    const double rhon = fma(drho, dx, rho);
+    const double prn = fma(dp, dx, pr);
+    const double sc = lorn * ixn;
+    p[0] = (R)rhon;
+    if constexpr (sizeof(R) == 4) {   // u = Gamma v = m Gamma / xi: one conversion of the factor
+      const R scr = (R)sc;
+      p[1] = u[1] * scr;
+      p[2] = u[2] * scr;
+      p[3] = u[3] * scr;
     } else {
-      pr = gm * (xi * ig2 - rho);
+      p[1] = (R)(mx * sc);
+      p[2] = (R)(my * sc);
+      p[3] = (R)(mz * sc);
     }
+    pr = prn;
+    rho = rhon;
+    lor = lorn;
     p[4] = (R)pr;
     aux[0] = (R)xi;
     aux[1] = (R)lor;
