@@ -564,7 +564,9 @@ def cpu_baseline(seconds_budget=12.0):
     * all_cores: the same scheme on 32^3 boxes, one independent box per process on every
       host core (up to 16), aggregate zone-updates/s over the common wall time;
     * config1_full: the 64^3 HD Sod problem (4x4x4 blocks, minmod, HLL, SSPRK2, CFL 0.4)
-      for its full 20 steps, 1 thread."""
+      for its full 20 steps, 1 thread;
+    * config3_sample / config4_sample: two steps of a refined Sedov problem and of one SRHD
+      solve of the batch's family, 1 thread."""
     import multiprocessing as mp
     from oracle import Config, Solver
     from paper_2607_19277_gb300 import workloads as W
@@ -592,6 +594,35 @@ def cpu_baseline(seconds_budget=12.0):
     out["config1_full"] = {"value": 64 ** 3 * 2 * 20 / el1, "unit": UNIT, "seconds": el1, "cores": 1,
                            "workload": "hd sod 64^3 (4x4x4 blocks), minmod, hll, ssprk2, cfl 0.4, 20 steps, fp64"}
     del c1
+    # bounded samples of the refined Sedov problem (config 3's scheme, base 32^3, three
+    # levels after the initial refinement) and of one SRHD solve of the batch (config 4's
+    # scheme, 32^3), a few steps each
+    c3 = Solver(Config(physics="hd", limiter="minmod", flux="hll", rk=2, cfl=0.4, base_blocks=(2, 2, 2),
+                       xmin=(-0.5,) * 3, xmax=(0.5,) * 3, bc=("outflow",) * 6, max_level=3,
+                       refine_vars=(0, 4), refine_weights=(0.5, 0.5), refine_tol=0.2))
+    c3.set_state(W.sedov(r0=0.06))
+    for _ in range(2):
+        c3.regrid(init=True)
+    nleaf = len(c3.leaves)
+    t0 = time.perf_counter()
+    for _ in range(2):
+        c3.step()
+    el3 = time.perf_counter() - t0
+    out["config3_sample"] = {"value": nleaf * 4096 * 2 * 2 / el3, "unit": UNIT, "seconds": el3, "cores": 1,
+                             "workload": "hd sedov, base 32^3, max level 3 (%d leaves), minmod, hll, ssprk2, "
+                                         "2 steps, fp64" % nleaf}
+    del c3
+    c4 = Solver(Config(physics="srhd", limiter="minmod", flux="tvdlf", rk=2, gamma=4.0 / 3.0, cfl=0.4,
+                       base_blocks=(2, 2, 2)))
+    c4.set_state(W.srhd_shells(20260005, 32, lorentz_max=2.0, p_amb=0.1, smooth=True))
+    t0 = time.perf_counter()
+    for _ in range(2):
+        c4.step()
+    el4 = time.perf_counter() - t0
+    out["config4_sample"] = {"value": 32 ** 3 * 2 * 2 / el4, "unit": UNIT, "seconds": el4, "cores": 1,
+                             "workload": "one srhd solve 32^3 of the batch's family, tvdlf, minmod, ssprk2, "
+                                         "2 steps, fp64 newton"}
+    del c4
     # every host core, independent boxes (the oracle's work splits over blocks/solves)
     nproc = max(1, min(os.cpu_count() or 1, 16))
     steps = 6
