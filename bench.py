@@ -337,6 +337,26 @@ def run_batched(steps, warmup, nsolve=256, fp64_solves=8):
     return out
 
 
+def run_probe(name):
+    """Small cases for full-section ncu captures (a few hundred MB on the device)."""
+    import torch
+    from paper_2607_19277_gb300 import agile, build, workloads as W
+    build.build()
+    if name == "srhd_batch_small":
+        cfgs = [agile.make_config(physics="srhd", limiter="minmod", flux="tvdlf", rk=2, gamma=4.0 / 3.0,
+                                  cfl=0.4, real_bytes=4, base_blocks=(4, 4, 4)) for _ in range(16)]
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            b = agile.Batch(cfgs, stream=stream)
+            for i in range(16):
+                b.set_state(i, W.srhd_shells(20260004 + i, 64, lorentz_max=2.0, p_amb=0.1, smooth=True))
+            for _ in range(3):
+                b.step()
+            b.sync()
+            b.close()
+        print("probe %s done" % name)
+
+
 def run_paper_scheme(steps=10, warmup=3):
     """The paper's single-device benchmark scheme (Section 3.1): hydrodynamics, LF (TVDLF),
     PLM van Leer, SSPRK3, periodic, 256^3 in 4096 blocks of 16^3, double shear layer
@@ -687,7 +707,13 @@ def main():
     ap.add_argument("--no-paper-scheme", action="store_true")
     ap.add_argument("--no-cooling", action="store_true")
     ap.add_argument("--no-ffhd", action="store_true")
+    ap.add_argument("--probe", choices=["srhd_batch_small"], default=None,
+                    help="run only a small profiling case (no JSON line): srhd_batch_small = 16 batched "
+                         "SRHD solves of 64^3 of the batched leg's family, 3 steps")
     args = ap.parse_args()
+    if args.probe:
+        run_probe(args.probe)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
