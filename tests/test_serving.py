@@ -166,3 +166,32 @@ def test_batched_server_reads_each_solve_at_its_step_count(monkeypatch):
     assert all(r.finished >= 0 and int(r.result[0]) == r.steps for r in reqs)
     assert rep.max_resident_bytes <= budget
     assert not FakeBatch.live                          # every batch closed
+
+
+def test_preparer_bounds_outstanding_work(monkeypatch):
+    """Initial conditions are prepared for the earliest waiting requests only, at most `limit`
+    held at once; a taken preparation frees its slot."""
+    import threading
+    gate = threading.Event()
+    started = []
+
+    def slow_prepare(r, rb):
+        started.append(r.rid)
+        gate.wait(5.0)
+        return np.full(1, r.rid)
+    monkeypatch.setattr(serving, "prepare", slow_prepare)
+    reqs = [serving.Request(rid=i, physics="hd", side=32, steps=1, seed=i, arrival=0.0) for i in range(6)]
+    p = serving._Preparer(workers=2, limit=3, real_bytes=4)
+    try:
+        p.feed(reqs)
+        assert sorted(p.futs) == [0, 1, 2]
+        assert not p.ready(reqs[0])
+        gate.set()
+        p.futs[0].result(5.0)
+        assert p.ready(reqs[0]) and int(p.take(reqs[0])[0]) == 0
+        p.feed(reqs[1:])
+        assert sorted(p.futs) == [1, 2, 3]
+        assert not p.ready(reqs[5])
+    finally:
+        gate.set()
+        p.close()
