@@ -338,9 +338,10 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   // CTA's jb-th block starts at parity jb & 1.
   __shared__ int s_next;
   __shared__ int s_src[6], s_slot[6];   // face sources / register slots of the current block
+  __shared__ R s_kc[12];                // per-(solve, level) constants, formed by thread 0
   // Launch constants, and the per-(solve, level) constants of the current block: they are
   // recomputed only when the block's solve or level differs from the previous block's (a
-  // CTA-uniform test), so the FP64 divisions and the exp stay off the per-block path.
+  // CTA-uniform test), by one thread.
   PhysParamsT<R> pp;
   pp.set(A.gamma, 0.0);
   const R ra = R(A.a), rb = R(A.b);
@@ -366,22 +367,43 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   const int sv = A.solve_of ? A.solve_of[b] : 0;
   unsigned long long* speeds = A.speeds ? A.speeds + 2 * sv : nullptr;
   const BlockDesc& bd = A.bd[b];
-  if (sv != key_sv || bd.level != key_lev) {
-    const double* dtch = A.dtch + 2 * sv;
-    const double dt = dtch[0];
-    pp.set_ch(dtch[1]);
-    idx = R(1.0 / bd.dx[0]);
-    idy = R(1.0 / bd.dx[1]);
-    idz = R(1.0 / bd.dx[2]);
-    rdt = R(dt);
-    if constexpr (P::QV >= 0) rq4 = R(0.25 / dt);
+  if (sv != key_sv || bd.level != key_lev) {   // CTA-uniform: every thread takes it or none
+    // one thread forms the constants in FP64 (divisions, the exp) and the CTA reads them
+    // back, so the FP64 units see one thread's work per change instead of the CTA's
+    if (t == 0) {
+      const double* dtch = A.dtch + 2 * sv;
+      const double dt = dtch[0], ch_ = dtch[1];
+      s_kc[0] = R(1.0 / bd.dx[0]);
+      s_kc[1] = R(1.0 / bd.dx[1]);
+      s_kc[2] = R(1.0 / bd.dx[2]);
+      s_kc[3] = R(dt);
+      s_kc[4] = P::QV >= 0 ? R(0.25 / dt) : R(0);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) dxr[d] = R(bd.dx[d]);
-    glm_fr = R(1);
-    if (glm_post) {
-      const double dxm = fmin(fmin(bd.dx[0], bd.dx[1]), bd.dx[2]);
-      glm_fr = R(exp(-0.5 * dt * dtch[1] * A.glm_alpha / dxm));
+      for (int d = 0; d < 3; ++d) s_kc[5 + d] = R(bd.dx[d]);
+      R fr = R(1);
+      if (glm_post) {
+        const double dxm = fmin(fmin(bd.dx[0], bd.dx[1]), bd.dx[2]);
+        fr = R(exp(-0.5 * dt * ch_ * A.glm_alpha / dxm));
+      }
+      s_kc[8] = fr;
+      PhysParamsT<R> q;
+      q.set_ch(ch_);
+      s_kc[9] = q.ch;
+      s_kc[10] = q.ich;
+      s_kc[11] = q.ch2;
     }
+    __syncthreads();
+    idx = s_kc[0];
+    idy = s_kc[1];
+    idz = s_kc[2];
+    rdt = s_kc[3];
+    rq4 = s_kc[4];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dxr[d] = s_kc[5 + d];
+    glm_fr = s_kc[8];
+    pp.ch = s_kc[9];
+    pp.ich = s_kc[10];
+    pp.ch2 = s_kc[11];
     key_sv = sv;
     key_lev = bd.level;
   }
