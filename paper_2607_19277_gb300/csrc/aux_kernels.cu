@@ -185,15 +185,14 @@ __global__ void __launch_bounds__(256) fixup_kernel(R* __restrict__ U, const R* 
 // ------------------------------------------------------------------------------ CFL speeds
 template <template <typename> class PT, typename R>
 __global__ void __launch_bounds__(256) speeds_kernel(const R* __restrict__ U,
-                                                      const BlockDesc* __restrict__ bd, double gamma,
+                                                      const BlockDesc* __restrict__ bd,
+                                                      const PhysParamsT<R> pp,   // formed on the host
                                                       unsigned long long* speeds, int* status,
                                                       const int* __restrict__ solve_of) {
   using P = PT<R>;
   constexpr int NV = P::NV, NA = P::NA, NT = NV + NA;
   const int b = blockIdx.x;
   const R dxr[3] = {R(bd[b].dx[0]), R(bd[b].dx[1]), R(bd[b].dx[2])};
-  PhysParamsT<R> pp;
-  pp.set(gamma, 0.0);
   R ssum = R(0), smax = R(0);
   int st = 0;
   const R* base = U + (size_t)b * NT * NCELL;
@@ -204,7 +203,7 @@ __global__ void __launch_bounds__(256) speeds_kernel(const R* __restrict__ U,
     if constexpr (NA > 0) aux[0] = base[(size_t)NV * NCELL + c];
     cell_speeds<PT, R>(u, aux, pp, dxr, ssum, smax, st);
   }
-  block_max2<256>((double)ssum, (double)smax, speeds + 2 * (solve_of ? solve_of[b] : 0));
+  block_max2<256>(ssum, smax, speeds + 2 * (solve_of ? solve_of[b] : 0));
   if (st) atomicOr(status, st);
 }
 
@@ -545,7 +544,12 @@ cudaError_t launch_fixup(const AuxArgs& a, const FixupTask* tasks, int ntasks, d
 
 cudaError_t launch_speeds(const AuxArgs& a, unsigned long long* speeds, cudaStream_t s) {
   if (a.nblk == 0) return cudaSuccess;
-#define CALL(PT) speeds_kernel<PT, R><<<a.nblk, 256, 0, s>>>((const R*)a.U, a.bd, a.gamma, speeds, a.status, a.solve_of)
+#define CALL(PT)                                                                                  \
+  do {                                                                                            \
+    PhysParamsT<R> pp;                                                                            \
+    pp.set(a.gamma, 0.0);                                                                         \
+    speeds_kernel<PT, R><<<a.nblk, 256, 0, s>>>((const R*)a.U, a.bd, pp, speeds, a.status, a.solve_of); \
+  } while (0)
   AGILE_DISPATCH(a.phys, a.real_bytes, CALL);
 #undef CALL
   return cudaGetLastError();

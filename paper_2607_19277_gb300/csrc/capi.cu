@@ -1354,7 +1354,6 @@ agile_status batch_enqueue_step(agile_batch* B) {
     A.b = nst == 2 ? w2[st][1] : w3[st][1];
     A.gamma = B->cfg.gamma;
     A.glm_alpha = B->cfg.glm_alpha;
-  A.htc_kappa0 = B->cfg.htc_kappa0;
     A.htc_kappa0 = B->cfg.htc_kappa0;
     A.glm_post = (mhd && last && fuse) ? 1 : 0;
     A.nblk = B->nblk;

@@ -140,15 +140,14 @@ template <template <typename> class PT, typename R>
 __global__ void __launch_bounds__(256) cooling_kernel(R* __restrict__ U, const BlockDesc* __restrict__ bd,
                                                        CoolDev c, const R* __restrict__ seg,
                                                        const double* __restrict__ dtch, double frac,
-                                                       double gamma, unsigned long long* speeds,
+                                                       const PhysParamsT<R> pp,   // formed on the host
+                                                       unsigned long long* speeds,
                                                        int* status, const int* __restrict__ solve_of) {
   using P = PT<R>;
   constexpr int NV = P::NV;
   const int b = blockIdx.x;
   const int sv = solve_of ? solve_of[b] : 0;
   const R dt = R(frac * dtch[2 * sv]);
-  PhysParamsT<R> pp;
-  pp.set(gamma, 0.0);
   const R ig1 = pp.ig1;
   const R dxr[3] = {R(bd[b].dx[0]), R(bd[b].dx[1]), R(bd[b].dx[2])};
   R ssum = R(0), smax = R(0);
@@ -168,15 +167,20 @@ __global__ void __launch_bounds__(256) cooling_kernel(R* __restrict__ U, const B
     base[(size_t)IE * NCELL + i] = u[IE];
     if (speeds) cell_speeds<PT, R>(u, aux, pp, dxr, ssum, smax, st);
   }
-  if (speeds) block_max2<256>((double)ssum, (double)smax, speeds + 2 * sv);
+  if (speeds) block_max2<256>(ssum, smax, speeds + 2 * sv);
   if (st) atomicOr(status, st);
 }
 
 cudaError_t launch_cooling(const AuxArgs& a, const CoolDev& c, const void* seg, const double* dtch,
                            double frac, unsigned long long* speeds, cudaStream_t s) {
   if (a.nblk == 0 || c.nseg <= 0) return cudaSuccess;
-#define CALL(PT) cooling_kernel<PT, R><<<a.nblk, 256, 0, s>>>((R*)a.Uw, a.bd, c, (const R*)seg, dtch, frac, \
-                                                              a.gamma, speeds, a.status, a.solve_of)
+#define CALL(PT)                                                                                   \
+  do {                                                                                             \
+    PhysParamsT<R> pp;                                                                             \
+    pp.set(a.gamma, 0.0);                                                                          \
+    cooling_kernel<PT, R><<<a.nblk, 256, 0, s>>>((R*)a.Uw, a.bd, c, (const R*)seg, dtch, frac, pp, speeds, \
+                                                 a.status, a.solve_of);                            \
+  } while (0)
   if (a.phys == PH_HD) {
     if (a.real_bytes == 8) { using R = double; CALL(HdPhys); }
     else { using R = float; CALL(HdPhys); }

@@ -39,6 +39,12 @@ struct StageArgs {
   int* work;                    // block counter of this launch (zeroed before it), dynamic scheduling
   int grid = 0;                 // persistent CTAs of the launch (0: CTAs-per-SM target x SMs)
   double htc_kappa0 = 0.0;      // ffhd with conduction: kappa_par = htc_kappa0 T^(5/2)
+  // FP32 copies of the equation parameters and the combine weights, formed on the host at
+  // launch (stage_go), so that the FP32 kernel never forms them from the FP64 fields (the
+  // compiler may recompute such values at every use instead of holding them in registers)
+  PhysParamsT<float> ppf;
+  float fa = 0.0f, fb = 0.0f;
+  int combine = 0;
 };
 
 // Conserved + auxiliary values of the cell (x, y, z) of block b in the halo view: the
@@ -114,13 +120,16 @@ __device__ __forceinline__ void cell_speeds(const R* u, R* aux, const PhysParams
   ssum = rmax(ssum, acc);
 }
 
-template <int NTHREADS>
-__device__ __forceinline__ void block_max2(double a, double b, unsigned long long* out) {
-  __shared__ double ra[NTHREADS / 32], rb[NTHREADS / 32];
+// Maxima of a and b over the CTA, widened to FP64 once and merged into out[0..1] (non-negative
+// values: their FP64 bit patterns order like the values). The reduction runs in the values'
+// own precision (a maximum is exact in any precision).
+template <int NTHREADS, typename T>
+__device__ __forceinline__ void block_max2(T a, T b, unsigned long long* out) {
+  __shared__ T ra[NTHREADS / 32], rb[NTHREADS / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
-    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    a = rmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = rmax(b, __shfl_xor_sync(0xffffffffu, b, o));
   }
   const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
@@ -129,13 +138,13 @@ __device__ __forceinline__ void block_max2(double a, double b, unsigned long lon
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double ma = ra[0], mb = rb[0];
+    T ma = ra[0], mb = rb[0];
     for (int i = 1; i < NTHREADS / 32; ++i) {
-      ma = fmax(ma, ra[i]);
-      mb = fmax(mb, rb[i]);
+      ma = rmax(ma, ra[i]);
+      mb = rmax(mb, rb[i]);
     }
-    atomic_max_pos(out, ma);
-    atomic_max_pos(out + 1, mb);
+    atomic_max_pos(out, (double)ma);
+    atomic_max_pos(out + 1, (double)mb);
   }
 }
 
@@ -343,9 +352,17 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   // recomputed only when the block's solve or level differs from the previous block's (a
   // CTA-uniform test), by one thread.
   PhysParamsT<R> pp;
-  pp.set(A.gamma, 0.0);
-  const R ra = R(A.a), rb = R(A.b);
-  const bool combine = A.a != 0.0;
+  R ra, rb;
+  if constexpr (sizeof(R) == 4) {
+    pp = A.ppf;
+    ra = A.fa;
+    rb = A.fb;
+  } else {
+    pp.set(A.gamma, 0.0);
+    ra = R(A.a);
+    rb = R(A.b);
+  }
+  const bool combine = A.combine != 0;
   const bool glm_post = A.glm_post != 0;
   constexpr uint32_t PLANE_BYTES = (uint32_t)(sizeof(R) * NT * 256);
   int key_sv = -1, key_lev = -1;
@@ -771,7 +788,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       }
     }
   }
-  if (speeds) block_max2<256>((double)ssum, (double)smax, speeds);
+  if (speeds) block_max2<256>(ssum, smax, speeds);
   if (t == 0) {
     // every read of this block's face table happened before the last plane's second barrier
     const int nx = A.work ? (int)gridDim.x + atomicAdd(A.work, 1) : b + (int)gridDim.x;

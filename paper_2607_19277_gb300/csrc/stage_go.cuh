@@ -29,7 +29,12 @@ static cudaError_t stage_go(const StageArgs& a, cudaStream_t s) {
   int grid = a.grid > 0 ? a.grid : MINB * sms;   // a tuned persistent grid, else the default
   if (grid > a.nblk) grid = a.nblk;
   if (grid <= 0) return cudaSuccess;
-  k<<<grid, 256, smem, s>>>(*static_cast<const CUtensorMap*>(a.tmap), a);
+  StageArgs args = a;
+  args.ppf.set(a.gamma, 0.0);
+  args.fa = (float)a.a;
+  args.fb = (float)a.b;
+  args.combine = a.a != 0.0 ? 1 : 0;
+  k<<<grid, 256, smem, s>>>(*static_cast<const CUtensorMap*>(args.tmap), args);
   return cudaGetLastError();
 }
 
