@@ -69,6 +69,10 @@ int build_cool_table(const double* T, const double* L, int n, double gamma, int 
   out->idln = uni ? 1.0 / dl : 0.0;
   out->T0 = T[0];
   out->g1 = gamma - 1.0;
+  out->lnT0f = (float)out->lnT0;
+  out->idlnf = (float)out->idln;
+  out->T0f = (float)out->T0;
+  out->g1f = (float)out->g1;
   return 0;
 }
 
@@ -89,13 +93,13 @@ template <> __device__ __forceinline__ double c_log1p<double>(double x) { return
 // T is not a number).
 template <typename R>
 __device__ __forceinline__ R cool_temperature(R rho, R T, R dt, const CoolDev& c, const R* seg) {
-  const R t0 = R(c.T0);
+  const R t0 = sizeof(R) == 4 ? R(c.T0f) : R(c.T0);
   if (!(T > t0)) return T;
   const R lt = c_log<R>(T);
   const int last = c.nseg - 1;
   int k;
   if (c.uniform) {
-    k = (int)((lt - R(c.lnT0)) * R(c.idln));
+    k = sizeof(R) == 4 ? (int)((lt - R(c.lnT0f)) * R(c.idlnf)) : (int)((lt - R(c.lnT0)) * R(c.idln));
     k = k < 0 ? 0 : (k > last ? last : k);
     // rounding of the index near a node: step to the segment that holds lt
     if (k > 0 && lt < seg[k * COOL_SEG + 0]) --k;
@@ -115,7 +119,7 @@ __device__ __forceinline__ R cool_temperature(R rho, R T, R dt, const CoolDev& c
   R avail = s[1] * (e != R(0) ? c_expm1<R>(e * x) / e : x);         // int_{T_k}^{T} dT/Lambda
   R lam_t = s[6] * c_exp<R>(-e * x);                                // Lambda(T) / T
   R top = T;
-  R r = R(c.g1) * rho * dt;
+  R r = (sizeof(R) == 4 ? R(c.g1f) : R(c.g1)) * rho * dt;
   for (int it = 0; it <= last; ++it) {     // at most one pass per segment below T
     if (r < avail) {
       const R q = r * lam_t;

@@ -77,6 +77,9 @@ struct CoolDev {
   int uniform = 0;     // nodes uniform in ln T
   double lnT0 = 0.0, idln = 0.0, T0 = 0.0;
   double g1 = 0.0;     // gamma - 1: a step consumes (gamma - 1) rho dt of int dT / Lambda
+  // the same four rounded to FP32 on the host: the FP32 kernel reads these, so that it never
+  // converts FP64 values per cell (conversions run on the FP64 units)
+  float lnT0f = 0.0f, idlnf = 0.0f, T0f = 0.0f, g1f = 0.0f;
 };
 struct CoolHost : CoolDev {
   std::vector<double> segd;
