@@ -27,6 +27,10 @@
  *    their integer block coordinates (x lowest bit). Arrays of per-block data follow it.
  *  - Cell order inside a block: [z][y][x], x fastest, 16 cells per edge, interior only.
  *  - Floating-point data crosses the ABI in FP64, whatever the stencil precision.
+ *  - Threads: calls on one mesh or batch must not overlap. Different meshes may be driven
+ *    from different host threads once each stage kernel has been launched at least once
+ *    (the first launch of a kernel sets its shared-memory attribute in process-wide state);
+ *    one process drives one GPU.
  */
 #ifndef AGILE_H
 #define AGILE_H
