@@ -407,3 +407,43 @@ class BatchedServer:
                      max_concurrent=max_conc)
         rep.latencies = [r.finished - r.arrival * time_scale for r in requests]
         return rep
+
+
+def main(argv=None):
+    """Command line: serve a seeded request stream and print the report as one JSON line.
+
+    python -m paper_2607_19277_gb300.serving [--requests 1000] [--rate 50] [--budget-gb 160]
+        [--sides 32,64,128,256] [--steps 50,500] [--fp64] [--batched]
+
+    The defaults are the full stream of the serving workload (1000 requests, Poisson mean
+    50/s, HD / MHD / SRHD, sides 32-256, 50-500 steps, 160 GB); the benchmark runs a bounded
+    sample of it."""
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(prog="python -m paper_2607_19277_gb300.serving")
+    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--budget-gb", type=float, default=160.0)
+    ap.add_argument("--sides", default="32,64,128,256")
+    ap.add_argument("--steps", default="50,500")
+    ap.add_argument("--fp64", action="store_true", help="the plain FP64 per-solve path")
+    ap.add_argument("--batched", action="store_true", help="per-module batches (FP32)")
+    a = ap.parse_args(argv)
+    sides = tuple(int(x) for x in a.sides.split(","))
+    steps = tuple(int(x) for x in a.steps.split(","))
+    if any(s % 16 or s <= 0 for s in sides) or len(steps) != 2 or steps[0] < 1 or steps[1] < steps[0]:
+        raise SystemExit("sides must be positive multiples of 16 and steps a range lo,hi")
+    reqs = request_stream(a.requests, rate=a.rate, sides=sides, steps=steps)
+    budget = int(a.budget_gb * 2 ** 30)
+    if a.batched:
+        srv = BatchedServer(budget, real_bytes=4)
+    else:
+        srv = Server(budget, real_bytes=8 if a.fp64 else 4)
+    rep = srv.run(reqs)
+    out = rep.summary()
+    out["path"] = "fp32_batched" if a.batched else ("fp64_plain" if a.fp64 else "fp32")
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

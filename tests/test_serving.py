@@ -195,3 +195,10 @@ def test_preparer_bounds_outstanding_work(monkeypatch):
     finally:
         gate.set()
         p.close()
+
+
+def test_command_line_rejects_bad_ranges():
+    with pytest.raises(SystemExit):
+        serving.main(["--sides", "32,40"])
+    with pytest.raises(SystemExit):
+        serving.main(["--steps", "10"])
