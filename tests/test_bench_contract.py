@@ -1,0 +1,36 @@
+"""Host-side arithmetic of bench.py's roofline fields: algorithmic bytes per zone-update for
+the workload shapes (n_v w per access: one read of the stage input and one write every
+stage, one read of U^n in combining stages), the ghost-inflated figure, the derived FP32 /
+FP64 peaks, and the measured-traffic guard (a figure only while the kernel sources hash to
+the captured version)."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+@pytest.mark.parametrize("nvar,w,rk,expect", [(5, 8, 2, 100.0), (5, 4, 2, 50.0), (9, 8, 3, 192.0),
+                                               (9, 4, 3, 96.0), (5, 4, 3, 160.0 / 3.0)])
+def test_algorithmic_bytes(nvar, w, rk, expect):
+    assert bench.algorithmic_bytes_per_zone(nvar, w, rk) == pytest.approx(expect, rel=1e-15)
+
+
+def test_ghost_inflated_bytes():
+    # 9 vars x 4 B: halo read (8000/4096 - 1) + ghost write and fill read (3904/4096 each)
+    extra = 36.0 * (8000.0 / 4096.0 - 1.0) + 2 * 36.0 * 3904.0 / 4096.0
+    assert bench.ghost_inflated_bytes_per_zone(9, 4, 3) == pytest.approx(96.0 + extra, rel=1e-15)
+
+
+def test_derived_alu_peaks():
+    assert bench.alu_peak_tflops(bench.FP32_LANES, 2070.0) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
+    assert bench.alu_peak_tflops(bench.FP64_LANES, 2070.0) == pytest.approx(152 * 2 * 2 * 2.07e9 / 1e12)
+
+
+def test_traffic_only_for_the_captured_sources(monkeypatch):
+    assert bench.stage_traffic() == pytest.approx(bench.STAGE_TRAFFIC_BYTES)
+    monkeypatch.setattr(bench, "STAGE_SRC_DIGEST", "0" * 16)
+    assert bench.stage_traffic() is None
