@@ -10,6 +10,9 @@ transposed operand fails at least one of them:
   * closed forms of the fast speed and relativistic characteristic speeds
   * SRHD Newtonian limit, con2prim round trip, boosted uniform state     -> SRHD fluxes and recovery
   * GLM decay closed form exp(-dt c_h alpha / dx)                        -> Section 2.3.3 operator split
+  * GLM face values = exact Riemann solution of the linear (B_n, psi) system
+    (eigen-decomposition); a div B wave splits into B_n +/- psi/c_h
+    characteristics at +/- c_h, second order                            -> Eq. 14 coupling, interface
   * conservation to round-off on periodic uniform and AMR meshes         -> flux fix-up, regrid
   * exact ghost values of a linear field on an AMR mesh                  -> srl / restriction / prolongation indices
   * brute-force 2:1 balance, hand-computed Loehner value, Sedov-Taylor radius.
@@ -264,6 +267,89 @@ def test_glm_decay_closed_form():
     psi = s.get_state()[2][:, 8]
     expect = psi0 * math.exp(-dt * cmax * 0.5 / (1.0 / 16))
     assert np.max(np.abs(psi - expect)) < 1e-15 * 10
+
+
+def _linear_glm_riemann_state(ql, qr, ch):
+    """State at x/t = 0 of the Riemann problem q_t + A q_x = 0, q = (B_n, psi),
+    A = [[0, 1], [c_h^2, 0]] (the flux pair F(B_n) = psi, F(psi) = c_h^2 B_n of Eq. 14),
+    from the eigen-decomposition of A: the jump qr - ql = sum_k alpha_k r_k, and the waves
+    with negative speed are the ones crossed between ql and x/t = 0."""
+    A = np.array([[0.0, 1.0], [ch * ch, 0.0]])
+    lam, R = np.linalg.eig(A)
+    alpha = np.linalg.solve(R, qr - ql)
+    q = ql.copy()
+    for k in range(2):
+        if lam[k] < 0.0:
+            q = q + alpha[k] * R[:, k]
+    return q
+
+
+def test_glm_interface_is_the_exact_linear_riemann_solution():
+    """The GLM face values (B_n*, psi*) that both face states carry are the exact solution
+    at the face of the linear (B_n, psi) subsystem; every other primitive passes through."""
+    rng = np.random.default_rng(7)
+    m = MHD(5.0 / 3.0)
+    for d in range(3):
+        for ch in (0.3, 1.0, 2.7):
+            PL = rng.normal(size=(9, 5))
+            PR = rng.normal(size=(9, 5))
+            QL, QR = m.glm_interface(PL, PR, d, ch)
+            for i in range(5):
+                q = _linear_glm_riemann_state(np.array([PL[5 + d, i], PL[8, i]]),
+                                              np.array([PR[5 + d, i], PR[8, i]]), ch)
+                for Q in (QL, QR):
+                    assert abs(Q[5 + d, i] - q[0]) <= 1e-13 * (1 + abs(q[0]))
+                    assert abs(Q[8, i] - q[1]) <= 1e-13 * (1 + abs(q[1]))
+            keep = [v for v in range(9) if v not in (5 + d, 8)]
+            assert np.array_equal(QL[keep], PL[keep]) and np.array_equal(QR[keep], PR[keep])
+
+
+def _glm_wave_error(n, ch=2.0, eps=1e-3, shift=0.25):
+    """A div B wave at rest: rho = p = 1, v = 0, B = (eps sin 2 pi x, 0, 0),
+    psi = eps c_h/2 cos 2 pi x, periodic, no damping (alpha = 0), c_h held fixed. B_x and psi
+    then obey the linear system of Eq. 14 alone (the Lorentz force is O(eps^2) and never
+    feeds back into them), so w+- = B_x +- psi / c_h are carried unchanged at +- c_h: the
+    exact solution after c_h t = shift. Returns the mean |error| of B_x and psi relative
+    to their amplitudes."""
+    s = Solver(Config(physics="mhd", limiter="vanleer", flux="hll", rk=3, glm_alpha=0.0,
+                      base_blocks=(n // 16, 1, 1), xmax=(1.0, 16.0 / n, 16.0 / n)))
+
+    def wp(x):
+        return eps * (np.sin(2 * math.pi * x) + 0.5 * np.cos(2 * math.pi * x))
+
+    def wm(x):
+        return eps * (np.sin(2 * math.pi * x) - 0.5 * np.cos(2 * math.pi * x))
+
+    def ic(x, y, z):
+        x = np.asarray(x)
+        P = np.zeros((9, x.size))
+        P[0] = 1.0
+        P[4] = 1.0
+        P[5] = 0.5 * (wp(x) + wm(x))
+        P[8] = 0.5 * ch * (wp(x) - wm(x))
+        return P
+    s.set_state(ic)
+    tend = shift / ch
+    nst = int(math.ceil(tend / (0.4 / n / (3.0 * ch))))
+    for _ in range(nst):
+        s.step(tend / nst, ch=ch)
+    eb = ep = 0.0
+    cnt = 0
+    for k, blk in s.leaves.items():
+        x, _, _ = s.cell_centres(k)
+        a, b = wp(x - ch * tend), wm(x + ch * tend)
+        eb += np.abs(blk[5, 2:18, 2:18, 2:18].ravel() - 0.5 * (a + b)).sum()
+        ep += np.abs(blk[8, 2:18, 2:18, 2:18].ravel() - 0.5 * ch * (a - b)).sum()
+        cnt += a.size
+    return eb / cnt / eps, ep / cnt / (eps * ch)
+
+
+def test_glm_div_b_wave_splits_at_plus_minus_ch_second_order():
+    e = [_glm_wave_error(n) for n in (16, 32, 64)]
+    for v in range(2):
+        orders = [math.log2(e[i][v] / e[i + 1][v]) for i in range(2)]
+        assert min(orders) >= 1.8, (e, orders)
+    assert max(e[-1]) < 2e-3, e
 
 
 # ------------------------------------------------------------------------ SRHD
