@@ -50,8 +50,7 @@ def test_hd_wave_with_losses(rb, tol):
 def test_mhd_with_losses(rb, tol):
     spec = dict(physics="mhd", limiter="vanleer", flux="hll", rk=3, base_blocks=(2, 2, 2))
     m, o, lev, g, r = _both(spec, W.random_smooth(9, 31, "mhd"), 3, rb)
-    _, cmax = m.max_speeds()
-    assert rel_l1(g, r, physics="mhd", cmax=cmax).max() < tol
+    assert rel_l1(g, r, physics="mhd").max() < tol     # psi against its own norm
     m.close()
 
 

@@ -61,7 +61,38 @@ def test_fullsize_mhd_step_sampled_blocks(rb, tol):
     for c in SAMPLES:
         ref = _oracle_block(c, dt, cmax)
         got = cons[index[c]]
-        err = rel_l1(got[None], ref[None], physics="mhd", cmax=cmax)
+        # FP64: psi against its own norm; FP32: psi (zero at t = 0) against c_max sum |B|
+        err = rel_l1(got[None], ref[None], physics="mhd", cmax=cmax if rb == 4 else None)
+        assert err.max() < tol, (c, err)
+
+
+@pytest.mark.parametrize("rb,tol", [(8, TOL_FP64), (4, TOL_FP32)])
+def test_fullsize_mhd_five_steps_sampled_blocks(rb, tol):
+    """Five SSPRK3 steps at full size, in the launch configuration the benchmark times.
+    Five steps move information by at most 5 x 3 x 2 = 30 cells < 32, so a block's state
+    depends only on the 5x5x5-block neighbourhood around it; the oracle evolves that
+    neighbourhood (periodic on itself, with the GPU's global dt and c_h of every step)."""
+    m = agile.Mesh(agile.make_config(real_bytes=rb, base_blocks=(NB,) * 3, **SPEC))
+    m.set_state(W.orszag_tang_3d(N))
+    hist = []
+    for _ in range(5):
+        smax, cmax = m.max_speeds()
+        dt = m.cfl_dt()
+        m.step(dt)
+        hist.append((dt, cmax))
+    lev, ijk, cons = m.get_state()
+    m.close()
+    index = {tuple(r): i for i, r in enumerate(ijk.tolist())}
+    for c in [(0, 0, 0), (9, 4, 13)]:
+        lo = [(ci - 2) / NB for ci in c]
+        hi = [(ci + 3) / NB for ci in c]
+        o = Solver(Config(base_blocks=(5, 5, 5), xmin=tuple(lo), xmax=tuple(hi), **SPEC))
+        o.set_state(_wrapped_ic())
+        for dt, ch in hist:
+            o.step(dt, ch=ch)
+        ref = o.leaves[(1, 2, 2, 2)][:9, 2:18, 2:18, 2:18]
+        got = cons[index[c]]
+        err = rel_l1(got[None], ref[None], physics="mhd", cmax=hist[-1][1] if rb == 4 else None)
         assert err.max() < tol, (c, err)
 
 

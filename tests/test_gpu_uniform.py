@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from paper_2607_19277_gb300 import workloads as W
-from parity_util import TOL_FP32, TOL_FP64, gpu_mesh, oracle_solver, rel_l1, run_both
+from parity_util import TOL_FP32, TOL_FP64, gpu_mesh, oracle_solver, psi_self_l1, rel_l1, run_both
 
 pytestmark = pytest.mark.gpu
 OUT, PER, REF = "outflow", "periodic", "reflect"
@@ -28,14 +28,37 @@ def test_sod_config1_fp64_20_steps():
     m.close()
 
 
-@pytest.mark.parametrize("rb,tol", [(8, TOL_FP64), (4, TOL_FP32)])
-def test_mhd_orszag_tang_glm(rb, tol):
+@pytest.mark.parametrize("rb", [8, 4])
+def test_mhd_orszag_tang_glm(rb):
     """Ideal MHD + GLM, Orszag-Tang-like field with seeded 1% velocity noise, van Leer, HLL,
-    SSPRK3, periodic (the 256^3 workload's physics on 32^3)."""
+    SSPRK3, periodic (the 256^3 workload's physics on 32^3).
+
+    FP64: every variable, psi included, within 1e-12 of its own norm. FP32: rho, m, e and B
+    within 1e-5; psi starts at zero and after 4 steps holds only the discretisation error of
+    div B (sum |psi| is about 2e-4 of c_max sum |B|), so FP32 rounding of the fluxes, relative
+    to c_h |B|, is a larger fraction of it: its error is held to 1e-5 of c_max sum |B| and,
+    against its own norm, to 2e-4 (measured about 5e-5)."""
     spec = dict(physics="mhd", limiter="vanleer", flux="hll", rk=3, base_blocks=(2, 2, 2))
     m, o, g, r, lev, _ = run_both(spec, W.orszag_tang_3d(32), 4, real_bytes=rb)
-    err = rel_l1(g, r, physics="mhd", cmax=o.signal_speeds()[0])
+    if rb == 8:
+        err = rel_l1(g, r, physics="mhd")
+        assert err.max() < TOL_FP64, err
+    else:
+        err = rel_l1(g, r, physics="mhd", cmax=o.signal_speeds()[0])
+        assert err.max() < TOL_FP32, err
+        assert psi_self_l1(g, r) < 2e-4
+    m.close()
+
+
+@pytest.mark.parametrize("rb,tol", [(8, TOL_FP64), (4, TOL_FP32)])
+def test_mhd_psi_of_natural_size_self_normalised(rb, tol):
+    """A smooth MHD state whose psi is of order c_h |B| from the start: every variable,
+    psi included, within the precision's bound against its own norm (no widened scale)."""
+    spec = dict(physics="mhd", limiter="vanleer", flux="hll", rk=3, base_blocks=(2, 2, 2))
+    m, o, g, r, lev, _ = run_both(spec, W.random_smooth(9, 31, "mhd"), 4, real_bytes=rb)
+    err = rel_l1(g, r, physics="mhd")
     assert err.max() < tol, err
+    assert psi_self_l1(g, r) < tol
     m.close()
 
 
