@@ -221,9 +221,10 @@ agile_status agile_get_aux(agile_mesh* mesh, double* aux);
 agile_status agile_conserved_sums(agile_mesh* mesh, double* sums);
 
 /* Conserved sums like agile_conserved_sums, for callers that cannot allocate device memory
- * at the time of the call: code running inside a CUDA stream capture (where cudaMalloc is
- * not allowed), a serving loop that reserved its whole device budget up front, or a host
- * whose allocator is not re-entrant from this thread. The paper has no counterpart; this is
+ * at the time of the call: a serving loop that reserved its whole device budget up front
+ * and forbids further allocation, or a host whose allocator is not re-entrant from this
+ * thread (a callback into a framework allocator that is itself mid-allocation). The paper
+ * has no counterpart; this is
  * a property of the library. It allocates nothing: its scratch (per-block partial sums and
  * the totals, about 1.2 MB) is a fixed array in device memory that every GPU that loads the
  * library holds until the process exits. The mesh and sums (host, [nvar]) are the caller's.

@@ -855,10 +855,10 @@ agile_status agile_kernel_timing(agile_mesh* m, double* stage_ms, long long* sta
 // ----------------------------------------------------------------------------------------
 // Conserved sums without any device allocation (agile_conserved_sums_noalloc).
 //
-// Some callers cannot allocate device memory at the moment they want the diagnostics: code
-// running inside a CUDA stream capture (cudaMalloc is not allowed while capturing), a
+// Some callers cannot allocate device memory at the moment they want the diagnostics: a
 // serving loop that reserved its whole device budget up front and forbids further
-// allocation, or a host whose allocator is not re-entrant from the calling thread. This
+// allocation, or a host whose allocator is not re-entrant from the calling thread (a
+// callback into a framework allocator that is itself in the middle of an allocation). This
 // variant keeps its scratch (per-block partial sums and the totals) in a fixed array in
 // device memory that every GPU loading the library holds until the process exits.
 // ----------------------------------------------------------------------------------------
