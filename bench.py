@@ -259,6 +259,46 @@ def run_gpu(real_bytes, steps, warmup, rank, world, dev):
                 e2e_s=e2e_s, state_bytes=state_bytes, nvar=9)
 
 
+def run_error_vs_fp64(nsteps):
+    """Error of the FP32 stencil on the headline workload against the FP64 stencil (whose
+    agreement with the FP64 oracle the parity tests establish): both meshes start from the
+    same state and take the same nsteps steps with the FP64 mesh's CFL dt; then the relative
+    L1 error per variable, sum |a - b| / sum |b| over all cells. psi starts at zero and holds
+    only the discretisation error of div B, so its error is also given on the c_max sum |B|
+    scale it is rounded on."""
+    from paper_2607_19277_gb300 import agile, workloads as W
+    ms = {rb: agile.Mesh(agile.make_config(real_bytes=rb, **spec())) for rb in (8, 4)}
+    for m in ms.values():
+        m.set_state(W.orszag_tang_3d(N_SIDE))
+    for _ in range(nsteps):
+        dt = ms[8].cfl_dt()
+        ms[8].step(dt)
+        ms[4].step(dt)
+    _, cmax = ms[8].max_speeds()
+    _, _, r = ms[8].get_state()
+    ms[8].close()
+    _, _, g = ms[4].get_state()
+    ms[4].close()
+    num = np.array([np.abs(g[:, v] - r[:, v]).sum() for v in range(9)])
+    den = np.array([np.abs(r[:, v]).sum() for v in range(9)])
+    del g, r
+    rel = num / den
+    names = ["rho", "m_x", "m_y", "m_z", "e", "B_x", "B_y", "B_z", "psi"]
+    # m_z and B_z start at (near) zero and stay small, so their own norms are small too; the
+    # error of each vector component on the scale of its whole vector is given beside it
+    vec = {"m": (1, 4), "B": (5, 8)}
+    on_vec = {}
+    for nm, (a, b) in vec.items():
+        for v in range(a, b):
+            on_vec[names[v]] = float(num[v] / den[a:b].sum())
+    return {"steps": nsteps, "reference": "FP64 stencil, same dt per step",
+            "rel_l1": {n: float(x) for n, x in zip(names, rel)},
+            "rel_l1_on_vector_scale": on_vec,
+            "max_rel_l1_rho_m_e_B": float(rel[:8].max()),
+            "psi_rel_l1_on_cmax_B_scale": float(num[8] / (cmax * den[5:8].sum())),
+            "psi_norm_over_cmax_B": float(den[8] / (cmax * den[5:8].sum()))}
+
+
 BATCH_SIDES = (32, 48, 64, 80, 96, 112, 128)
 
 
@@ -335,26 +375,6 @@ def run_batched(steps, warmup, nsolve=256, fp64_solves=8):
     out["fp64_plain_per_solve"] = {"value": z64 / (t64 / 1e3), "unit": UNIT, "solves": fp64_solves,
                                    "steps": st64}
     return out
-
-
-def run_probe(name):
-    """Small cases for full-section ncu captures (a few hundred MB on the device)."""
-    import torch
-    from paper_2607_19277_gb300 import agile, build, workloads as W
-    build.build()
-    if name == "srhd_batch_small":
-        cfgs = [agile.make_config(physics="srhd", limiter="minmod", flux="tvdlf", rk=2, gamma=4.0 / 3.0,
-                                  cfl=0.4, real_bytes=4, base_blocks=(4, 4, 4)) for _ in range(16)]
-        stream = torch.cuda.Stream()
-        with torch.cuda.stream(stream):
-            b = agile.Batch(cfgs, stream=stream)
-            for i in range(16):
-                b.set_state(i, W.srhd_shells(20260004 + i, 64, lorentz_max=2.0, p_amb=0.1, smooth=True))
-            for _ in range(3):
-                b.step()
-            b.sync()
-            b.close()
-        print("probe %s done" % name)
 
 
 def run_paper_scheme(steps=10, warmup=3):
@@ -694,6 +714,34 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
+def summary_of(line):
+    """The headline numbers of every leg in one short object, printed last in the line."""
+    def get(d, *path):
+        for p in path:
+            if not isinstance(d, dict) or p not in d:
+                return None
+            d = d[p]
+        return d
+    out = {"fp32_value": line.get("value"), "fp32_hbm_frac": get(line, "roofline", "frac"),
+           "fp32_alu_frac": get(line, "roofline", "alu", "frac"),
+           "fp32_stage_launch_ms": get(line, "roofline", "launch_ms"),
+           "fp64_value": get(line, "fp64", "value"), "fp64_alu_frac": get(line, "fp64", "roofline", "frac"),
+           "e2e": get(line, "e2e", "value"),
+           "fp32_max_rel_l1_vs_fp64": get(line, "error_vs_fp64", "max_rel_l1_rho_m_e_B"),
+           "fp32_psi_rel_l1_vs_fp64": get(line, "error_vs_fp64", "rel_l1", "psi"),
+           "paper_scheme_hd_fp32": get(line, "paper_scheme_hd", "fp32", "value"),
+           "paper_scheme_hd_fp64": get(line, "paper_scheme_hd", "fp64", "value"),
+           "batched_srhd_fp32": get(line, "batched", "value"),
+           "batched_srhd_fp64_plain": get(line, "batched", "fp64_plain_per_solve", "value"),
+           "sedov_5level_fp32": get(line, "sedov_5level", "fp32", "value"),
+           "sedov_5level_fp64": get(line, "sedov_5level", "fp64", "value"),
+           "serving_fp32_batched_p99_s": get(line, "serving", "fp32_batched", "latency_p99_s"),
+           "serving_fp32_batched_value": get(line, "serving", "fp32_batched", "zone_updates_per_s"),
+           "serving_fp64_plain_p99_s": get(line, "serving", "fp64_plain", "latency_p99_s"),
+           "cpu_oracle_1core": get(line, "cpu_baseline", "value")}
+    return {k: v for k, v in out.items() if v is not None}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -707,13 +755,7 @@ def main():
     ap.add_argument("--no-paper-scheme", action="store_true")
     ap.add_argument("--no-cooling", action="store_true")
     ap.add_argument("--no-ffhd", action="store_true")
-    ap.add_argument("--probe", choices=["srhd_batch_small"], default=None,
-                    help="run only a small profiling case (no JSON line): srhd_batch_small = 16 batched "
-                         "SRHD solves of 64^3 of the batched leg's family, 3 steps")
     args = ap.parse_args()
-    if args.probe:
-        run_probe(args.probe)
-        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
@@ -771,15 +813,20 @@ def main():
                    "stages_per_step": 3, "dt": "on-device CFL reduction",
                    "l2": "state 604 MB (fp32) / 1.2 GB (fp64) per buffer > 129 MB L2, no flush",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"bound": "alu", "achieved": s32["tflops"], "peak": s32["peak_alu"],
-                     "unit": "TFLOP/s", "frac": s32["tflops"] / s32["peak_alu"], "traffic": traffic,
+        "roofline": {"bound": "hbm", "achieved": s32["achieved"], "peak": hbm, "unit": "GB/s",
+                     "frac": s32["achieved"] / hbm, "traffic": traffic,
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read+write, mean of the 3 stages)",
                      "algorithmic_bytes_per_launch": s32["bytes_per_zone"] * N_SIDE ** 3,
+                     "bytes_per_zone_update": s32["bytes_per_zone"],
+                     "peak_kind": peak_kind + " hbm_gbs (MEASURED_PEAKS.json)",
                      "kernel": "stage_kernel<MhdPhys,float,vanleer,hll>",
-                     "flops_per_zone_update": MHD_HLL_VL_FLOPS,
-                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % s32["mhz"],
                      "launch_ms": s32["launch_ms"],
-                     "stage_kernel_share_of_step": s32["stage_share"]},
+                     "stage_kernel_share_of_step": s32["stage_share"],
+                     "alu": {"achieved": s32["tflops"], "peak": s32["peak_alu"], "unit": "TFLOP/s",
+                             "frac": s32["tflops"] / s32["peak_alu"],
+                             "flops_per_zone_update": MHD_HLL_VL_FLOPS,
+                             "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % s32["mhz"],
+                             "note": "the kernel is bound by FP32 instruction issue, not by HBM"}},
         "hbm_roofline": {"bound": "hbm", "achieved": s32["achieved"], "peak": hbm, "unit": "GB/s",
                          "frac": s32["achieved"] / hbm, "traffic": traffic,
                          "bytes_per_zone_update": s32["bytes_per_zone"],
@@ -842,8 +889,14 @@ def main():
             line["serving"] = run_serving()
         except Exception as e:
             line["serving"] = {"error": str(e)}
+    if not args.no_fp64 and world == 1:
+        try:
+            line["error_vs_fp64"] = run_error_vs_fp64(min(args.warmup + steps, 50))
+        except Exception as e:
+            line["error_vs_fp64"] = {"error": str(e)}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
+    line["summary"] = summary_of(line)
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

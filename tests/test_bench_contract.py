@@ -40,3 +40,14 @@ def test_traffic_only_for_the_captured_sources(monkeypatch):
     assert bench.stage_traffic() == pytest.approx(bench.STAGE_TRAFFIC_BYTES)
     monkeypatch.setattr(bench, "STAGE_SRC_DIGEST", "0" * 16)
     assert bench.stage_traffic() is None
+
+
+def test_summary_collects_the_legs_and_drops_missing_ones():
+    line = {"value": 1.0, "roofline": {"frac": 0.3, "launch_ms": 0.9, "alu": {"frac": 0.4}},
+            "fp64": {"value": 2.0, "roofline": {"frac": 0.5}},
+            "error_vs_fp64": {"max_rel_l1_rho_m_e_B": 1e-6, "rel_l1": {"psi": 1e-4}},
+            "serving": {"fp32_batched": {"latency_p99_s": 0.2}}}
+    s = bench.summary_of(line)
+    assert s == {"fp32_value": 1.0, "fp32_hbm_frac": 0.3, "fp32_alu_frac": 0.4, "fp32_stage_launch_ms": 0.9,
+                 "fp64_value": 2.0, "fp64_alu_frac": 0.5, "fp32_max_rel_l1_vs_fp64": 1e-6,
+                 "fp32_psi_rel_l1_vs_fp64": 1e-4, "serving_fp32_batched_p99_s": 0.2}
