@@ -19,6 +19,8 @@
 
 namespace agile {
 
+enum : int { STAGE_LAYOUT_RING4 = 1, STAGE_LAYOUT_RING5_DB = 2 };
+
 struct StageArgs {
   const void* Us;           // stage input state (with aux)
   const void* Un;           // U^n for the combine (a != 0)
@@ -39,6 +41,8 @@ struct StageArgs {
   int* work;                    // block counter of this launch (zeroed before it), dynamic scheduling
   int grid = 0;                 // persistent CTAs of the launch (0: CTAs-per-SM target x SMs)
   double htc_kappa0 = 0.0;      // ffhd with conduction: kappa_par = htc_kappa0 T^(5/2)
+  int layout = 0;               // staging layout (STAGE_LAYOUT_*), 0: the default for the physics
+  double eta = 0.0;             // resistive mhd: uniform resistivity
   // FP32 copies of the equation parameters and the combine weights, formed on the host at
   // launch (stage_go), so that the FP32 kernel never forms them from the FP64 fields (the
   // compiler may recompute such values at every use instead of holding them in registers)
@@ -271,52 +275,59 @@ __host__ __device__ constexpr int swapv(int v) {
 }
 
 constexpr uint32_t WAIT_LIMIT = 1u << 22;   // ~0.1 s of polling per wait at most
-
-// Slot of plane p (-2 .. 17) in the primitive ring. The ring is thread-private (every thread
-// reads and writes only its own column), holds the three planes a z-face needs, and plane p
-// + 3 takes the slot of plane p.
-__device__ __forceinline__ int pslot(int p) { return (p + 3) % 3; }
 constexpr int ST_ETIMEOUT = 4;
 
-template <template <typename> class PT, typename R>
+// Slot of plane p (-2 .. 17) in the primitive ring of three 20 x 20 planes: plane p + 3 takes
+// the slot of plane p.
+__device__ __forceinline__ int pslot(int p) { return (p + 3) % 3; }
+
+// Shared memory of the stage kernel for one staging layout: RAW raw-plane slots the TMA fills
+// (4: the ring holds planes k .. k+3 at plane k; 5: one more plane in flight) and SFB buffers
+// of the x/y face fluxes (2: the fluxes of plane k+1 are formed while those of plane k are
+// still being read, so one CTA barrier per plane suffices).
+template <template <typename> class PT, typename R, int RAW, int SFB>
 struct StageSmem {
   static constexpr int NV = PT<R>::NV, NT = PT<R>::NV + PT<R>::NA;
-  static constexpr size_t bars = 128;                                  // 4 mbarriers (+pad)
-  static constexpr size_t raw = bars;                                  // [4][NT][256]
-  static constexpr size_t prim = raw + sizeof(R) * 4 * NT * 256;       // [3][NT][256]
-  static constexpr size_t cur = prim + sizeof(R) * 3 * NT * 256;       // [NV][20][20]
-  static constexpr size_t fx = cur + sizeof(R) * NV * 400;             // [NV][16 x 16 + 16]
-  static constexpr size_t fy = fx + sizeof(R) * NV * 272;              // [NV][17][16]
-  static constexpr size_t halo = fy + sizeof(R) * NV * 272;            // [NT][128] raw halo
-  static constexpr size_t total = halo + sizeof(R) * NT * 128;
+  static constexpr size_t bars = 128;                                  // RAW mbarriers (+pad)
+  static constexpr size_t raw = bars;                                  // [RAW][NT][256]
+  static constexpr size_t ring = raw + sizeof(R) * RAW * NT * 256;     // [3][NT][20 x 20]
+  static constexpr size_t fx = ring + sizeof(R) * 3 * NT * 400;        // [SFB][NV][16 x 16 + 16]
+  static constexpr size_t fy = fx + sizeof(R) * SFB * NV * 272;        // [SFB][NV][17][16]
+  static constexpr size_t total = fy + sizeof(R) * SFB * NV * 272;
 };
 
-// The per-stage macro-kernel. Plane k of the block is processed in three phases
-// separated by CTA barriers:
-//   1. primitives of plane k+2 (own column; raw data landed in the TMA ring) into the
-//      primitive ring, plane k (interior from the ring + x/y halo converted here) into
-//      the current-plane buffer;
-//   2. the x- and y-face fluxes of plane k (shared memory) and the z-face flux at k+1/2
-//      (from the primitive ring of this column, carried to the next plane in registers);
-//   3. flux divergence, SSPRK combine and store of cell (x, y, k).
-// Raw planes arrive by TMA one iteration ahead: the ring holds planes k .. k+3.
-template <template <typename> class PT, typename R, int LIM, int FLUX, int MINB>
+// The per-stage macro-kernel. Plane k of a block is one iteration:
+//   A. primitives of plane k+2 of this thread's own column (raw data from the TMA ring) into
+//      the primitive ring;
+//   B. primitives of the x/y halo of plane k+1, whose raw values this thread fetched with
+//      cp.async into the ring's 20 x 20 frame one plane earlier (converted in place; the two
+//      halves of the CTA take turns), and the fetch of plane k+2's halo;
+//   C. the x- and y-face fluxes of plane k (ring plane k: interior and halo, complete since
+//      the previous barrier) into shared memory, and the z-face flux at k+1/2 (ring planes
+//      k .. k+2 of this column, carried to the next plane in registers);
+//   -- CTA barrier --
+//   D. flux divergence, SSPRK combine and store of cell (x, y, k);
+//   -- CTA barrier, with one flux buffer only: the next plane's faces overwrite it --
+// Raw planes arrive by TMA one or two planes ahead of their conversion.
+template <template <typename> class PT, typename R, int LIM, int FLUX, int MINB, int RAW, int SFB>
 __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant__ CUtensorMap tmap,
                                                            StageArgs A) {
+  static_assert(RAW == 4 || RAW == 5, "four or five raw slots");
+  static_assert(SFB == 1 || (SFB == 2 && RAW == 5), "a second flux buffer needs the fifth raw slot");
   using P = PT<R>;
-  using S = StageSmem<PT, R>;
+  using S = StageSmem<PT, R, RAW, SFB>;
   constexpr int NV = P::NV, NA = P::NA, NT = NV + NA;
   // FP32 HD / MHD with HLL or TVDLF: x- and y-faces solved as packed pairs
   constexpr bool PAIRED = sizeof(R) == 4 && PairPhys<P>::OK && (FLUX == FLUX_HLL || FLUX == FLUX_TVDLF);
   constexpr int NAW = NA > 0 ? NA : 1;
+  constexpr bool RESP = res_of<P>::value;   // resistive MHD sources
+  constexpr int PHASES = 20 / RAW;   // completions of each raw slot's barrier per block (planes -2..17)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   R* sRaw = reinterpret_cast<R*>(smem_raw + S::raw);
-  R* sPr = reinterpret_cast<R*>(smem_raw + S::prim);
-  R* sC = reinterpret_cast<R*>(smem_raw + S::cur);
-  R* sFx = reinterpret_cast<R*>(smem_raw + S::fx);
-  R* sFy = reinterpret_cast<R*>(smem_raw + S::fy);
-  R* sHalo = reinterpret_cast<R*>(smem_raw + S::halo);
+  R* sP = reinterpret_cast<R*>(smem_raw + S::ring);
+  R* sFx0 = reinterpret_cast<R*>(smem_raw + S::fx);
+  R* sFy0 = reinterpret_cast<R*>(smem_raw + S::fy);
 
   const R* __restrict__ Us = static_cast<const R*>(A.Us);
   const R* __restrict__ Un = static_cast<const R*>(A.Un);
@@ -328,6 +339,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   const int tx = t & 15, ty = t >> 4;
   const int warp = t >> 5;
   const int cell2 = ty * 16 + tx;
+  const int cellp = (ty + 2) * 20 + tx + 2;   // this thread's cell in a 20 x 20 ring plane
   // Faces of the x/y pass: column fc of row fr, the two half-warps of warp w on rows
   // (w & 3) + 8 (w >> 2) and 4 rows further, which the 20-wide plane rows put 16 banks apart
   // (the four-cell stencil loads are free of bank conflicts).
@@ -335,16 +347,25 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   const int fr = (warp & 3) + 8 * (warp >> 2) + 4 * ((t >> 4) & 1);
   // x-face fluxes: [NV][16 rows][16] for faces 0..15 of each row, then [NV][16] for face 16
   const int fxr = tx < 15 ? cell2 + 1 : 256 + ty;   // this cell's right x-face
+  // Halo cell of this thread: h < 64 x-faces, above y-faces; the half t >> 7 of the CTA owns
+  // the halo of the planes of its parity.
+  const int hh = t & 127;
+  int hx, hy;
+  {
+    const int side = (hh >> 5) & 1, layer = (hh >> 4) & 1, rr = hh & 15;
+    const int c = side ? NB + layer : layer - 2;
+    if (hh < 64) { hx = c; hy = rr; } else { hx = rr; hy = c; }
+  }
+  const int hoff = (hy + 2) * 20 + hx + 2;
   if (t == 0) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) mbar_init(bar + i, 1);
+    for (int i = 0; i < RAW; ++i) mbar_init(bar + i, 1);
     fence_mbar_init();
   }
   __syncthreads();
   int st = 0;
   // Persistent loop: this CTA starts with block blockIdx.x and then takes the next free block
-  // from the launch's counter; every block completes 5 phases of each ring barrier, so the
-  // CTA's jb-th block starts at parity jb & 1.
+  // from the launch's counter; every block completes PHASES phases of each raw slot's barrier.
   __shared__ int s_next;
   __shared__ int s_src[6], s_slot[6];   // face sources / register slots of the current block
   __shared__ R s_kc[12];                // per-(solve, level) constants, formed by thread 0
@@ -369,6 +390,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   R idx = R(0), idy = R(0), idz = R(0), rdt = R(0), glm_fr = R(1);
   R rq4 = R(0);                        // 1 / tau = 1 / (4 dt) of the conduction relaxation
   const R kap0 = R(A.htc_kappa0);
+  const R reta = R(A.eta);
   R dxr[3] = {R(0), R(0), R(0)};
   if (t == 0 && blockIdx.x < A.nblk) {
 #pragma unroll
@@ -425,14 +447,14 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     key_lev = bd.level;
   }
 
-  // plane p (-2 .. 17) -> TMA sequence q = p + 2, ring slot q & 3, phase parity (q >> 2) & 1
+  // plane p (-2 .. 17) -> TMA sequence q = p + 2, raw slot q % RAW, phase (q / RAW) of this block
   auto plane_tma = [&](int p) -> bool {   // does plane p come by TMA (else loaded directly)?
     if (p >= 0 && p < NB) return true;
     return src[p < 0 ? 4 : 5] >= 0;
   };
   auto issue = [&](int p) {               // thread 0 only
     const int q = p + 2;
-    uint64_t* br = bar + (q & 3);
+    uint64_t* br = bar + (q % RAW);
     if (plane_tma(p)) {
       int blk = b, z = p;
       if (p < 0 || p >= NB) {
@@ -440,18 +462,19 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
         z = p & (NB - 1);
       }
       mbar_expect_tx(br, PLANE_BYTES);
-      tma_load_4d(sRaw + (size_t)(q & 3) * NT * 256, &tmap, br, 0, 0, z, blk * NT);
+      tma_load_4d(sRaw + (size_t)(q % RAW) * NT * 256, &tmap, br, 0, 0, z, blk * NT);
     } else {
       mbar_arrive(br);
     }
   };
+  auto ring = [&](int p) -> R* { return sP + (size_t)pslot(p) * NT * 400; };
   // Primitive recovery of this thread's own column at plane p into the primitive ring.
   auto convert_own = [&](int p) {
     const int q = p + 2;
     R u[NT];
     if (plane_tma(p)) {
-      if (!mbar_wait(bar + (q & 3), ((q >> 2) + jb) & 1, WAIT_LIMIT)) st |= ST_ETIMEOUT;
-      const R* r = sRaw + (size_t)(q & 3) * NT * 256 + cell2;
+      if (!mbar_wait(bar + (q % RAW), ((q / RAW) + jb * PHASES) & 1, WAIT_LIMIT)) st |= ST_ETIMEOUT;
+      const R* r = sRaw + (size_t)(q % RAW) * NT * 256 + cell2;
 #pragma unroll
       for (int v = 0; v < NT; ++v) u[v] = r[v * 256];
     } else {
@@ -465,12 +488,53 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       aux[0] = R(0);
     }
     P::cons2prim(u, pr, aux, pp, st);
-    R* w = sPr + (size_t)pslot(p) * NT * 256 + cell2;
+    R* w = ring(p) + cellp;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) w[v * 256] = pr[v];
+    for (int v = 0; v < NV; ++v) w[v * 400] = pr[v];
     if constexpr (NA > 0) {
 #pragma unroll
-      for (int i = 0; i < NA; ++i) w[(NV + i) * 256] = aux[i];
+      for (int i = 0; i < NA; ++i) w[(NV + i) * 400] = aux[i];
+    }
+  };
+  // Halo source of this thread's halo cell: the address at plane 0 and the step per plane
+  // (a plane of a block pool, or a row of a ghost slot), formed once per block.
+  int hvs, hnd;
+  const R* ha0 = cell_addr<P, R>(Us, G, src, b, hx, hy, 0, &hvs, &hnd);
+  ptrdiff_t hinc;
+  {
+    int vs1, nd1;
+    hinc = cell_addr<P, R>(Us, G, src, b, hx, hy, 1, &vs1, &nd1) - ha0;
+  }
+  auto halo_mine = [&](int p) { return (t >> 7) == (p & 1); };
+  auto prefetch_halo = [&](int p) {       // raw values of the halo of plane p into its frame
+    if (halo_mine(p)) {
+      const R* a = ha0 + (ptrdiff_t)p * hinc;
+      R* d = ring(p) + hoff;
+#pragma unroll
+      for (int v = 0; v < NT; ++v) cp_async_elem(d + v * 400, a + (size_t)v * hvs);
+      cp_async_commit();
+    }
+  };
+  auto convert_halo = [&](int p) {        // the same thread's fetch, converted in place
+    if (halo_mine(p)) {
+      cp_async_wait_all();
+      R* d = ring(p) + hoff;
+      R u[NT], pr[NV], aux[NAW];
+#pragma unroll
+      for (int v = 0; v < NT; ++v) u[v] = d[v * 400];
+      if (hnd >= 0) {
+        if (P::IV >= 0) u[P::IV + hnd] = -u[P::IV + hnd];
+        if (P::BOFF >= 0) u[P::BOFF + hnd] = -u[P::BOFF + hnd];
+      }
+      if constexpr (NA > 0) {
+#pragma unroll
+        for (int i = 0; i < NA; ++i) aux[i] = u[NV + i];
+      } else {
+        aux[0] = R(0);
+      }
+      P::cons2prim(u, pr, aux, pp, st);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) d[v * 400] = pr[v];
     }
   };
   // z-face flux at k + 1/2 of this column. hz holds half the limited slope of plane k
@@ -478,12 +542,12 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   // plane k + 1, so each plane's z-slope is formed once.
   auto zface = [&](int k, R* f, R* hz) {
     R bq[NV], c[NV], d[NV], pl[NV], pr[NV];
-    const R* r1 = sPr + (size_t)pslot(k) * NT * 256 + cell2;
-    const R* r2 = sPr + (size_t)pslot(k + 1) * NT * 256 + cell2;
-    const R* r3 = sPr + (size_t)pslot(k + 2) * NT * 256 + cell2;
+    const R* r1 = ring(k) + cellp;
+    const R* r2 = ring(k + 1) + cellp;
+    const R* r3 = ring(k + 2) + cellp;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      bq[v] = r1[v * 256]; c[v] = r2[v * 256]; d[v] = r3[v * 256];
+      bq[v] = r1[v * 400]; c[v] = r2[v * 400]; d[v] = r3[v * 400];
       const R h = v < P::NREC ? half_slope<R, LIM>(c[v] - bq[v], d[v] - c[v]) : R(0);
       pl[v] = bq[v] + hz[v];
       pr[v] = c[v] - h;
@@ -492,72 +556,51 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     if constexpr (PAIRED) riemann_z_lr<P, FLUX>(pl, pr, f, pp);
     else riemann<P, R, 2, FLUX>(pl, pr, f, pp);
   };
-  auto xface = [&](int fi, int row, R* f) {  // x-face fi - 1/2 of row `row` in plane buffer
+  auto xface = [&](const R* C, int fi, int row, R* f) {  // x-face fi - 1/2 of row `row`
     R a[NV], bq[NV], c[NV], d[NV], pl[NV], pr[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const R* r = sC + v * 400 + (row + 2) * 20 + fi;
+      const R* r = C + v * 400 + (row + 2) * 20 + fi;
       a[v] = r[0]; bq[v] = r[1]; c[v] = r[2]; d[v] = r[3];
     }
     plm<NV, R, LIM, P::NREC>(a, bq, c, d, pl, pr);
     riemann<P, R, 0, FLUX>(pl, pr, f, pp);
   };
-  auto yface = [&](int fj, int col, R* f) {  // y-face fj - 1/2 of column `col`
+  auto yface = [&](const R* C, int fj, int col, R* f) {  // y-face fj - 1/2 of column `col`
     R a[NV], bq[NV], c[NV], d[NV], pl[NV], pr[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const R* r = sC + v * 400 + fj * 20 + col + 2;
+      const R* r = C + v * 400 + fj * 20 + col + 2;
       a[v] = r[0]; bq[v] = r[20]; c[v] = r[40]; d[v] = r[60];
     }
     plm<NV, R, LIM, P::NREC>(a, bq, c, d, pl, pr);
     riemann<P, R, 1, FLUX>(pl, pr, f, pp);
   };
 
-  // Halo cell h (0..127) of plane k: x-faces for h < 64, y-faces above; the half of the
-  // CTA with t - 128 (k & 1) in [0, 128) owns plane k's halo. Its raw values are fetched
-  // one plane ahead with cp.async into sHalo[v][h] by the same thread.
-  auto halo_xy = [&](int h, int& x, int& y) {
-    const int side = (h >> 5) & 1, layer = (h >> 4) & 1, rr = h & 15;
-    const int c = side ? NB + layer : layer - 2;
-    if (h < 64) { x = c; y = rr; } else { x = rr; y = c; }
-  };
-  auto prefetch_halo = [&](int k) {
-    const int h = t - 128 * (k & 1);
-    if (h >= 0 && h < 128) {
-      int x, y, vs, nd;
-      halo_xy(h, x, y);
-      const R* a = cell_addr<P, R>(Us, G, src, b, x, y, k, &vs, &nd);
-#pragma unroll
-      for (int v = 0; v < NT; ++v) cp_async_elem(sHalo + v * 128 + h, a + (size_t)v * vs);
-      cp_async_commit();
-    }
-  };
-
-  prefetch_halo(0);
+  // ---- prologue: raw planes by TMA, halo fetches of planes 0 and 1, primitives of planes
+  // -2 .. 1 of this column, the z-face at -1/2, the halo of plane 0
   if (t == 0) {
     fence_proxy_async();   // the previous block's reads of the ring precede these copies
-    for (int p = -2; p <= 1; ++p) issue(p);
+    for (int p = -2; p <= RAW - 3; ++p) issue(p);
   }
-  // Prologue: planes -2 .. 1 of this column, then the z-face at -1/2. Ring slots at
-  // iteration k: k&3 -> plane k+2 (converted now), (k+1)&3 -> plane k+3 (in flight),
-  // (k+2)&3 -> plane k (its update), (k+3)&3 -> plane k+1.
+  prefetch_halo(0);
+  prefetch_halo(1);
   convert_own(-2);
   convert_own(-1);
   __syncthreads();   // raw slots of planes -2 and -1 are free
   if (t == 0) {
     fence_proxy_async();
-    issue(2);
-    issue(3);
+    for (int p = RAW - 2; p <= 3; ++p) issue(p);
   }
   convert_own(0);
   R fzd[NV], fzu[NV], hz[NV];
-  {  // z-slope of plane 0 from planes -1, 0 and 1 ... before plane 1 takes plane -2's slot
-    const R* r0 = sPr + (size_t)pslot(-2) * NT * 256 + cell2;
-    const R* r1 = sPr + (size_t)pslot(-1) * NT * 256 + cell2;
-    const R* r2 = sPr + (size_t)pslot(0) * NT * 256 + cell2;
+  {  // z-slope of plane -1 from planes -2, -1 and 0 ... before plane 1 takes plane -2's slot
+    const R* r0 = ring(-2) + cellp;
+    const R* r1 = ring(-1) + cellp;
+    const R* r2 = ring(0) + cellp;
 #pragma unroll
     for (int v = 0; v < NV; ++v)
-      hz[v] = v < P::NREC ? half_slope<R, LIM>(r1[v * 256] - r0[v * 256], r2[v * 256] - r1[v * 256]) : R(0);
+      hz[v] = v < P::NREC ? half_slope<R, LIM>(r1[v * 400] - r0[v * 400], r2[v * 400] - r1[v * 400]) : R(0);
   }
   convert_own(1);
   zface(-1, fzd, hz);
@@ -565,68 +608,78 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
 #pragma unroll
     for (int v = 0; v < NV; ++v) FR[((size_t)slot[4] * NV + v) * 256 + cell2] = fzd[v];
   }
+  convert_halo(0);
+  __syncthreads();   // plane 0 of the ring (interior and halo) is complete
 
   R ssum = R(0), smax = R(0);
 
   R Tkm1 = R(0);   // conduction: T = p / rho of this column at plane k - 1
+  R Bkm1[3] = {R(0), R(0), R(0)};   // resistivity: B of this column at plane k - 1
   for (int k = 0; k < NB; ++k) {
-    // ---- phase 1
+    R* sFx = sFx0 + (SFB == 2 ? (k & 1) : 0) * NV * 272;
+    R* sFy = sFy0 + (SFB == 2 ? (k & 1) : 0) * NV * 272;
+    if (RAW == 4 && t == 0 && k >= 1 && k + 3 <= NB + 1) {
+      fence_proxy_async();
+      issue(k + 3);   // raw slot of plane k-1, read by its update before the previous barrier
+    }
+    // ---- A, B
     if constexpr (P::QV >= 0) {   // plane k - 1 leaves the primitive ring now
-      const R* r = sPr + (size_t)pslot(k - 1) * NT * 256 + cell2;
-      Tkm1 = rdiv(r[P::IE * 256], r[0]);
+      const R* r = ring(k - 1) + cellp;
+      Tkm1 = rdiv(r[P::IE * 400], r[0]);
+    }
+    if constexpr (RESP) {
+      const R* r = ring(k - 1) + cellp;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) Bkm1[i] = r[(P::BOFF + i) * 400];
     }
     if (k + 2 <= NB + 1) convert_own(k + 2);
-    {
-      const R* r = sPr + (size_t)pslot(k) * NT * 256 + cell2;
-#pragma unroll
-      for (int v = 0; v < NV; ++v) sC[v * 400 + (ty + 2) * 20 + tx + 2] = r[v * 256];
-    }
-    {
-      const int h = t - 128 * (k & 1);       // halves of the CTA take turns on the halo
-      if (h >= 0 && h < 128) {
-        int x, y, vs, nd;
-        halo_xy(h, x, y);
-        cell_addr<P, R>(Us, G, src, b, x, y, k, &vs, &nd);
-        cp_async_wait_all();
-        R u[NT], p[NV], aux[NAW];
-#pragma unroll
-        for (int v = 0; v < NT; ++v) u[v] = sHalo[v * 128 + h];
-        if (nd >= 0) {
-          if (P::IV >= 0) u[P::IV + nd] = -u[P::IV + nd];
-          if (P::BOFF >= 0) u[P::BOFF + nd] = -u[P::BOFF + nd];
-        }
-        if constexpr (NA > 0) {
-#pragma unroll
-          for (int i = 0; i < NA; ++i) aux[i] = u[NV + i];
-        } else {
-          aux[0] = R(0);
-        }
-        P::cons2prim(u, p, aux, pp, st);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) sC[v * 400 + (y + 2) * 20 + x + 2] = p[v];
-      }
-    }
-    __syncthreads();
-    // ---- phase 2
-    if (t == 0 && k >= 1 && k + 3 <= NB + 1) {
-      fence_proxy_async();
-      issue(k + 3);   // slot (k+1)&3: plane k-1's raw data, read by its update before this barrier
-    }
-    if (k + 1 < NB) prefetch_halo(k + 1);   // the other half of the CTA; sHalo is free now
+    if (k + 1 < NB) convert_halo(k + 1);
+    if (k + 2 < NB) prefetch_halo(k + 2);
+    // ---- C
+    const R* Ck = ring(k);
     // conduction target kappa0 T^(5/2) b.grad T of cell (tx, ty, k) (Eq. 10): central
-    // differences of T = p / rho over the face neighbours (x, y from the plane buffer, z
-    // from the ring and the carried plane k - 1), b of the cell
+    // differences of T = p / rho over the face neighbours (x, y from the ring plane k with
+    // its halo, z from ring plane k + 1 and the carried plane k - 1), b of the cell
     R htc_g = R(0);
     if constexpr (P::QV >= 0) {
-      const R* C = sC + (ty + 2) * 20 + tx + 2;
+      const R* C = Ck + cellp;
       auto T_at = [&](int o) { return rdiv(C[P::IE * 400 + o], C[o]); };
-      const R* rp = sPr + (size_t)pslot(k + 1) * NT * 256 + cell2;
+      const R* rp = ring(k + 1) + cellp;
       const R Tc = T_at(0);
       const R gx = (T_at(1) - T_at(-1)) * (R(0.5) * idx);
       const R gy = (T_at(20) - T_at(-20)) * (R(0.5) * idy);
-      const R gz = (rdiv(rp[P::IE * 256], rp[0]) - Tkm1) * (R(0.5) * idz);
+      const R gz = (rdiv(rp[P::IE * 400], rp[0]) - Tkm1) * (R(0.5) * idz);
       const R bgrad = (C[P::BOFF * 400] * gx + C[(P::BOFF + 1) * 400] * gy) + C[(P::BOFF + 2) * 400] * gz;
       htc_g = kap0 * (Tc * Tc * rsqrt_(Tc)) * bgrad;
+    }
+    // resistive sources of cell (tx, ty, k) (Section 2.3.3): eta lap B for the induction
+    // equation and eta (J.J + B.lap B) for the energy equation, J = curl B, from the face
+    // neighbours (x, y from the ring plane k with its halo, z from ring plane k + 1 and the
+    // carried plane k - 1): central differences and the 7-point Laplacian
+    R rsrc[4] = {R(0), R(0), R(0), R(0)};
+    if constexpr (RESP) {
+      const R* C = Ck + cellp;
+      const R* rp = ring(k + 1) + cellp;
+      const R ix2 = idx * idx, iy2 = idy * idy, iz2 = idz * idz;
+      const R hx = R(0.5) * idx, hy = R(0.5) * idy, hzz = R(0.5) * idz;
+      R bc[3], lap[3], gx[3], gy[3], gz[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const R* q = C + (P::BOFF + i) * 400;
+        const R b0 = q[0], xp = q[1], xm = q[-1], yp = q[20], ym = q[-20];
+        const R zp = rp[(P::BOFF + i) * 400], zm = Bkm1[i];
+        bc[i] = b0;
+        lap[i] = (((xp - b0) - (b0 - xm)) * ix2 + ((yp - b0) - (b0 - ym)) * iy2) + ((zp - b0) - (b0 - zm)) * iz2;
+        gx[i] = (xp - xm) * hx;
+        gy[i] = (yp - ym) * hy;
+        gz[i] = (zp - zm) * hzz;
+      }
+      const R j0 = gy[2] - gz[1], j1 = gz[0] - gx[2], j2 = gx[1] - gy[0];
+      const R jj = (j0 * j0 + j1 * j1) + j2 * j2;
+      const R blap = (bc[0] * lap[0] + bc[1] * lap[1]) + bc[2] * lap[2];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) rsrc[i] = reta * lap[i];
+      rsrc[3] = reta * (jj + blap);
     }
     // U^n of cell (tx, ty, k) for the stage combine, loaded now so that the face work of
     // this phase covers its latency
@@ -644,8 +697,8 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
         f2 a[NV], bq[NV], c[NV], d[NV], pl[NV], pr[NV], fp[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const R* rx = sC + v * 400 + (fr + 2) * 20 + fc;
-          const R* ry = sC + swapv<P>(v) * 400 + fr * 20 + fc + 2;
+          const R* rx = Ck + v * 400 + (fr + 2) * 20 + fc;
+          const R* ry = Ck + swapv<P>(v) * 400 + fr * 20 + fc + 2;
           a[v] = f2_of(rx[0], ry[0]);
           bq[v] = f2_of(rx[1], ry[20]);
           c[v] = f2_of(rx[2], ry[40]);
@@ -669,14 +722,14 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
           for (int v = 0; v < NV; ++v) FR[((size_t)slot[2] * NV + swapv<P>(v)) * 256 + k * 16 + fc] = fy[v];
         }
       } else {
-        xface(fc, fr, f);
+        xface(Ck, fc, fr, f);
 #pragma unroll
         for (int v = 0; v < NV; ++v) sFx[v * 272 + fr * 16 + fc] = f[v];
         if (FR && fc == 0 && slot[0] >= 0) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) FR[((size_t)slot[0] * NV + v) * 256 + k * 16 + fr] = f[v];
         }
-        yface(fr, fc, f);
+        yface(Ck, fr, fc, f);
 #pragma unroll
         for (int v = 0; v < NV; ++v) sFy[v * 272 + fr * 16 + fc] = f[v];
         if (FR && fr == 0 && slot[2] >= 0) {
@@ -694,7 +747,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
         R a[NV], bq[NV], c[NV], d[NV], pl[NV], pr[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const R* q = sC + v * 400 + base;
+          const R* q = Ck + v * 400 + base;
           a[v] = q[0]; bq[v] = q[stp]; c[v] = q[2 * stp]; d[v] = q[3 * stp];
         }
         swap_xy<P, R>(a, yd);
@@ -721,11 +774,15 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       }
     }
     __syncthreads();
-    // ---- phase 3: flux divergence and stage combine of cell (tx, ty, k)
+    if (RAW == 5 && t == 0 && k + 4 <= NB + 1) {
+      fence_proxy_async();
+      issue(k + 4);   // raw slot of plane k-1, whose update finished before this barrier
+    }
+    // ---- D: flux divergence and stage combine of cell (tx, ty, k)
     {
       const size_t cell = (size_t)k * 256 + cell2;
       const size_t base = (size_t)b * NT * NCELL + cell;
-      const R* raw = sRaw + (size_t)((k + 2) & 3) * NT * 256 + cell2;
+      const R* raw = sRaw + (size_t)((k + 2) % RAW) * NT * 256 + cell2;
       R out[NV];
       if constexpr (P::SOURCE) {
         // all flux divergences first: the source needs those of other variables
@@ -739,9 +796,9 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
           fzd[v] = fzu[v];
         }
         R pc[NV];
-        const R* pk = sPr + (size_t)pslot(k) * NT * 256 + cell2;
+        const R* pk = Ck + cellp;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) pc[v] = pk[v * 256];
+        for (int v = 0; v < NV; ++v) pc[v] = pk[v * 400];
         P::source(L, pc);
         if constexpr (P::QV >= 0) L[P::QV] = (htc_g - pc[P::QV]) * rq4;   // -(q - target) / tau
 #pragma unroll
@@ -759,7 +816,11 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
           const R lx = (sFx[v * 272 + fxr] - sFx[v * 272 + cell2]) * idx;
           const R ly = (sFy[v * 272 + (ty + 1) * 16 + tx] - sFy[v * 272 + ty * 16 + tx]) * idy;
           const R lz = (fzu[v] - fzd[v]) * idz;
-          const R L = -((lx + ly) + lz);
+          R L = -((lx + ly) + lz);
+          if constexpr (RESP) {
+            if (v >= P::BOFF && v < P::BOFF + 3) L = L + rsrc[v - P::BOFF];
+            if (v == P::IE) L = L + rsrc[3];
+          }
           R val = raw[v * 256] + rdt * L;
           if (combine) val = ra * unk[v] + rb * val;
           out[v] = val;
@@ -771,10 +832,10 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       for (int v = 0; v < NV; ++v) Uo[base + (size_t)v * NCELL] = out[v];
       R auxk[NAW];
       if constexpr (NA > 0) {
-        const R* pa = sPr + (size_t)pslot(k) * NT * 256 + cell2;
+        const R* pa = Ck + cellp;
 #pragma unroll
         for (int i = 0; i < NA; ++i) {
-          auxk[i] = pa[(NV + i) * 256];
+          auxk[i] = pa[(NV + i) * 400];
           Uo[base + (size_t)(NV + i) * NCELL] = auxk[i];
         }
       } else {
@@ -787,10 +848,11 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
         cell_speeds<PT, R>(out, ad, pp, dxr, ssum, smax, st);
       }
     }
+    if (SFB == 1) __syncthreads();   // the flux buffer and plane k's raw slot are reused next
   }
   if (speeds) block_max2<256>(ssum, smax, speeds);
   if (t == 0) {
-    // every read of this block's face table happened before the last plane's second barrier
+    // every read of this block's face table happened before the last plane's barrier
     const int nx = A.work ? (int)gridDim.x + atomicAdd(A.work, 1) : b + (int)gridDim.x;
     s_next = nx;
     if (nx < A.nblk) {
@@ -801,15 +863,15 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       }
     }
   }
-  __syncthreads();       // ring, halo staging and reduction scratch are reused by the next block
+  __syncthreads();       // ring, raw slots, flux buffers and reduction scratch are reused next
   b = s_next;
   }
   if (st) atomicOr(A.status, st);
 }
 
-template <template <typename> class PT, typename R>
+template <template <typename> class PT, typename R, int RAW, int SFB>
 constexpr size_t stage_smem_bytes() {
-  return StageSmem<PT, R>::total;
+  return StageSmem<PT, R, RAW, SFB>::total;
 }
 
 }  // namespace agile

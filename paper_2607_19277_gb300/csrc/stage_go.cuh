@@ -4,17 +4,22 @@
 
 namespace agile {
 
-template <template <typename> class PT, typename R, int LIM, int FLUX>
-static cudaError_t stage_go(const StageArgs& a, cudaStream_t s) {
-  // CTAs per SM the register budget targets: 1 in FP64; in FP32 3 when three CTAs' shared
-  // memory fits an SM (233472 bytes, 1 KB reserved per CTA), else 2
-  constexpr size_t SMEM = stage_smem_bytes<PT, R>();
-  constexpr int MINB = sizeof(R) == 8 ? 1 : (3 * (SMEM + 1024) <= 233472 ? 3 : 2);
-  auto k = stage_kernel<PT, R, LIM, FLUX, MINB>;
-  const size_t smem = SMEM;
+// CTAs per SM a staging layout allows: FP64 targets one (its register budget); FP32 three when
+// three CTAs' shared memory fits an SM (233472 bytes, 1 KB reserved per CTA), else two.
+template <template <typename> class PT, typename R, int RAW, int SFB>
+constexpr int stage_minb() {
+  constexpr size_t SMEM = stage_smem_bytes<PT, R, RAW, SFB>();
+  return sizeof(R) == 8 ? 1 : (3 * (SMEM + 1024) <= 233472 ? 3 : (2 * (SMEM + 1024) <= 233472 ? 2 : 1));
+}
+
+template <template <typename> class PT, typename R, int LIM, int FLUX, int RAW, int SFB>
+static cudaError_t stage_go_layout(const StageArgs& a, cudaStream_t s) {
+  constexpr size_t SMEM = stage_smem_bytes<PT, R, RAW, SFB>();
+  constexpr int MINB = stage_minb<PT, R, RAW, SFB>();
+  auto k = stage_kernel<PT, R, LIM, FLUX, MINB, RAW, SFB>;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -34,8 +39,23 @@ static cudaError_t stage_go(const StageArgs& a, cudaStream_t s) {
   args.fa = (float)a.a;
   args.fb = (float)a.b;
   args.combine = a.a != 0.0 ? 1 : 0;
-  k<<<grid, 256, smem, s>>>(*static_cast<const CUtensorMap*>(args.tmap), args);
+  k<<<grid, 256, SMEM, s>>>(*static_cast<const CUtensorMap*>(args.tmap), args);
   return cudaGetLastError();
+}
+
+// Staging layouts: STAGE_LAYOUT_RING4 = four raw slots, one flux buffer, two barriers per
+// plane; STAGE_LAYOUT_RING5_DB = five raw slots, two flux buffers, one barrier per plane.
+// The default (layout 0) takes the second where it keeps as many CTAs per SM as the first
+// (FP32 stencils only; FP64 keeps the first).
+template <template <typename> class PT, typename R, int LIM, int FLUX>
+static cudaError_t stage_go(const StageArgs& a, cudaStream_t s) {
+  if constexpr (sizeof(R) == 8) {
+    return stage_go_layout<PT, R, LIM, FLUX, 4, 1>(a, s);
+  } else {
+    constexpr bool db_default = stage_minb<PT, R, 5, 2>() >= stage_minb<PT, R, 4, 1>();
+    const bool db = a.layout == STAGE_LAYOUT_RING5_DB || (a.layout == 0 && db_default);
+    return db ? stage_go_layout<PT, R, LIM, FLUX, 5, 2>(a, s) : stage_go_layout<PT, R, LIM, FLUX, 4, 1>(a, s);
+  }
 }
 
 }  // namespace agile
