@@ -101,6 +101,14 @@ typedef struct {
  *                 approximation h = 5/2 theta + sqrt(9/4 theta^2 + 1), theta = p/rho
  *                 (Section 2.3.4); gamma is then unused by the physics
  *  htc_kappa0     AGILE_FFHD_HTC: conduction coefficient kappa0 >= 0 (ignored otherwise)
+ *  eta            AGILE_MHD_GLM: uniform resistivity eta >= 0 (Section 2.3.3: -curl(eta J) in
+ *                 the induction equation and div(B x eta J) in the energy equation, J =
+ *                 curl B), added in every RK stage as the sources eta lap B and
+ *                 eta (J.J + B.lap B) of the stage state, evaluated with the compact
+ *                 second-order stencil over the six face neighbours; with eta > 0 the CFL
+ *                 step also obeys the diffusive bound: dt = cfl / max(max_cells sum_d
+ *                 (|v_d| + c_d) / dx_d, 2 eta sum_d dx_d^-2 at the finest level). Meshes
+ *                 only (batches take eta = 0). Must be 0 for the other modules.
  */
 typedef struct {
   int physics;
@@ -124,6 +132,7 @@ typedef struct {
   double lohner_eps;
   int eos;
   double htc_kappa0;
+  double eta;
 } agile_config;
 
 /* Create a mesh of level-1 blocks (Fig. 1, "init level one") with uninitialised state.
@@ -333,17 +342,22 @@ agile_status agile_batch_regrid_flags(agile_batch* batch, int solve, const int* 
 
 /* Autotuner of the batched stage launches (no counterpart in the paper): times `trials`
  * launches of the first RK stage (which reads the solution and writes only a stage buffer,
- * so the solution is not modified) for six launch shapes, the persistent grid at 1, 2 and 3
- * CTAs per SM, each with blocks taken from an atomic counter or strided by the grid, and
- * keeps the fastest for every later step (the CUDA graph of a step is captured again).
+ * so the solution is not modified) for twelve launch shapes and keeps the fastest for every
+ * later step (the CUDA graph of a step is captured again). A shape is a staging layout of
+ * the stage kernel's shared memory (1: four raw-plane TMA slots and one face-flux buffer,
+ * two CTA barriers per plane; 2: five raw slots and two flux buffers, one barrier per plane,
+ * more shared memory per CTA; FP64 stencils time layout 1 only), a persistent grid of 1, 2
+ * or 3 CTAs per SM, and blocks taken from an atomic counter or strided by the grid.
  * Results do not depend on the choice: every block's arithmetic is the same.
  *  trials   1..100 timed launches per shape (after one untimed launch)
- *  grid     out: CTAs of the chosen shape; dynamic: out, 1 for the atomic counter
- *  ms       out (may be NULL, else 6 floats): mean ms per launch of the shapes in the
- *           order (1 CTA/SM, counter), (1, strided), (2, counter), (2, strided), (3,
- *           counter), (3, strided)
+ *  grid     out: CTAs of the chosen shape; dynamic: out, 1 for the atomic counter;
+ *  layout   out: the chosen staging layout (1 or 2); each may be NULL
+ *  ms       out (may be NULL, else 12 floats): mean ms per launch of the shapes in the
+ *           order layout 1: (1 CTA/SM, counter), (1, strided), (2, counter), (2, strided),
+ *           (3, counter), (3, strided), then the same six for layout 2 (-1 where not timed)
  * Synchronises the batch's stream. */
-agile_status agile_batch_autotune(agile_batch* batch, int trials, int* grid, int* dynamic, float* ms);
+agile_status agile_batch_autotune(agile_batch* batch, int trials, int* grid, int* dynamic, int* layout,
+                                  float* ms);
 
 /* Copy the current state of solve src_solve of batch src into solve dst_solve of batch dst
  * (device to device; no counterpart in the paper: it lets a request loop rebuild its batch

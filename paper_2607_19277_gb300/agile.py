@@ -50,7 +50,7 @@ class agile_config(C.Structure):
                 ("refine_nvars", C.c_int), ("refine_vars", C.c_int * 9),
                 ("refine_weights", C.c_double * 9), ("refine_tol", C.c_double),
                 ("derefine_ratio", C.c_double), ("lohner_eps", C.c_double), ("eos", C.c_int),
-                ("htc_kappa0", C.c_double)]
+                ("htc_kappa0", C.c_double), ("eta", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -118,7 +118,7 @@ def load(path: str = LIB_PATH):
         "agile_batch_cfl_dt": (C.c_int, [P, dp]),
         "agile_batch_get_state": (C.c_int, [P, C.c_int, ip, ip, dp]),
         "agile_batch_copy_solve": (C.c_int, [P, C.c_int, P, C.c_int]),
-        "agile_batch_autotune": (C.c_int, [P, C.c_int, ip, ip, C.POINTER(C.c_float)]),
+        "agile_batch_autotune": (C.c_int, [P, C.c_int, ip, ip, ip, C.POINTER(C.c_float)]),
         "agile_batch_regrid": (C.c_int, [P, C.c_int, C.c_int, ip, ip]),
         "agile_batch_regrid_flags": (C.c_int, [P, C.c_int, ip, C.c_int, ip, ip]),
         "agile_batch_sync": (C.c_int, [P]),
@@ -137,7 +137,7 @@ def make_config(physics="hd", limiter="minmod", flux="hll", rk=2, real_bytes=8, 
                 cfl=0.4, glm_alpha=0.5, base_blocks=(4, 4, 4), xmin=(0.0, 0.0, 0.0),
                 xmax=(1.0, 1.0, 1.0), bc=("periodic",) * 6, max_level=1, refine_vars=(0,),
                 refine_weights=(1.0,), refine_tol=0.2, derefine_ratio=1.0 / 8.0,
-                lohner_eps=0.01, eos="ideal", htc_kappa0=0.0) -> agile_config:
+                lohner_eps=0.01, eos="ideal", htc_kappa0=0.0, eta=0.0) -> agile_config:
     c = agile_config()
     c.physics = PHYSICS[physics]
     c.limiter = LIMITER[limiter]
@@ -163,6 +163,7 @@ def make_config(physics="hd", limiter="minmod", flux="hll", rk=2, real_bytes=8, 
     c.lohner_eps = lohner_eps
     c.eos = EOS[eos] if isinstance(eos, str) else eos
     c.htc_kappa0 = htc_kappa0
+    c.eta = eta
     return c
 
 
@@ -520,11 +521,12 @@ class Batch:
         return nr.value, nc.value
 
     def autotune(self, trials=3):
-        """Pick the fastest stage-launch shape; returns (grid, dynamic, ms per shape)."""
-        g, d = C.c_int(), C.c_int()
-        ms = (C.c_float * 6)()      # the library writes six values
-        self._ck(self.lib.agile_batch_autotune(self.ptr, int(trials), C.byref(g), C.byref(d), ms))
-        return g.value, bool(d.value), list(ms)
+        """Pick the fastest stage-launch shape; returns (grid, dynamic, ms per shape, layout)."""
+        g, d, lay = C.c_int(), C.c_int(), C.c_int()
+        ms = (C.c_float * 12)()     # the library writes twelve values
+        self._ck(self.lib.agile_batch_autotune(self.ptr, int(trials), C.byref(g), C.byref(d),
+                                               C.byref(lay), ms))
+        return g.value, bool(d.value), list(ms), lay.value
 
     def copy_solve(self, solve, src, src_solve):
         """Device-to-device copy of solve src_solve of Batch src into solve `solve`."""

@@ -127,7 +127,20 @@ bool scheme_ok(const agile_config& c) {
   if (c.eos != AGILE_EOS_IDEAL && !(c.eos == AGILE_EOS_SYNGE && c.physics == AGILE_SRHD)) return false;
   if (ffhd && c.max_level != 1) return false;
   if (c.physics == AGILE_FFHD_HTC && !(c.htc_kappa0 >= 0.0 && c.htc_kappa0 < 1e300)) return false;
+  if (!(c.eta >= 0.0 && c.eta < 1e300) || (c.eta > 0.0 && c.physics != AGILE_MHD_GLM)) return false;
   return true;
+}
+
+// 2 eta sum_d dx_d^-2 at the finest level of the mesh (0 without resistivity): the largest
+// rate of the resistive diffusion term, which bounds the step like the signal speeds do.
+double resistive_rate(const agile_config& c, int finest_level) {
+  if (!(c.eta > 0.0)) return 0.0;
+  double r = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const double dx = (c.xmax[d] - c.xmin[d]) / ((double)c.base_blocks[d] * NB * (double)(1 << (finest_level - 1)));
+    r += 1.0 / (dx * dx);
+  }
+  return 2.0 * c.eta * r;
 }
 
 AuxArgs aux_args(agile_mesh* m, void* U) {
@@ -289,6 +302,12 @@ agile_status apply_ic(agile_mesh* m, void* U, const std::vector<int>& blocks, co
   dfree_t(m, d_prim);
   dfree_t(m, d_blocks);
   return AGILE_OK;
+}
+
+// Resistive rate of the mesh at its current finest level (leaves are sorted by level).
+double mesh_res_rate(const agile_mesh* m) {
+  if (!(m->cfg.eta > 0.0) || m->mesh->blocks().empty()) return 0.0;
+  return resistive_rate(m->cfg, m->mesh->blocks().back().lev);
 }
 
 agile_status ensure_speeds(agile_mesh* m) {
@@ -551,7 +570,7 @@ agile_status agile_cfl_dt(agile_mesh* m, double* dt_out) {
   double smax;
   memcpy(&smax, &h[0], sizeof(double));
   if (!(smax > 0.0)) return fail(m, AGILE_EUNPHYS, "zero or invalid signal speed");
-  *dt_out = m->cfg.cfl / smax;
+  *dt_out = m->cfg.cfl / std::max(smax, mesh_res_rate(m));
   return AGILE_OK;
 }
 
@@ -572,7 +591,7 @@ agile_status agile_step(agile_mesh* m, double dt) {
   if (!m) return AGILE_EINVAL;
   agile_status s = ensure_speeds(m);
   if (s) return s;
-  CK(m, launch_set_dt(m->d_speeds, m->d_dtch, dt, m->cfg.cfl, m->stream));
+  CK(m, launch_set_dt(m->d_speeds, m->d_dtch, dt, m->cfg.cfl, m->stream, 1, mesh_res_rate(m)));
   CK(m, cudaMemsetAsync(m->d_work, 0, 4 * sizeof(int), m->stream));
   m->total_launches++;
   const bool mhd = m->cfg.physics == AGILE_MHD_GLM;
@@ -612,6 +631,7 @@ agile_status agile_step(agile_mesh* m, double dt) {
     A.gamma = m->cfg.gamma;
     A.glm_alpha = m->cfg.glm_alpha;
     A.htc_kappa0 = m->cfg.htc_kappa0;
+    A.eta = m->cfg.eta;
     A.glm_post = (mhd && last && fuse) ? 1 : 0;
     A.nblk = m->nblk;
     A.status = m->d_status;
@@ -627,6 +647,7 @@ agile_status agile_step(agile_mesh* m, double dt) {
     }
     cudaError_t e;
     if (m->cfg.physics == AGILE_HD) e = launch_stage_hd(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
+    else if (mhd && m->cfg.eta > 0.0) e = launch_stage_mhd_res(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
     else if (mhd) e = launch_stage_mhd(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
     else if (m->cfg.eos == AGILE_EOS_SYNGE)
       e = launch_stage_srhd_synge(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
@@ -981,6 +1002,7 @@ struct agile_batch {
   std::string err;
   int grid = 0;                     // persistent CTAs of the stage launches (0: default)
   bool dynamic = true;              // blocks taken from an atomic counter (else strided)
+  int layout = 0;                   // staging layout of the stage kernel (0: the default)
   // refinement: ghost slots, flux registers and their tasks of all solves (indices offset)
   void* G = nullptr;
   void* FR = nullptr;
@@ -1363,6 +1385,7 @@ agile_status batch_enqueue_step(agile_batch* B) {
     A.solve_of = B->d_solve_of;
     A.work = B->dynamic ? B->d_work + st : nullptr;
     A.grid = B->grid;
+    A.layout = B->layout;
     cudaError_t e;
     if (B->cfg.physics == AGILE_HD) e = launch_stage_hd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
     else if (mhd) e = launch_stage_mhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
@@ -1387,7 +1410,7 @@ agile_status batch_enqueue_step(agile_batch* B) {
 }
 
 // One launch of the first stage (U^n -> the stage-1 buffer; the solution is not modified).
-agile_status batch_stage1(agile_batch* B, int grid, bool dynamic) {
+agile_status batch_stage1(agile_batch* B, int grid, bool dynamic, int layout) {
   if (dynamic) BCK(B, cudaMemsetAsync(B->d_work, 0, sizeof(int), B->stream));
   StageArgs A;
   A.Us = B->U[0];
@@ -1410,6 +1433,7 @@ agile_status batch_stage1(agile_batch* B, int grid, bool dynamic) {
   A.solve_of = B->d_solve_of;
   A.work = dynamic ? B->d_work : nullptr;
   A.grid = grid;
+  A.layout = layout;
   cudaError_t e;
   const bool mhd = B->cfg.physics == AGILE_MHD_GLM;
   if (B->cfg.physics == AGILE_HD) e = launch_stage_hd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
@@ -1428,7 +1452,8 @@ agile_status batch_stage1(agile_batch* B, int grid, bool dynamic) {
 
 extern "C" {
 
-agile_status agile_batch_autotune(agile_batch* B, int trials, int* grid, int* dynamic, float* ms) {
+agile_status agile_batch_autotune(agile_batch* B, int trials, int* grid, int* dynamic, int* layout,
+                                  float* ms) {
   if (!B || trials < 1 || trials > 100) return bfail(B, AGILE_EINVAL, "bad argument");
   agile_status s = batch_ensure_speeds(B);
   if (s) return s;
@@ -1442,12 +1467,21 @@ agile_status agile_batch_autotune(agile_batch* B, int trials, int* grid, int* dy
   BCK(B, cudaEventCreate(&e1));
   float best = 0.0f;
   int bi = -1;
-  for (int c = 0; c < 6 && !s; ++c) {
-    const int g = grids[c >> 1];
+  // shape c: staging layout c / 6 (four raw slots and one flux buffer, or five raw slots and
+  // two flux buffers), grid (c % 6) >> 1, counter or strided assignment c & 1
+  const int layouts[2] = {STAGE_LAYOUT_RING4, STAGE_LAYOUT_RING5_DB};
+  const bool fp64 = B->rb == 8;                       // FP64 stencils have the first layout only
+  for (int c = 0; c < 12 && !s; ++c) {
+    const int g = grids[(c % 6) >> 1];
     const bool dyn = (c & 1) == 0;
-    s = batch_stage1(B, g, dyn);                        // warm-up
+    const int lay = layouts[c / 6];
+    if (fp64 && c >= 6) {
+      if (ms) ms[c] = -1.0f;
+      continue;
+    }
+    s = batch_stage1(B, g, dyn, lay);                   // warm-up
     if (!s) BCK(B, cudaEventRecord(e0, B->stream));
-    for (int t = 0; t < trials && !s; ++t) s = batch_stage1(B, g, dyn);
+    for (int t = 0; t < trials && !s; ++t) s = batch_stage1(B, g, dyn, lay);
     if (s) break;
     BCK(B, cudaEventRecord(e1, B->stream));
     BCK(B, cudaEventSynchronize(e1));
@@ -1463,14 +1497,16 @@ agile_status agile_batch_autotune(agile_batch* B, int trials, int* grid, int* dy
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s) return s;
-  B->grid = grids[bi >> 1];
+  B->grid = grids[(bi % 6) >> 1];
   B->dynamic = (bi & 1) == 0;
+  B->layout = layouts[bi / 6];
   if (B->graph) {                     // the next step captures the tuned launches
     cudaGraphExecDestroy(B->graph);
     B->graph = nullptr;
   }
   if (grid) *grid = B->grid;
   if (dynamic) *dynamic = B->dynamic ? 1 : 0;
+  if (layout) *layout = B->layout;
   return batch_status(B);
 }
 
@@ -1483,7 +1519,7 @@ agile_status agile_batch_create(const agile_config* cfgs, int nsolve, const agil
     const agile_config& c = cfgs[i];
     if (c.physics != c0.physics || c.limiter != c0.limiter || c.flux != c0.flux || c.rk != c0.rk ||
         c.real_bytes != c0.real_bytes || c.gamma != c0.gamma || c.cfl != c0.cfl ||
-        c.glm_alpha != c0.glm_alpha || c.eos != c0.eos || c.htc_kappa0 != c0.htc_kappa0 || c.max_level < 1 ||
+        c.glm_alpha != c0.glm_alpha || c.eos != c0.eos || c.htc_kappa0 != c0.htc_kappa0 || c.eta != 0.0 || c.max_level < 1 ||
         c.max_level > 12 ||
         c.refine_nvars < 0 || c.refine_nvars > 9)
       return AGILE_EINVAL;
