@@ -144,6 +144,40 @@ class MHD:
         cf = self.fast_speed(P, d)
         return P[1 + d] - cf, P[1 + d] + cf
 
+    def resistive_source(self, B, dx, eta):
+        """Resistive terms of Section 2.3.3 as cell-centred sources on a block interior.
+
+        The induction equation carries -curl(eta J) and the energy equation
+        div(B x eta J), J = curl B, with uniform eta. With div B = 0 these are eta lap B and
+        eta (J.J + B . lap B): the Ohmic heating eta J^2 plus the change of the magnetic
+        energy B . dB/dt. Both are evaluated with the compact second-order stencil over the
+        six face neighbours: lap_d a = ((a_+ - a_0) - (a_0 - a_-)) / dx_d^2 and
+        d_d a = (a_+ - a_-) / (2 dx_d) (the grad(div B) part of -curl curl B, which needs
+        edge neighbours, is the divergence error GLM controls and is not taken).
+        B: (3, 20, 20, 20) primitives [z, y, x] with filled face ghosts.
+        Returns (S_B (3, 16, 16, 16), S_e (16, 16, 16))."""
+        I = slice(2, 18)
+
+        def sl(d, o):
+            r = [I, I, I]
+            r[2 - d] = slice(2 + o, 18 + o)
+            return tuple(r)
+
+        def d1(a, d):
+            return (a[sl(d, 1)] - a[sl(d, -1)]) / (2.0 * dx[d])
+
+        def d2(a, d):
+            return ((a[sl(d, 1)] - a[sl(d, 0)]) - (a[sl(d, 0)] - a[sl(d, -1)])) / (dx[d] * dx[d])
+
+        lap = np.stack([(d2(B[i], 0) + d2(B[i], 1)) + d2(B[i], 2) for i in range(3)])
+        J = np.stack([d1(B[2], 1) - d1(B[1], 2),
+                      d1(B[0], 2) - d1(B[2], 0),
+                      d1(B[1], 0) - d1(B[0], 1)])
+        Bc = B[(slice(None), I, I, I)]
+        jj = (J[0] * J[0] + J[1] * J[1]) + J[2] * J[2]
+        blap = (Bc[0] * lap[0] + Bc[1] * lap[1]) + Bc[2] * lap[2]
+        return eta * lap, eta * (jj + blap)
+
     def glm_interface(self, PL, PR, d, ch):
         """Exact solution of the linear (B_d, psi) subsystem at a face (Dedner et al. 2002).
 

@@ -61,6 +61,7 @@ class Config:
     lohner_eps: float = 0.01
     cooling: tuple = None          # (T, Lambda) table: optically thin losses (hd, mhd)
     htc_kappa0: float = 0.0        # ffhd_htc: kappa_par = htc_kappa0 T^(5/2)
+    eta: float = 0.0               # mhd: uniform resistivity (Section 2.3.3)
 
 
 def morton3(ix: int, iy: int, iz: int) -> int:
@@ -121,6 +122,8 @@ class Solver:
         self.phys = make_physics(cfg.physics, cfg.gamma, cfg.eos, cfg.htc_kappa0)
         if cfg.physics in ("ffhd", "ffhd_htc") and cfg.max_level != 1:
             raise ValueError("ffhd runs on uniform meshes (max_level 1)")
+        if cfg.eta < 0.0 or (cfg.eta > 0.0 and cfg.physics != "mhd"):
+            raise ValueError("resistivity eta >= 0 applies to mhd")
         self.cool = None
         if cfg.cooling is not None:
             if cfg.physics not in ("hd", "mhd", "ffhd", "ffhd_htc"):
@@ -590,10 +593,20 @@ class Solver:
             smax = max(smax, float(tot.max()))
         return cmax, smax
 
+    def resistive_rate(self):
+        """2 eta sum_d dx_d^-2 at the finest level in use: the forward-Euler stability bound
+        of the resistive diffusion term (its 7-point Laplacian) is dt <= 1 / that."""
+        if self.cfg.eta <= 0.0:
+            return 0.0
+        lev = max(k[0] for k in self.leaves)
+        return 2.0 * self.cfg.eta * sum(1.0 / (h * h) for h in self.dx(lev))
+
     def cfl_dt(self):
-        """Set dt (Fig. 2): dt = CFL / max_cells sum_d (|v_d| + c_d)/dx_d."""
+        """Set dt (Fig. 2): dt = CFL / max_cells sum_d (|v_d| + c_d)/dx_d; with resistivity
+        the same Courant number scales the diffusive bound: dt = CFL / max(that maximum,
+        2 eta sum_d dx_d^-2)."""
         _, smax = self.signal_speeds()
-        return self.cfg.cfl / smax
+        return self.cfg.cfl / max(smax, self.resistive_rate())
 
     def _glm_decay(self, dt, ch):
         """psi <- psi exp(-dt/2 c_h alpha_GLM / min_d dx_d) (one Strang half, Section 2.3.3)."""
@@ -614,7 +627,7 @@ class Solver:
         a caller evolving a sub-domain of a larger mesh passes the global values."""
         cmax, smax = self.signal_speeds()
         if dt is None or dt <= 0:
-            dt = self.cfg.cfl / smax
+            dt = self.cfg.cfl / max(smax, self.resistive_rate())
         if ch is None:
             ch = cmax
         if self.phys.glm:
@@ -633,6 +646,11 @@ class Solver:
                 rhs = self._rhs(fluxes, key)
                 if hasattr(self.phys, "source"):
                     rhs = self.phys.source(self._pcell[key], rhs)
+                if self.cfg.eta > 0.0:
+                    # resistive sources from the stage state with its face ghosts
+                    sb, se = self.phys.resistive_source(blk[5:8], self.dx(key[0]), self.cfg.eta)
+                    rhs[5:8] = rhs[5:8] + sb
+                    rhs[4] = rhs[4] + se
                 if hasattr(self.phys, "htc_target"):
                     # relaxation of q_par towards its target over tau = 4 dt (Eq. 10)
                     rhs[3] = -(us[3] - self._htc[key]) / (4.0 * dt)
