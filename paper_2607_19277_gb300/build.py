@@ -16,7 +16,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libagile.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-CU_SOURCES = ["stage_hd.cu", "stage_mhd.cu", "stage_srhd.cu", "stage_srhd_synge.cu", "stage_ffhd.cu", "aux_kernels.cu",
+CU_SOURCES = ["stage_hd.cu", "stage_mhd.cu", "stage_mhd_res.cu", "stage_srhd.cu", "stage_srhd_synge.cu", "stage_ffhd.cu", "aux_kernels.cu",
               "cooling.cu", "capi.cu"]
 CPP_SOURCES = ["mesh.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

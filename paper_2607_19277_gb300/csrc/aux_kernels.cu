@@ -208,12 +208,12 @@ __global__ void __launch_bounds__(256) speeds_kernel(const R* __restrict__ U,
 }
 
 __global__ void set_dt_kernel(const unsigned long long* speeds, double* dtch, double dt_host,
-                              double cfl, int nsolve) {
+                              double cfl, int nsolve, double rate_floor) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nsolve) return;
   const double smax = __longlong_as_double((long long)speeds[2 * i]);
   const double cmax = __longlong_as_double((long long)speeds[2 * i + 1]);
-  dtch[2 * i] = dt_host > 0.0 ? dt_host : cfl / smax;
+  dtch[2 * i] = dt_host > 0.0 ? dt_host : cfl / fmax(smax, rate_floor);
   dtch[2 * i + 1] = cmax;
 }
 
@@ -556,8 +556,8 @@ cudaError_t launch_speeds(const AuxArgs& a, unsigned long long* speeds, cudaStre
 }
 
 cudaError_t launch_set_dt(const unsigned long long* speeds, double* dtch, double dt_host,
-                          double cfl, cudaStream_t s, int nsolve) {
-  set_dt_kernel<<<(nsolve + 127) / 128, 128, 0, s>>>(speeds, dtch, dt_host, cfl, nsolve);
+                          double cfl, cudaStream_t s, int nsolve, double rate_floor) {
+  set_dt_kernel<<<(nsolve + 127) / 128, 128, 0, s>>>(speeds, dtch, dt_host, cfl, nsolve, rate_floor);
   return cudaGetLastError();
 }
 

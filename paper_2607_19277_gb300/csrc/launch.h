@@ -13,6 +13,7 @@ struct StageArgs;
 // Per-stage update (macro-kernel), dispatched on physics / precision / limiter / flux.
 cudaError_t launch_stage_hd(int real_bytes, int lim, int flux, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_stage_mhd(int real_bytes, int lim, int flux, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_stage_mhd_res(int real_bytes, int lim, int flux, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_stage_srhd(int real_bytes, int lim, int flux, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_stage_srhd_synge(int real_bytes, int lim, int flux, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_stage_ffhd(int real_bytes, int lim, int flux, const StageArgs& a, cudaStream_t s);
@@ -46,7 +47,7 @@ cudaError_t launch_speeds(const AuxArgs& a, unsigned long long* speeds, cudaStre
 // dtch[solve] = {dt, c_h}: dt from the host value or (dt <= 0) cfl / max sum_d s_d / dx_d,
 // for each of nsolve solves (speeds[solve][2]).
 cudaError_t launch_set_dt(const unsigned long long* speeds, double* dtch, double dt_host,
-                          double cfl, cudaStream_t s, int nsolve = 1);
+                          double cfl, cudaStream_t s, int nsolve = 1, double rate_floor = 0.0);
 // psi *= exp(-dt/2 c_h alpha / min dx) on every block.
 cudaError_t launch_glm_decay(const AuxArgs& a, const double* dtch, cudaStream_t s);
 // Loehner estimate: emax[nblk] (FP64, no FMA).

@@ -214,6 +214,10 @@ struct PairPhys<MhdPhys<float>> {
   }
 };
 
+// The resistive MHD trait solves its faces like ideal MHD (the resistive terms are sources).
+template <>
+struct PairPhys<MhdResPhys<float>> : PairPhys<MhdPhys<float>> {};
+
 // HLL or TVDLF flux of the pair from reconstructed primitive states (modified in place).
 template <class P, int FLUX>
 __device__ __forceinline__ void riemann2(f2* pl, f2* pr, f2* f, const PairK& k) {

@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace agile {
 
 enum : int { LIM_MINMOD = 0, LIM_VANLEER = 1 };
@@ -248,6 +250,26 @@ struct MhdPhys {
     pl[8] = ss;
     pr[8] = ss;
   }
+};
+
+// Ideal MHD with uniform resistivity eta (Section 2.3.3: -curl(eta J) in the induction
+// equation, div(B x eta J) in the energy equation): the MHD trait with the RES flag, for
+// which the stage kernel adds eta lap B to the induction equation and eta (J.J + B.lap B)
+// to the energy equation, from the stage state with the compact stencil over the six face
+// neighbours (central differences for J = curl B, the 7-point Laplacian).
+template <typename R>
+struct MhdResPhys : MhdPhys<R> {
+  static constexpr bool RES = true;
+};
+
+// Whether a trait carries the resistive terms.
+template <class P, class = void>
+struct res_of {
+  static constexpr bool value = false;
+};
+template <class P>
+struct res_of<P, std::void_t<decltype(P::RES)>> {
+  static constexpr bool value = P::RES;
 };
 
 // ------------------------------------------------------------------------------ SRHD

@@ -50,6 +50,18 @@ def test_invalid_config_rejected_on_host(lib, field, value):
     assert st == 1 and not out.value     # AGILE_EINVAL
 
 
+def test_resistivity_only_for_mhd_and_non_negative(lib):
+    from paper_2607_19277_gb300 import agile
+    out = C.c_void_p()
+    for kw in (dict(physics="hd", eta=0.1), dict(physics="mhd", eta=-1.0), dict(physics="mhd", eta=float("nan"))):
+        cfg = agile.make_config(**kw)
+        assert lib.agile_mesh_create(C.byref(cfg), None, None, C.byref(out)) == 1, kw
+        assert not out.value
+    cfg = agile.make_config(physics="mhd", eta=0.1)
+    batch = C.c_void_p()
+    assert lib.agile_batch_create(C.byref(cfg), 1, None, None, C.byref(batch)) == 1   # meshes only
+
+
 def test_half_periodic_and_srhd_hll_rejected(lib):
     from paper_2607_19277_gb300 import agile
     out = C.c_void_p()
