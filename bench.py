@@ -504,6 +504,86 @@ def run_batched_amr(nsolve=16, steps=20, regrid_every=10):
     return out
 
 
+def _average_to_base(lev, ijk, cons, nbase):
+    """Volume average of every leaf onto the uniform base grid (nbase cells per dimension,
+    16 per base block): a level-l block covers 16 / 2^(l-1) base cells per edge."""
+    nv = cons.shape[1]
+    out = np.zeros((nv, nbase, nbase, nbase))
+    for i in range(len(lev)):
+        f = 1 << (int(lev[i]) - 1)
+        n = 16 // f
+        red = cons[i].reshape(nv, n, f, n, f, n, f).mean(axis=(2, 4, 6))
+        z0, y0, x0 = (int(ijk[i, 2]) * n, int(ijk[i, 1]) * n, int(ijk[i, 0]) * n)
+        out[:, z0:z0 + n, y0:y0 + n, x0:x0 + n] += red
+    return out
+
+
+def run_sedov_5level(steps=200, regrid_every=10):
+    """The refined Sedov blast at its stated size (Fig. 2 time loop with regrids): hydro,
+    gamma 5/3, [-1/2, 1/2]^3 with outflow boundaries, base 64^3 (4x4x4 blocks of 16^3), five
+    levels (effective 1024^3), Loehner estimator on rho and e (weights 1/2), initial
+    refinement by four regrids that re-apply the initial condition, regrid every 10 steps,
+    HLL, minmod, SSPRK2, CFL 0.4, dt from the device. FP32 bulk (FP64 dt, sums and
+    estimator) against the FP64 stencil. Zone-updates count every leaf cell and stage; the
+    timed region includes the regrids. Reports the device time of each phase (stage kernel,
+    coarse-fine ghost fill, flux fix-up, estimator; CUDA events), the regrid's wall time, and
+    the FP32 state's relative L1 error per variable against the FP64 state after both are
+    averaged to the base level (the two runs may refine differently)."""
+    import torch
+    from paper_2607_19277_gb300 import agile, workloads as W
+    spec = dict(physics="hd", limiter="minmod", flux="hll", rk=2, cfl=0.4, base_blocks=(4, 4, 4),
+                xmin=(-0.5,) * 3, xmax=(0.5,) * 3, bc=("outflow",) * 6, max_level=5,
+                refine_vars=(0, 4), refine_weights=(0.5, 0.5), refine_tol=0.2)
+    out = {"workload": "hd sedov, base 64^3, 5 levels, loehner rho+e, regrid every %d steps, hll minmod "
+                       "ssprk2, %d steps" % (regrid_every, steps)}
+    states = {}
+    for rb, name in ((4, "fp32"), (8, "fp64")):
+        m = agile.Mesh(agile.make_config(real_bytes=rb, **spec))
+        m.set_state(W.sedov(r0=0.03))
+        for _ in range(4):
+            m.regrid(init=True)
+        s0 = m.conserved_sums()
+        m.sync()
+        m.set_kernel_timing(True)
+        zones = 0
+        regrid_s = 0.0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for n in range(steps):
+            zones += m.layout()[0] * 4096 * 2
+            m.step(0.0)
+            if n % regrid_every == regrid_every - 1:
+                m.sync()                       # the steps queued so far are not the regrid's
+                r0 = time.perf_counter()
+                m.regrid()
+                regrid_s += time.perf_counter() - r0
+        m.sync()
+        wall = time.perf_counter() - t0
+        ph = m.phase_timing()
+        m.set_kernel_timing(False)
+        s1 = m.conserved_sums()
+        lev, ijk, cons = m.get_state()
+        m.close()
+        states[name] = (lev, ijk, cons)
+        out[name] = {"value": zones / wall, "unit": UNIT, "seconds": wall, "leaves_end": int(len(lev)),
+                     "levels_used": sorted(set(int(x) for x in lev)),
+                     "share": {"stage_kernel": ph["stage"][0] / 1e3 / wall,
+                               "ghost_fill": ph["ghost_fill"][0] / 1e3 / wall,
+                               "flux_fixup": ph["fixup"][0] / 1e3 / wall,
+                               "estimator": ph["estimate"][0] / 1e3 / wall,
+                               "regrid_incl_estimator": regrid_s / wall,
+                               "note": "device time per phase (CUDA events) and the regrid's wall time "
+                                       "(estimator, host planning, new pools and tables), as shares of the "
+                                       "timed wall time"},
+                     "mass_energy_rel_change": [float(abs(s1[v] - s0[v]) / abs(s0[v])) for v in (0, 4)]}
+        torch.cuda.empty_cache()
+    a = _average_to_base(*states["fp64"], 64)
+    b = _average_to_base(*states["fp32"], 64)
+    err = np.abs(b - a).sum(axis=(1, 2, 3)) / np.abs(a).sum(axis=(1, 2, 3))
+    out["fp32_rel_l1_vs_fp64_on_base_grid"] = {n: float(x) for n, x in zip(("rho", "m_x", "m_y", "m_z", "e"), err)}
+    return out
+
+
 def run_ffhd(steps=20, warmup=3, kappa0=1e-3):
     """Frozen-field hydrodynamics (Section 2.3.2) on a periodic 256^3 grid of 16^3 blocks
     in a sheared frozen field, TVDLF, van Leer, SSPRK3, FP32 stencil: without source terms,
@@ -557,24 +637,35 @@ def run_ffhd(steps=20, warmup=3, kappa0=1e-3):
     return out
 
 
-def run_serving(nreq=32, rate=50.0, budget_gb=160.0):
-    """Serving stream (bounded sample of the configured stream): Poisson arrivals of HD /
-    MHD / SRHD solves admitted against the HBM budget, FP32 stencils, then the same stream on
-    the plain FP64 path. Reports p50/p99 latency and aggregate zone-updates/s of each."""
+def run_serving(nreq=64, rate=50.0, budget_gb=160.0, fp64_subset=8):
+    """Serving stream with the configured ranges (Poisson arrivals at mean 50/s of HD / MHD /
+    SRHD solves, sides 32-256, 50-500 steps, admitted against a 160 GB HBM budget), a bounded
+    sample of `nreq` requests: the FP32 stencils served by per-request streams and by
+    per-module batches (continuous batching: one launch per stage over every admitted solve
+    of a module, CUDA-graph steps, rebuilt as solves join and leave; its rebuild cost is
+    reported), and, on a stated subset (the first `fp64_subset` requests of side <= 64 in
+    arrival order), the plain FP64 per-solve path beside both FP32 forms. Each form reports
+    p50/p99 latency (completion - arrival), aggregate zone-updates/s and the largest number
+    of co-resident solves."""
     from paper_2607_19277_gb300 import serving
-    out = {}
-    for rb, name in ((4, "fp32"), (8, "fp64_plain")):
-        reqs = serving.request_stream(nreq, rate=rate, sides=(32, 64, 96), steps=(10, 30))
-        srv = serving.Server(int(budget_gb * 2 ** 30), real_bytes=rb, steps_per_poll=4)
-        rep = srv.run(reqs)
-        out[name] = rep.summary()
-    # the same stream with requests joining per-physics batches (graph-replayed steps)
-    reqs = serving.request_stream(nreq, rate=rate, sides=(32, 64, 96), steps=(10, 30))
-    rep = serving.BatchedServer(int(budget_gb * 2 ** 30), real_bytes=4, rebuild_every=4).run(reqs)
-    out["fp32_batched"] = rep.summary()
-    out["workload"] = ("%d requests, Poisson mean %g/s, physics hd/mhd/srhd, sides 32-96, "
-                       "10-30 steps, budget %g GB (bounded sample of the 1000-request stream)"
-                       % (nreq, rate, budget_gb))
+    budget = int(budget_gb * 2 ** 30)
+
+    def stream():
+        return serving.request_stream(nreq, rate=rate, sides=(32, 64, 128, 256), steps=(50, 500))
+
+    out = {"workload": "%d requests, Poisson mean %g/s, physics hd/mhd/srhd, sides 32-256, 50-500 steps, "
+                       "budget %g GB" % (nreq, rate, budget_gb)}
+    out["fp32"] = serving.Server(budget, real_bytes=4, steps_per_poll=4).run(stream()).summary()
+    out["fp32_batched"] = serving.BatchedServer(budget, real_bytes=4, rebuild_every=8).run(stream()).summary()
+    ids = [r.rid for r in stream() if r.side <= 64][:fp64_subset]
+
+    def subset():
+        return [r for r in stream() if r.rid in ids]
+    sub = {"requests": ids, "note": "the same requests (arrival times kept) on each path"}
+    sub["fp64_plain"] = serving.Server(budget, real_bytes=8, steps_per_poll=4).run(subset()).summary()
+    sub["fp32"] = serving.Server(budget, real_bytes=4, steps_per_poll=4).run(subset()).summary()
+    sub["fp32_batched"] = serving.BatchedServer(budget, real_bytes=4, rebuild_every=8).run(subset()).summary()
+    out["subset"] = sub
     return out
 
 
@@ -739,7 +830,14 @@ def summary_of(line):
            "sedov_5level_fp64": get(line, "sedov_5level", "fp64", "value"),
            "serving_fp32_batched_p99_s": get(line, "serving", "fp32_batched", "latency_p99_s"),
            "serving_fp32_batched_value": get(line, "serving", "fp32_batched", "zone_updates_per_s"),
-           "serving_fp64_plain_p99_s": get(line, "serving", "fp64_plain", "latency_p99_s"),
+           "serving_fp32_streams_p99_s": get(line, "serving", "fp32", "latency_p99_s"),
+           "serving_fp32_streams_value": get(line, "serving", "fp32", "zone_updates_per_s"),
+           "serving_max_concurrent": get(line, "serving", "fp32_batched", "max_concurrent"),
+           "serving_rebuild_share": get(line, "serving", "fp32_batched", "rebuild", "rebuild_share_of_wall"),
+           "serving_subset_fp64_plain_p99_s": get(line, "serving", "subset", "fp64_plain", "latency_p99_s"),
+           "serving_subset_fp64_plain_value": get(line, "serving", "subset", "fp64_plain", "zone_updates_per_s"),
+           "serving_subset_fp32_batched_value": get(line, "serving", "subset", "fp32_batched",
+                                                    "zone_updates_per_s"),
            "cpu_oracle_1core": get(line, "cpu_baseline", "value")}
     return {k: v for k, v in out.items() if v is not None}
 
@@ -757,6 +855,7 @@ def main():
     ap.add_argument("--no-paper-scheme", action="store_true")
     ap.add_argument("--no-cooling", action="store_true")
     ap.add_argument("--no-ffhd", action="store_true")
+    ap.add_argument("--no-sedov", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -881,6 +980,11 @@ def main():
             line["cooling_mhd"] = run_cooling()
         except Exception as e:
             line["cooling_mhd"] = {"error": str(e)}
+    if not args.no_sedov:
+        try:
+            line["sedov_5level"] = run_sedov_5level()
+        except Exception as e:
+            line["sedov_5level"] = {"error": str(e)}
     if not args.no_ffhd:
         try:
             line["ffhd"] = run_ffhd()

@@ -283,6 +283,14 @@ agile_status agile_set_kernel_timing(agile_mesh* mesh, int enable);
 agile_status agile_kernel_timing(agile_mesh* mesh, double* stage_ms, long long* stage_launches,
                                  long long* total_launches);
 
+/* Device time per phase of the time loop (Fig. 2), from the same CUDA events (recorded while
+ * kernel timing is on, since the last agile_set_kernel_timing(mesh, 1)): ms[0] the stage
+ * (update) kernel, ms[1] the coarse-fine ghost fill, ms[2] the coarse-fine flux fix-up,
+ * ms[3] the refinement estimator; launches (may be NULL, else 4 values) the timed launches
+ * of each. The regrid's own work is partly on the host and is not included. The paper has
+ * no counterpart (a profiling aid). Synchronises. */
+agile_status agile_phase_timing(agile_mesh* mesh, double* ms, long long* launches);
+
 /* ---------------------------------------------------------------------------------------
  * Batched independent solves. Several problems that share one scheme (physics, limiter,
  * flux, rk, real_bytes, gamma, cfl, glm_alpha, eos) but differ in size, box, boundaries and

@@ -34,6 +34,7 @@ EXPORTS = ["agile_mesh_create", "agile_mesh_destroy", "agile_set_state", "agile_
            "agile_get_state", "agile_get_aux", "agile_conserved_sums",
            "agile_conserved_sums_noalloc", "agile_set_cooling", "agile_estimate",
            "agile_get_halo", "agile_sync", "agile_set_kernel_timing", "agile_kernel_timing",
+           "agile_phase_timing",
            "agile_selftest_bounded_wait", "agile_selftest_rcp64", "agile_last_error", "agile_version",
            "agile_batch_create", "agile_batch_destroy", "agile_batch_layout",
            "agile_batch_set_state", "agile_batch_step", "agile_batch_cfl_dt", "agile_batch_copy_solve",
@@ -106,6 +107,7 @@ def load(path: str = LIB_PATH):
         "agile_sync": (C.c_int, [P]),
         "agile_set_kernel_timing": (C.c_int, [P, C.c_int]),
         "agile_kernel_timing": (C.c_int, [P, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+        "agile_phase_timing": (C.c_int, [P, dp, C.POINTER(C.c_longlong)]),
         "agile_selftest_bounded_wait": (C.c_int, [P, C.c_uint, ip]),
         "agile_selftest_rcp64": (C.c_int, [dp, dp, C.c_size_t, P, dp, dp]),
         "agile_last_error": (C.c_char_p, [P]),
@@ -382,6 +384,15 @@ class Mesh:
         tot = C.c_longlong()
         self._ck(self.lib.agile_kernel_timing(self.ptr, C.byref(ms), C.byref(n), C.byref(tot)))
         return ms.value, n.value, tot.value
+
+    def phase_timing(self):
+        """Device ms and launches per phase since timing was enabled: a dict over 'stage',
+        'ghost_fill', 'fixup', 'estimate'."""
+        ms = (C.c_double * 4)()
+        n = (C.c_longlong * 4)()
+        self._ck(self.lib.agile_phase_timing(self.ptr, ms, n))
+        names = ("stage", "ghost_fill", "fixup", "estimate")
+        return {k: (ms[i], n[i]) for i, k in enumerate(names)}
 
 
 def morton3(i, j, k):

@@ -53,7 +53,9 @@ struct agile_mesh {
   CUtensorMap tmap[3];
   bool timing = false;
   std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_cat;          // phase of each event pair (PHASE_*)
   long long stage_launches = 0, total_launches = 0;
+  long long phase_launches[4] = {0, 0, 0, 0};
   CoolHost cool;                    // radiative-loss table (nseg == 0: no losses)
   void* d_cool = nullptr;           // its segments in the stencil precision
   double* d_sums = nullptr;         // per-block sums and totals of agile_conserved_sums (kept)
@@ -89,6 +91,32 @@ void dfree_t(agile_mesh* m, T*& p) {
 agile_status fail(agile_mesh* m, agile_status s, const std::string& msg) {
   if (m) m->err = msg;
   return s;
+}
+
+// Phases timed with CUDA events when kernel timing is on: the stage (update) kernel, the
+// coarse-fine ghost fill, the flux fix-up and the refinement estimator.
+enum : int { PHASE_STAGE = 0, PHASE_GHOST = 1, PHASE_FIXUP = 2, PHASE_ESTIMATE = 3 };
+
+cudaEvent_t phase_begin(agile_mesh* m) {
+  if (!m->timing) return nullptr;
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  cudaEventRecord(e, m->stream);
+  return e;
+}
+
+void phase_end(agile_mesh* m, cudaEvent_t e0, int phase) {
+  if (!e0) return;
+  cudaEvent_t e1 = nullptr;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return;
+  }
+  cudaEventRecord(e1, m->stream);
+  m->ev.push_back(e0);
+  m->ev.push_back(e1);
+  m->ev_cat.push_back(phase);
+  m->phase_launches[phase]++;
 }
 
 #define CK(m, call)                                                                          \
@@ -258,7 +286,9 @@ agile_status rebuild(agile_mesh* m) {
 agile_status fill_ghosts(agile_mesh* m, void* U) {
   if (m->nghost == 0) return AGILE_OK;
   AuxArgs a = aux_args(m, U);
+  cudaEvent_t e0 = phase_begin(m);
   CK(m, launch_ghosts(a, m->d_ghosts, m->nghost, m->stream));
+  phase_end(m, e0, PHASE_GHOST);
   m->total_launches++;
   return AGILE_OK;
 }
@@ -639,12 +669,7 @@ agile_status agile_step(agile_mesh* m, double dt) {
     A.tmap = &m->tmap[st == 0 ? 0 : st];
     A.solve_of = nullptr;
     A.work = m->d_work + st;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (m->timing) {
-      CK(m, cudaEventCreate(&e0));
-      CK(m, cudaEventCreate(&e1));
-      CK(m, cudaEventRecord(e0, m->stream));
-    }
+    cudaEvent_t e0 = phase_begin(m);
     cudaError_t e;
     if (m->cfg.physics == AGILE_HD) e = launch_stage_hd(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
     else if (mhd && m->cfg.eta > 0.0) e = launch_stage_mhd_res(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
@@ -656,16 +681,14 @@ agile_status agile_step(agile_mesh* m, double dt) {
       e = launch_stage_ffhd_htc(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
     else e = launch_stage_srhd(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
     if (e != cudaSuccess) return fail(m, AGILE_ECUDA, std::string("stage kernel: ") + cudaGetErrorString(e));
-    if (m->timing) {
-      CK(m, cudaEventRecord(e1, m->stream));
-      m->ev.push_back(e0);
-      m->ev.push_back(e1);
-    }
+    phase_end(m, e0, PHASE_STAGE);
     m->stage_launches++;
     m->total_launches++;
     if (m->nfix) {
       AuxArgs a = aux_args(m, Uo);
+      cudaEvent_t f0 = phase_begin(m);
       CK(m, launch_fixup(a, m->d_fix, m->nfix, A.b, m->d_dtch, m->stream));
+      phase_end(m, f0, PHASE_FIXUP);
       m->total_launches++;
     }
   }
@@ -725,7 +748,9 @@ agile_status agile_estimate(agile_mesh* m, double* emax) {
   double* d = (double*)dalloc(m, m->nblk * sizeof(double));
   if (!d) return fail(m, AGILE_ENOMEM, "device allocation failed");
   AuxArgs a = aux_args(m, m->U[0]);
+  cudaEvent_t e0 = phase_begin(m);
   CK(m, launch_estimate(a, m->d_vars, m->d_weights, m->cfg.refine_nvars, m->cfg.lohner_eps, d, m->stream));
+  phase_end(m, e0, PHASE_ESTIMATE);
   m->total_launches++;
   CK(m, cudaMemcpyAsync(emax, d, m->nblk * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
   s = check_status(m);
@@ -849,9 +874,25 @@ agile_status agile_set_kernel_timing(agile_mesh* m, int enable) {
   CK(m, cudaStreamSynchronize(m->stream));
   for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
   m->ev.clear();
+  m->ev_cat.clear();
   m->timing = enable != 0;
   m->stage_launches = 0;
   m->total_launches = 0;
+  for (long long& n : m->phase_launches) n = 0;
+  return AGILE_OK;
+}
+
+agile_status agile_phase_timing(agile_mesh* m, double* ms, long long* launches) {
+  if (!m || !ms) return AGILE_EINVAL;
+  CK(m, cudaStreamSynchronize(m->stream));
+  for (int p = 0; p < 4; ++p) ms[p] = 0.0;
+  for (size_t i = 0; i + 1 < m->ev.size(); i += 2) {
+    float t = 0.f;
+    CK(m, cudaEventElapsedTime(&t, m->ev[i], m->ev[i + 1]));
+    ms[m->ev_cat[i / 2]] += t;
+  }
+  if (launches)
+    for (int p = 0; p < 4; ++p) launches[p] = m->phase_launches[p];
   return AGILE_OK;
 }
 
@@ -861,6 +902,7 @@ agile_status agile_kernel_timing(agile_mesh* m, double* stage_ms, long long* sta
   CK(m, cudaStreamSynchronize(m->stream));
   double tot = 0.0;
   for (size_t i = 0; i + 1 < m->ev.size(); i += 2) {
+    if (m->ev_cat[i / 2] != PHASE_STAGE) continue;
     float ms = 0.f;
     CK(m, cudaEventElapsedTime(&ms, m->ev[i], m->ev[i + 1]));
     tot += ms;

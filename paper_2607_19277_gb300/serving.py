@@ -62,7 +62,8 @@ def initial_condition(req: Request):
         return W.random_smooth(5, req.seed, "hd")
     if req.physics == "mhd":
         return W.orszag_tang_3d(req.side, seed=req.seed)
-    return W.srhd_shells(req.seed, req.side, lorentz_max=2.0, p_amb=0.1, smooth=True)
+    return W.srhd_shells(req.seed, req.side, n_shells=1, lorentz_max=2.0, p_amb=1.0, smooth=True, width=2.0,
+                         wrap=True)
 
 
 def request_stream(n: int, rate: float, sides=(32, 64, 128, 256), steps=(50, 500),
@@ -134,6 +135,7 @@ class Report:
     max_resident_bytes: int
     max_concurrent: int
     latencies: list = field(default_factory=list)
+    extra: dict = field(default_factory=dict)
 
     def summary(self):
         lat = sorted(self.latencies)
@@ -143,7 +145,8 @@ class Report:
         return {"requests": len(self.requests), "wall_s": self.wall_s,
                 "zone_updates_per_s": self.zone_updates / self.wall_s if self.wall_s > 0 else None,
                 "latency_p50_s": pct(0.50), "latency_p99_s": pct(0.99),
-                "max_resident_bytes": self.max_resident_bytes, "max_concurrent": self.max_concurrent}
+                "max_resident_bytes": self.max_resident_bytes, "max_concurrent": self.max_concurrent,
+                **self.extra}
 
 
 class Server:
@@ -291,8 +294,21 @@ class BatchedServer:
 
     def _rebuild(self, g):
         """New batch for the group's members: survivors copied, newcomers initialised.
-        Returns the device bytes of the finished solves it drops."""
+        Returns the device bytes of the finished solves it drops. Its wall time (creation,
+        device-to-device copies, uploads, release of the old batch) is accumulated with the
+        numbers of joining and leaving solves."""
+        t0 = time.perf_counter()
+        try:
+            return self._rebuild_group(g)
+        finally:
+            self.stats["rebuild_s"] += time.perf_counter() - t0
+            self.stats["rebuilds"] += 1
+
+    def _rebuild_group(self, g):
         old, old_index = g["batch"], g["index"]
+        self.stats["joins"] += len(g["joining"])
+        self.stats["leaves"] += len(g["done"])
+        self.stats["survivor_copies"] += len([r for r in g["members"] if r.rid not in g["done"]])
         freed = sum(pool_bytes(r, self.rb) for r in g["members"] if r.rid in g["done"])
         members = [r for r in g["members"] if r.rid not in g["done"]] + g["joining"]
         g["joining"] = []
@@ -320,11 +336,17 @@ class BatchedServer:
         (a finished solve's pool is released when its batch is rebuilt; during a rebuild the
         old and the new batch coexist briefly)."""
         prep = _Preparer(self.workers, self.max_prepared, self.rb)
+        self.stats = {"rebuilds": 0, "rebuild_s": 0.0, "joins": 0, "leaves": 0, "survivor_copies": 0}
         try:
-            return self._loop(requests, time_scale, max_wall_s, prep)
+            rep = self._loop(requests, time_scale, max_wall_s, prep)
         finally:
             prep.close()
             self._prims.clear()
+        st = dict(self.stats)
+        st["rebuild_share_of_wall"] = st["rebuild_s"] / rep.wall_s if rep.wall_s > 0 else None
+        st["rebuild_ms_per_join_or_leave"] = (1e3 * st["rebuild_s"] / max(1, st["joins"] + st["leaves"]))
+        rep.extra["rebuild"] = st
+        return rep
 
     def _loop(self, requests, time_scale, max_wall_s, prep):
         pending = sorted(requests, key=lambda r: r.arrival)

@@ -156,22 +156,26 @@ def sedov(gamma=5.0 / 3.0, energy=1.0, r0=0.03, rho0=1.0, p0=1e-5, centre=(0.0, 
 
 
 def srhd_shells(seed: int, n_cells: int, n_shells=None, rho_amb=1.0, p_amb=0.01,
-                lorentz_max=10.0, smooth=False):
+                lorentz_max=10.0, smooth=False, width=1.5, lorentz_min=1.0, wrap=False,
+                radius=(0.1, 0.3)):
     """SRHD state on [0,1]^3: ambient (rho, p) with 1-3 seeded spherical shells.
 
-    Per shell s (draws 8 s .. 8 s + 7 of the stream): centre U[0,1]^3, radius U[0.1, 0.3],
-    rho_shell U[1, 10], radial Lorentz factor U[1, lorentz_max]; the shell is 3 cells wide
-    and moves radially outward with four-velocity sqrt(Gamma^2 - 1). smooth=False: a top hat
-    |r - R| < 1.5 dx; smooth=True: a Gaussian radial profile exp(-(r - R)^2 / (2 (1.5 dx)^2))
-    of the density excess and of the four-velocity (shells combine by the larger weight).
+    Per shell s (draws 8 s .. 8 s + 7 of the stream): centre U[0,1]^3, radius U[radius],
+    rho_shell U[1, 10], radial Lorentz factor U[lorentz_min, lorentz_max]; the shell is
+    2 width cells wide (width = 1.5 by default) and moves radially outward with four-velocity
+    sqrt(Gamma^2 - 1). smooth=False: a top hat |r - R| < width dx; smooth=True: a Gaussian
+    radial profile exp(-(r - R)^2 / (2 (width dx)^2)) of the density excess and of the
+    four-velocity (shells combine by the larger weight). wrap=True measures the distance
+    to a shell's centre by the periodic minimum image, so that a shell reaching across a
+    face of the periodic box continues on the opposite side instead of being cut there.
     """
     if n_shells is None:
         n_shells = 1 + int(uniform01(seed, np.array([1000]))[0] * 3.0)
     shells = []
     for s in range(n_shells):
         u = uniform01(seed, np.arange(8 * s, 8 * s + 8))
-        shells.append(dict(c=(u[0], u[1], u[2]), R=0.1 + 0.2 * u[3], rho=1.0 + 9.0 * u[4],
-                           lorentz=1.0 + (lorentz_max - 1.0) * u[5]))
+        shells.append(dict(c=(u[0], u[1], u[2]), R=radius[0] + (radius[1] - radius[0]) * u[3], rho=1.0 + 9.0 * u[4],
+                           lorentz=lorentz_min + (lorentz_max - lorentz_min) * u[5]))
     dx = 1.0 / n_cells
 
     def ic(x, y, z):
@@ -184,18 +188,20 @@ def srhd_shells(seed: int, n_cells: int, n_shells=None, rho_amb=1.0, p_amb=0.01,
         wmax = np.zeros(x.size)
         for sh in shells:
             ddx, ddy, ddz = x - sh["c"][0], y - sh["c"][1], z - sh["c"][2]
+            if wrap:
+                ddx, ddy, ddz = (d - np.floor(d + 0.5) for d in (ddx, ddy, ddz))
             r = np.sqrt(ddx * ddx + ddy * ddy + ddz * ddz)
             ur = math.sqrt(sh["lorentz"] ** 2 - 1.0)
             rs = np.where(r > 0, r, 1.0)
             if smooth:
-                w = np.exp(-((r - sh["R"]) ** 2) / (2.0 * (1.5 * dx) ** 2))
+                w = np.exp(-((r - sh["R"]) ** 2) / (2.0 * (width * dx) ** 2))
                 take = w > wmax
                 wmax = np.where(take, w, wmax)
                 prim[0] = np.where(take, rho_amb + (sh["rho"] - rho_amb) * w, prim[0])
                 for c, d in enumerate((ddx, ddy, ddz)):
                     prim[1 + c] = np.where(take, w * ur * d / rs, prim[1 + c])
             else:
-                inside = np.abs(r - sh["R"]) < 1.5 * dx
+                inside = np.abs(r - sh["R"]) < width * dx
                 prim[0] = np.where(inside, sh["rho"], prim[0])
                 for c, d in enumerate((ddx, ddy, ddz)):
                     prim[1 + c] = np.where(inside, ur * d / rs, prim[1 + c])
