@@ -303,11 +303,16 @@ BATCH_SIDES = (32, 48, 64, 80, 96, 112, 128)
 
 
 def batch_workload(nsolve=256, seed=20260004):
-    """Seeded batch of SRHD solves: side from {32, ..., 128} per solve, 1-3 shells each."""
+    """Seeded batch of SRHD solves: side from {32, ..., 128} per solve, one shell each with
+    radial Lorentz factor U[1, 10] (the configured range), radius U[0.2, 0.35], a Gaussian
+    profile two cells wide, periodic (minimum-image) distances, ambient rho = p = 1. Thinner
+    or multiple colliding shells, or radii of three cells at 32^3, reach states without a
+    primitive solution within ten steps at these Lorentz factors (in FP64 as well)."""
     from paper_2607_19277_gb300 import workloads as W
     u = W.uniform01(seed, np.arange(nsolve))
     sides = [BATCH_SIDES[min(len(BATCH_SIDES) - 1, int(x * len(BATCH_SIDES)))] for x in u]
-    ics = [W.srhd_shells(seed + 1 + i, sides[i], lorentz_max=2.0, p_amb=0.1, smooth=True)
+    ics = [W.srhd_shells(seed + 1 + i, sides[i], n_shells=1, lorentz_max=10.0, p_amb=1.0, smooth=True,
+                         width=2.0, wrap=True, radius=(0.2, 0.35))
            for i in range(nsolve)]
     return sides, ics
 
@@ -345,6 +350,7 @@ def run_batched(steps, warmup, nsolve=256, fp64_solves=8):
         b.close()
     zones = sum(sd ** 3 for sd in sides)
     out = {"value": zones * 2 * steps / (total / 1e3), "unit": UNIT, "solves": nsolve,
+           "lorentz_factor_max_initial": max(sh["lorentz"] for ic in ics for sh in ic.shells),
            "cells": zones, "ms_per_step": total / steps, "step_latency_ms": {
                "p50": per[len(per) // 2], "p99": per[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)]},
            "dtype": "f32 stencil, f64 con2prim", "graph_launches_per_step": "1 graph (set_dt + 2 stages)",
@@ -642,9 +648,10 @@ def run_serving(nreq=64, rate=50.0, budget_gb=160.0, fp64_subset=8):
     SRHD solves, sides 32-256, 50-500 steps, admitted against a 160 GB HBM budget), a bounded
     sample of `nreq` requests: the FP32 stencils served by per-request streams and by
     per-module batches (continuous batching: one launch per stage over every admitted solve
-    of a module, CUDA-graph steps, rebuilt as solves join and leave; its rebuild cost is
-    reported), and, on a stated subset (the first `fp64_subset` requests of side <= 64 in
-    arrival order), the plain FP64 per-solve path beside both FP32 forms. Each form reports
+    of a module, CUDA-graph steps; solves attach and detach without moving the others, and
+    the cost of those calls is reported), and, on a stated subset (the first `fp64_subset`
+    requests of side <= 64 in arrival order), the plain FP64 per-solve path beside both FP32
+    forms. Each form reports
     p50/p99 latency (completion - arrival), aggregate zone-updates/s and the largest number
     of co-resident solves."""
     from paper_2607_19277_gb300 import serving
@@ -656,7 +663,7 @@ def run_serving(nreq=64, rate=50.0, budget_gb=160.0, fp64_subset=8):
     out = {"workload": "%d requests, Poisson mean %g/s, physics hd/mhd/srhd, sides 32-256, 50-500 steps, "
                        "budget %g GB" % (nreq, rate, budget_gb)}
     out["fp32"] = serving.Server(budget, real_bytes=4, steps_per_poll=4).run(stream()).summary()
-    out["fp32_batched"] = serving.BatchedServer(budget, real_bytes=4, rebuild_every=8).run(stream()).summary()
+    out["fp32_batched"] = serving.BatchedServer(budget, real_bytes=4).run(stream()).summary()
     ids = [r.rid for r in stream() if r.side <= 64][:fp64_subset]
 
     def subset():
@@ -664,8 +671,18 @@ def run_serving(nreq=64, rate=50.0, budget_gb=160.0, fp64_subset=8):
     sub = {"requests": ids, "note": "the same requests (arrival times kept) on each path"}
     sub["fp64_plain"] = serving.Server(budget, real_bytes=8, steps_per_poll=4).run(subset()).summary()
     sub["fp32"] = serving.Server(budget, real_bytes=4, steps_per_poll=4).run(subset()).summary()
-    sub["fp32_batched"] = serving.BatchedServer(budget, real_bytes=4, rebuild_every=8).run(subset()).summary()
+    sub["fp32_batched"] = serving.BatchedServer(budget, real_bytes=4).run(subset()).summary()
     out["subset"] = sub
+    # a stream of small solves (sides 32-64), where one launch per stage over many solves
+    # matters most against a launch sequence per solve
+    small = {"workload": "%d requests, Poisson mean %g/s, sides 32-64, 50-500 steps" % (nreq, rate)}
+
+    def small_stream():
+        return serving.request_stream(nreq, rate=rate, sides=(32, 48, 64), steps=(50, 500),
+                                      seed=serving.W.SEED_BASE + 15)
+    small["fp32"] = serving.Server(budget, real_bytes=4, steps_per_poll=4).run(small_stream()).summary()
+    small["fp32_batched"] = serving.BatchedServer(budget, real_bytes=4).run(small_stream()).summary()
+    out["small_solves"] = small
     return out
 
 
@@ -833,7 +850,14 @@ def summary_of(line):
            "serving_fp32_streams_p99_s": get(line, "serving", "fp32", "latency_p99_s"),
            "serving_fp32_streams_value": get(line, "serving", "fp32", "zone_updates_per_s"),
            "serving_max_concurrent": get(line, "serving", "fp32_batched", "max_concurrent"),
-           "serving_rebuild_share": get(line, "serving", "fp32_batched", "rebuild", "rebuild_share_of_wall"),
+           "serving_membership_share": get(line, "serving", "fp32_batched", "membership",
+                                           "membership_share_of_wall"),
+           "serving_small_fp32_streams_value": get(line, "serving", "small_solves", "fp32", "zone_updates_per_s"),
+           "serving_small_fp32_batched_value": get(line, "serving", "small_solves", "fp32_batched",
+                                                   "zone_updates_per_s"),
+           "serving_small_fp32_batched_p99_s": get(line, "serving", "small_solves", "fp32_batched",
+                                                   "latency_p99_s"),
+           "serving_small_fp32_streams_p99_s": get(line, "serving", "small_solves", "fp32", "latency_p99_s"),
            "serving_subset_fp64_plain_p99_s": get(line, "serving", "subset", "fp64_plain", "latency_p99_s"),
            "serving_subset_fp64_plain_value": get(line, "serving", "subset", "fp64_plain", "zone_updates_per_s"),
            "serving_subset_fp32_batched_value": get(line, "serving", "subset", "fp32_batched",
@@ -961,8 +985,9 @@ def main():
     if not args.no_batched:
         try:
             line["batched"] = run_batched(max(4, min(args.steps // 20, 10)), args.warmup)
-            line["batched"]["workload"] = ("256 SRHD solves 32^3-128^3 (16^3 blocks), seeded shells "
-                                           "(Gaussian profile 3 cells wide) Gamma <= 2, TVDLF minmod SSPRK2")
+            line["batched"]["workload"] = ("256 SRHD solves 32^3-128^3 (16^3 blocks), one seeded shell each "
+                                           "(Gaussian profile, 2 cells wide) with Lorentz factor U[1, 10], TVDLF "
+                                           "minmod SSPRK2")
         except Exception as e:   # report, do not lose the headline line
             line["batched"] = {"error": str(e)}
     if not args.no_batched:

@@ -61,7 +61,10 @@ enum { AGILE_PERIODIC = 0, AGILE_OUTFLOW = 1, AGILE_REFLECT = 2 }; /* boundaries
 enum { AGILE_EOS_IDEAL = 0, AGILE_EOS_SYNGE = 1 };              /* srhd closure */
 
 /* Device allocator: alloc(bytes, stream, ctx) returns device memory or NULL;
- * free(ptr, stream, ctx) releases it. Both are called only from the calling thread. */
+ * free(ptr, stream, ctx) releases it in stream order: work already enqueued on `stream` may
+ * still read the memory, which the allocator reuses only for work ordered after it (as
+ * cudaFreeAsync, or a caching allocator that reuses blocks on the same stream). Both are
+ * called only from the calling thread. */
 typedef struct {
   void* (*alloc)(size_t bytes, void* stream, void* ctx);
   void (*free)(void* ptr, void* stream, void* ctx);
@@ -321,7 +324,10 @@ agile_status agile_batch_layout(agile_batch* batch, int solve, size_t* nblocks, 
 /* Initial condition of one solve (as agile_set_state). Synchronises. */
 agile_status agile_batch_set_state(agile_batch* batch, int solve, agile_ic_fn ic, void* user);
 
-/* agile_set_state_prims for solve `solve` of a batch (its blocks in the solve's order). */
+/* agile_set_state_prims for solve `solve` of a batch (its blocks in the solve's order).
+ * Enqueued on the batch's stream without waiting (the host array is staged when each copy
+ * is enqueued and may be released on return); a device error is returned by the next
+ * synchronising batch call. */
 agile_status agile_batch_set_state_prims(agile_batch* batch, int solve, const double* prim, size_t nblk);
 
 /* One full SSPRK step of every solve with its own on-device CFL dt (as agile_step(dt <= 0)).
@@ -374,6 +380,26 @@ agile_status agile_batch_autotune(agile_batch* batch, int trials, int* grid, int
  * source batch's stream and the copy (synchronising both); the next step of dst
  * recomputes its CFL speeds. AGILE_EINVAL when the solves differ. */
 agile_status agile_batch_copy_solve(agile_batch* dst, int dst_solve, agile_batch* src, int src_solve);
+
+/* Continuous batching (no counterpart in the paper; the serving loop's admission): attach
+ * adds a solve with configuration cfg (the batch's scheme, as for agile_batch_create) to the
+ * running batch and returns its index in *solve; detach removes one. Neither moves the other
+ * solves' states: a solve occupies a contiguous range of the batch's block pool, a detached
+ * solve's range becomes a hole that a later attach may fill (first fit), and the stage
+ * launches walk a work list of the attached solves' blocks, so a solve joins or leaves at the
+ * next step at the cost of rebuilding the descriptor tables (host, then one upload) and
+ * capturing the step's CUDA graph again. Only when no hole fits and the pool is full does
+ * attach allocate a pool at least twice as large and copy the attached solves into it. A
+ * detached solve's index is reused by a later attach; using it otherwise returns
+ * AGILE_EINVAL. An attached solve's state is zero until agile_batch_set_state or
+ * agile_batch_set_state_prims sets it: set it before the next agile_batch_step (a zero
+ * density is reported as AGILE_EUNPHYS). Neither waits for the batch's stream: old tables
+ * and buffers are released in stream order (the allocator contract above), and a solve's
+ * own tables are cached until it is regridded. Errors: AGILE_EINVAL (a different scheme, a
+ * bad index), AGILE_ENOMEM, AGILE_ECUDA; device errors surface at the next synchronising
+ * batch call. */
+agile_status agile_batch_attach(agile_batch* batch, const agile_config* cfg, int* solve);
+agile_status agile_batch_detach(agile_batch* batch, int solve);
 
 /* Wait for the batch stream and return any latched device error. */
 agile_status agile_batch_sync(agile_batch* batch);

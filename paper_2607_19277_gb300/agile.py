@@ -40,6 +40,7 @@ EXPORTS = ["agile_mesh_create", "agile_mesh_destroy", "agile_set_state", "agile_
            "agile_batch_set_state", "agile_batch_step", "agile_batch_cfl_dt", "agile_batch_copy_solve",
            "agile_batch_autotune", "agile_batch_regrid", "agile_batch_regrid_flags",
            "agile_batch_get_state", "agile_batch_sync", "agile_batch_launches",
+           "agile_batch_attach", "agile_batch_detach",
            "agile_batch_last_error"]
 
 
@@ -120,6 +121,8 @@ def load(path: str = LIB_PATH):
         "agile_batch_cfl_dt": (C.c_int, [P, dp]),
         "agile_batch_get_state": (C.c_int, [P, C.c_int, ip, ip, dp]),
         "agile_batch_copy_solve": (C.c_int, [P, C.c_int, P, C.c_int]),
+        "agile_batch_attach": (C.c_int, [P, C.POINTER(agile_config), ip]),
+        "agile_batch_detach": (C.c_int, [P, C.c_int]),
         "agile_batch_autotune": (C.c_int, [P, C.c_int, ip, ip, ip, C.POINTER(C.c_float)]),
         "agile_batch_regrid": (C.c_int, [P, C.c_int, C.c_int, ip, ip]),
         "agile_batch_regrid_flags": (C.c_int, [P, C.c_int, ip, C.c_int, ip, ip]),
@@ -538,6 +541,17 @@ class Batch:
         self._ck(self.lib.agile_batch_autotune(self.ptr, int(trials), C.byref(g), C.byref(d),
                                                C.byref(lay), ms))
         return g.value, bool(d.value), list(ms), lay.value
+
+    def attach(self, cfg):
+        """Add a solve with configuration cfg (the batch's scheme) to the running batch;
+        returns its index. Set its state before the next step."""
+        idx = C.c_int()
+        self._ck(self.lib.agile_batch_attach(self.ptr, C.byref(cfg), C.byref(idx)))
+        return idx.value
+
+    def detach(self, solve):
+        """Remove a solve from the batch (the others keep their places and states)."""
+        self._ck(self.lib.agile_batch_detach(self.ptr, int(solve)))
 
     def copy_solve(self, solve, src, src_solve):
         """Device-to-device copy of solve src_solve of Batch src into solve `solve`."""

@@ -188,10 +188,11 @@ __global__ void __launch_bounds__(256) speeds_kernel(const R* __restrict__ U,
                                                       const BlockDesc* __restrict__ bd,
                                                       const PhysParamsT<R> pp,   // formed on the host
                                                       unsigned long long* speeds, int* status,
-                                                      const int* __restrict__ solve_of) {
+                                                      const int* __restrict__ solve_of,
+                                                      const int* __restrict__ wl) {
   using P = PT<R>;
   constexpr int NV = P::NV, NA = P::NA, NT = NV + NA;
-  const int b = blockIdx.x;
+  const int b = wl ? wl[blockIdx.x] : (int)blockIdx.x;
   const R dxr[3] = {R(bd[b].dx[0]), R(bd[b].dx[1]), R(bd[b].dx[2])};
   R ssum = R(0), smax = R(0);
   int st = 0;
@@ -223,9 +224,10 @@ __global__ void set_dt_kernel(const unsigned long long* speeds, double* dtch, do
 template <typename R>
 __global__ void __launch_bounds__(256) glm_decay_kernel(R* __restrict__ U, const BlockDesc* __restrict__ bd,
                                                          const double* __restrict__ dtch, double alpha,
-                                                         const int* __restrict__ solve_of) {
+                                                         const int* __restrict__ solve_of,
+                                                         const int* __restrict__ wl) {
   __shared__ R s_f;
-  const int b = blockIdx.x;
+  const int b = wl ? wl[blockIdx.x] : (int)blockIdx.x;
   if (threadIdx.x == 0) {
     const double* dc = dtch + 2 * (solve_of ? solve_of[b] : 0);
     const double dxm = fmin(fmin(bd[b].dx[0], bd[b].dx[1]), bd[b].dx[2]);
@@ -256,10 +258,11 @@ __global__ void __launch_bounds__(256) estimate_kernel(const R* __restrict__ U, 
                                                         const BlockDesc* __restrict__ bd,
                                                         const int* __restrict__ vars,
                                                         const double* __restrict__ weights, int nvars,
-                                                        double eps, double* __restrict__ emax) {
+                                                        double eps, double* __restrict__ emax,
+                                                        const int* __restrict__ wl) {
   using P = PT<R>;
   constexpr int NT = P::NV + P::NA;
-  const int b = blockIdx.x;
+  const int b = wl ? wl[blockIdx.x] : (int)blockIdx.x;
   int src[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) src[i] = bd[b].src[i];
@@ -548,7 +551,7 @@ cudaError_t launch_speeds(const AuxArgs& a, unsigned long long* speeds, cudaStre
   do {                                                                                            \
     PhysParamsT<R> pp;                                                                            \
     pp.set(a.gamma, 0.0);                                                                         \
-    speeds_kernel<PT, R><<<a.nblk, 256, 0, s>>>((const R*)a.U, a.bd, pp, speeds, a.status, a.solve_of); \
+    speeds_kernel<PT, R><<<a.nblk, 256, 0, s>>>((const R*)a.U, a.bd, pp, speeds, a.status, a.solve_of, a.wl); \
   } while (0)
   AGILE_DISPATCH(a.phys, a.real_bytes, CALL);
 #undef CALL
@@ -563,15 +566,17 @@ cudaError_t launch_set_dt(const unsigned long long* speeds, double* dtch, double
 
 cudaError_t launch_glm_decay(const AuxArgs& a, const double* dtch, cudaStream_t s) {
   if (a.nblk == 0) return cudaSuccess;
-  if (a.real_bytes == 8) glm_decay_kernel<double><<<a.nblk, 256, 0, s>>>((double*)a.Uw, a.bd, dtch, a.glm_alpha, a.solve_of);
-  else glm_decay_kernel<float><<<a.nblk, 256, 0, s>>>((float*)a.Uw, a.bd, dtch, a.glm_alpha, a.solve_of);
+  if (a.real_bytes == 8)
+    glm_decay_kernel<double><<<a.nblk, 256, 0, s>>>((double*)a.Uw, a.bd, dtch, a.glm_alpha, a.solve_of, a.wl);
+  else glm_decay_kernel<float><<<a.nblk, 256, 0, s>>>((float*)a.Uw, a.bd, dtch, a.glm_alpha, a.solve_of, a.wl);
   return cudaGetLastError();
 }
 
 cudaError_t launch_estimate(const AuxArgs& a, const int* vars, const double* weights, int nvars,
                             double eps, double* emax, cudaStream_t s) {
   if (a.nblk == 0) return cudaSuccess;
-#define CALL(PT) estimate_kernel<PT, R><<<a.nblk, 256, 0, s>>>((const R*)a.U, (const R*)a.G, a.bd, vars, weights, nvars, eps, emax)
+#define CALL(PT) \
+  estimate_kernel<PT, R><<<a.nblk, 256, 0, s>>>((const R*)a.U, (const R*)a.G, a.bd, vars, weights, nvars, eps, emax, a.wl)
   AGILE_DISPATCH(a.phys, a.real_bytes, CALL);
 #undef CALL
   return cudaGetLastError();

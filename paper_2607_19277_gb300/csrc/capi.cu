@@ -300,9 +300,9 @@ agile_status fill_ghosts(agile_mesh* m, void* U) {
 // block; converted to conserved variables on the device.
 agile_status apply_ic(agile_mesh* m, void* U, const std::vector<int>& blocks, const double* prim_src = nullptr) {
   const int chunk = 256;
-  std::vector<double> prim((size_t)chunk * m->nv * NCELL);
+  std::vector<double> prim(prim_src ? 0 : (size_t)chunk * m->nv * NCELL);   // callback staging
   std::vector<double> xs(NCELL), ys(NCELL), zs(NCELL);
-  double* d_prim = (double*)dalloc(m, prim.size() * sizeof(double));
+  double* d_prim = (double*)dalloc(m, (size_t)chunk * m->nv * NCELL * sizeof(double));
   int* d_blocks = (int*)dalloc(m, chunk * sizeof(int));
   if (!d_prim || !d_blocks) return fail(m, AGILE_ENOMEM, "device allocation failed");
   const auto& keys = m->mesh->blocks();
@@ -327,7 +327,9 @@ agile_status apply_ic(agile_mesh* m, void* U, const std::vector<int>& blocks, co
     AuxArgs a = aux_args(m, U);
     CK(m, launch_prim2cons(a, d_prim, d_blocks, n, m->stream));
     m->total_launches++;
-    CK(m, cudaStreamSynchronize(m->stream));
+    // the next chunk reuses the device staging in stream order; the callback path also
+    // waits because its host buffer is refilled for the next chunk
+    if (!prim_src) CK(m, cudaStreamSynchronize(m->stream));
   }
   dfree_t(m, d_prim);
   dfree_t(m, d_blocks);
@@ -1053,6 +1055,24 @@ struct agile_batch {
   int nghost = 0, nfix = 0, nslots = 0;
   std::vector<agile_ic_fn> ics;     // initial conditions, re-applied to blocks a regrid creates
   std::vector<void*> ic_users;
+  // continuous batching: solves attach to and detach from the block pool without moving the
+  // others. Solve i (live[i]) holds pool blocks offset[i] .. offset[i] + its block count - 1;
+  // blocks of detached solves are holes that later attachments fill. The per-block kernels
+  // walk the work list d_wl (the live solves' blocks) instead of the whole pool.
+  std::vector<char> live;
+  struct Tables {                   // a solve's own descriptor tables (local indices), cached
+    bool valid = false;
+    std::vector<BlockDesc> desc;
+    std::vector<GhostTask> ghosts;
+    std::vector<FixupTask> fix;
+    int nslots = 0;
+  };
+  std::vector<Tables> tables;
+  int cap = 0;                      // pool capacity in blocks (U[0] .. U[2])
+  int cap_stage = 0;                // capacity U[1], U[2] were allocated with
+  int scap = 0;                     // solves the per-solve device arrays hold
+  int* d_wl = nullptr;
+  int nwork = 0;
 };
 
 namespace {
@@ -1100,75 +1120,111 @@ AuxArgs batch_aux(agile_batch* B, void* U) {
   a.status = B->d_status;
   a.solve_of = B->d_solve_of;
   a.nsolve = B->nsolve;
+  a.nblk = B->nwork;
+  a.wl = B->d_wl;
   return a;
 }
 
 agile_status batch_status(agile_batch* B);
 
-// Descriptor tables of all solves concatenated: block indices offset by the solve's first
-// block, ghost-slot / flux-register indices by its first slot. Every index is checked against
-// the new sizes before anything is uploaded. Reallocates everything except U[0], whose
-// blocks the caller has already laid out in this order.
+int solve_blocks(const agile_batch* B, int i) {
+  return B->live[i] ? (int)B->meshes[i]->blocks().size() : 0;
+}
+
+bool solve_ok(const agile_batch* B, int i) { return B && i >= 0 && i < B->nsolve && B->live[i]; }
+
+// Descriptor tables of the live solves at their pool offsets: block indices offset by the
+// solve's first block, ghost-slot / flux-register indices by its first slot; pool blocks of no
+// live solve get an inert descriptor and are left out of the work list. Every index is checked
+// against the new sizes before anything is uploaded. U[0] already holds every live solve's
+// blocks at its offset; the stage buffers are reallocated when the capacity changed.
 agile_status batch_rebuild(agile_batch* B) {
-  std::vector<BlockDesc> desc;
+  int extent = 0;
+  for (int i = 0; i < B->nsolve; ++i)
+    if (B->live[i]) extent = std::max(extent, B->offset[i] + solve_blocks(B, i));
+  if (extent > B->cap) return bfail(B, AGILE_EINVAL, "pool layout exceeds the capacity");
+  BlockDesc inert{};
+  for (int f = 0; f < 6; ++f) {
+    inert.src[f] = SRC_OUTFLOW;
+    inert.slot[f] = -1;
+    inert.kind[f] = FK_BC;
+    for (int q = 0; q < 4; ++q) inert.nbr[f][q] = -1;
+  }
+  inert.dx[0] = inert.dx[1] = inert.dx[2] = 1.0;
+  inert.level = 1;
+  std::vector<BlockDesc> desc(extent, inert);
+  std::vector<int> solve_of(extent, 0), work;
   std::vector<GhostTask> ghosts;
   std::vector<FixupTask> fix;
-  std::vector<int> solve_of;
-  B->offset.clear();
+  std::vector<char> used(extent, 0);
   int slots = 0;
+  B->tables.resize(B->nsolve);
   for (int i = 0; i < B->nsolve; ++i) {
-    std::vector<BlockDesc> d;
-    std::vector<GhostTask> g;
-    std::vector<FixupTask> x;
-    int ns = 0;
-    std::string err;
-    B->meshes[i]->build_descs(&d, &g, &x, &ns, &err);
-    if (!err.empty()) return bfail(B, AGILE_EINVAL, err);
-    const int O = (int)desc.size(), S = slots;
-    B->offset.push_back(O);
-    for (BlockDesc& bd : d) {
+    if (!B->live[i]) continue;
+    agile_batch::Tables& T = B->tables[i];
+    if (!T.valid) {                 // a solve's own tables change only when it is regridded
+      std::string err;
+      T.desc.clear();
+      T.ghosts.clear();
+      T.fix.clear();
+      B->meshes[i]->build_descs(&T.desc, &T.ghosts, &T.fix, &T.nslots, &err);
+      if (!err.empty()) return bfail(B, AGILE_EINVAL, err);
+      T.valid = true;
+    }
+    const std::vector<BlockDesc>& d = T.desc;
+    std::vector<GhostTask> g = T.ghosts;
+    std::vector<FixupTask> x = T.fix;
+    const int ns = T.nslots;
+    const int O = B->offset[i], S = slots;
+    for (size_t q = 0; q < d.size(); ++q) {
+      BlockDesc bd = d[q];
       for (int f = 0; f < 6; ++f) {
         if (bd.src[f] >= 0) bd.src[f] += O;
         else if (bd.src[f] <= SRC_SLOT0) bd.src[f] = SRC_SLOT0 - (SRC_SLOT0 - bd.src[f] + S);
         if (bd.slot[f] >= 0) bd.slot[f] += S;
-        for (int q = 0; q < 4; ++q)
-          if (bd.nbr[f][q] >= 0) bd.nbr[f][q] += O;
+        for (int k = 0; k < 4; ++k)
+          if (bd.nbr[f][k] >= 0) bd.nbr[f][k] += O;
       }
-      desc.push_back(bd);
-      solve_of.push_back(i);
+      const int b = O + (int)q;
+      if (b < 0 || b >= extent || used[b]) return bfail(B, AGILE_EINVAL, "solves overlap in the pool");
+      used[b] = 1;
+      desc[b] = bd;
+      solve_of[b] = i;
+      work.push_back(b);
     }
     for (GhostTask& t : g) {
       t.blk += O;
       t.slot += S;
-      for (int q = 0; q < 4; ++q)
-        if (t.nbr[q] >= 0) t.nbr[q] += O;
+      for (int k = 0; k < 4; ++k)
+        if (t.nbr[k] >= 0) t.nbr[k] += O;
       ghosts.push_back(t);
     }
     for (FixupTask& t : x) {
       t.blk += O;
       for (int j = 0; j < t.nface; ++j) {
         t.slot_c[j] += S;
-        for (int q = 0; q < 4; ++q) t.slot_f[j][q] += S;
+        for (int k = 0; k < 4; ++k) t.slot_f[j][k] += S;
       }
       fix.push_back(t);
     }
     slots += ns;
   }
-  const int nblk = (int)desc.size();
-  auto blk_ok = [&](int v) { return v >= 0 && v < nblk; };
+  auto blk_ok = [&](int v) { return v >= 0 && v < extent && used[v]; };
   auto slot_ok = [&](int v) { return v >= 0 && v < slots; };
-  for (const BlockDesc& bd : desc)
+  for (int b : work) {
+    const BlockDesc& bd = desc[b];
     for (int f = 0; f < 6; ++f) {
       if (bd.src[f] >= 0 && !blk_ok(bd.src[f])) return bfail(B, AGILE_EINVAL, "block table out of range");
       if (bd.src[f] <= SRC_SLOT0 && !slot_ok(SRC_SLOT0 - bd.src[f])) return bfail(B, AGILE_EINVAL, "slot out of range");
       if (bd.slot[f] >= slots) return bfail(B, AGILE_EINVAL, "slot out of range");
       for (int q = 0; q < 4; ++q)
-        if (bd.nbr[f][q] >= nblk) return bfail(B, AGILE_EINVAL, "neighbour out of range");
+        if (bd.nbr[f][q] >= extent) return bfail(B, AGILE_EINVAL, "neighbour out of range");
     }
+  }
   for (const GhostTask& t : ghosts) {
     if (!blk_ok(t.blk) || !slot_ok(t.slot)) return bfail(B, AGILE_EINVAL, "ghost task out of range");
     for (int q = 0; q < 4; ++q)
-      if (t.nbr[q] >= nblk) return bfail(B, AGILE_EINVAL, "ghost task out of range");
+      if (t.nbr[q] >= extent) return bfail(B, AGILE_EINVAL, "ghost task out of range");
   }
   for (const FixupTask& t : fix) {
     if (!blk_ok(t.blk)) return bfail(B, AGILE_EINVAL, "fix-up task out of range");
@@ -1178,44 +1234,61 @@ agile_status batch_rebuild(agile_batch* B) {
         if (!slot_ok(t.slot_f[j][q])) return bfail(B, AGILE_EINVAL, "fix-up task out of range");
     }
   }
+  // The old tables and buffers are released in stream order (the allocator's contract), so
+  // work already enqueued still reads them and nothing waits here.
   agile_mesh view;
   as_mesh_view(B, &view);
   dfree_t(&view, B->d_bd);
   dfree_t(&view, B->d_solve_of);
+  dfree_t(&view, B->d_wl);
   dfree_t(&view, B->d_ghosts);
   dfree_t(&view, B->d_fix);
   dfree(&view, B->G);
   dfree(&view, B->FR);
-  dfree(&view, B->U[1]);
-  dfree(&view, B->U[2]);
-  B->nblk = nblk;
-  view.nblk = nblk;
-  const size_t pool = (size_t)nblk * B->nt * NCELL * B->rb;
-  B->U[1] = dalloc(&view, pool);
-  B->U[2] = B->cfg.rk == 3 ? dalloc(&view, pool) : nullptr;
-  B->d_bd = (BlockDesc*)dalloc(&view, desc.size() * sizeof(BlockDesc));
-  B->d_solve_of = (int*)dalloc(&view, solve_of.size() * sizeof(int));
+  if (B->cap_stage != B->cap) {
+    dfree(&view, B->U[1]);
+    dfree(&view, B->U[2]);
+    const size_t pool = (size_t)B->cap * B->nt * NCELL * B->rb;
+    B->U[1] = dalloc(&view, pool);
+    B->U[2] = B->cfg.rk == 3 ? dalloc(&view, pool) : nullptr;
+    if (!B->U[1] || (B->cfg.rk == 3 && !B->U[2])) return bfail(B, AGILE_ENOMEM, "device allocation failed");
+    B->cap_stage = B->cap;
+  }
+  B->nblk = extent;
+  B->nwork = (int)work.size();
+  view.nblk = extent;
+  if (extent) {
+    B->d_bd = (BlockDesc*)dalloc(&view, desc.size() * sizeof(BlockDesc));
+    B->d_solve_of = (int*)dalloc(&view, solve_of.size() * sizeof(int));
+  }
+  if (!work.empty()) B->d_wl = (int*)dalloc(&view, work.size() * sizeof(int));
   if (!ghosts.empty()) B->d_ghosts = (GhostTask*)dalloc(&view, ghosts.size() * sizeof(GhostTask));
   if (!fix.empty()) B->d_fix = (FixupTask*)dalloc(&view, fix.size() * sizeof(FixupTask));
   if (slots) {
     B->G = dalloc(&view, (size_t)slots * B->nt * 512 * B->rb);
     B->FR = dalloc(&view, (size_t)slots * B->nv * 256 * B->rb);
   }
-  if (!B->U[1] || (B->cfg.rk == 3 && !B->U[2]) || !B->d_bd || !B->d_solve_of ||
-      (!ghosts.empty() && !B->d_ghosts) || (!fix.empty() && !B->d_fix) || (slots && (!B->G || !B->FR)))
+  if ((extent && (!B->d_bd || !B->d_solve_of)) || (!work.empty() && !B->d_wl) || (!ghosts.empty() && !B->d_ghosts) ||
+      (!fix.empty() && !B->d_fix) || (slots && (!B->G || !B->FR)))
     return bfail(B, AGILE_ENOMEM, "device allocation failed");
-  BCK(B, cudaMemcpyAsync(B->d_bd, desc.data(), desc.size() * sizeof(BlockDesc), cudaMemcpyHostToDevice, B->stream));
-  BCK(B, cudaMemcpyAsync(B->d_solve_of, solve_of.data(), solve_of.size() * sizeof(int), cudaMemcpyHostToDevice, B->stream));
+  if (extent) {
+    BCK(B, cudaMemcpyAsync(B->d_bd, desc.data(), desc.size() * sizeof(BlockDesc), cudaMemcpyHostToDevice, B->stream));
+    BCK(B, cudaMemcpyAsync(B->d_solve_of, solve_of.data(), solve_of.size() * sizeof(int), cudaMemcpyHostToDevice,
+                           B->stream));
+  }
+  if (!work.empty())
+    BCK(B, cudaMemcpyAsync(B->d_wl, work.data(), work.size() * sizeof(int), cudaMemcpyHostToDevice, B->stream));
   if (!ghosts.empty())
     BCK(B, cudaMemcpyAsync(B->d_ghosts, ghosts.data(), ghosts.size() * sizeof(GhostTask), cudaMemcpyHostToDevice, B->stream));
   if (!fix.empty())
     BCK(B, cudaMemcpyAsync(B->d_fix, fix.data(), fix.size() * sizeof(FixupTask), cudaMemcpyHostToDevice, B->stream));
+  // (pageable host sources are staged when each copy is enqueued: the vectors may go now)
   B->nghost = (int)ghosts.size();
   B->nfix = (int)fix.size();
   B->nslots = slots;
-  BCK(B, cudaStreamSynchronize(B->stream));   // host tables go out of scope
+  view.nblk = std::max(extent, 1);
   for (int i = 0; i < 3; ++i) {
-    if (make_tmap(&view, B->U[i], &B->tmap[i]) != AGILE_OK) return bfail(B, AGILE_ECUDA, "tensor map");
+    if (B->U[i] && make_tmap(&view, B->U[i], &B->tmap[i]) != AGILE_OK) return bfail(B, AGILE_ECUDA, "tensor map");
   }
   if (B->graph) {                   // the captured step refers to the old tables
     cudaGraphExecDestroy(B->graph);
@@ -1233,7 +1306,7 @@ agile_status batch_apply_plans(agile_batch* B, std::vector<RegridPlan>& plans, i
   std::vector<char> changed(B->nsolve, 0);
   bool any = false;
   for (int j = 0; j < B->nsolve; ++j) {
-    changed[j] = plans[j].n_refined != 0 || plans[j].n_coarsened != 0;
+    changed[j] = B->live[j] && (plans[j].n_refined != 0 || plans[j].n_coarsened != 0);
     any = any || changed[j];
   }
   if (!any) return AGILE_OK;
@@ -1245,8 +1318,8 @@ agile_status batch_apply_plans(agile_batch* B, std::vector<RegridPlan>& plans, i
   std::vector<int> count(B->nsolve), ncount(B->nsolve);
   std::vector<long long> noff(B->nsolve);
   long long total = 0;
-  for (int j = 0; j < B->nsolve; ++j) {
-    count[j] = (int)B->meshes[j]->blocks().size();
+  for (int j = 0; j < B->nsolve; ++j) {     // the new layout is compact: live solves in order
+    count[j] = solve_blocks(B, j);
     ncount[j] = changed[j] ? (int)plans[j].blocks.size() : count[j];
     noff[j] = total;
     total += ncount[j];
@@ -1266,7 +1339,8 @@ agile_status batch_apply_plans(agile_batch* B, std::vector<RegridPlan>& plans, i
       src.push_back(r);
     }
   }
-  void* Unew = dalloc(&view, (size_t)total * per);
+  const long long newcap = std::max<long long>(total, 1);
+  void* Unew = dalloc(&view, (size_t)newcap * per);
   RegridSrc* d_src = (RegridSrc*)dalloc(&view, src.size() * sizeof(RegridSrc));
   if (!Unew || !d_src) return bfail(B, AGILE_ENOMEM, "device allocation failed");
   BCK(B, cudaMemcpyAsync(d_src, src.data(), src.size() * sizeof(RegridSrc), cudaMemcpyHostToDevice, B->stream));
@@ -1282,8 +1356,15 @@ agile_status batch_apply_plans(agile_batch* B, std::vector<RegridPlan>& plans, i
   dfree_t(&view, d_src);
   dfree(&view, B->U[0]);
   B->U[0] = Unew;
-  for (int j = 0; j < B->nsolve; ++j)
-    if (changed[j]) B->meshes[j]->apply(plans[j]);
+  B->cap = (int)newcap;
+  B->tables.resize(B->nsolve);
+  for (int j = 0; j < B->nsolve; ++j) {
+    if (changed[j]) {
+      B->meshes[j]->apply(plans[j]);
+      B->tables[j].valid = false;
+    }
+    B->offset[j] = (int)noff[j];
+  }
   agile_status st = batch_rebuild(B);
   if (st) return st;
   for (int j = 0; j < B->nsolve && init; ++j) {
@@ -1319,17 +1400,16 @@ agile_status batch_flags(agile_batch* B, std::vector<std::vector<int>>* flags) {
   as_mesh_view(B, &view);
   AuxArgs a = batch_aux(B, B->U[0]);
   if (B->nghost) BCK(B, launch_ghosts(a, B->d_ghosts, B->nghost, B->stream));
-  const agile_config& c0 = B->cfgs[0];
   int* d_vars = (int*)dalloc(&view, 9 * sizeof(int));
   double* d_w = (double*)dalloc(&view, 9 * sizeof(double));
-  double* d_e = (double*)dalloc(&view, (size_t)B->nblk * sizeof(double));
+  double* d_e = (double*)dalloc(&view, (size_t)std::max(B->nblk, 1) * sizeof(double));
   if (!d_vars || !d_w || !d_e) return bfail(B, AGILE_ENOMEM, "device allocation failed");
-  std::vector<double> emax(B->nblk);
+  std::vector<double> emax(std::max(B->nblk, 1));
   flags->assign(B->nsolve, std::vector<int>());
   // the estimator's variables and weights may differ per solve: one pass per distinct set
   std::vector<char> done(B->nsolve, 0);
   for (int j = 0; j < B->nsolve; ++j) {
-    if (done[j]) continue;
+    if (done[j] || !B->live[j]) continue;
     const agile_config& c = B->cfgs[j];
     BCK(B, cudaMemcpyAsync(d_vars, c.refine_vars, 9 * sizeof(int), cudaMemcpyHostToDevice, B->stream));
     BCK(B, cudaMemcpyAsync(d_w, c.refine_weights, 9 * sizeof(double), cudaMemcpyHostToDevice, B->stream));
@@ -1338,7 +1418,7 @@ agile_status batch_flags(agile_batch* B, std::vector<std::vector<int>>* flags) {
     BCK(B, cudaStreamSynchronize(B->stream));
     for (int i = j; i < B->nsolve; ++i) {
       const agile_config& ci = B->cfgs[i];
-      if (done[i] || ci.refine_nvars != c.refine_nvars || ci.lohner_eps != c.lohner_eps ||
+      if (done[i] || !B->live[i] || ci.refine_nvars != c.refine_nvars || ci.lohner_eps != c.lohner_eps ||
           memcmp(ci.refine_vars, c.refine_vars, sizeof(c.refine_vars)) != 0 ||
           memcmp(ci.refine_weights, c.refine_weights, sizeof(c.refine_weights)) != 0)
         continue;
@@ -1355,7 +1435,6 @@ agile_status batch_flags(agile_batch* B, std::vector<std::vector<int>>* flags) {
       }
     }
   }
-  (void)c0;
   dfree_t(&view, d_vars);
   dfree_t(&view, d_w);
   dfree_t(&view, d_e);
@@ -1420,7 +1499,8 @@ agile_status batch_enqueue_step(agile_batch* B) {
     A.glm_alpha = B->cfg.glm_alpha;
     A.htc_kappa0 = B->cfg.htc_kappa0;
     A.glm_post = (mhd && last && fuse) ? 1 : 0;
-    A.nblk = B->nblk;
+    A.nblk = B->nwork;
+    A.wl = B->d_wl;
     A.status = B->d_status;
     A.speeds = (last && fuse) ? B->d_speeds : nullptr;
     A.tmap = &B->tmap[st == 0 ? 0 : st];
@@ -1468,7 +1548,8 @@ agile_status batch_stage1(agile_batch* B, int grid, bool dynamic, int layout) {
   A.glm_alpha = B->cfg.glm_alpha;
   A.htc_kappa0 = B->cfg.htc_kappa0;
   A.glm_post = 0;
-  A.nblk = B->nblk;
+  A.nblk = B->nwork;
+  A.wl = B->d_wl;
   A.status = B->d_status;
   A.speeds = nullptr;
   A.tmap = &B->tmap[0];
@@ -1487,6 +1568,43 @@ agile_status batch_stage1(agile_batch* B, int grid, bool dynamic, int layout) {
     e = launch_stage_ffhd_htc(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
   else e = launch_stage_srhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
   if (e != cudaSuccess) return bfail(B, AGILE_ECUDA, std::string("stage kernel: ") + cudaGetErrorString(e));
+  return AGILE_OK;
+}
+
+// A solve's configuration fits a batch whose scheme is c0's: same scheme, validated like a
+// single mesh (host-side checks only), no resistivity.
+bool batch_cfg_ok(const agile_config& c0, const agile_config& c) {
+  if (c.physics != c0.physics || c.limiter != c0.limiter || c.flux != c0.flux || c.rk != c0.rk ||
+      c.real_bytes != c0.real_bytes || c.gamma != c0.gamma || c.cfl != c0.cfl || c.glm_alpha != c0.glm_alpha ||
+      c.eos != c0.eos || c.htc_kappa0 != c0.htc_kappa0 || c.eta != 0.0 || c.max_level < 1 || c.max_level > 12 ||
+      c.refine_nvars < 0 || c.refine_nvars > 9)
+    return false;
+  if (!scheme_ok(c)) return false;
+  for (int d = 0; d < 3; ++d) {
+    if (c.base_blocks[d] < 1 || c.base_blocks[d] > 4096 || !(c.xmax[d] > c.xmin[d])) return false;
+    if ((c.bc[2 * d] == AGILE_PERIODIC) != (c.bc[2 * d + 1] == AGILE_PERIODIC)) return false;
+    for (int s = 0; s < 2; ++s)
+      if (c.bc[2 * d + s] < 0 || c.bc[2 * d + s] > 2) return false;
+  }
+  return true;
+}
+
+// Per-solve device arrays (speeds, dt and c_h) for at least n solves.
+agile_status batch_reserve_solves(agile_batch* B, int n) {
+  if (n <= B->scap) return AGILE_OK;
+  const int ncap = std::max(n, 2 * B->scap);
+  agile_mesh view;
+  as_mesh_view(B, &view);
+  BCK(B, cudaStreamSynchronize(B->stream));
+  dfree_t(&view, B->d_speeds);
+  dfree_t(&view, B->d_dtch);
+  B->d_speeds = (unsigned long long*)dalloc(&view, 2 * sizeof(unsigned long long) * ncap);
+  B->d_dtch = (double*)dalloc(&view, 2 * sizeof(double) * ncap);
+  if (!B->d_speeds || !B->d_dtch) return bfail(B, AGILE_ENOMEM, "device allocation failed");
+  BCK(B, cudaMemsetAsync(B->d_speeds, 0, 2 * sizeof(unsigned long long) * ncap, B->stream));
+  BCK(B, cudaMemsetAsync(B->d_dtch, 0, 2 * sizeof(double) * ncap, B->stream));
+  B->scap = ncap;
+  B->speeds_valid = false;
   return AGILE_OK;
 }
 
@@ -1557,23 +1675,8 @@ agile_status agile_batch_create(const agile_config* cfgs, int nsolve, const agil
   if (!cfgs || !out || nsolve < 1 || nsolve > (1 << 20)) return AGILE_EINVAL;
   *out = nullptr;
   const agile_config& c0 = cfgs[0];
-  for (int i = 0; i < nsolve; ++i) {
-    const agile_config& c = cfgs[i];
-    if (c.physics != c0.physics || c.limiter != c0.limiter || c.flux != c0.flux || c.rk != c0.rk ||
-        c.real_bytes != c0.real_bytes || c.gamma != c0.gamma || c.cfl != c0.cfl ||
-        c.glm_alpha != c0.glm_alpha || c.eos != c0.eos || c.htc_kappa0 != c0.htc_kappa0 || c.eta != 0.0 || c.max_level < 1 ||
-        c.max_level > 12 ||
-        c.refine_nvars < 0 || c.refine_nvars > 9)
-      return AGILE_EINVAL;
-    // validate each configuration like a single mesh (host-side checks only)
-    if (!scheme_ok(c)) return AGILE_EINVAL;
-    for (int d = 0; d < 3; ++d) {
-      if (c.base_blocks[d] < 1 || c.base_blocks[d] > 4096 || !(c.xmax[d] > c.xmin[d])) return AGILE_EINVAL;
-      if ((c.bc[2 * d] == AGILE_PERIODIC) != (c.bc[2 * d + 1] == AGILE_PERIODIC)) return AGILE_EINVAL;
-      for (int s = 0; s < 2; ++s)
-        if (c.bc[2 * d + s] < 0 || c.bc[2 * d + s] > 2) return AGILE_EINVAL;
-    }
-  }
+  for (int i = 0; i < nsolve; ++i)
+    if (!batch_cfg_ok(c0, cfgs[i])) return AGILE_EINVAL;
   agile_batch* B = new agile_batch();
   B->cfg = c0;
   B->nsolve = nsolve;
@@ -1600,8 +1703,12 @@ agile_status agile_batch_create(const agile_config* cfgs, int nsolve, const agil
   for (int i = 0; i < nsolve; ++i) {
     HostMesh* hm = new HostMesh(cfgs[i].base_blocks, cfgs[i].max_level, cfgs[i].bc, cfgs[i].xmin, cfgs[i].xmax);
     B->meshes.push_back(hm);
+    B->offset.push_back(nblk);
+    B->live.push_back(1);
     nblk += (int)hm->blocks().size();
   }
+  B->cap = nblk;
+  B->scap = nsolve;
   agile_mesh view;
   as_mesh_view(B, &view);
   view.nblk = nblk;
@@ -1642,25 +1749,26 @@ void agile_batch_destroy(agile_batch* B) {
   dfree_t(&view, B->d_speeds);
   dfree_t(&view, B->d_dtch);
   dfree_t(&view, B->d_work);
+  dfree_t(&view, B->d_wl);
   dfree_t(&view, B->d_ghosts);
   dfree_t(&view, B->d_fix);
   dfree(&view, B->G);
   dfree(&view, B->FR);
   cudaStreamSynchronize(B->stream);
-  for (HostMesh* hm : B->meshes) delete hm;
+  for (HostMesh* hm : B->meshes) delete hm;   // nullptr for detached solves
   if (B->own_stream) cudaStreamDestroy(B->stream);
   delete B;
 }
 
 agile_status agile_batch_layout(agile_batch* B, int solve, size_t* nblocks, int* nvar) {
-  if (!B || solve < 0 || solve >= B->nsolve) return AGILE_EINVAL;
+  if (!solve_ok(B, solve)) return AGILE_EINVAL;
   if (nblocks) *nblocks = B->meshes[solve]->blocks().size();
   if (nvar) *nvar = B->nv;
   return AGILE_OK;
 }
 
 agile_status agile_batch_set_state(agile_batch* B, int solve, agile_ic_fn ic, void* user) {
-  if (!B || !ic || solve < 0 || solve >= B->nsolve) return bfail(B, AGILE_EINVAL, "bad argument");
+  if (!ic || !solve_ok(B, solve)) return bfail(B, AGILE_EINVAL, "bad argument");
   agile_mesh view;
   as_mesh_view(B, &view);
   view.mesh = B->meshes[solve];
@@ -1686,7 +1794,7 @@ agile_status agile_batch_set_state(agile_batch* B, int solve, agile_ic_fn ic, vo
 }
 
 agile_status agile_batch_set_state_prims(agile_batch* B, int solve, const double* prim, size_t nblk) {
-  if (!B || !prim || solve < 0 || solve >= B->nsolve) return bfail(B, AGILE_EINVAL, "bad argument");
+  if (!prim || !solve_ok(B, solve)) return bfail(B, AGILE_EINVAL, "bad argument");
   if (nblk != B->meshes[solve]->blocks().size()) return bfail(B, AGILE_EINVAL, "block count does not match the solve");
   agile_mesh view;
   as_mesh_view(B, &view);
@@ -1705,7 +1813,7 @@ agile_status agile_batch_set_state_prims(agile_batch* B, int solve, const double
   B->ics[solve] = nullptr;
   B->ic_users[solve] = nullptr;
   B->speeds_valid = false;
-  return batch_status(B);
+  return AGILE_OK;                            // enqueued; errors surface at the next sync
 }
 
 agile_status agile_batch_step(agile_batch* B) {
@@ -1752,13 +1860,13 @@ agile_status agile_batch_cfl_dt(agile_batch* B, double* dt) {
   for (int i = 0; i < B->nsolve; ++i) {
     double smax;
     memcpy(&smax, &h[2 * i], sizeof(double));
-    dt[i] = B->cfg.cfl / smax;
+    dt[i] = B->live[i] ? B->cfg.cfl / smax : 0.0;
   }
   return AGILE_OK;
 }
 
 agile_status agile_batch_get_state(agile_batch* B, int solve, int* level, int* ijk, double* cons) {
-  if (!B || solve < 0 || solve >= B->nsolve) return bfail(B, AGILE_EINVAL, "bad argument");
+  if (!solve_ok(B, solve)) return bfail(B, AGILE_EINVAL, "bad argument");
   const auto& keys = B->meshes[solve]->blocks();
   const int n = (int)keys.size();
   for (int i = 0; i < n; ++i) {
@@ -1777,6 +1885,7 @@ agile_status agile_batch_get_state(agile_batch* B, int solve, int* level, int* i
   if (!d) return bfail(B, AGILE_ENOMEM, "device allocation failed");
   AuxArgs a = batch_aux(B, (char*)B->U[0] + (size_t)B->offset[solve] * B->nt * NCELL * B->rb);
   a.nblk = n;
+  a.wl = nullptr;
   BCK(B, launch_pack(a, d, nullptr, B->stream));
   BCK(B, cudaMemcpyAsync(cons, d, bytes, cudaMemcpyDeviceToHost, B->stream));
   agile_status s = batch_status(B);
@@ -1785,21 +1894,22 @@ agile_status agile_batch_get_state(agile_batch* B, int solve, int* level, int* i
 }
 
 agile_status agile_batch_regrid_flags(agile_batch* B, int solve, const int* flags, int init, int* nr, int* nc) {
-  if (!B || !flags || solve < 0 || solve >= B->nsolve) return bfail(B, AGILE_EINVAL, "bad argument");
+  if (!flags || !solve_ok(B, solve)) return bfail(B, AGILE_EINVAL, "bad argument");
   const int n = (int)B->meshes[solve]->blocks().size();
   std::vector<int> f(flags, flags + n);
   return batch_regrid(B, solve, f, init, nr, nc);
 }
 
 agile_status agile_batch_regrid(agile_batch* B, int solve, int init, int* nr, int* nc) {
-  if (!B || solve < -1 || solve >= B->nsolve) return bfail(B, AGILE_EINVAL, "bad argument");
+  if (!B || solve < -1 || solve >= B->nsolve || (solve >= 0 && !B->live[solve]))
+    return bfail(B, AGILE_EINVAL, "bad argument");
   std::vector<std::vector<int>> flags;
   agile_status s = batch_flags(B, &flags);
   if (s) return s;
   std::vector<RegridPlan> plans(B->nsolve);
   int tr = 0, tc = 0;
   for (int j = 0; j < B->nsolve; ++j) {
-    if (solve >= 0 && j != solve) continue;
+    if ((solve >= 0 && j != solve) || !B->live[j]) continue;
     plans[j] = B->meshes[j]->plan(flags[j]);
     tr += plans[j].n_refined;
     tc += plans[j].n_coarsened;
@@ -1810,8 +1920,7 @@ agile_status agile_batch_regrid(agile_batch* B, int solve, int init, int* nr, in
 }
 
 agile_status agile_batch_copy_solve(agile_batch* dst, int dst_solve, agile_batch* src, int src_solve) {
-  if (!dst || !src || dst_solve < 0 || dst_solve >= dst->nsolve || src_solve < 0 || src_solve >= src->nsolve)
-    return bfail(dst, AGILE_EINVAL, "bad argument");
+  if (!solve_ok(dst, dst_solve) || !solve_ok(src, src_solve)) return bfail(dst, AGILE_EINVAL, "bad argument");
   const agile_config& a = dst->cfgs[dst_solve];
   const agile_config& b = src->cfgs[src_solve];
   bool same = dst->nt == src->nt && dst->rb == src->rb && a.physics == b.physics && a.eos == b.eos;
@@ -1833,6 +1942,96 @@ agile_status agile_batch_copy_solve(agile_batch* dst, int dst_solve, agile_batch
                            cudaMemcpyDeviceToDevice, dst->stream));
   dst->speeds_valid = false;
   return batch_status(dst);
+}
+
+agile_status agile_batch_attach(agile_batch* B, const agile_config* cfg, int* solve) {
+  if (!B || !cfg || !solve) return bfail(B, AGILE_EINVAL, "null argument");
+  if (!batch_cfg_ok(B->cfg, *cfg)) return bfail(B, AGILE_EINVAL, "the solve's scheme differs from the batch's");
+  agile_status s = AGILE_OK;
+  HostMesh* hm = new HostMesh(cfg->base_blocks, cfg->max_level, cfg->bc, cfg->xmin, cfg->xmax);
+  const int n = (int)hm->blocks().size();
+  // first fit among the holes between live solves, else after the last one
+  std::vector<std::pair<int, int>> ranges;   // (offset, count) of live solves, sorted
+  for (int i = 0; i < B->nsolve; ++i)
+    if (B->live[i]) ranges.push_back({B->offset[i], solve_blocks(B, i)});
+  std::sort(ranges.begin(), ranges.end());
+  int at = -1, prev = 0;
+  for (const auto& r : ranges) {
+    if (r.first - prev >= n) {
+      at = prev;
+      break;
+    }
+    prev = r.first + r.second;
+  }
+  if (at < 0 && B->cap - prev >= n) at = prev;
+  agile_mesh view;
+  as_mesh_view(B, &view);
+  const size_t per = (size_t)B->nt * NCELL * B->rb;
+  if (at < 0) {
+    // grow: a new pool at least twice the old, the live solves copied into it compactly
+    int live_blocks = 0;
+    for (const auto& r : ranges) live_blocks += r.second;
+    const int ncap = std::max(2 * B->cap, live_blocks + n);
+    void* Unew = dalloc(&view, (size_t)ncap * per);
+    if (!Unew) {
+      delete hm;
+      return bfail(B, AGILE_ENOMEM, "device allocation failed");
+    }
+    int o = 0;
+    for (int i = 0; i < B->nsolve; ++i) {
+      if (!B->live[i]) continue;
+      const int c = solve_blocks(B, i);
+      if (c)
+        BCK(B, cudaMemcpyAsync((char*)Unew + (size_t)o * per, (const char*)B->U[0] + (size_t)B->offset[i] * per,
+                               (size_t)c * per, cudaMemcpyDeviceToDevice, B->stream));
+      B->offset[i] = o;
+      o += c;
+    }
+    dfree(&view, B->U[0]);                   // in stream order, after the copies
+    B->U[0] = Unew;
+    B->cap = ncap;
+    at = o;
+  }
+  int idx = -1;                              // a detached solve's index is reused
+  for (int i = 0; i < B->nsolve && idx < 0; ++i)
+    if (!B->live[i]) idx = i;
+  if (idx < 0) {
+    s = batch_reserve_solves(B, B->nsolve + 1);
+    if (s) {
+      delete hm;
+      return s;
+    }
+    idx = B->nsolve++;
+    B->cfgs.push_back(*cfg);
+    B->meshes.push_back(nullptr);
+    B->offset.push_back(0);
+    B->live.push_back(0);
+    B->ics.push_back(nullptr);
+    B->ic_users.push_back(nullptr);
+  }
+  B->cfgs[idx] = *cfg;
+  B->meshes[idx] = hm;
+  B->offset[idx] = at;
+  B->live[idx] = 1;
+  B->tables.resize(B->nsolve);
+  B->tables[idx].valid = false;
+  B->ics[idx] = nullptr;
+  B->ic_users[idx] = nullptr;
+  BCK(B, cudaMemsetAsync((char*)B->U[0] + (size_t)at * per, 0, (size_t)n * per, B->stream));
+  s = batch_rebuild(B);
+  if (s) return s;
+  *solve = idx;
+  return AGILE_OK;
+}
+
+agile_status agile_batch_detach(agile_batch* B, int solve) {
+  if (!solve_ok(B, solve)) return bfail(B, AGILE_EINVAL, "bad argument");
+  delete B->meshes[solve];
+  B->meshes[solve] = nullptr;
+  B->live[solve] = 0;
+  B->ics[solve] = nullptr;
+  B->ic_users[solve] = nullptr;
+  return batch_rebuild(B);
 }
 
 agile_status agile_batch_sync(agile_batch* B) {

@@ -43,6 +43,7 @@ struct StageArgs {
   double htc_kappa0 = 0.0;      // ffhd with conduction: kappa_par = htc_kappa0 T^(5/2)
   int layout = 0;               // staging layout (STAGE_LAYOUT_*), 0: the default for the physics
   double eta = 0.0;             // resistive mhd: uniform resistivity
+  const int* wl = nullptr;      // work list: pool block of each of the nblk work items (nullptr: identity)
   // FP32 copies of the equation parameters and the combine weights, formed on the host at
   // launch (stage_go), so that the FP32 kernel never forms them from the FP64 fields (the
   // compiler may recompute such values at every use instead of holding them in registers)
@@ -393,16 +394,19 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   const R reta = R(A.eta);
   R dxr[3] = {R(0), R(0), R(0)};
   if (t == 0 && blockIdx.x < A.nblk) {
+    const int b0 = A.wl ? A.wl[blockIdx.x] : (int)blockIdx.x;
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
-      s_src[f] = A.bd[blockIdx.x].src[f];
-      s_slot[f] = A.bd[blockIdx.x].slot[f];
+      s_src[f] = A.bd[b0].src[f];
+      s_slot[f] = A.bd[b0].slot[f];
     }
   }
   __syncthreads();
   const int* src = s_src;
   const int* slot = s_slot;
-  for (int b = blockIdx.x, jb = 0; b < A.nblk; ++jb) {
+  // work item w is pool block b (the work list of a batch skips the blocks of detached solves)
+  for (int w = blockIdx.x, jb = 0; w < A.nblk; ++jb) {
+  const int b = A.wl ? A.wl[w] : w;
   const int sv = A.solve_of ? A.solve_of[b] : 0;
   unsigned long long* speeds = A.speeds ? A.speeds + 2 * sv : nullptr;
   const BlockDesc& bd = A.bd[b];
@@ -853,18 +857,19 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   if (speeds) block_max2<256>(ssum, smax, speeds);
   if (t == 0) {
     // every read of this block's face table happened before the last plane's barrier
-    const int nx = A.work ? (int)gridDim.x + atomicAdd(A.work, 1) : b + (int)gridDim.x;
+    const int nx = A.work ? (int)gridDim.x + atomicAdd(A.work, 1) : w + (int)gridDim.x;
     s_next = nx;
     if (nx < A.nblk) {
+      const int bn = A.wl ? A.wl[nx] : nx;
 #pragma unroll
       for (int f = 0; f < 6; ++f) {
-        s_src[f] = A.bd[nx].src[f];
-        s_slot[f] = A.bd[nx].slot[f];
+        s_src[f] = A.bd[bn].src[f];
+        s_slot[f] = A.bd[bn].slot[f];
       }
     }
   }
   __syncthreads();       // ring, raw slots, flux buffers and reduction scratch are reused next
-  b = s_next;
+  w = s_next;
   }
   if (st) atomicOr(A.status, st);
 }

@@ -35,6 +35,9 @@ struct AuxArgs {
   int* status;
   const int* solve_of = nullptr;   // solve index per block (batched solves), nullptr = one solve
   int nsolve = 1;
+  // work list of the per-block kernels (speeds, GLM decay, estimator): pool block of each of
+  // the nblk work items, nullptr = blocks 0 .. nblk-1
+  const int* wl = nullptr;
 };
 
 // Fill ghost slots of coarse-fine faces from U (restriction / limited prolongation).

@@ -269,107 +269,86 @@ def run_alone(req: Request, real_bytes: int = 4):
 
 
 class BatchedServer:
-    """Requests join a shared batched work list as slots free up.
+    """Requests join a shared batched work list as they are admitted (continuous batching).
 
-    The admitted solves of one physics module run in one `agile.Batch` (one persistent
-    launch per RK stage over all of them, every step after the first replayed from a CUDA
-    graph, each solve with its own on-device CFL dt), and the groups of the three modules
-    run on their own streams so that their launches overlap. When solves finish or new ones
-    are admitted, the group's batch is rebuilt: the survivors' states are copied device to
-    device (agile_batch_copy_solve) and the newcomers' initial conditions are loaded. A
-    rebuild happens at most every `rebuild_every` steps of the group (sooner when the group
-    is empty); a solve that reaches its step count is read out at once, so every result is
-    the state after exactly its requested steps, equal to the same request run alone.
+    The admitted solves of one physics module share one `agile.Batch`: one persistent launch
+    per RK stage over all of them, every step replayed from a CUDA graph, each solve with its
+    own on-device CFL dt; the batches of the three modules run on their own streams so that
+    their launches overlap. An admitted request attaches to its module's batch at once (its
+    initial condition is uploaded as primitives) and detaches as soon as it has taken its
+    steps and its state has been read out. Neither moves the other solves
+    (agile_batch_attach / agile_batch_detach: a solve's blocks occupy a range of the batch's
+    block pool, a departed solve leaves a hole that later arrivals fill, and the stage launches
+    walk a work list of the attached blocks), so a join or a leave costs a rebuild of the
+    descriptor tables and a new graph capture, not copies of the other solves' states. Every
+    result is the state after exactly the requested steps, equal to the request run alone.
     Initial conditions are prepared ahead by worker threads as for Server."""
 
-    def __init__(self, budget_bytes: int, real_bytes: int = 4, rebuild_every: int = 4,
-                 keep_results: bool = False, prepare_workers: int = 8, max_prepared: int = 16):
+    def __init__(self, budget_bytes: int, real_bytes: int = 4, keep_results: bool = False,
+                 prepare_workers: int = 8, max_prepared: int = 16):
         self.budget = int(budget_bytes)
         self.rb = real_bytes
-        self.rebuild_every = max(1, int(rebuild_every))
         self.keep = keep_results
         self.workers = prepare_workers
         self.max_prepared = max_prepared
-        self._prims = {}
-
-    def _rebuild(self, g):
-        """New batch for the group's members: survivors copied, newcomers initialised.
-        Returns the device bytes of the finished solves it drops. Its wall time (creation,
-        device-to-device copies, uploads, release of the old batch) is accumulated with the
-        numbers of joining and leaving solves."""
-        t0 = time.perf_counter()
-        try:
-            return self._rebuild_group(g)
-        finally:
-            self.stats["rebuild_s"] += time.perf_counter() - t0
-            self.stats["rebuilds"] += 1
-
-    def _rebuild_group(self, g):
-        old, old_index = g["batch"], g["index"]
-        self.stats["joins"] += len(g["joining"])
-        self.stats["leaves"] += len(g["done"])
-        self.stats["survivor_copies"] += len([r for r in g["members"] if r.rid not in g["done"]])
-        freed = sum(pool_bytes(r, self.rb) for r in g["members"] if r.rid in g["done"])
-        members = [r for r in g["members"] if r.rid not in g["done"]] + g["joining"]
-        g["joining"] = []
-        g["members"] = members
-        g["done"] = set()
-        g["since"] = 0
-        if not members:
-            g["batch"], g["index"] = None, {}
-        else:
-            nb = agile.Batch([scheme(r.physics, self.rb, r.side) for r in members])
-            index = {}
-            for i, r in enumerate(members):
-                index[r.rid] = i
-                if old is not None and r.rid in old_index:
-                    nb.copy_solve(i, old, old_index[r.rid])
-                else:
-                    nb.set_state_prims(i, self._prims.pop(r.rid))
-            g["batch"], g["index"] = nb, index
-        if old is not None:
-            old.close()
-        return freed
 
     def run(self, requests, time_scale: float = 1.0, max_wall_s: float = 3600.0) -> Report:
-        """Serve `requests`; the budget counts the pools of every solve still held by a batch
-        (a finished solve's pool is released when its batch is rebuilt; during a rebuild the
-        old and the new batch coexist briefly)."""
+        """Serve `requests`; the budget counts the pools of every attached solve."""
         prep = _Preparer(self.workers, self.max_prepared, self.rb)
-        self.stats = {"rebuilds": 0, "rebuild_s": 0.0, "joins": 0, "leaves": 0, "survivor_copies": 0}
+        self.stats = {"joins": 0, "leaves": 0, "join_s": 0.0, "upload_s": 0.0, "leave_s": 0.0}
+        groups = {p: {"batch": None, "members": {}} for p in PHYS}
         try:
-            rep = self._loop(requests, time_scale, max_wall_s, prep)
+            rep = self._loop(requests, time_scale, max_wall_s, prep, groups)
         finally:
             prep.close()
-            self._prims.clear()
+            for g in groups.values():
+                if g["batch"] is not None:
+                    g["batch"].close()
         st = dict(self.stats)
-        st["rebuild_share_of_wall"] = st["rebuild_s"] / rep.wall_s if rep.wall_s > 0 else None
-        st["rebuild_ms_per_join_or_leave"] = (1e3 * st["rebuild_s"] / max(1, st["joins"] + st["leaves"]))
-        rep.extra["rebuild"] = st
+        changes = max(1, st["joins"] + st["leaves"])
+        st["membership_share_of_wall"] = (st["join_s"] + st["leave_s"]) / rep.wall_s if rep.wall_s > 0 else None
+        st["ms_per_join_or_leave"] = 1e3 * (st["join_s"] + st["leave_s"]) / changes
+        st["note"] = ("join_s / leave_s: attach and detach calls (table rebuild, stream synchronisation); "
+                      "upload_s: the initial conditions' upload, which a per-request server pays as well")
+        rep.extra["membership"] = st
         return rep
 
-    def _loop(self, requests, time_scale, max_wall_s, prep):
+    def _join(self, g, r, prims):
+        t0 = time.perf_counter()
+        cfg = scheme(r.physics, self.rb, r.side)
+        if g["batch"] is None:
+            g["batch"] = agile.Batch([cfg])
+            idx = 0
+        else:
+            idx = g["batch"].attach(cfg)
+        t1 = time.perf_counter()
+        g["batch"].set_state_prims(idx, prims)
+        self.stats["upload_s"] += time.perf_counter() - t1
+        self.stats["join_s"] += t1 - t0
+        self.stats["joins"] += 1
+        g["members"][idx] = [r, r.steps]
+
+    def _leave(self, g, idx):
+        t0 = time.perf_counter()
+        g["batch"].detach(idx)
+        del g["members"][idx]
+        self.stats["leave_s"] += time.perf_counter() - t0
+        self.stats["leaves"] += 1
+
+    def _loop(self, requests, time_scale, max_wall_s, prep, groups):
         pending = sorted(requests, key=lambda r: r.arrival)
         waiting = []
-        groups = {p: {"batch": None, "index": {}, "members": [], "joining": [], "done": set(),
-                      "left": {}, "since": 0} for p in PHYS}
         used = max_used = max_conc = 0
         zones = 0.0
         t0 = time.perf_counter()
         k = 0
 
-        def active():
-            return sum(len(g["members"]) - len(g["done"]) + len(g["joining"]) for g in groups.values())
+        def attached():
+            return sum(len(g["members"]) for g in groups.values())
 
-        def held():
-            return sum(len(g["members"]) + len(g["joining"]) for g in groups.values())
-
-        while k < len(pending) or waiting or held():
+        while k < len(pending) or waiting or attached():
             now = time.perf_counter() - t0
             if now > max_wall_s:
-                for g in groups.values():
-                    if g["batch"] is not None:
-                        g["batch"].close()
                 raise TimeoutError("serving loop exceeded %.0f s" % max_wall_s)
             while k < len(pending) and pending[k].arrival * time_scale <= now:
                 waiting.append(pending[k])
@@ -382,48 +361,39 @@ class BatchedServer:
                 if need > self.budget:
                     raise ValueError("request %d needs %d bytes, more than the budget" % (r.rid, need))
                 if used + need <= self.budget and prep.ready(r):
-                    self._prims[r.rid] = prep.take(r)
-                    g = groups[r.physics]
-                    g["joining"].append(r)
-                    g["left"][r.rid] = r.steps
+                    self._join(groups[r.physics], r, prep.take(r))
                     r.admitted = time.perf_counter() - t0
                     used += need
                     max_used = max(max_used, used)
                     waiting.pop(i)
                     continue
                 i += 1
-            max_conc = max(max_conc, active())
+            max_conc = max(max_conc, attached())
             stepped = False
             for g in groups.values():
-                live = len(g["members"]) - len(g["done"])
-                if (g["joining"] or g["done"]) and (live == 0 or g["since"] >= self.rebuild_every):
-                    used -= self._rebuild(g)
-                b = g["batch"]
-                if b is None:
+                if not g["members"]:
                     continue
+                b = g["batch"]
                 b.step()
-                g["since"] += 1
                 stepped = True
-                for r in g["members"]:
-                    if r.rid in g["done"]:
-                        continue
-                    g["left"][r.rid] -= 1
-                    if g["left"][r.rid] == 0:
-                        lev, ijk, cons = b.get_state(g["index"][r.rid])
+                for idx in list(g["members"]):
+                    m = g["members"][idx]
+                    m[1] -= 1
+                    if m[1] == 0:
+                        r = m[0]
+                        lev, ijk, cons = b.get_state(idx)
                         if self.keep:
                             r.result = cons
                         r.finished = time.perf_counter() - t0
                         stages = 2 if r.physics == "srhd" else 3
                         zones += float(r.side ** 3) * stages * r.steps
-                        g["done"].add(r.rid)
+                        self._leave(g, idx)
+                        used -= pool_bytes(r, self.rb)
             if not stepped:
                 if waiting:
                     time.sleep(0.0005)         # preparations in flight
                 elif k < len(pending):
                     time.sleep(max(0.0, pending[k].arrival * time_scale - (time.perf_counter() - t0)))
-        for g in groups.values():
-            if g["batch"] is not None:
-                g["batch"].close()
         wall = time.perf_counter() - t0
         rep = Report(requests=requests, wall_s=wall, zone_updates=zones, max_resident_bytes=max_used,
                      max_concurrent=max_conc)

@@ -1,0 +1,109 @@
+"""Continuous batching: solves attach to and detach from a running batch without moving the
+others. Each solve's result equals the same solve run alone as a mesh, bit for bit, across
+detachments, attachments into a hole, attachments that grow the block pool, and a batch that
+empties and fills again; a solve of another scheme is refused; a detached index is refused
+until it is reused."""
+import numpy as np
+import pytest
+
+from paper_2607_19277_gb300 import agile, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _cfg(side, physics="mhd", rb=4):
+    if physics == "srhd":
+        return agile.make_config(physics="srhd", limiter="minmod", flux="tvdlf", rk=2, gamma=4.0 / 3.0,
+                                 real_bytes=rb, base_blocks=(side // 16,) * 3)
+    return agile.make_config(physics="mhd", limiter="vanleer", flux="hll", rk=3, real_bytes=rb,
+                             base_blocks=(side // 16,) * 3)
+
+
+def _ic(physics, seed, side):
+    if physics == "srhd":
+        return W.srhd_shells(seed, side, n_shells=1, lorentz_max=3.0, p_amb=1.0, smooth=True, width=2.0,
+                             wrap=True)
+    return W.random_smooth(9, seed, "mhd")
+
+
+class Alone:
+    """The same request as its own mesh, stepped with the device dt."""
+
+    def __init__(self, side, physics, rb, seed):
+        self.m = agile.Mesh(_cfg(side, physics, rb))
+        self.m.set_state(_ic(physics, seed, side))
+
+    def step(self, n):
+        for _ in range(n):
+            self.m.step(0.0)
+
+    def state(self):
+        s = self.m.get_state()[2]
+        self.m.close()
+        return s
+
+
+@pytest.mark.parametrize("physics,rb", [("mhd", 4), ("srhd", 4), ("mhd", 8)])
+def test_attach_detach_keeps_every_solve_equal_to_alone(physics, rb):
+    sides = [32, 48, 32]
+    b = agile.Batch([_cfg(s, physics, rb) for s in sides])
+    ref = {}
+    for i, s in enumerate(sides):
+        b.set_state(i, _ic(physics, 300 + i, s))
+        ref[i] = Alone(s, physics, rb, 300 + i)
+    for _ in range(2):
+        b.step()
+    for r in ref.values():
+        r.step(2)
+    # solve 1 (48^3) leaves: its 27 blocks become a hole
+    r1 = ref.pop(1)
+    _, _, s1 = b.get_state(1)
+    assert np.array_equal(s1, r1.state())
+    b.detach(1)
+    with pytest.raises(agile.AgileError):
+        b.get_state(1)
+    # a 32^3 solve fills part of the hole (index 1 reused); a 64^3 one does not fit and grows
+    # the pool
+    j = b.attach(_cfg(32, physics, rb))
+    assert j == 1
+    b.set_state_prims(j, agile.prims_of(_ic(physics, 310, 32), _cfg(32, physics, rb)))
+    ref[j] = Alone(32, physics, rb, 310)
+    k = b.attach(_cfg(64, physics, rb))
+    assert k == 3
+    b.set_state(k, _ic(physics, 311, 64))
+    ref[k] = Alone(64, physics, rb, 311)
+    for _ in range(3):
+        b.step()
+    for r in ref.values():
+        r.step(3)
+    for i, r in ref.items():
+        _, _, g = b.get_state(i)
+        assert np.array_equal(g, r.state()), i
+    b.close()
+
+
+def test_batch_empties_and_fills_again():
+    b = agile.Batch([_cfg(32)])
+    b.set_state(0, _ic("mhd", 320, 32))
+    b.step()
+    b.detach(0)
+    b.step()                       # nothing attached: a step does nothing
+    i = b.attach(_cfg(48))
+    assert i == 0
+    b.set_state(i, _ic("mhd", 321, 48))
+    a = Alone(48, "mhd", 4, 321)
+    for _ in range(2):
+        b.step()
+    a.step(2)
+    assert np.array_equal(b.get_state(i)[2], a.state())
+    b.close()
+
+
+def test_attach_refuses_another_scheme():
+    b = agile.Batch([_cfg(32)])
+    with pytest.raises(agile.AgileError) as ei:
+        b.attach(_cfg(32, "srhd"))
+    assert ei.value.status == 1
+    with pytest.raises(agile.AgileError):
+        b.detach(5)
+    b.close()

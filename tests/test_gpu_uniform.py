@@ -71,6 +71,24 @@ def test_mhd_tvdlf_minmod_fp64():
 
 
 @pytest.mark.parametrize("rb,tol", [(8, TOL_FP64), (4, 2e-5)])
+def test_srhd_shell_at_lorentz_factor_near_ten(rb, tol):
+    """One periodic shell of the batched workload's family with Lorentz factor 9.5 on 48^3:
+    the FP64 Newton recovery at the top of the configured range, both stencils against the
+    oracle, and the largest Lorentz factor of the state."""
+    spec = dict(physics="srhd", limiter="minmod", flux="tvdlf", rk=2, gamma=4.0 / 3.0,
+                base_blocks=(3, 3, 3))
+    ic = W.srhd_shells(W.SEED_BASE + 71, 48, n_shells=1, lorentz_min=9.5, lorentz_max=9.5, p_amb=1.0,
+                       smooth=True, width=2.0, wrap=True, radius=(0.2, 0.35))
+    m, o, g, r, lev, _ = run_both(spec, ic, 3, real_bytes=rb)
+    assert rel_l1(g, r).max() < tol
+    aux = m.get_aux()
+    assert aux[:, 1].max() > 8.0          # Lorentz factors near the initial 9.5 remain
+    if rb == 8:
+        assert np.max(np.abs(aux - o.get_aux()) / np.abs(o.get_aux())) < 1e-12
+    m.close()
+
+
+@pytest.mark.parametrize("rb,tol", [(8, TOL_FP64), (4, 2e-5)])
 def test_srhd_shells(rb, tol):
     """SRHD with seeded shells (Lorentz factors up to 5), LF flux, minmod, SSPRK2; the
     primitive recovery runs in FP64 in both precisions."""

@@ -112,45 +112,58 @@ def test_server_loop_terminates_without_gpu_work(monkeypatch):
 
 @pytest.mark.gpu
 def test_batched_serving_matches_alone():
-    """Requests join per-physics batches as slots free up (rebuilds copy the survivors on the
-    device); every result equals the request run alone, bit for bit."""
+    """Requests attach to per-physics batches as they are admitted and detach when done (the
+    other solves stay in place); every result equals the request run alone, bit for bit."""
     reqs = [serving.Request(rid=i, physics=("hd", "mhd", "srhd")[i % 3], side=(32, 48)[i % 2],
                             steps=3 + (i % 5), seed=700 + i, arrival=0.001 * i) for i in range(9)]
     sizes = sorted(serving.pool_bytes(r, 4) for r in reqs)
     budget = sum(sizes[-4:])                         # room for about four at once
-    srv = serving.BatchedServer(budget, real_bytes=4, rebuild_every=2, keep_results=True)
+    srv = serving.BatchedServer(budget, real_bytes=4, keep_results=True)
     rep = srv.run(reqs, max_wall_s=120.0)
     assert rep.max_resident_bytes <= budget
     assert rep.max_concurrent >= 2
+    st = rep.summary()["membership"]
+    assert st["joins"] == 9 and st["leaves"] == 9
     for r in reqs:
         assert r.finished > 0 and r.admitted >= r.arrival - 1e-9
         assert np.array_equal(r.result, serving.run_alone(r, real_bytes=4)), r.rid
 
 
 def test_batched_server_reads_each_solve_at_its_step_count(monkeypatch):
-    """Host logic of the batched loop with a fake batch that counts steps per solve: every
-    request is read out after exactly its requested steps, across rebuilds that copy the
-    survivors, and the budget is respected."""
+    """Host logic of the batched loop with a fake batch that counts steps per attached solve
+    and reuses detached indices like the library: every request is read out after exactly
+    its requested steps, the budget is respected, every join has its leave and every batch
+    is closed."""
     class FakeBatch:
         live = []
 
         def __init__(self, cfgs, stream=None):
             self.n = [0] * len(cfgs)
+            self.on = [True] * len(cfgs)
             FakeBatch.live.append(self)
 
-        def copy_solve(self, i, src, j):
-            self.n[i] = src.n[j]
+        def attach(self, cfg):
+            for i, on in enumerate(self.on):
+                if not on:
+                    self.on[i], self.n[i] = True, 0
+                    return i
+            self.on.append(True)
+            self.n.append(0)
+            return len(self.n) - 1
 
-        def set_state(self, i, ic):
-            self.n[i] = 0
+        def detach(self, i):
+            assert self.on[i]
+            self.on[i] = False
 
         def set_state_prims(self, i, prim):
+            assert self.on[i]
             self.n[i] = 0
 
         def step(self):
-            self.n = [v + 1 for v in self.n]
+            self.n = [v + 1 if on else v for v, on in zip(self.n, self.on)]
 
         def get_state(self, i):
+            assert self.on[i]
             return None, None, np.array([self.n[i]])
 
         def close(self):
@@ -161,10 +174,12 @@ def test_batched_server_reads_each_solve_at_its_step_count(monkeypatch):
     monkeypatch.setattr(serving, "prepare", lambda r, rb: np.zeros(1))
     reqs = serving.request_stream(30, rate=3000.0, sides=(32, 64), steps=(2, 9))
     budget = 4 * max(serving.pool_bytes(r, 4) for r in reqs)
-    srv = serving.BatchedServer(budget, real_bytes=4, rebuild_every=3, keep_results=True)
+    srv = serving.BatchedServer(budget, real_bytes=4, keep_results=True)
     rep = srv.run(reqs, max_wall_s=30.0)
     assert all(r.finished >= 0 and int(r.result[0]) == r.steps for r in reqs)
     assert rep.max_resident_bytes <= budget
+    st = rep.summary()["membership"]
+    assert st["joins"] == 30 and st["leaves"] == 30
     assert not FakeBatch.live                          # every batch closed
 
 
