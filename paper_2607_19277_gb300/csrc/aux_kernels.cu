@@ -250,9 +250,51 @@ __global__ void __launch_bounds__(256) glm_decay_kernel(R* __restrict__ U, const
 }
 
 // ------------------------------------------------------------------------------ estimator
+// One variable of cell (x, y, z) in the halo view of block b (the rules of load_cell: a
+// same-level neighbour's interior, a physical boundary image with the normal vector
+// components negated at a reflecting wall, or a ghost slot).
+template <class P, typename R>
+__device__ __forceinline__ R load_var(const R* __restrict__ U, const R* __restrict__ G, const int* src, int b,
+                                      int x, int y, int z, int iv) {
+  constexpr int NT = P::NV + P::NA;
+  int f = -1;
+  if (x < 0) f = 0;
+  else if (x > NB - 1) f = 1;
+  else if (y < 0) f = 2;
+  else if (y > NB - 1) f = 3;
+  else if (z < 0) f = 4;
+  else if (z > NB - 1) f = 5;
+  int q[3] = {x, y, z};
+  int blk = b;
+  bool neg = false;
+  if (f >= 0) {
+    const int d = f >> 1, s = f & 1;
+    const int sv = src[f];
+    if (sv >= 0) {
+      q[d] &= NB - 1;
+      blk = sv;
+    } else if (sv == SRC_OUTFLOW) {
+      q[d] = s ? NB - 1 : 0;
+    } else if (sv == SRC_REFLECT) {
+      q[d] = s ? 2 * NB - 1 - q[d] : -1 - q[d];
+      neg = (P::IV >= 0 && iv == P::IV + d) || (P::BOFF >= 0 && iv == P::BOFF + d);
+    } else {
+      const int slot = SRC_SLOT0 - sv;
+      const int layer = s ? q[d] - NB : q[d] + 2;
+      const int t1 = d == 0 ? q[1] : q[0];
+      const int t2 = d == 2 ? q[1] : q[2];
+      return G[((size_t)slot * NT + iv) * 512 + layer * 256 + t2 * 16 + t1];
+    }
+  }
+  const R v = U[((size_t)blk * NT + iv) * NCELL + q[2] * 256 + q[1] * 16 + q[0]];
+  return neg ? -v : v;
+}
+
 // Loehner (1987) second-derivative estimate per cell and variable (axis terms only):
 // E_u = sqrt(sum_d (u+ - 2u0 + u-)^2 / sum_d (|u+ - u0| + |u0 - u-| + eps (|u+| + 2|u0| + |u-|))^2),
-// E = sum_u w_u E_u; every operation rounded on its own (no FMA) in this order.
+// E = sum_u w_u E_u; every operation rounded on its own (no FMA) in this order. Per refinement
+// variable the CTA stages the block's interior (coalesced) and its six face layers in shared
+// memory; each thread keeps the running sums of its 16 cells in registers.
 template <template <typename> class PT, typename R>
 __global__ void __launch_bounds__(256) estimate_kernel(const R* __restrict__ U, const R* __restrict__ G,
                                                         const BlockDesc* __restrict__ bd,
@@ -263,54 +305,71 @@ __global__ void __launch_bounds__(256) estimate_kernel(const R* __restrict__ U, 
   using P = PT<R>;
   constexpr int NT = P::NV + P::NA;
   const int b = wl ? wl[blockIdx.x] : (int)blockIdx.x;
-  int src[6];
+  const int t = threadIdx.x;
+  __shared__ int src[6];
+  __shared__ R sI[NCELL];          // interior of the staged variable
+  __shared__ R sF[6][256];         // its face layers: face f, cell (t1 + 16 t2) as in the ghost slots
+  if (t < 6) src[t] = bd[b].src[t];
+  double etot[16];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) src[i] = bd[b].src[i];
-  double best = 0.0;
-  for (int c = threadIdx.x; c < NCELL; c += 256) {
-    const int x = c & 15, y = (c >> 4) & 15, z = c >> 8;
-    R u0[NT], up[3][NT], um[3][NT];
-    load_cell<P, R>(U, G, src, b, x, y, z, u0);
-    for (int d = 0; d < 3; ++d) {
-      int p[3] = {x, y, z}, m[3] = {x, y, z};
-      p[d] += 1;
-      m[d] -= 1;
-      load_cell<P, R>(U, G, src, b, p[0], p[1], p[2], up[d]);
-      load_cell<P, R>(U, G, src, b, m[0], m[1], m[2], um[d]);
+  for (int j = 0; j < 16; ++j) etot[j] = 0.0;
+  for (int i = 0; i < nvars; ++i) {
+    const int iv = vars[i];
+    const double w = weights[i];
+    __syncthreads();               // src is set; the previous variable's reads are done
+    const R* base = U + ((size_t)b * NT + iv) * NCELL;
+#pragma unroll 4
+    for (int c = t; c < NCELL; c += 256) sI[c] = base[c];
+    for (int e = t; e < 6 * 256; e += 256) {
+      const int f = e >> 8, d = f >> 1, s = f & 1, t1 = e & 15, t2 = (e >> 4) & 15;
+      int q[3];
+      q[d] = s ? NB : -1;
+      q[d == 0 ? 1 : 0] = t1;
+      q[d == 2 ? 1 : 2] = t2;
+      sF[f][t2 * 16 + t1] = load_var<P, R>(U, G, src, b, q[0], q[1], q[2], iv);
     }
-    double etot = 0.0;
-    for (int i = 0; i < nvars; ++i) {
-      const int iv = vars[i];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int c = t + 256 * j;
+      const int x = c & 15, y = (c >> 4) & 15, z = c >> 8;
+      const int pos[3] = {x, y, z};
+      const double o = (double)sI[c];
       double num = 0.0, den = 0.0;
+#pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const double a = (double)up[d][iv], o = (double)u0[iv], m = (double)um[d][iv];
-        const double t = __dadd_rn(__dsub_rn(a, __dmul_rn(2.0, o)), m);
+        const int st = d == 0 ? 1 : (d == 1 ? 16 : 256);
+        const int t1 = d == 0 ? y : x, t2 = d == 2 ? y : z;
+        const double a = (double)(pos[d] < NB - 1 ? sI[c + st] : sF[2 * d + 1][t2 * 16 + t1]);
+        const double m = (double)(pos[d] > 0 ? sI[c - st] : sF[2 * d][t2 * 16 + t1]);
+        const double tt = __dadd_rn(__dsub_rn(a, __dmul_rn(2.0, o)), m);
         const double q = __dadd_rn(__dadd_rn(fabs(__dsub_rn(a, o)), fabs(__dsub_rn(o, m))),
                                    __dmul_rn(eps, __dadd_rn(__dadd_rn(fabs(a), __dmul_rn(2.0, fabs(o))),
                                                             fabs(m))));
-        const double t2 = __dmul_rn(t, t), q2 = __dmul_rn(q, q);
-        num = d == 0 ? t2 : __dadd_rn(num, t2);
+        const double t2q = __dmul_rn(tt, tt), q2 = __dmul_rn(q, q);
+        num = d == 0 ? t2q : __dadd_rn(num, t2q);
         den = d == 0 ? q2 : __dadd_rn(den, q2);
       }
       const double e = den > 0.0 ? __dsqrt_rn(__ddiv_rn(num, den)) : 0.0;
-      const double we = __dmul_rn(weights[i], e);
-      etot = i == 0 ? we : __dadd_rn(etot, we);
+      const double we = __dmul_rn(w, e);
+      etot[j] = i == 0 ? we : __dadd_rn(etot[j], we);
     }
-    best = fmax(best, etot);
   }
+  double best = 0.0;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) best = fmax(best, etot[j]);
   __shared__ double red[8];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  if ((t & 31) == 0) red[t >> 5] = best;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (t == 0) {
     double m = red[0];
     for (int i = 1; i < 8; ++i) m = fmax(m, red[i]);
     emax[b] = m;
   }
 }
 
-// ------------------------------------------------------------------------------ regrid
 template <template <typename> class PT, typename R>
 __global__ void __launch_bounds__(256) regrid_kernel(const R* __restrict__ Uold, const R* __restrict__ Gold,
                                                       const BlockDesc* __restrict__ bdold,

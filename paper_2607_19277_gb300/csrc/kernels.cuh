@@ -710,32 +710,43 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
         }
         plm2<NV, LIM>(a, bq, c, d, pl, pr);
         riemann2<P, FLUX>(pl, pr, fp, PairK(pp));
-        R fy[NV];
+        // the flux buffers hold F / dx (the divergence then needs differences only); the
+        // flux registers of the coarse-fine correction take the fluxes themselves
+        const f2 kxy = f2_of(idx, idy);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          f2_split(fp[v], f[v], fy[v]);
-          sFx[v * 272 + fr * 16 + fc] = f[v];
-          sFy[swapv<P>(v) * 272 + fr * 16 + fc] = fy[v];
+          R sx, sy;
+          f2_split(fp[v] * kxy, sx, sy);
+          sFx[v * 272 + fr * 16 + fc] = sx;
+          sFy[swapv<P>(v) * 272 + fr * 16 + fc] = sy;
         }
         if (FR && fc == 0 && slot[0] >= 0) {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) FR[((size_t)slot[0] * NV + v) * 256 + k * 16 + fr] = f[v];
+          for (int v = 0; v < NV; ++v) {
+            R fx_, fy_;
+            f2_split(fp[v], fx_, fy_);
+            FR[((size_t)slot[0] * NV + v) * 256 + k * 16 + fr] = fx_;
+          }
         }
         if (FR && fr == 0 && slot[2] >= 0) {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) FR[((size_t)slot[2] * NV + swapv<P>(v)) * 256 + k * 16 + fc] = fy[v];
+          for (int v = 0; v < NV; ++v) {
+            R fx_, fy_;
+            f2_split(fp[v], fx_, fy_);
+            FR[((size_t)slot[2] * NV + swapv<P>(v)) * 256 + k * 16 + fc] = fy_;
+          }
         }
       } else {
         xface(Ck, fc, fr, f);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) sFx[v * 272 + fr * 16 + fc] = f[v];
+        for (int v = 0; v < NV; ++v) sFx[v * 272 + fr * 16 + fc] = f[v] * idx;
         if (FR && fc == 0 && slot[0] >= 0) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) FR[((size_t)slot[0] * NV + v) * 256 + k * 16 + fr] = f[v];
         }
         yface(Ck, fr, fc, f);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) sFy[v * 272 + fr * 16 + fc] = f[v];
+        for (int v = 0; v < NV; ++v) sFy[v * 272 + fr * 16 + fc] = f[v] * idy;
         if (FR && fr == 0 && slot[2] >= 0) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) FR[((size_t)slot[2] * NV + v) * 256 + k * 16 + fc] = f[v];
@@ -763,8 +774,9 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
         swap_xy<P, R>(f, yd);
         const int fs = yd ? 1 : 0;
         R* dstp = yd ? sFy + 16 * 16 + r : sFx + 256 + r;
+        const R ids = yd ? idy : idx;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) dstp[v * 272] = f[v];
+        for (int v = 0; v < NV; ++v) dstp[v * 272] = f[v] * ids;
         const int sl = slot[1 + 2 * fs];
         if (FR && sl >= 0) {
 #pragma unroll
@@ -793,8 +805,8 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
         R L[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const R lx = (sFx[v * 272 + fxr] - sFx[v * 272 + cell2]) * idx;
-          const R ly = (sFy[v * 272 + (ty + 1) * 16 + tx] - sFy[v * 272 + ty * 16 + tx]) * idy;
+          const R lx = sFx[v * 272 + fxr] - sFx[v * 272 + cell2];
+          const R ly = sFy[v * 272 + (ty + 1) * 16 + tx] - sFy[v * 272 + ty * 16 + tx];
           const R lz = (fzu[v] - fzd[v]) * idz;
           L[v] = -((lx + ly) + lz);
           fzd[v] = fzu[v];
@@ -817,8 +829,8 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       } else {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const R lx = (sFx[v * 272 + fxr] - sFx[v * 272 + cell2]) * idx;
-          const R ly = (sFy[v * 272 + (ty + 1) * 16 + tx] - sFy[v * 272 + ty * 16 + tx]) * idy;
+          const R lx = sFx[v * 272 + fxr] - sFx[v * 272 + cell2];
+          const R ly = sFy[v * 272 + (ty + 1) * 16 + tx] - sFy[v * 272 + ty * 16 + tx];
           const R lz = (fzu[v] - fzd[v]) * idz;
           R L = -((lx + ly) + lz);
           if constexpr (RESP) {
