@@ -161,7 +161,9 @@ agile_status agile_set_state(agile_mesh* mesh, agile_ic_fn ic, void* user);
 
 /* Set the conserved interiors of all leaves: cons[nblk][nvar][16^3] in block order.
  * nblk must equal the current number of leaves. SRHD auxiliaries are cleared (the next
- * primitive recovery starts from the bracket midpoint). */
+ * primitive recovery starts from the bracket midpoint). Resuming a run from its
+ * agile_get_state output therefore continues it bit for bit for hd, mhd and ffhd, and for
+ * srhd within the recovery's tolerance (the converged xi agree to about 1e-14 in FP64). */
 agile_status agile_set_state_blocks(agile_mesh* mesh, const double* cons, size_t nblk);
 
 /* Initial state from primitive values on the host (Fig. 1, the values an agile_ic_fn
