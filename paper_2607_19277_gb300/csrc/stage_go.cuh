@@ -4,12 +4,15 @@
 
 namespace agile {
 
-// CTAs per SM a staging layout allows: FP64 targets one (its register budget); FP32 three when
-// three CTAs' shared memory fits an SM (233472 bytes, 1 KB reserved per CTA), else two.
+// CTAs per SM a staging layout allows, by the shared memory of an SM (233472 bytes, 1 KB
+// reserved per CTA) and the register budget it implies: FP32 three when three CTAs fit, else
+// two; FP64 two when two CTAs fit (hydrodynamics, whose FP64 kernel fits 128 registers), else
+// one (its full register budget).
 template <template <typename> class PT, typename R, int RAW, int SFB>
 constexpr int stage_minb() {
   constexpr size_t SMEM = stage_smem_bytes<PT, R, RAW, SFB>();
-  return sizeof(R) == 8 ? 1 : (3 * (SMEM + 1024) <= 233472 ? 3 : (2 * (SMEM + 1024) <= 233472 ? 2 : 1));
+  if (sizeof(R) == 8) return 2 * (SMEM + 1024) <= 233472 ? 2 : 1;
+  return 3 * (SMEM + 1024) <= 233472 ? 3 : (2 * (SMEM + 1024) <= 233472 ? 2 : 1);
 }
 
 template <template <typename> class PT, typename R, int LIM, int FLUX, int RAW, int SFB>
