@@ -356,10 +356,10 @@ def run_batched(steps, warmup, nsolve=256, fp64_solves=8):
            "dtype": "f32 stencil, f64 con2prim", "graph_launches_per_step": "1 graph (set_dt + 2 stages)",
            "kernel_launches_in_timed_region": launches,
            "autotune": {"grid": tuned[0], "dynamic_blocks": tuned[1],
-                        "staging_layout": {1: "4 raw slots, 1 flux buffer", 2: "5 raw slots, 2 flux buffers"}
-                        [tuned[3]],
+                        "staging_layout": {1: "4 raw slots, 1 flux buffer", 2: "5 raw slots, 2 flux buffers",
+                                           3: "3 raw slots, 2 flux buffers, stage input from L2"}[tuned[3]],
                         "stage1_ms": {"%s,%d/SM,%s" % (lay, g, a): tuned[2][6 * li + 2 * (g - 1) + ai]
-                                      for li, lay in enumerate(("ring4", "ring5db"))
+                                      for li, lay in enumerate(("ring4", "ring5db", "ring3db"))
                                       for g in (1, 2, 3) for ai, a in enumerate(("counter", "strided"))}}}
     # plain FP64 per-solve path: each solve its own mesh, solved one after the other
     z64 = 0

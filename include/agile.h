@@ -358,19 +358,22 @@ agile_status agile_batch_regrid_flags(agile_batch* batch, int solve, const int* 
 
 /* Autotuner of the batched stage launches (no counterpart in the paper): times `trials`
  * launches of the first RK stage (which reads the solution and writes only a stage buffer,
- * so the solution is not modified) for twelve launch shapes and keeps the fastest for every
- * later step (the CUDA graph of a step is captured again). A shape is a staging layout of
- * the stage kernel's shared memory (1: four raw-plane TMA slots and one face-flux buffer,
+ * so the solution is not modified) for eighteen launch shapes and keeps the fastest for
+ * every later step (the CUDA graph of a step is captured again). A shape is a staging layout
+ * of the stage kernel's shared memory (1: four raw-plane TMA slots and one face-flux buffer,
  * two CTA barriers per plane; 2: five raw slots and two flux buffers, one barrier per plane,
- * more shared memory per CTA; FP64 stencils time layout 1 only), a persistent grid of 1, 2
- * or 3 CTAs per SM, and blocks taken from an atomic counter or strided by the grid.
+ * more shared memory per CTA; 3: three raw slots and two flux buffers, one barrier per
+ * plane, the update reading its stage input from global memory; FP64 stencils time layout 1
+ * only), a persistent grid of 1, 2 or 3 CTAs per SM, and blocks taken from an atomic counter
+ * or strided by the grid.
  * Results do not depend on the choice: every block's arithmetic is the same.
  *  trials   1..100 timed launches per shape (after one untimed launch)
  *  grid     out: CTAs of the chosen shape; dynamic: out, 1 for the atomic counter;
- *  layout   out: the chosen staging layout (1 or 2); each may be NULL
- *  ms       out (may be NULL, else 12 floats): mean ms per launch of the shapes in the
+ *  layout   out: the chosen staging layout (1, 2 or 3); each may be NULL
+ *  ms       out (may be NULL, else 18 floats): mean ms per launch of the shapes in the
  *           order layout 1: (1 CTA/SM, counter), (1, strided), (2, counter), (2, strided),
- *           (3, counter), (3, strided), then the same six for layout 2 (-1 where not timed)
+ *           (3, counter), (3, strided), then the same six for layouts 2 and 3 (-1 where not
+ *           timed)
  * Synchronises the batch's stream. */
 agile_status agile_batch_autotune(agile_batch* batch, int trials, int* grid, int* dynamic, int* layout,
                                   float* ms);

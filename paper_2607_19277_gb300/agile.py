@@ -537,7 +537,7 @@ class Batch:
     def autotune(self, trials=3):
         """Pick the fastest stage-launch shape; returns (grid, dynamic, ms per shape, layout)."""
         g, d, lay = C.c_int(), C.c_int(), C.c_int()
-        ms = (C.c_float * 12)()     # the library writes twelve values
+        ms = (C.c_float * 18)()     # the library writes eighteen values
         self._ck(self.lib.agile_batch_autotune(self.ptr, int(trials), C.byref(g), C.byref(d),
                                                C.byref(lay), ms))
         return g.value, bool(d.value), list(ms), lay.value

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -1073,6 +1074,7 @@ struct agile_batch {
   int scap = 0;                     // solves the per-solve device arrays hold
   int* d_wl = nullptr;
   int nwork = 0;
+  int tab_cap = 0;                  // blocks d_bd, d_solve_of and d_wl hold (the capacity)
 };
 
 namespace {
@@ -1257,20 +1259,24 @@ agile_status batch_rebuild(agile_batch* B) {
   B->nblk = extent;
   B->nwork = (int)work.size();
   view.nblk = extent;
-  if (extent) {
-    B->d_bd = (BlockDesc*)dalloc(&view, desc.size() * sizeof(BlockDesc));
-    B->d_solve_of = (int*)dalloc(&view, solve_of.size() * sizeof(int));
+  // the block tables are sized for the whole capacity, so that an attachment into free pool
+  // blocks can write its own range of them (batch_patch)
+  B->tab_cap = 0;
+  if (B->cap) {
+    B->d_bd = (BlockDesc*)dalloc(&view, (size_t)B->cap * sizeof(BlockDesc));
+    B->d_solve_of = (int*)dalloc(&view, (size_t)B->cap * sizeof(int));
+    B->d_wl = (int*)dalloc(&view, (size_t)B->cap * sizeof(int));
   }
-  if (!work.empty()) B->d_wl = (int*)dalloc(&view, work.size() * sizeof(int));
   if (!ghosts.empty()) B->d_ghosts = (GhostTask*)dalloc(&view, ghosts.size() * sizeof(GhostTask));
   if (!fix.empty()) B->d_fix = (FixupTask*)dalloc(&view, fix.size() * sizeof(FixupTask));
   if (slots) {
     B->G = dalloc(&view, (size_t)slots * B->nt * 512 * B->rb);
     B->FR = dalloc(&view, (size_t)slots * B->nv * 256 * B->rb);
   }
-  if ((extent && (!B->d_bd || !B->d_solve_of)) || (!work.empty() && !B->d_wl) || (!ghosts.empty() && !B->d_ghosts) ||
+  if ((B->cap && (!B->d_bd || !B->d_solve_of || !B->d_wl)) || (!ghosts.empty() && !B->d_ghosts) ||
       (!fix.empty() && !B->d_fix) || (slots && (!B->G || !B->FR)))
     return bfail(B, AGILE_ENOMEM, "device allocation failed");
+  B->tab_cap = B->cap;
   if (extent) {
     BCK(B, cudaMemcpyAsync(B->d_bd, desc.data(), desc.size() * sizeof(BlockDesc), cudaMemcpyHostToDevice, B->stream));
     BCK(B, cudaMemcpyAsync(B->d_solve_of, solve_of.data(), solve_of.size() * sizeof(int), cudaMemcpyHostToDevice,
@@ -1286,7 +1292,7 @@ agile_status batch_rebuild(agile_batch* B) {
   B->nghost = (int)ghosts.size();
   B->nfix = (int)fix.size();
   B->nslots = slots;
-  view.nblk = std::max(extent, 1);
+  view.nblk = std::max(B->cap, 1);      // the tensor maps span the pool's capacity
   for (int i = 0; i < 3; ++i) {
     if (B->U[i] && make_tmap(&view, B->U[i], &B->tmap[i]) != AGILE_OK) return bfail(B, AGILE_ECUDA, "tensor map");
   }
@@ -1627,11 +1633,12 @@ agile_status agile_batch_autotune(agile_batch* B, int trials, int* grid, int* dy
   BCK(B, cudaEventCreate(&e1));
   float best = 0.0f;
   int bi = -1;
-  // shape c: staging layout c / 6 (four raw slots and one flux buffer, or five raw slots and
-  // two flux buffers), grid (c % 6) >> 1, counter or strided assignment c & 1
-  const int layouts[2] = {STAGE_LAYOUT_RING4, STAGE_LAYOUT_RING5_DB};
+  // shape c: staging layout c / 6 (four raw slots and one flux buffer; five raw slots and two
+  // flux buffers; three raw slots and two flux buffers with the stage input read from global
+  // memory), grid (c % 6) >> 1, counter or strided assignment c & 1
+  const int layouts[3] = {STAGE_LAYOUT_RING4, STAGE_LAYOUT_RING5_DB, STAGE_LAYOUT_RING3_DB};
   const bool fp64 = B->rb == 8;                       // FP64 stencils have the first layout only
-  for (int c = 0; c < 12 && !s; ++c) {
+  for (int c = 0; c < 18 && !s; ++c) {
     const int g = grids[(c % 6) >> 1];
     const bool dyn = (c & 1) == 0;
     const int lay = layouts[c / 6];
@@ -1944,12 +1951,98 @@ agile_status agile_batch_copy_solve(agile_batch* dst, int dst_solve, agile_batch
   return batch_status(dst);
 }
 
+// A membership change of one solve that has no coarse-fine faces (no ghost slots, ghost tasks
+// or flux-register fix-ups), with the pool and its block tables at capacity: only the solve's
+// own range of the block tables and the work list change. The other solves' descriptors stay
+// where they are on the device (their slot offsets do not move, the solve contributing none),
+// so the cost is that of the one solve plus the work list, not of the whole batch. Returns
+// false (nothing changed) where these conditions do not hold; the caller then rebuilds.
+bool batch_patch(agile_batch* B, int solve, bool attach, agile_status* st) {
+  *st = AGILE_OK;
+  if (B->tab_cap != B->cap || B->cap_stage != B->cap || !B->d_bd || !B->d_solve_of || !B->d_wl) return false;
+  if (solve < 0 || solve >= (int)B->tables.size()) return false;
+  agile_batch::Tables& T = B->tables[solve];
+  if (attach && !T.valid) {
+    std::string err;
+    T.desc.clear();
+    T.ghosts.clear();
+    T.fix.clear();
+    B->meshes[solve]->build_descs(&T.desc, &T.ghosts, &T.fix, &T.nslots, &err);
+    if (!err.empty()) return false;
+    T.valid = true;
+  }
+  if (!T.valid || !T.ghosts.empty() || !T.fix.empty() || T.nslots) return false;
+  const int O = B->offset[solve], n = (int)T.desc.size();
+  if (O < 0 || O + n > B->cap) return false;
+  std::vector<BlockDesc> d(T.desc);
+  for (BlockDesc& bd : d) {
+    for (int f = 0; f < 6; ++f) {
+      if (bd.src[f] <= SRC_SLOT0 || bd.slot[f] >= 0) return false;   // a slot after all
+      if (bd.src[f] >= 0) {
+        if (bd.src[f] >= n) return false;
+        bd.src[f] += O;
+      }
+      for (int k = 0; k < 4; ++k) {
+        if (bd.nbr[f][k] >= n) return false;
+        if (bd.nbr[f][k] >= 0) bd.nbr[f][k] += O;
+      }
+    }
+  }
+  if (!attach) {                    // the range becomes a hole: inert descriptors
+    BlockDesc inert{};
+    for (int f = 0; f < 6; ++f) {
+      inert.src[f] = SRC_OUTFLOW;
+      inert.slot[f] = -1;
+      inert.kind[f] = FK_BC;
+      for (int q = 0; q < 4; ++q) inert.nbr[f][q] = -1;
+    }
+    inert.dx[0] = inert.dx[1] = inert.dx[2] = 1.0;
+    inert.level = 1;
+    std::fill(d.begin(), d.end(), inert);
+  }
+  std::vector<int> so(n, attach ? solve : 0), work;
+  work.reserve(B->nwork + (attach ? n : 0));
+  int extent = 0;
+  for (int i = 0; i < B->nsolve; ++i) {      // the work list: live solves in index order
+    if (!B->live[i] || (!attach && i == solve)) continue;
+    const int c = solve_blocks(B, i);
+    for (int q = 0; q < c; ++q) work.push_back(B->offset[i] + q);
+    extent = std::max(extent, B->offset[i] + c);
+  }
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    if (!bytes || *st) return;
+    const cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, B->stream);
+    if (e != cudaSuccess) *st = bfail(B, AGILE_ECUDA, std::string("table upload: ") + cudaGetErrorString(e));
+  };
+  up(B->d_bd + O, d.data(), d.size() * sizeof(BlockDesc));
+  up(B->d_solve_of + O, so.data(), so.size() * sizeof(int));
+  up(B->d_wl, work.data(), work.size() * sizeof(int));
+  if (*st) return true;
+  B->nwork = (int)work.size();
+  B->nblk = std::max(B->nblk, extent);       // per-block scratch covers every pool block in use
+  if (!attach) T = agile_batch::Tables();
+  if (B->graph) {                            // the captured step refers to the old work list
+    cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+  }
+  B->steps_done = 0;
+  B->speeds_valid = false;
+  return true;
+}
+
 agile_status agile_batch_attach(agile_batch* B, const agile_config* cfg, int* solve) {
   if (!B || !cfg || !solve) return bfail(B, AGILE_EINVAL, "null argument");
   if (!batch_cfg_ok(B->cfg, *cfg)) return bfail(B, AGILE_EINVAL, "the solve's scheme differs from the batch's");
   agile_status s = AGILE_OK;
-  HostMesh* hm = new HostMesh(cfg->base_blocks, cfg->max_level, cfg->bc, cfg->xmin, cfg->xmax);
+  std::unique_ptr<HostMesh> hm(new HostMesh(cfg->base_blocks, cfg->max_level, cfg->bc, cfg->xmin, cfg->xmax));
   const int n = (int)hm->blocks().size();
+  int idx = -1;                              // a detached solve's index is reused
+  for (int i = 0; i < B->nsolve && idx < 0; ++i)
+    if (!B->live[i]) idx = i;
+  if (idx < 0) {                             // per-solve device arrays first: nothing moved yet
+    s = batch_reserve_solves(B, B->nsolve + 1);
+    if (s) return s;
+  }
   // first fit among the holes between live solves, else after the last one
   std::vector<std::pair<int, int>> ranges;   // (offset, count) of live solves, sorted
   for (int i = 0; i < B->nsolve; ++i)
@@ -1973,34 +2066,32 @@ agile_status agile_batch_attach(agile_batch* B, const agile_config* cfg, int* so
     for (const auto& r : ranges) live_blocks += r.second;
     const int ncap = std::max(2 * B->cap, live_blocks + n);
     void* Unew = dalloc(&view, (size_t)ncap * per);
-    if (!Unew) {
-      delete hm;
-      return bfail(B, AGILE_ENOMEM, "device allocation failed");
-    }
+    if (!Unew) return bfail(B, AGILE_ENOMEM, "device allocation failed");
+    std::vector<int> noff(B->nsolve, 0);
     int o = 0;
     for (int i = 0; i < B->nsolve; ++i) {
       if (!B->live[i]) continue;
       const int c = solve_blocks(B, i);
-      if (c)
-        BCK(B, cudaMemcpyAsync((char*)Unew + (size_t)o * per, (const char*)B->U[0] + (size_t)B->offset[i] * per,
-                               (size_t)c * per, cudaMemcpyDeviceToDevice, B->stream));
-      B->offset[i] = o;
+      if (c) {
+        const cudaError_t e = cudaMemcpyAsync((char*)Unew + (size_t)o * per,
+                                              (const char*)B->U[0] + (size_t)B->offset[i] * per, (size_t)c * per,
+                                              cudaMemcpyDeviceToDevice, B->stream);
+        if (e != cudaSuccess) {
+          dfree(&view, Unew);
+          return bfail(B, AGILE_ECUDA, std::string("pool growth copy: ") + cudaGetErrorString(e));
+        }
+      }
+      noff[i] = o;
       o += c;
     }
+    for (int i = 0; i < B->nsolve; ++i)
+      if (B->live[i]) B->offset[i] = noff[i];
     dfree(&view, B->U[0]);                   // in stream order, after the copies
     B->U[0] = Unew;
     B->cap = ncap;
     at = o;
   }
-  int idx = -1;                              // a detached solve's index is reused
-  for (int i = 0; i < B->nsolve && idx < 0; ++i)
-    if (!B->live[i]) idx = i;
   if (idx < 0) {
-    s = batch_reserve_solves(B, B->nsolve + 1);
-    if (s) {
-      delete hm;
-      return s;
-    }
     idx = B->nsolve++;
     B->cfgs.push_back(*cfg);
     B->meshes.push_back(nullptr);
@@ -2010,7 +2101,7 @@ agile_status agile_batch_attach(agile_batch* B, const agile_config* cfg, int* so
     B->ic_users.push_back(nullptr);
   }
   B->cfgs[idx] = *cfg;
-  B->meshes[idx] = hm;
+  B->meshes[idx] = hm.release();
   B->offset[idx] = at;
   B->live[idx] = 1;
   B->tables.resize(B->nsolve);
@@ -2018,7 +2109,7 @@ agile_status agile_batch_attach(agile_batch* B, const agile_config* cfg, int* so
   B->ics[idx] = nullptr;
   B->ic_users[idx] = nullptr;
   BCK(B, cudaMemsetAsync((char*)B->U[0] + (size_t)at * per, 0, (size_t)n * per, B->stream));
-  s = batch_rebuild(B);
+  if (!batch_patch(B, idx, true, &s)) s = batch_rebuild(B);
   if (s) return s;
   *solve = idx;
   return AGILE_OK;
@@ -2026,12 +2117,15 @@ agile_status agile_batch_attach(agile_batch* B, const agile_config* cfg, int* so
 
 agile_status agile_batch_detach(agile_batch* B, int solve) {
   if (!solve_ok(B, solve)) return bfail(B, AGILE_EINVAL, "bad argument");
+  agile_status s = AGILE_OK;
+  const bool patched = batch_patch(B, solve, false, &s);   // reads the solve's tables and mesh
   delete B->meshes[solve];
   B->meshes[solve] = nullptr;
   B->live[solve] = 0;
   B->ics[solve] = nullptr;
   B->ic_users[solve] = nullptr;
-  return batch_rebuild(B);
+  if (s) return s;
+  return patched ? AGILE_OK : batch_rebuild(B);
 }
 
 agile_status agile_batch_sync(agile_batch* B) {

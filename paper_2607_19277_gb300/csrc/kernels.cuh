@@ -19,7 +19,7 @@
 
 namespace agile {
 
-enum : int { STAGE_LAYOUT_RING4 = 1, STAGE_LAYOUT_RING5_DB = 2 };
+enum : int { STAGE_LAYOUT_RING4 = 1, STAGE_LAYOUT_RING5_DB = 2, STAGE_LAYOUT_RING3_DB = 3 };
 
 struct StageArgs {
   const void* Us;           // stage input state (with aux)
@@ -283,9 +283,11 @@ constexpr int ST_ETIMEOUT = 4;
 __device__ __forceinline__ int pslot(int p) { return (p + 3) % 3; }
 
 // Shared memory of the stage kernel for one staging layout: RAW raw-plane slots the TMA fills
-// (4: the ring holds planes k .. k+3 at plane k; 5: one more plane in flight) and SFB buffers
-// of the x/y face fluxes (2: the fluxes of plane k+1 are formed while those of plane k are
-// still being read, so one CTA barrier per plane suffices).
+// (4: the ring holds planes k .. k+3 at plane k; 5: one more plane in flight; 3: planes k+2 ..
+// k+4 only, the update of plane k then reading its stage input from global memory, where the
+// TMA has just passed it through L2) and SFB buffers of the x/y face fluxes (2: the fluxes of
+// plane k+1 are formed while those of plane k are still being read, so one CTA barrier per
+// plane suffices).
 template <template <typename> class PT, typename R, int RAW, int SFB>
 struct StageSmem {
   static constexpr int NV = PT<R>::NV, NT = PT<R>::NV + PT<R>::NA;
@@ -313,8 +315,9 @@ struct StageSmem {
 template <template <typename> class PT, typename R, int LIM, int FLUX, int MINB, int RAW, int SFB>
 __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant__ CUtensorMap tmap,
                                                            StageArgs A) {
-  static_assert(RAW == 4 || RAW == 5, "four or five raw slots");
-  static_assert(SFB == 1 || (SFB == 2 && RAW == 5), "a second flux buffer needs the fifth raw slot");
+  static_assert(RAW >= 3 && RAW <= 5, "three to five raw slots");
+  static_assert((RAW == 4) == (SFB == 1), "one flux buffer with four raw slots, two with three or five");
+  constexpr bool US_GLOBAL = RAW == 3;   // the update reads U_s of its cell from global memory
   using P = PT<R>;
   using S = StageSmem<PT, R, RAW, SFB>;
   constexpr int NV = P::NV, NA = P::NA, NT = NV + NA;
@@ -322,7 +325,8 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   constexpr bool PAIRED = sizeof(R) == 4 && PairPhys<P>::OK && (FLUX == FLUX_HLL || FLUX == FLUX_TVDLF);
   constexpr int NAW = NA > 0 ? NA : 1;
   constexpr bool RESP = res_of<P>::value;   // resistive MHD sources
-  constexpr int PHASES = 20 / RAW;   // completions of each raw slot's barrier per block (planes -2..17)
+  // completions of raw slot s's barrier per block (planes -2 .. 17 = TMA sequence 0 .. 19)
+  auto phases = [](int s) { return (20 + RAW - 1 - s) / RAW; };
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   R* sRaw = reinterpret_cast<R*>(smem_raw + S::raw);
@@ -477,7 +481,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     const int q = p + 2;
     R u[NT];
     if (plane_tma(p)) {
-      if (!mbar_wait(bar + (q % RAW), ((q / RAW) + jb * PHASES) & 1, WAIT_LIMIT)) st |= ST_ETIMEOUT;
+      if (!mbar_wait(bar + (q % RAW), ((q / RAW) + jb * phases(q % RAW)) & 1, WAIT_LIMIT)) st |= ST_ETIMEOUT;
       const R* r = sRaw + (size_t)(q % RAW) * NT * 256 + cell2;
 #pragma unroll
       for (int v = 0; v < NT; ++v) u[v] = r[v * 256];
@@ -594,7 +598,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   __syncthreads();   // raw slots of planes -2 and -1 are free
   if (t == 0) {
     fence_proxy_async();
-    for (int p = RAW - 2; p <= 3; ++p) issue(p);
+    for (int p = RAW - 2; p <= (RAW == 3 ? 2 : 3); ++p) issue(p);
   }
   convert_own(0);
   R fzd[NV], fzu[NV], hz[NV];
@@ -614,6 +618,11 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   }
   convert_halo(0);
   __syncthreads();   // plane 0 of the ring (interior and halo) is complete
+  if (RAW == 3 && t == 0) {   // raw slots of planes 0 and 1, converted above
+    fence_proxy_async();
+    issue(3);
+    issue(4);
+  }
 
   R ssum = R(0), smax = R(0);
 
@@ -752,7 +761,10 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
           for (int v = 0; v < NV; ++v) FR[((size_t)slot[2] * NV + v) * 256 + k * 16 + fc] = f[v];
         }
       }
-      if (warp == (k & 7)) {      // the 32 block-boundary faces, one warp per plane in turn
+      // the 32 block-boundary faces, one warp per plane in turn, taken from the half of the
+      // CTA that converts no halo in this plane (B converted plane k+1's halo in the half
+      // (k+1) & 1), so that no warp carries both extra pieces of work between two barriers
+      if (warp == 4 * (k & 1) + ((k >> 1) & 3)) {
         // lanes 0-15: x-face 16 - 1/2 of row r; lanes 16-31: y-face 16 - 1/2 of column r,
         // evaluated with the x-face solver on x/y-swapped states (no divergence)
         const int lane = t & 31, r = lane & 15;
@@ -794,11 +806,17 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
       fence_proxy_async();
       issue(k + 4);   // raw slot of plane k-1, whose update finished before this barrier
     }
+    if (RAW == 3 && t == 0 && k + 5 <= NB + 1) {
+      fence_proxy_async();
+      issue(k + 5);   // raw slot of plane k+2, converted by every thread before this barrier
+    }
     // ---- D: flux divergence and stage combine of cell (tx, ty, k)
     {
       const size_t cell = (size_t)k * 256 + cell2;
       const size_t base = (size_t)b * NT * NCELL + cell;
-      const R* raw = sRaw + (size_t)((k + 2) % RAW) * NT * 256 + cell2;
+      // U_s of the cell: the raw TMA slot, or global memory (layout with three slots)
+      const R* raw = US_GLOBAL ? Us + base : sRaw + (size_t)((k + 2) % RAW) * NT * 256 + cell2;
+      constexpr int RSTR = US_GLOBAL ? NCELL : 256;
       R out[NV];
       if constexpr (P::SOURCE) {
         // all flux divergences first: the source needs those of other variables
@@ -819,7 +837,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
         if constexpr (P::QV >= 0) L[P::QV] = (htc_g - pc[P::QV]) * rq4;   // -(q - target) / tau
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          R val = raw[v * 256];
+          R val = raw[(size_t)v * RSTR];
           if (v < P::FROZEN) {
             val = val + rdt * L[v];
             if (combine) val = ra * unk[v] + rb * val;
@@ -837,7 +855,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
             if (v >= P::BOFF && v < P::BOFF + 3) L = L + rsrc[v - P::BOFF];
             if (v == P::IE) L = L + rsrc[3];
           }
-          R val = raw[v * 256] + rdt * L;
+          R val = raw[(size_t)v * RSTR] + rdt * L;
           if (combine) val = ra * unk[v] + rb * val;
           out[v] = val;
           fzd[v] = fzu[v];

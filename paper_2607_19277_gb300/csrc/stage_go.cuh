@@ -47,17 +47,24 @@ static cudaError_t stage_go_layout(const StageArgs& a, cudaStream_t s) {
 }
 
 // Staging layouts: STAGE_LAYOUT_RING4 = four raw slots, one flux buffer, two barriers per
-// plane; STAGE_LAYOUT_RING5_DB = five raw slots, two flux buffers, one barrier per plane.
-// The default (layout 0) takes the second where it keeps as many CTAs per SM as the first
-// (FP32 stencils only; FP64 keeps the first).
+// plane; STAGE_LAYOUT_RING5_DB = five raw slots, two flux buffers, one barrier per plane;
+// STAGE_LAYOUT_RING3_DB = three raw slots, two flux buffers, one barrier per plane, the update
+// reading its stage input from global memory (L2) instead of a raw slot. The default (layout
+// 0) takes layout 2 where it keeps as many CTAs per SM as layout 1, else layout 1 (FP32
+// stencils; FP64 keeps layout 1). Layout 3 is an autotuner choice: at equal CTAs per SM its
+// global re-read of U_s costs about what its saved barrier gains (MHD 0.870 against 0.860 ms,
+// FFHD 0.459 against 0.450 ms per 256^3 stage launch).
 template <template <typename> class PT, typename R, int LIM, int FLUX>
 static cudaError_t stage_go(const StageArgs& a, cudaStream_t s) {
   if constexpr (sizeof(R) == 8) {
     return stage_go_layout<PT, R, LIM, FLUX, 4, 1>(a, s);
   } else {
-    constexpr bool db_default = stage_minb<PT, R, 5, 2>() >= stage_minb<PT, R, 4, 1>();
-    const bool db = a.layout == STAGE_LAYOUT_RING5_DB || (a.layout == 0 && db_default);
-    return db ? stage_go_layout<PT, R, LIM, FLUX, 5, 2>(a, s) : stage_go_layout<PT, R, LIM, FLUX, 4, 1>(a, s);
+    constexpr int dflt = stage_minb<PT, R, 5, 2>() >= stage_minb<PT, R, 4, 1>() ? STAGE_LAYOUT_RING5_DB
+                                                                                 : STAGE_LAYOUT_RING4;
+    const int lay = a.layout == 0 ? dflt : a.layout;
+    if (lay == STAGE_LAYOUT_RING5_DB) return stage_go_layout<PT, R, LIM, FLUX, 5, 2>(a, s);
+    if (lay == STAGE_LAYOUT_RING3_DB) return stage_go_layout<PT, R, LIM, FLUX, 3, 2>(a, s);
+    return stage_go_layout<PT, R, LIM, FLUX, 4, 1>(a, s);
   }
 }
 

@@ -51,3 +51,18 @@ def test_summary_collects_the_legs_and_drops_missing_ones():
     assert s == {"fp32_value": 1.0, "fp32_hbm_frac": 0.3, "fp32_alu_frac": 0.4, "fp32_stage_launch_ms": 0.9,
                  "fp64_value": 2.0, "fp64_alu_frac": 0.5, "fp32_max_rel_l1_vs_fp64": 1e-6,
                  "fp32_psi_rel_l1_vs_fp64": 1e-4, "serving_fp32_batched_p99_s": 0.2}
+
+
+def test_average_to_base_grid_is_volume_weighted():
+    """Leaves of level 1 and 2 averaged onto a 32^3 base grid (2 base blocks per edge): a
+    level-2 block covers 8 base cells per edge, each the mean of 2^3 fine cells."""
+    import numpy as np
+    rng = np.random.default_rng(3)
+    lev = np.array([1, 2])
+    ijk = np.array([[0, 0, 0], [2, 0, 0]])      # level-2 block (2,0,0) sits in base block (1,0,0)
+    cons = rng.random((2, 5, 16, 16, 16))
+    out = bench._average_to_base(lev, ijk, cons, 32)
+    assert np.array_equal(out[:, :16, :16, :16], cons[0])
+    fine = cons[1].reshape(5, 8, 2, 8, 2, 8, 2).mean(axis=(2, 4, 6))
+    assert np.allclose(out[:, :8, :8, 16:24], fine, rtol=0, atol=1e-15)
+    assert not out[:, 16:, :, :].any()

@@ -170,3 +170,27 @@ def test_sedov_amr_evolution_matches_oracle():
     assert np.array_equal(lev, olev) and np.array_equal(ijk, oijk)
     assert rel_l1(g, r, lev).max() < TOL_FP64
     m.close()
+
+
+def test_phase_timing_counts_every_phase_of_a_refined_step():
+    """agile_phase_timing: with kernel timing on, a step of a refined mesh records the stage
+    kernel, the coarse-fine ghost fill and the flux fix-up once per RK stage, and a regrid
+    records the estimator and the ghost fill it reads; the stage time equals
+    agile_kernel_timing's."""
+    spec = dict(physics="hd", limiter="minmod", flux="hll", rk=2, base_blocks=(2, 2, 2), max_level=2,
+                xmin=(-0.5,) * 3, xmax=(0.5,) * 3, bc=(OUT,) * 6, refine_vars=(0, 4),
+                refine_weights=(0.5, 0.5))
+    m = gpu_mesh(spec)
+    m.set_state(W.sedov(r0=0.1, centre=(0.25, 0.25, 0.25)))   # inside one base block
+    m.regrid(init=True)
+    assert 8 < m.layout()[0] < 64                              # coarse-fine faces exist
+    m.set_kernel_timing(True)
+    m.step(0.0)
+    m.regrid()
+    ph = m.phase_timing()
+    stage_ms, stage_launches, _ = m.kernel_timing()
+    m.close()
+    assert ph["stage"][1] == 2 and ph["ghost_fill"][1] == 3 and ph["fixup"][1] == 2
+    assert ph["estimate"][1] == 1
+    assert all(ms > 0.0 for ms, _ in ph.values())
+    assert ph["stage"][0] == stage_ms and stage_launches == 2

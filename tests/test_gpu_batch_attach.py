@@ -107,3 +107,54 @@ def test_attach_refuses_another_scheme():
     with pytest.raises(agile.AgileError):
         b.detach(5)
     b.close()
+
+
+def test_uniform_solves_come_and_go_beside_a_refined_one():
+    """A refined solve (ghost slots, ghost tasks and flux-register fix-ups) stays in the batch
+    while uniform solves attach before and after it in the index order and detach again: the
+    uniform changes patch only their own table ranges and the work list, the refined solve's
+    slot offsets stay valid, and every solve equals its run alone bit for bit."""
+    amr = agile.make_config(physics="hd", limiter="minmod", flux="hll", rk=2, real_bytes=8, base_blocks=(2, 2, 2),
+                            max_level=3, refine_vars=(0, 4), refine_weights=(0.5, 0.5), refine_tol=0.05)
+    uni = agile.make_config(physics="hd", limiter="minmod", flux="hll", rk=2, real_bytes=8, base_blocks=(2, 2, 2))
+    ic = {0: W.random_smooth(5, 330, "hd"), 1: W.random_smooth(5, 331, "hd")}
+    b = agile.Batch([uni, amr])
+    alone = {}
+    for i, c in ((0, uni), (1, amr)):
+        b.set_state(i, ic[i])
+        alone[i] = agile.Mesh(c)
+        alone[i].set_state(ic[i])
+    flags = np.zeros(b.layout(1)[0], np.int32)
+    flags[0] = 1
+    assert b.regrid_flags(1, flags) == tuple(alone[1].regrid_flags(flags))
+
+    def both(n):
+        for _ in range(n):
+            b.step()
+            for m in alone.values():
+                m.step(0.0)
+
+    both(2)
+    # the uniform solve before the refined one leaves, a new one takes its index, another
+    # one is appended after the refined one
+    _, _, s0 = b.get_state(0)
+    assert np.array_equal(s0, alone.pop(0).get_state()[2])
+    b.detach(0)
+    for i, seed in ((0, 332), (2, 333)):
+        j = b.attach(uni)
+        assert j == i
+        ic[j] = W.random_smooth(5, seed, "hd")
+        b.set_state(j, ic[j])
+        alone[j] = agile.Mesh(uni)
+        alone[j].set_state(ic[j])
+    both(3)
+    b.detach(2)
+    alone.pop(2).close()
+    both(2)
+    for i, m in alone.items():
+        lb, ijkb, cb = b.get_state(i)
+        lm, ijkm, cm = m.get_state()
+        assert np.array_equal(lb, lm) and np.array_equal(ijkb, ijkm), i
+        assert np.array_equal(cb, cm), i
+        m.close()
+    b.close()
