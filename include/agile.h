@@ -313,7 +313,9 @@ typedef struct agile_batch agile_batch;
 /* Create nsolve solves from cfgs[nsolve], each with its level-1 blocks (refine with
  * agile_batch_regrid). The solves share physics, limiter, flux, rk, real_bytes, gamma, cfl,
  * glm_alpha, eos and htc_kappa0 (AGILE_EINVAL otherwise); grids, boundaries and refinement
- * settings are per solve. alloc as for meshes;
+ * settings are per solve. alloc as for meshes; it is also called with the batch's own
+ * upload stream (a non-blocking stream the batch creates at its first upload), for buffers
+ * it frees only after an event behind their last reader on the batch stream has completed.
  * cuda_stream NULL makes the batch create its own non-blocking stream (graphs cannot be
  * captured on the legacy default stream). Errors: AGILE_EINVAL, AGILE_ENOMEM, AGILE_ECUDA. */
 agile_status agile_batch_create(const agile_config* cfgs, int nsolve, const agile_allocator* alloc,
@@ -327,9 +329,10 @@ agile_status agile_batch_layout(agile_batch* batch, int solve, size_t* nblocks, 
 agile_status agile_batch_set_state(agile_batch* batch, int solve, agile_ic_fn ic, void* user);
 
 /* agile_set_state_prims for solve `solve` of a batch (its blocks in the solve's order).
- * Enqueued on the batch's stream without waiting (the host array is staged when each copy
- * is enqueued and may be released on return); a device error is returned by the next
- * synchronising batch call. */
+ * The host array is copied to a device buffer on the batch's own upload stream before the
+ * call returns (it may be released then; the copy does not wait for the steps already
+ * enqueued on the batch stream), and its conversion is enqueued on the batch stream behind
+ * them. A device error is returned by the next synchronising batch call. */
 agile_status agile_batch_set_state_prims(agile_batch* batch, int solve, const double* prim, size_t nblk);
 
 /* One full SSPRK step of every solve with its own on-device CFL dt (as agile_step(dt <= 0)).
@@ -394,13 +397,19 @@ agile_status agile_batch_copy_solve(agile_batch* dst, int dst_solve, agile_batch
  * launches walk a work list of the attached solves' blocks, so a solve joins or leaves at the
  * next step at the cost of rebuilding the descriptor tables (host, then one upload) and
  * capturing the step's CUDA graph again. Only when no hole fits and the pool is full does
- * attach allocate a pool at least twice as large and copy the attached solves into it. A
+ * attach allocate a new pool (the attached solves, this one and an eighth more) and copy the
+ * attached solves into it compactly; a detach that leaves a pool of more than 4096 blocks
+ * less than two thirds used repacks it the same way to the attached solves and an eighth more, so
+ * the pool's capacity follows the attached solves in both directions. A
  * detached solve's index is reused by a later attach; using it otherwise returns
  * AGILE_EINVAL. An attached solve's state is zero until agile_batch_set_state or
  * agile_batch_set_state_prims sets it: set it before the next agile_batch_step (a zero
  * density is reported as AGILE_EUNPHYS). Neither waits for the batch's stream: old tables
- * and buffers are released in stream order (the allocator contract above), and a solve's
- * own tables are cached until it is regridded. Errors: AGILE_EINVAL (a different scheme, a
+ * and buffers are released in stream order (the allocator contract above), a solve's own
+ * tables are cached until it is regridded, and where the solve has no coarse-fine faces
+ * and fits the pool's free blocks only its own range of the block tables and the work list
+ * are written (uploaded on the batch's upload stream, copied into place on the batch
+ * stream). Errors: AGILE_EINVAL (a different scheme, a
  * bad index), AGILE_ENOMEM, AGILE_ECUDA; device errors surface at the next synchronising
  * batch call. */
 agile_status agile_batch_attach(agile_batch* batch, const agile_config* cfg, int* solve);

@@ -38,6 +38,7 @@ struct agile_mesh {
   void* FR = nullptr;
   int nslots = 0;
   BlockDesc* d_bd = nullptr;
+  int* d_wl = nullptr;             // stage kernel work order (blocks by level, z-slab, 2-D Morton)
   GhostTask* d_ghosts = nullptr;
   FixupTask* d_fix = nullptr;
   int nghost = 0, nfix = 0;
@@ -241,6 +242,32 @@ agile_status make_tmap(agile_mesh* m, void* U, CUtensorMap* out) {
 
 // (Re)build descriptors, slots and scratch for the current host mesh; U[0] must already
 // hold nblk blocks.
+// 2-D Morton code of (x, y) (16 bits each).
+uint64_t morton2(uint32_t x, uint32_t y) {
+  uint64_t c = 0;
+  for (int i = 0; i < 16; ++i) c |= (uint64_t)((x >> i) & 1) << (2 * i) | (uint64_t)((y >> i) & 1) << (2 * i + 1);
+  return c;
+}
+
+// Order in which the stage kernel's persistent CTAs take the blocks: by level, then by z
+// index, then in 2-D Morton order within the z-slab. A slab's blocks run together, so the
+// x/y halos a block reads belong to blocks that run at the same time and the z halos to the
+// slabs just before and after it, which keeps the halo re-reads in L2 (the pool itself stays
+// in 3-D Morton order).
+std::vector<int> slab_order(const HostMesh& hm) {
+  const auto& keys = hm.blocks();
+  std::vector<int> w(keys.size());
+  for (size_t i = 0; i < keys.size(); ++i) w[i] = (int)i;
+  std::stable_sort(w.begin(), w.end(), [&](int a, int b) {
+    const Key& p = keys[a];
+    const Key& q = keys[b];
+    if (p.lev != q.lev) return p.lev < q.lev;
+    if (p.z != q.z) return p.z < q.z;
+    return morton2(p.x, p.y) < morton2(q.x, q.y);
+  });
+  return w;
+}
+
 agile_status rebuild(agile_mesh* m) {
   std::vector<BlockDesc> desc;
   std::vector<GhostTask> ghosts;
@@ -257,6 +284,9 @@ agile_status rebuild(agile_mesh* m) {
   dfree(m, m->FR);
   dfree(m, m->U[1]);
   dfree(m, m->U[2]);
+  dfree_t(m, m->d_wl);
+  const std::vector<int> order = slab_order(*m->mesh);
+  m->d_wl = (int*)dalloc(m, order.size() * sizeof(int));
   m->d_bd = (BlockDesc*)dalloc(m, desc.size() * sizeof(BlockDesc));
   m->d_ghosts = (GhostTask*)dalloc(m, ghosts.size() * sizeof(GhostTask));
   m->d_fix = (FixupTask*)dalloc(m, fix.size() * sizeof(FixupTask));
@@ -264,10 +294,12 @@ agile_status rebuild(agile_mesh* m) {
   m->FR = dalloc(m, (size_t)nslots * m->nv * 256 * m->rb);
   m->U[1] = dalloc(m, pool_bytes(m, m->nblk));
   m->U[2] = m->cfg.rk == 3 ? dalloc(m, pool_bytes(m, m->nblk)) : nullptr;
-  if (!m->d_bd || !m->d_ghosts || !m->d_fix || !m->G || !m->FR || !m->U[1] ||
+  if (!m->d_bd || !m->d_wl || !m->d_ghosts || !m->d_fix || !m->G || !m->FR || !m->U[1] ||
       (m->cfg.rk == 3 && !m->U[2]))
     return fail(m, AGILE_ENOMEM, "device allocation failed");
   CK(m, cudaMemcpyAsync(m->d_bd, desc.data(), desc.size() * sizeof(BlockDesc), cudaMemcpyHostToDevice, m->stream));
+  if (!order.empty())
+    CK(m, cudaMemcpyAsync(m->d_wl, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, m->stream));
   if (!ghosts.empty())
     CK(m, cudaMemcpyAsync(m->d_ghosts, ghosts.data(), ghosts.size() * sizeof(GhostTask), cudaMemcpyHostToDevice, m->stream));
   if (!fix.empty())
@@ -535,6 +567,7 @@ void agile_mesh_destroy(agile_mesh* m) {
   dfree(m, m->G);
   dfree(m, m->FR);
   dfree_t(m, m->d_bd);
+  dfree_t(m, m->d_wl);
   dfree_t(m, m->d_ghosts);
   dfree_t(m, m->d_fix);
   dfree_t(m, m->d_status);
@@ -667,6 +700,7 @@ agile_status agile_step(agile_mesh* m, double dt) {
     A.eta = m->cfg.eta;
     A.glm_post = (mhd && last && fuse) ? 1 : 0;
     A.nblk = m->nblk;
+    A.wl = m->d_wl;
     A.status = m->d_status;
     A.speeds = (last && speeds_in_stage) ? m->d_speeds : nullptr;
     A.tmap = &m->tmap[st == 0 ? 0 : st];
@@ -1066,6 +1100,7 @@ struct agile_batch {
     std::vector<BlockDesc> desc;
     std::vector<GhostTask> ghosts;
     std::vector<FixupTask> fix;
+    std::vector<int> order;         // the stage kernel's work order of its blocks (slab_order)
     int nslots = 0;
   };
   std::vector<Tables> tables;
@@ -1075,7 +1110,24 @@ struct agile_batch {
   int* d_wl = nullptr;
   int nwork = 0;
   int tab_cap = 0;                  // blocks d_bd, d_solve_of and d_wl hold (the capacity)
+  // Host-to-device uploads of membership changes and initial states go through device
+  // buffers written on their own stream: a copy from pageable host memory returns only when
+  // it has been carried out, so on the batch stream it would wait for every step already
+  // enqueued there. The batch stream waits for the upload instead; a buffer is released once
+  // an event after its last reader on the batch stream has completed.
+  cudaStream_t up_stream = nullptr;
+  struct Upload {
+    void* p;
+    size_t bytes;
+    cudaEvent_t done;
+  };
+  std::vector<Upload> uploads;
+  size_t upload_bytes = 0;          // bytes of the upload buffers not yet released
 };
+
+// Upload buffers held at once (bytes): past this, a new upload first waits for the oldest
+// buffers' readers, so that uploads running ahead of the batch stream stay bounded.
+constexpr size_t UPLOAD_HELD_MAX = (size_t)4 << 30;
 
 namespace {
 
@@ -1129,6 +1181,98 @@ AuxArgs batch_aux(agile_batch* B, void* U) {
 
 agile_status batch_status(agile_batch* B);
 
+// Release the upload buffers whose readers have run (all of them with wait = true, after
+// the batch stream has been synchronised).
+void batch_reap_uploads(agile_batch* B, bool wait) {
+  agile_mesh view;
+  as_mesh_view(B, &view);
+  view.stream = B->up_stream;
+  size_t k = 0;
+  for (size_t i = 0; i < B->uploads.size(); ++i) {
+    agile_batch::Upload& u = B->uploads[i];
+    if (wait || cudaEventQuery(u.done) == cudaSuccess) {
+      if (wait) cudaEventSynchronize(u.done);
+      dfree(&view, u.p);
+      cudaEventDestroy(u.done);
+      B->upload_bytes -= u.bytes;
+    } else {
+      B->uploads[k++] = u;
+    }
+  }
+  B->uploads.resize(k);
+}
+
+// Wait for the oldest upload buffers' readers until `bytes` more stay within the bound.
+void batch_bound_uploads(agile_batch* B, size_t bytes) {
+  agile_mesh view;
+  as_mesh_view(B, &view);
+  view.stream = B->up_stream;
+  size_t k = 0;
+  while (k < B->uploads.size() && B->upload_bytes + bytes > UPLOAD_HELD_MAX) {
+    agile_batch::Upload& u = B->uploads[k++];   // oldest first: recorded in stream order
+    cudaEventSynchronize(u.done);
+    dfree(&view, u.p);
+    cudaEventDestroy(u.done);
+    B->upload_bytes -= u.bytes;
+  }
+  B->uploads.erase(B->uploads.begin(), B->uploads.begin() + k);
+}
+
+// Copy `bytes` of host memory into a new device buffer on the upload stream (not behind the
+// batch stream's enqueued work) and make the batch stream wait for the copy. The caller
+// enqueues the buffer's readers on the batch stream, then calls batch_upload_done.
+void* batch_upload(agile_batch* B, const void* src, size_t bytes, agile_status* st) {
+  *st = AGILE_OK;
+  batch_reap_uploads(B, false);
+  batch_bound_uploads(B, bytes);
+  if (!B->up_stream && cudaStreamCreateWithFlags(&B->up_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    *st = bfail(B, AGILE_ECUDA, "upload stream");
+    return nullptr;
+  }
+  agile_mesh view;
+  as_mesh_view(B, &view);
+  view.stream = B->up_stream;
+  void* p = dalloc(&view, bytes);
+  if (!p) {
+    *st = bfail(B, AGILE_ENOMEM, "device allocation failed");
+    return nullptr;
+  }
+  cudaEvent_t ev = nullptr;
+  cudaError_t e = cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, B->up_stream);
+  // the host source may be released on return, pinned or not: wait for this copy alone
+  if (e == cudaSuccess) e = cudaStreamSynchronize(B->up_stream);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev, B->up_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(B->stream, ev, 0);
+  if (ev) cudaEventDestroy(ev);      // the wait above holds the recorded state
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(B->up_stream);
+    dfree(&view, p);
+    *st = bfail(B, AGILE_ECUDA, std::string("upload: ") + cudaGetErrorString(e));
+    return nullptr;
+  }
+  return p;
+}
+
+// The readers of upload buffer p are enqueued on the batch stream: release p after them.
+agile_status batch_upload_done(agile_batch* B, void* p, size_t bytes) {
+  agile_batch::Upload u{p, bytes, nullptr};
+  cudaError_t e = cudaEventCreateWithFlags(&u.done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(u.done, B->stream);
+  if (e != cudaSuccess) {            // keep the buffer until the batch stream is idle
+    if (u.done) cudaEventDestroy(u.done);
+    cudaStreamSynchronize(B->stream);
+    agile_mesh view;
+    as_mesh_view(B, &view);
+    view.stream = B->up_stream;
+    dfree(&view, p);
+    return bfail(B, AGILE_ECUDA, std::string("upload event: ") + cudaGetErrorString(e));
+  }
+  B->uploads.push_back(u);
+  B->upload_bytes += bytes;
+  return AGILE_OK;
+}
+
 int solve_blocks(const agile_batch* B, int i) {
   return B->live[i] ? (int)B->meshes[i]->blocks().size() : 0;
 }
@@ -1171,6 +1315,7 @@ agile_status batch_rebuild(agile_batch* B) {
       T.fix.clear();
       B->meshes[i]->build_descs(&T.desc, &T.ghosts, &T.fix, &T.nslots, &err);
       if (!err.empty()) return bfail(B, AGILE_EINVAL, err);
+      T.order = slab_order(*B->meshes[i]);
       T.valid = true;
     }
     const std::vector<BlockDesc>& d = T.desc;
@@ -1192,8 +1337,8 @@ agile_status batch_rebuild(agile_batch* B) {
       used[b] = 1;
       desc[b] = bd;
       solve_of[b] = i;
-      work.push_back(b);
     }
+    for (int q : T.order) work.push_back(O + q);
     for (GhostTask& t : g) {
       t.blk += O;
       t.slot += S;
@@ -1762,6 +1907,11 @@ void agile_batch_destroy(agile_batch* B) {
   dfree(&view, B->G);
   dfree(&view, B->FR);
   cudaStreamSynchronize(B->stream);
+  batch_reap_uploads(B, true);
+  if (B->up_stream) {
+    cudaStreamSynchronize(B->up_stream);
+    cudaStreamDestroy(B->up_stream);
+  }
   for (HostMesh* hm : B->meshes) delete hm;   // nullptr for detached solves
   if (B->own_stream) cudaStreamDestroy(B->stream);
   delete B;
@@ -1810,13 +1960,29 @@ agile_status agile_batch_set_state_prims(agile_batch* B, int solve, const double
   view.ic = nullptr;
   view.ic_user = nullptr;
   view.d_status = B->d_status;
+  // the primitives and the local block indices uploaded without waiting for the steps
+  // already enqueued, converted on the batch stream after them
   std::vector<int> local(nblk);
   for (size_t i = 0; i < nblk; ++i) local[i] = (int)i;
   char* base = (char*)B->U[0] + (size_t)B->offset[solve] * B->nt * NCELL * B->rb;
+  agile_status s = AGILE_OK;
+  const size_t pbytes = nblk * B->nv * NCELL * sizeof(double), lbytes = nblk * sizeof(int);
+  void* d_prim = batch_upload(B, prim, pbytes, &s);
+  if (!d_prim) return s;
+  void* d_local = batch_upload(B, local.data(), lbytes, &s);
+  if (!d_local) {
+    batch_upload_done(B, d_prim, pbytes);
+    return s;
+  }
   view.nblk = (int)nblk;
-  agile_status s = apply_ic(&view, base, local, prim);
+  AuxArgs a = aux_args(&view, base);
+  const cudaError_t e = launch_prim2cons(a, (const double*)d_prim, (const int*)d_local, (int)nblk, B->stream);
   view.mesh = nullptr;
-  if (s) return bfail(B, s, view.err);
+  s = batch_upload_done(B, d_prim, pbytes);
+  const agile_status s2 = batch_upload_done(B, d_local, lbytes);
+  if (e != cudaSuccess) return bfail(B, AGILE_ECUDA, std::string("prim2cons: ") + cudaGetErrorString(e));
+  if (s) return s;
+  if (s2) return s2;
   B->ics[solve] = nullptr;
   B->ic_users[solve] = nullptr;
   B->speeds_valid = false;
@@ -1969,6 +2135,7 @@ bool batch_patch(agile_batch* B, int solve, bool attach, agile_status* st) {
     T.fix.clear();
     B->meshes[solve]->build_descs(&T.desc, &T.ghosts, &T.fix, &T.nslots, &err);
     if (!err.empty()) return false;
+    T.order = slab_order(*B->meshes[solve]);
     T.valid = true;
   }
   if (!T.valid || !T.ghosts.empty() || !T.fix.empty() || T.nslots) return false;
@@ -2006,17 +2173,31 @@ bool batch_patch(agile_batch* B, int solve, bool attach, agile_status* st) {
   for (int i = 0; i < B->nsolve; ++i) {      // the work list: live solves in index order
     if (!B->live[i] || (!attach && i == solve)) continue;
     const int c = solve_blocks(B, i);
-    for (int q = 0; q < c; ++q) work.push_back(B->offset[i] + q);
+    const agile_batch::Tables& Ti = B->tables[i];
+    if (!Ti.valid || (int)Ti.order.size() != c) return false;
+    for (int q : Ti.order) work.push_back(B->offset[i] + q);
     extent = std::max(extent, B->offset[i] + c);
   }
-  auto up = [&](void* dst, const void* src, size_t bytes) {
+  // one upload of [descriptors | solve indices | work list], copied into place on the batch
+  // stream behind the steps that still read the old work list
+  const size_t bd_bytes = d.size() * sizeof(BlockDesc), so_bytes = so.size() * sizeof(int);
+  const size_t wl_bytes = work.size() * sizeof(int);
+  std::vector<char> h(bd_bytes + so_bytes + wl_bytes + 1);
+  memcpy(h.data(), d.data(), bd_bytes);
+  memcpy(h.data() + bd_bytes, so.data(), so_bytes);
+  memcpy(h.data() + bd_bytes + so_bytes, work.data(), wl_bytes);
+  char* dev = (char*)batch_upload(B, h.data(), h.size(), st);
+  if (!dev) return true;
+  auto cp = [&](void* dst, const char* src, size_t bytes) {
     if (!bytes || *st) return;
-    const cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, B->stream);
-    if (e != cudaSuccess) *st = bfail(B, AGILE_ECUDA, std::string("table upload: ") + cudaGetErrorString(e));
+    const cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, B->stream);
+    if (e != cudaSuccess) *st = bfail(B, AGILE_ECUDA, std::string("table copy: ") + cudaGetErrorString(e));
   };
-  up(B->d_bd + O, d.data(), d.size() * sizeof(BlockDesc));
-  up(B->d_solve_of + O, so.data(), so.size() * sizeof(int));
-  up(B->d_wl, work.data(), work.size() * sizeof(int));
+  cp(B->d_bd + O, dev, bd_bytes);
+  cp(B->d_solve_of + O, dev + bd_bytes, so_bytes);
+  cp(B->d_wl, dev + bd_bytes + so_bytes, wl_bytes);
+  const agile_status sd = batch_upload_done(B, dev, h.size());
+  if (!*st) *st = sd;
   if (*st) return true;
   B->nwork = (int)work.size();
   B->nblk = std::max(B->nblk, extent);       // per-block scratch covers every pool block in use
@@ -2028,6 +2209,45 @@ bool batch_patch(agile_batch* B, int solve, bool attach, agile_status* st) {
   B->steps_done = 0;
   B->speeds_valid = false;
   return true;
+}
+
+// A new pool of ncap blocks with the live solves copied into it compactly, in index order;
+// *end (may be NULL) receives the first free block. The caller rebuilds the tables (the
+// stage buffers follow the capacity there).
+agile_status batch_repool(agile_batch* B, int ncap, int* end) {
+  agile_mesh view;
+  as_mesh_view(B, &view);
+  const size_t per = (size_t)B->nt * NCELL * B->rb;
+  void* Unew = dalloc(&view, (size_t)std::max(ncap, 1) * per);
+  if (!Unew) return bfail(B, AGILE_ENOMEM, "device allocation failed");
+  std::vector<int> noff(B->nsolve, 0);
+  int o = 0;
+  for (int i = 0; i < B->nsolve; ++i) {
+    if (!B->live[i]) continue;
+    const int c = solve_blocks(B, i);
+    if (o + c > ncap) {
+      dfree(&view, Unew);
+      return bfail(B, AGILE_EINVAL, "new pool smaller than the live solves");
+    }
+    if (c) {
+      const cudaError_t e = cudaMemcpyAsync((char*)Unew + (size_t)o * per,
+                                            (const char*)B->U[0] + (size_t)B->offset[i] * per, (size_t)c * per,
+                                            cudaMemcpyDeviceToDevice, B->stream);
+      if (e != cudaSuccess) {
+        dfree(&view, Unew);
+        return bfail(B, AGILE_ECUDA, std::string("pool copy: ") + cudaGetErrorString(e));
+      }
+    }
+    noff[i] = o;
+    o += c;
+  }
+  for (int i = 0; i < B->nsolve; ++i)
+    if (B->live[i]) B->offset[i] = noff[i];
+  dfree(&view, B->U[0]);                     // in stream order, after the copies
+  B->U[0] = Unew;
+  B->cap = ncap;
+  if (end) *end = o;
+  return AGILE_OK;
 }
 
 agile_status agile_batch_attach(agile_batch* B, const agile_config* cfg, int* solve) {
@@ -2061,35 +2281,12 @@ agile_status agile_batch_attach(agile_batch* B, const agile_config* cfg, int* so
   as_mesh_view(B, &view);
   const size_t per = (size_t)B->nt * NCELL * B->rb;
   if (at < 0) {
-    // grow: a new pool at least twice the old, the live solves copied into it compactly
+    // grow: a new pool with room for this solve and an eighth more, the live solves copied
+    // into it compactly
     int live_blocks = 0;
     for (const auto& r : ranges) live_blocks += r.second;
-    const int ncap = std::max(2 * B->cap, live_blocks + n);
-    void* Unew = dalloc(&view, (size_t)ncap * per);
-    if (!Unew) return bfail(B, AGILE_ENOMEM, "device allocation failed");
-    std::vector<int> noff(B->nsolve, 0);
-    int o = 0;
-    for (int i = 0; i < B->nsolve; ++i) {
-      if (!B->live[i]) continue;
-      const int c = solve_blocks(B, i);
-      if (c) {
-        const cudaError_t e = cudaMemcpyAsync((char*)Unew + (size_t)o * per,
-                                              (const char*)B->U[0] + (size_t)B->offset[i] * per, (size_t)c * per,
-                                              cudaMemcpyDeviceToDevice, B->stream);
-        if (e != cudaSuccess) {
-          dfree(&view, Unew);
-          return bfail(B, AGILE_ECUDA, std::string("pool growth copy: ") + cudaGetErrorString(e));
-        }
-      }
-      noff[i] = o;
-      o += c;
-    }
-    for (int i = 0; i < B->nsolve; ++i)
-      if (B->live[i]) B->offset[i] = noff[i];
-    dfree(&view, B->U[0]);                   // in stream order, after the copies
-    B->U[0] = Unew;
-    B->cap = ncap;
-    at = o;
+    s = batch_repool(B, live_blocks + n + std::max(n, (live_blocks + n) / 8), &at);
+    if (s) return s;
   }
   if (idx < 0) {
     idx = B->nsolve++;
@@ -2125,6 +2322,15 @@ agile_status agile_batch_detach(agile_batch* B, int solve) {
   B->ics[solve] = nullptr;
   B->ic_users[solve] = nullptr;
   if (s) return s;
+  // a pool less than two thirds used shrinks to its live blocks and an eighth more, so that
+  // the capacity follows the attached solves down as well as up (at most 1.5 times them)
+  int live_blocks = 0;
+  for (int i = 0; i < B->nsolve; ++i) live_blocks += solve_blocks(B, i);
+  if (B->cap > 4096 && 3LL * live_blocks < 2LL * B->cap) {
+    s = batch_repool(B, live_blocks + live_blocks / 8, nullptr);
+    if (s) return s;
+    return batch_rebuild(B);
+  }
   return patched ? AGILE_OK : batch_rebuild(B);
 }
 

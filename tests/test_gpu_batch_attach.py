@@ -158,3 +158,40 @@ def test_uniform_solves_come_and_go_beside_a_refined_one():
         assert np.array_equal(cb, cm), i
         m.close()
     b.close()
+
+
+def test_pool_repacks_when_half_empty_and_grows_again():
+    """Detaching solves until a pool of more than 4096 blocks is less than two thirds used
+    repacks it (the live solves copied into a smaller pool), a later attach grows it again; the solves that stay equal
+    their runs alone bit for bit throughout."""
+    cfg = agile.make_config(physics="hd", limiter="vanleer", flux="tvdlf", rk=3, real_bytes=4,
+                            base_blocks=(8, 8, 8))                     # 512 blocks each
+    b = agile.Batch([cfg] * 10)
+    keep = {1: None, 4: None, 7: None, 9: None}
+    for i in range(10):
+        b.set_state(i, W.random_smooth(5, 340 + i, "hd"))
+    for i in keep:
+        keep[i] = agile.Mesh(cfg)
+        keep[i].set_state(W.random_smooth(5, 340 + i, "hd"))
+
+    def both(n):
+        for _ in range(n):
+            b.step()
+            for m in keep.values():
+                m.step(0.0)
+
+    both(1)
+    for i in range(10):            # the fourth detach leaves 3072 of 5120 blocks: repacked
+        if i not in keep:          # into 3456 blocks; the next two leave holes
+            b.detach(i)
+    both(2)
+    for seed in (350, 351, 352):   # two attachments fill the holes, the third grows the pool
+        j = b.attach(cfg)
+        b.set_state(j, W.random_smooth(5, seed, "hd"))
+        keep[j] = agile.Mesh(cfg)
+        keep[j].set_state(W.random_smooth(5, seed, "hd"))
+    both(2)
+    for i, m in keep.items():
+        assert np.array_equal(b.get_state(i)[2], m.get_state()[2]), i
+        m.close()
+    b.close()
