@@ -282,8 +282,9 @@ agile_status agile_get_halo(agile_mesh* mesh, size_t block, double* out);
 agile_status agile_sync(agile_mesh* mesh);
 
 /* Kernel timing with CUDA events recorded on the mesh's stream around every launch of the
- * stage (update) kernel. enable = 1 resets and starts accumulating; agile_kernel_timing
- * synchronises and returns the summed milliseconds and the launch count. */
+ * stage (update) kernel (for SRHD together with the primitive-recovery pass before it).
+ * enable = 1 resets and starts accumulating; agile_kernel_timing synchronises and returns
+ * the summed milliseconds and the launch count of the stage kernel. */
 agile_status agile_set_kernel_timing(agile_mesh* mesh, int enable);
 agile_status agile_kernel_timing(agile_mesh* mesh, double* stage_ms, long long* stage_launches,
                                  long long* total_launches);
@@ -397,9 +398,9 @@ agile_status agile_batch_copy_solve(agile_batch* dst, int dst_solve, agile_batch
  * launches walk a work list of the attached solves' blocks, so a solve joins or leaves at the
  * next step at the cost of rebuilding the descriptor tables (host, then one upload) and
  * capturing the step's CUDA graph again. Only when no hole fits and the pool is full does
- * attach allocate a new pool (the attached solves, this one and an eighth more) and copy the
+ * attach allocate a new pool (the attached solves, this one and a quarter more) and copy the
  * attached solves into it compactly; a detach that leaves a pool of more than 4096 blocks
- * less than two thirds used repacks it the same way to the attached solves and an eighth more, so
+ * less than 60% used repacks it the same way to the attached solves and a quarter more, so
  * the pool's capacity follows the attached solves in both directions. A
  * detached solve's index is reused by a later attach; using it otherwise returns
  * AGILE_EINVAL. An attached solve's state is zero until agile_batch_set_state or

@@ -428,6 +428,67 @@ __global__ void __launch_bounds__(256) regrid_kernel(const R* __restrict__ Uold,
   }
 }
 
+// ------------------------------------------------------------------------ recovery pass
+// Primitives and auxiliaries of every cell of U_s (the work list's blocks, 16 CTAs of one
+// z-plane each) and of its ghost slots (two CTAs of 256 cells each per slot) into W / WG,
+// laid out as U_s / the slots are. One recovery per stored cell: the same function the stage
+// kernel applies, on the same inputs, so the primitives are the same bit for bit. With
+// speeds non-null (the first stage of a step) it also reduces the CFL maxima of the leaf
+// cells per solve from these primitives, as the stage kernel's fused reduction would have
+// from the same state at the end of the previous step.
+template <template <typename> class PT, typename R>
+__global__ void __launch_bounds__(256) prim_pass_kernel(const R* __restrict__ U, R* __restrict__ W,
+                                                        const R* __restrict__ G, R* __restrict__ WG,
+                                                        const int* __restrict__ wl, int nwork,
+                                                        PhysParamsT<R> pp, int* status,
+                                                        const BlockDesc* __restrict__ bd,
+                                                        const int* __restrict__ solve_of,
+                                                        unsigned long long* speeds) {
+  using P = PT<R>;
+  constexpr int NV = P::NV, NA = P::NA, NT = NV + NA;
+  const int item = blockIdx.x;
+  const R* src;
+  R* dst;
+  int vs;
+  int b = -1;
+  if (item < nwork * 16) {
+    const int w = item >> 4, z = item & 15;
+    b = wl ? wl[w] : w;
+    const size_t off = (size_t)b * NT * NCELL + (size_t)z * 256 + threadIdx.x;
+    src = U + off;
+    dst = W + off;
+    vs = NCELL;
+  } else {
+    const int j = item - nwork * 16;          // slot j / 2, cells (j % 2) * 256 ..
+    const size_t off = (size_t)(j >> 1) * NT * 512 + (size_t)(j & 1) * 256 + threadIdx.x;
+    src = G + off;
+    dst = WG + off;
+    vs = 512;
+  }
+  R u[NT], p[NV], aux[NA > 0 ? NA : 1];
+#pragma unroll
+  for (int v = 0; v < NT; ++v) u[v] = src[(size_t)v * vs];
+  if constexpr (NA > 0) {
+#pragma unroll
+    for (int i = 0; i < NA; ++i) aux[i] = u[NV + i];
+  } else {
+    aux[0] = R(0);
+  }
+  int st = 0;
+  P::cons2prim(u, p, aux, pp, st);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) dst[(size_t)v * vs] = p[v];
+#pragma unroll
+  for (int i = 0; i < NA; ++i) dst[(size_t)(NV + i) * vs] = aux[i];
+  if (st) atomicOr(status, st);
+  if (speeds && b >= 0) {             // CTA-uniform: a pool plane, not a ghost slot
+    const R dxr[3] = {R(bd[b].dx[0]), R(bd[b].dx[1]), R(bd[b].dx[2])};
+    R ssum = R(0), smax = R(0);
+    prim_speeds<PT, R>(p, pp, dxr, ssum, smax);
+    block_max2<256>(ssum, smax, speeds + 2 * (solve_of ? solve_of[b] : 0));
+  }
+}
+
 // ------------------------------------------------------------------------------ state I/O
 template <template <typename> class PT, typename R>
 __global__ void prim2cons_kernel(R* __restrict__ U, const double* __restrict__ prim,
@@ -645,6 +706,31 @@ cudaError_t launch_regrid(const AuxArgs& a, void* Unew, const RegridSrc* src, in
   if (nnew == 0) return cudaSuccess;
 #define CALL(PT) regrid_kernel<PT, R><<<nnew, 256, 0, s>>>((const R*)a.U, (const R*)a.G, a.bd, (R*)Unew, src)
   AGILE_DISPATCH(a.phys, a.real_bytes, CALL);
+#undef CALL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prim_pass(const AuxArgs& a, void* W, void* WG, int nslots, unsigned long long* speeds,
+                             cudaStream_t s) {
+  const long long grid = 16LL * a.nblk + 2LL * nslots;
+  if (grid == 0) return cudaSuccess;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (a.phys != PH_SRHD && a.phys != PH_SRHD_SYNGE) return cudaErrorInvalidValue;
+#define CALL(PT)                                                                               \
+  do {                                                                                         \
+    PhysParamsT<R> pp;                                                                         \
+    pp.set(a.gamma, 0.0);                                                                      \
+    prim_pass_kernel<PT, R><<<(unsigned)grid, 256, 0, s>>>((const R*)a.U, (R*)W, (const R*)a.G, \
+                                                           (R*)WG, a.wl, a.nblk, pp, a.status,   \
+                                                           a.bd, a.solve_of, speeds);            \
+  } while (0)
+  if (a.phys == PH_SRHD) {
+    if (a.real_bytes == 8) { using R = double; CALL(SrhdPhys); }
+    else { using R = float; CALL(SrhdPhys); }
+  } else {
+    if (a.real_bytes == 8) { using R = double; CALL(SrhdSyngePhys); }
+    else { using R = float; CALL(SrhdSyngePhys); }
+  }
 #undef CALL
   return cudaGetLastError();
 }

@@ -53,6 +53,11 @@ struct agile_mesh {
   void* ic_user = nullptr;
   std::string err;
   CUtensorMap tmap[3];
+  // SRHD: primitives of the stage input from the recovery pass (pool and ghost slots) and
+  // the tensor map the stage kernel's TMA reads them through
+  void* W = nullptr;
+  void* WG = nullptr;
+  CUtensorMap tmapW;
   bool timing = false;
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_cat;          // phase of each event pair (PHASE_*)
@@ -284,8 +289,16 @@ agile_status rebuild(agile_mesh* m) {
   dfree(m, m->FR);
   dfree(m, m->U[1]);
   dfree(m, m->U[2]);
+  dfree(m, m->W);
+  dfree(m, m->WG);
   dfree_t(m, m->d_wl);
   const std::vector<int> order = slab_order(*m->mesh);
+  const bool prim_pass = phys_prim_pass(phys_kind(m->cfg));
+  if (prim_pass) {
+    m->W = dalloc(m, pool_bytes(m, m->nblk));
+    m->WG = dalloc(m, (size_t)std::max(nslots, 1) * m->nt * 512 * m->rb);
+    if (!m->W || !m->WG) return fail(m, AGILE_ENOMEM, "device allocation failed");
+  }
   m->d_wl = (int*)dalloc(m, order.size() * sizeof(int));
   m->d_bd = (BlockDesc*)dalloc(m, desc.size() * sizeof(BlockDesc));
   m->d_ghosts = (GhostTask*)dalloc(m, ghosts.size() * sizeof(GhostTask));
@@ -313,6 +326,8 @@ agile_status rebuild(agile_mesh* m) {
     agile_status s = make_tmap(m, m->U[i], &m->tmap[i]);
     if (s) return s;
   }
+  agile_status sw = make_tmap(m, m->W, &m->tmapW);
+  if (sw) return sw;
   return AGILE_OK;
 }
 
@@ -568,6 +583,8 @@ void agile_mesh_destroy(agile_mesh* m) {
   dfree(m, m->FR);
   dfree_t(m, m->d_bd);
   dfree_t(m, m->d_wl);
+  dfree(m, m->W);
+  dfree(m, m->WG);
   dfree_t(m, m->d_ghosts);
   dfree_t(m, m->d_fix);
   dfree_t(m, m->d_status);
@@ -655,11 +672,17 @@ agile_status agile_max_speeds(agile_mesh* m, double* sum_over_dx, double* cmax) 
 
 agile_status agile_step(agile_mesh* m, double dt) {
   if (!m) return AGILE_EINVAL;
-  agile_status s = ensure_speeds(m);
-  if (s) return s;
-  CK(m, launch_set_dt(m->d_speeds, m->d_dtch, dt, m->cfg.cfl, m->stream, 1, mesh_res_rate(m)));
+  // SRHD (a recovery pass before each stage): the first stage's pass also reduces the CFL
+  // maxima of U^n and dt is set after it, instead of a reduction at the end of the step
+  const bool lead = m->W != nullptr;
+  agile_status s = AGILE_OK;
+  if (!lead) {
+    s = ensure_speeds(m);
+    if (s) return s;
+    CK(m, launch_set_dt(m->d_speeds, m->d_dtch, dt, m->cfg.cfl, m->stream, 1, mesh_res_rate(m)));
+    m->total_launches++;
+  }
   CK(m, cudaMemsetAsync(m->d_work, 0, 4 * sizeof(int), m->stream));
-  m->total_launches++;
   const bool mhd = m->cfg.physics == AGILE_MHD_GLM;
   if (mhd) {
     AuxArgs a = aux_args(m, m->U[0]);
@@ -671,7 +694,7 @@ agile_status agile_step(agile_mesh* m, double dt) {
   const int nst = m->cfg.rk;
   const bool fuse = m->nfix == 0;
   const bool cool = m->cool.nseg > 0;
-  const bool speeds_in_stage = fuse && !cool;   // else the post-step pass reduces them
+  const bool speeds_in_stage = fuse && !cool && !lead;   // else the post-step pass reduces them
   if (cool) {                                   // first Strang half of the losses
     AuxArgs a = aux_args(m, m->U[0]);
     CK(m, launch_cooling(a, m->cool, m->d_cool, m->d_dtch, 0.5, nullptr, m->stream));
@@ -707,6 +730,19 @@ agile_status agile_step(agile_mesh* m, double dt) {
     A.solve_of = nullptr;
     A.work = m->d_work + st;
     cudaEvent_t e0 = phase_begin(m);
+    if (m->W) {                      // one recovery per stored cell, read by the stage kernel
+      AuxArgs pa = aux_args(m, Us);
+      if (st == 0) CK(m, cudaMemsetAsync(m->d_speeds, 0, 2 * sizeof(unsigned long long), m->stream));
+      CK(m, launch_prim_pass(pa, m->W, m->WG, m->nslots, st == 0 ? m->d_speeds : nullptr, m->stream));
+      m->total_launches++;
+      if (st == 0) {
+        CK(m, launch_set_dt(m->d_speeds, m->d_dtch, dt, m->cfg.cfl, m->stream, 1, mesh_res_rate(m)));
+        m->total_launches++;
+      }
+      A.W = m->W;
+      A.WG = m->WG;
+      A.tmap = &m->tmapW;
+    }
     cudaError_t e;
     if (m->cfg.physics == AGILE_HD) e = launch_stage_hd(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
     else if (mhd && m->cfg.eta > 0.0) e = launch_stage_mhd_res(m->rb, m->cfg.limiter, m->cfg.flux, A, m->stream);
@@ -740,6 +776,8 @@ agile_status agile_step(agile_mesh* m, double dt) {
     CK(m, launch_cooling(a, m->cool, m->d_cool, m->d_dtch, 0.5, m->d_speeds, m->stream));
     m->total_launches++;
     m->speeds_valid = true;
+  } else if (lead) {
+    m->speeds_valid = false;                   // the next step's first pass reduces them
   } else if (fuse) {
     m->speeds_valid = true;
   } else {
@@ -1110,6 +1148,9 @@ struct agile_batch {
   int* d_wl = nullptr;
   int nwork = 0;
   int tab_cap = 0;                  // blocks d_bd, d_solve_of and d_wl hold (the capacity)
+  void* W = nullptr;                // SRHD: primitives of the stage input (capacity blocks),
+  void* WG = nullptr;               // of its ghost slots, and the tensor map over W
+  CUtensorMap tmapW;
   // Host-to-device uploads of membership changes and initial states go through device
   // buffers written on their own stream: a copy from pageable host memory returns only when
   // it has been carried out, so on the batch stream it would wait for every step already
@@ -1123,6 +1164,8 @@ struct agile_batch {
   };
   std::vector<Upload> uploads;
   size_t upload_bytes = 0;          // bytes of the upload buffers not yet released
+  std::vector<Upload> upload_free;  // released buffers kept for reuse by later uploads
+  size_t upload_free_bytes = 0;
 };
 
 // Upload buffers held at once (bytes): past this, a new upload first waits for the oldest
@@ -1181,8 +1224,26 @@ AuxArgs batch_aux(agile_batch* B, void* U) {
 
 agile_status batch_status(agile_batch* B);
 
-// Release the upload buffers whose readers have run (all of them with wait = true, after
-// the batch stream has been synchronised).
+// A released upload buffer: kept for reuse while the kept ones stay within the bound, else
+// freed (largest first).
+void batch_keep_upload(agile_batch* B, void* p, size_t bytes) {
+  agile_mesh view;
+  as_mesh_view(B, &view);
+  view.stream = B->up_stream;
+  B->upload_free.push_back({p, bytes, nullptr});
+  B->upload_free_bytes += bytes;
+  while (B->upload_free_bytes > UPLOAD_HELD_MAX && !B->upload_free.empty()) {
+    size_t big = 0;
+    for (size_t i = 1; i < B->upload_free.size(); ++i)
+      if (B->upload_free[i].bytes > B->upload_free[big].bytes) big = i;
+    dfree(&view, B->upload_free[big].p);
+    B->upload_free_bytes -= B->upload_free[big].bytes;
+    B->upload_free.erase(B->upload_free.begin() + big);
+  }
+}
+
+// Release the upload buffers whose readers have run (all of them, and the kept ones too,
+// with wait = true, after the batch stream has been synchronised).
 void batch_reap_uploads(agile_batch* B, bool wait) {
   agile_mesh view;
   as_mesh_view(B, &view);
@@ -1192,14 +1253,20 @@ void batch_reap_uploads(agile_batch* B, bool wait) {
     agile_batch::Upload& u = B->uploads[i];
     if (wait || cudaEventQuery(u.done) == cudaSuccess) {
       if (wait) cudaEventSynchronize(u.done);
-      dfree(&view, u.p);
       cudaEventDestroy(u.done);
       B->upload_bytes -= u.bytes;
+      if (wait) dfree(&view, u.p);
+      else batch_keep_upload(B, u.p, u.bytes);
     } else {
       B->uploads[k++] = u;
     }
   }
   B->uploads.resize(k);
+  if (wait) {
+    for (agile_batch::Upload& u : B->upload_free) dfree(&view, u.p);
+    B->upload_free.clear();
+    B->upload_free_bytes = 0;
+  }
 }
 
 // Wait for the oldest upload buffers' readers until `bytes` more stay within the bound.
@@ -1208,20 +1275,23 @@ void batch_bound_uploads(agile_batch* B, size_t bytes) {
   as_mesh_view(B, &view);
   view.stream = B->up_stream;
   size_t k = 0;
+  std::vector<agile_batch::Upload> done;
   while (k < B->uploads.size() && B->upload_bytes + bytes > UPLOAD_HELD_MAX) {
     agile_batch::Upload& u = B->uploads[k++];   // oldest first: recorded in stream order
     cudaEventSynchronize(u.done);
-    dfree(&view, u.p);
     cudaEventDestroy(u.done);
     B->upload_bytes -= u.bytes;
+    done.push_back(u);
   }
   B->uploads.erase(B->uploads.begin(), B->uploads.begin() + k);
+  for (const agile_batch::Upload& u : done) batch_keep_upload(B, u.p, u.bytes);
 }
 
-// Copy `bytes` of host memory into a new device buffer on the upload stream (not behind the
+// Copy `bytes` of host memory into a device buffer on the upload stream (not behind the
 // batch stream's enqueued work) and make the batch stream wait for the copy. The caller
-// enqueues the buffer's readers on the batch stream, then calls batch_upload_done.
-void* batch_upload(agile_batch* B, const void* src, size_t bytes, agile_status* st) {
+// enqueues the buffer's readers on the batch stream, then calls batch_upload_done with the
+// buffer's size (*size_out, at least `bytes`).
+void* batch_upload(agile_batch* B, const void* src, size_t bytes, agile_status* st, size_t* size_out) {
   *st = AGILE_OK;
   batch_reap_uploads(B, false);
   batch_bound_uploads(B, bytes);
@@ -1232,11 +1302,26 @@ void* batch_upload(agile_batch* B, const void* src, size_t bytes, agile_status* 
   agile_mesh view;
   as_mesh_view(B, &view);
   view.stream = B->up_stream;
-  void* p = dalloc(&view, bytes);
+  // the smallest kept buffer that holds the upload (at most twice its size), else a new one
+  void* p = nullptr;
+  size_t fit = (size_t)-1, cap_bytes = bytes;
+  for (size_t i = 0; i < B->upload_free.size(); ++i) {
+    const size_t c = B->upload_free[i].bytes;
+    if (c >= bytes && c / 2 <= bytes && (fit == (size_t)-1 || c < B->upload_free[fit].bytes)) fit = i;
+  }
+  if (fit != (size_t)-1) {
+    p = B->upload_free[fit].p;
+    cap_bytes = B->upload_free[fit].bytes;
+    B->upload_free_bytes -= cap_bytes;
+    B->upload_free.erase(B->upload_free.begin() + fit);
+  } else {
+    p = dalloc(&view, bytes);
+  }
   if (!p) {
     *st = bfail(B, AGILE_ENOMEM, "device allocation failed");
     return nullptr;
   }
+  if (size_out) *size_out = cap_bytes;
   cudaEvent_t ev = nullptr;
   cudaError_t e = cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, B->up_stream);
   // the host source may be released on return, pinned or not: wait for this copy alone
@@ -1392,14 +1477,23 @@ agile_status batch_rebuild(agile_batch* B) {
   dfree_t(&view, B->d_fix);
   dfree(&view, B->G);
   dfree(&view, B->FR);
+  const bool prim_pass = phys_prim_pass(phys_kind(B->cfg));
   if (B->cap_stage != B->cap) {
     dfree(&view, B->U[1]);
     dfree(&view, B->U[2]);
+    dfree(&view, B->W);
     const size_t pool = (size_t)B->cap * B->nt * NCELL * B->rb;
     B->U[1] = dalloc(&view, pool);
     B->U[2] = B->cfg.rk == 3 ? dalloc(&view, pool) : nullptr;
-    if (!B->U[1] || (B->cfg.rk == 3 && !B->U[2])) return bfail(B, AGILE_ENOMEM, "device allocation failed");
+    if (prim_pass) B->W = dalloc(&view, std::max(pool, (size_t)1));
+    if (!B->U[1] || (B->cfg.rk == 3 && !B->U[2]) || (prim_pass && !B->W))
+      return bfail(B, AGILE_ENOMEM, "device allocation failed");
     B->cap_stage = B->cap;
+  }
+  dfree(&view, B->WG);
+  if (prim_pass) {
+    B->WG = dalloc(&view, (size_t)std::max(slots, 1) * B->nt * 512 * B->rb);
+    if (!B->WG) return bfail(B, AGILE_ENOMEM, "device allocation failed");
   }
   B->nblk = extent;
   B->nwork = (int)work.size();
@@ -1441,6 +1535,7 @@ agile_status batch_rebuild(agile_batch* B) {
   for (int i = 0; i < 3; ++i) {
     if (B->U[i] && make_tmap(&view, B->U[i], &B->tmap[i]) != AGILE_OK) return bfail(B, AGILE_ECUDA, "tensor map");
   }
+  if (make_tmap(&view, B->W, &B->tmapW) != AGILE_OK) return bfail(B, AGILE_ECUDA, "tensor map");
   if (B->graph) {                   // the captured step refers to the old tables
     cudaGraphExecDestroy(B->graph);
     B->graph = nullptr;
@@ -1617,7 +1712,8 @@ agile_status batch_ensure_speeds(agile_batch* B) {
 
 // Enqueue one full step of every solve (device dt) on the batch stream.
 agile_status batch_enqueue_step(agile_batch* B) {
-  BCK(B, launch_set_dt(B->d_speeds, B->d_dtch, 0.0, B->cfg.cfl, B->stream, B->nsolve));
+  const bool lead = B->W != nullptr;  // SRHD: dt after the first stage's recovery pass (agile_step)
+  if (!lead) BCK(B, launch_set_dt(B->d_speeds, B->d_dtch, 0.0, B->cfg.cfl, B->stream, B->nsolve));
   BCK(B, cudaMemsetAsync(B->d_work, 0, 4 * sizeof(int), B->stream));
   const bool mhd = B->cfg.physics == AGILE_MHD_GLM;
   if (mhd) {
@@ -1635,7 +1731,7 @@ agile_status batch_enqueue_step(agile_batch* B) {
       AuxArgs ga = batch_aux(B, Us);
       BCK(B, launch_ghosts(ga, B->d_ghosts, B->nghost, B->stream));
     }
-    if (last) BCK(B, cudaMemsetAsync(B->d_speeds, 0, 2 * sizeof(unsigned long long) * B->nsolve, B->stream));
+    if (last && !lead) BCK(B, cudaMemsetAsync(B->d_speeds, 0, 2 * sizeof(unsigned long long) * B->nsolve, B->stream));
     StageArgs A;
     A.Us = Us;
     A.Un = B->U[0];
@@ -1653,12 +1749,21 @@ agile_status batch_enqueue_step(agile_batch* B) {
     A.nblk = B->nwork;
     A.wl = B->d_wl;
     A.status = B->d_status;
-    A.speeds = (last && fuse) ? B->d_speeds : nullptr;
+    A.speeds = (last && fuse && !lead) ? B->d_speeds : nullptr;
     A.tmap = &B->tmap[st == 0 ? 0 : st];
     A.solve_of = B->d_solve_of;
     A.work = B->dynamic ? B->d_work + st : nullptr;
     A.grid = B->grid;
     A.layout = B->layout;
+    if (B->W) {                       // one recovery per stored cell, read by the stage kernel
+      AuxArgs pa = batch_aux(B, Us);
+      if (st == 0) BCK(B, cudaMemsetAsync(B->d_speeds, 0, 2 * sizeof(unsigned long long) * B->nsolve, B->stream));
+      BCK(B, launch_prim_pass(pa, B->W, B->WG, B->nslots, st == 0 ? B->d_speeds : nullptr, B->stream));
+      if (st == 0) BCK(B, launch_set_dt(B->d_speeds, B->d_dtch, 0.0, B->cfg.cfl, B->stream, B->nsolve));
+      A.W = B->W;
+      A.WG = B->WG;
+      A.tmap = &B->tmapW;
+    }
     cudaError_t e;
     if (B->cfg.physics == AGILE_HD) e = launch_stage_hd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
     else if (mhd) e = launch_stage_mhd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
@@ -1677,7 +1782,7 @@ agile_status batch_enqueue_step(agile_batch* B) {
   if (!fuse) {                        // after the last fix-up: GLM half, then the CFL speeds
     AuxArgs a = batch_aux(B, B->U[0]);
     if (mhd) BCK(B, launch_glm_decay(a, B->d_dtch, B->stream));
-    BCK(B, launch_speeds(a, B->d_speeds, B->stream));
+    if (!lead) BCK(B, launch_speeds(a, B->d_speeds, B->stream));
   }
   return AGILE_OK;
 }
@@ -1685,12 +1790,16 @@ agile_status batch_enqueue_step(agile_batch* B) {
 // One launch of the first stage (U^n -> the stage-1 buffer; the solution is not modified).
 agile_status batch_stage1(agile_batch* B, int grid, bool dynamic, int layout) {
   if (dynamic) BCK(B, cudaMemsetAsync(B->d_work, 0, sizeof(int), B->stream));
+  if (B->nghost) {                    // coarse-fine halos of U^n, as the first stage reads them
+    AuxArgs ga = batch_aux(B, B->U[0]);
+    BCK(B, launch_ghosts(ga, B->d_ghosts, B->nghost, B->stream));
+  }
   StageArgs A;
   A.Us = B->U[0];
   A.Un = B->U[0];
   A.Uout = B->U[1];
   A.bd = B->d_bd;
-  A.gs = nullptr;
+  A.gs = B->G;
   A.fr = nullptr;
   A.dtch = B->d_dtch;
   A.a = 0.0;
@@ -1708,6 +1817,13 @@ agile_status batch_stage1(agile_batch* B, int grid, bool dynamic, int layout) {
   A.work = dynamic ? B->d_work : nullptr;
   A.grid = grid;
   A.layout = layout;
+  if (B->W) {
+    AuxArgs pa = batch_aux(B, B->U[0]);
+    BCK(B, launch_prim_pass(pa, B->W, B->WG, B->nslots, nullptr, B->stream));
+    A.W = B->W;
+    A.WG = B->WG;
+    A.tmap = &B->tmapW;
+  }
   cudaError_t e;
   const bool mhd = B->cfg.physics == AGILE_MHD_GLM;
   if (B->cfg.physics == AGILE_HD) e = launch_stage_hd(B->rb, B->cfg.limiter, B->cfg.flux, A, B->stream);
@@ -1906,6 +2022,8 @@ void agile_batch_destroy(agile_batch* B) {
   dfree_t(&view, B->d_fix);
   dfree(&view, B->G);
   dfree(&view, B->FR);
+  dfree(&view, B->W);
+  dfree(&view, B->WG);
   cudaStreamSynchronize(B->stream);
   batch_reap_uploads(B, true);
   if (B->up_stream) {
@@ -1967,19 +2085,20 @@ agile_status agile_batch_set_state_prims(agile_batch* B, int solve, const double
   char* base = (char*)B->U[0] + (size_t)B->offset[solve] * B->nt * NCELL * B->rb;
   agile_status s = AGILE_OK;
   const size_t pbytes = nblk * B->nv * NCELL * sizeof(double), lbytes = nblk * sizeof(int);
-  void* d_prim = batch_upload(B, prim, pbytes, &s);
+  size_t pcap = 0, lcap = 0;
+  void* d_prim = batch_upload(B, prim, pbytes, &s, &pcap);
   if (!d_prim) return s;
-  void* d_local = batch_upload(B, local.data(), lbytes, &s);
+  void* d_local = batch_upload(B, local.data(), lbytes, &s, &lcap);
   if (!d_local) {
-    batch_upload_done(B, d_prim, pbytes);
+    batch_upload_done(B, d_prim, pcap);
     return s;
   }
   view.nblk = (int)nblk;
   AuxArgs a = aux_args(&view, base);
   const cudaError_t e = launch_prim2cons(a, (const double*)d_prim, (const int*)d_local, (int)nblk, B->stream);
   view.mesh = nullptr;
-  s = batch_upload_done(B, d_prim, pbytes);
-  const agile_status s2 = batch_upload_done(B, d_local, lbytes);
+  s = batch_upload_done(B, d_prim, pcap);
+  const agile_status s2 = batch_upload_done(B, d_local, lcap);
   if (e != cudaSuccess) return bfail(B, AGILE_ECUDA, std::string("prim2cons: ") + cudaGetErrorString(e));
   if (s) return s;
   if (s2) return s2;
@@ -1991,7 +2110,7 @@ agile_status agile_batch_set_state_prims(agile_batch* B, int solve, const double
 
 agile_status agile_batch_step(agile_batch* B) {
   if (!B) return AGILE_EINVAL;
-  agile_status s = batch_ensure_speeds(B);
+  agile_status s = B->W ? AGILE_OK : batch_ensure_speeds(B);   // SRHD: the first pass reduces them
   if (s) return s;
   if (B->steps_done == 0) {   // first step eagerly: sets kernel attributes outside any capture
     s = batch_enqueue_step(B);
@@ -2016,9 +2135,11 @@ agile_status agile_batch_step(agile_batch* B) {
     BCK(B, cudaGraphLaunch(B->graph, B->stream));
   }
   B->launches += B->cfg.rk + 1 + (B->cfg.physics == AGILE_MHD_GLM ? 1 : 0) +
-                 (B->nghost ? B->cfg.rk : 0) + (B->nfix ? B->cfg.rk + 1 + (B->cfg.physics == AGILE_MHD_GLM ? 1 : 0) : 0);
+                 (B->nghost ? B->cfg.rk : 0) +
+                 (B->nfix ? B->cfg.rk + (B->W ? 0 : 1) + (B->cfg.physics == AGILE_MHD_GLM ? 1 : 0) : 0) +
+                 (B->W ? B->cfg.rk : 0);
   B->steps_done++;
-  B->speeds_valid = true;
+  B->speeds_valid = B->W == nullptr;   // SRHD: U^{n+1}'s maxima come with the next step's first pass
   return AGILE_OK;
 }
 
@@ -2186,7 +2307,8 @@ bool batch_patch(agile_batch* B, int solve, bool attach, agile_status* st) {
   memcpy(h.data(), d.data(), bd_bytes);
   memcpy(h.data() + bd_bytes, so.data(), so_bytes);
   memcpy(h.data() + bd_bytes + so_bytes, work.data(), wl_bytes);
-  char* dev = (char*)batch_upload(B, h.data(), h.size(), st);
+  size_t dcap = 0;
+  char* dev = (char*)batch_upload(B, h.data(), h.size(), st, &dcap);
   if (!dev) return true;
   auto cp = [&](void* dst, const char* src, size_t bytes) {
     if (!bytes || *st) return;
@@ -2196,7 +2318,7 @@ bool batch_patch(agile_batch* B, int solve, bool attach, agile_status* st) {
   cp(B->d_bd + O, dev, bd_bytes);
   cp(B->d_solve_of + O, dev + bd_bytes, so_bytes);
   cp(B->d_wl, dev + bd_bytes + so_bytes, wl_bytes);
-  const agile_status sd = batch_upload_done(B, dev, h.size());
+  const agile_status sd = batch_upload_done(B, dev, dcap);
   if (!*st) *st = sd;
   if (*st) return true;
   B->nwork = (int)work.size();
@@ -2281,11 +2403,11 @@ agile_status agile_batch_attach(agile_batch* B, const agile_config* cfg, int* so
   as_mesh_view(B, &view);
   const size_t per = (size_t)B->nt * NCELL * B->rb;
   if (at < 0) {
-    // grow: a new pool with room for this solve and an eighth more, the live solves copied
+    // grow: a new pool with room for this solve and a quarter more, the live solves copied
     // into it compactly
     int live_blocks = 0;
     for (const auto& r : ranges) live_blocks += r.second;
-    s = batch_repool(B, live_blocks + n + std::max(n, (live_blocks + n) / 8), &at);
+    s = batch_repool(B, live_blocks + n + std::max(n, (live_blocks + n) / 4), &at);
     if (s) return s;
   }
   if (idx < 0) {
@@ -2322,12 +2444,12 @@ agile_status agile_batch_detach(agile_batch* B, int solve) {
   B->ics[solve] = nullptr;
   B->ic_users[solve] = nullptr;
   if (s) return s;
-  // a pool less than two thirds used shrinks to its live blocks and an eighth more, so that
-  // the capacity follows the attached solves down as well as up (at most 1.5 times them)
+  // a pool less than 60% used shrinks to its live blocks and a quarter more, so that the
+  // capacity follows the attached solves down as well as up (at most 1/0.6 times them)
   int live_blocks = 0;
   for (int i = 0; i < B->nsolve; ++i) live_blocks += solve_blocks(B, i);
-  if (B->cap > 4096 && 3LL * live_blocks < 2LL * B->cap) {
-    s = batch_repool(B, live_blocks + live_blocks / 8, nullptr);
+  if (B->cap > 4096 && 5LL * live_blocks < 3LL * B->cap) {
+    s = batch_repool(B, live_blocks + live_blocks / 4, nullptr);
     if (s) return s;
     return batch_rebuild(B);
   }

@@ -36,7 +36,11 @@ struct StageArgs {
   int nblk;
   int* status;
   unsigned long long* speeds;   // fused reduction of [max sum_d s_d/dx_d, max s_d] per solve, or nullptr
-  const void* tmap;             // host CUtensorMap of the pool Us (x, y, z, block*var)
+  const void* tmap;             // host CUtensorMap of the pool Us, or of W for a physics with a
+                                // primitive-recovery pass (x, y, z, block*var)
+  const void* W = nullptr;      // primitives (and auxiliaries) of Us, per block as Us, from the
+                                // recovery pass (physics with prim_pass_of), else unused
+  const void* WG = nullptr;     // the same for the ghost slots
   const int* solve_of;          // solve index of each block (batched solves), nullptr = one solve
   int* work;                    // block counter of this launch (zeroed before it), dynamic scheduling
   int grid = 0;                 // persistent CTAs of the launch (0: CTAs-per-SM target x SMs)
@@ -108,11 +112,9 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long* addr, double 
 // ssum = max sum_d s_d / dx_d and smax = max_d s_d are accumulated in R (a maximum is exact
 // in any precision; the caller widens the result to FP64 once). dxr = dx rounded to R.
 template <template <typename> class PT, typename R>
-__device__ __forceinline__ void cell_speeds(const R* u, R* aux, const PhysParamsT<R>& pp,
-                                            const R* dxr, R& ssum, R& smax, int& st) {
+__device__ __forceinline__ void prim_speeds(const R* p, const PhysParamsT<R>& pp, const R* dxr, R& ssum,
+                                            R& smax) {
   using P = PT<R>;
-  R p[P::NV];
-  P::cons2prim(u, p, aux, pp, st);
   R lm, lp;
   P::template lambdas<0>(p, lm, lp, pp);
   const R s0 = rmax(rabs(lm), rabs(lp));
@@ -123,6 +125,15 @@ __device__ __forceinline__ void cell_speeds(const R* u, R* aux, const PhysParams
   smax = rmax(smax, rmax(rmax(s0, s1), s2));
   const R acc = (s0 / dxr[0] + s1 / dxr[1]) + s2 / dxr[2];
   ssum = rmax(ssum, acc);
+}
+// The same from the conserved values (and auxiliaries) of the cell.
+template <template <typename> class PT, typename R>
+__device__ __forceinline__ void cell_speeds(const R* u, R* aux, const PhysParamsT<R>& pp,
+                                            const R* dxr, R& ssum, R& smax, int& st) {
+  using P = PT<R>;
+  R p[P::NV];
+  P::cons2prim(u, p, aux, pp, st);
+  prim_speeds<PT, R>(p, pp, dxr, ssum, smax);
 }
 
 // Maxima of a and b over the CTA, widened to FP64 once and merged into out[0..1] (non-negative
@@ -317,8 +328,11 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
                                                            StageArgs A) {
   static_assert(RAW >= 3 && RAW <= 5, "three to five raw slots");
   static_assert((RAW == 4) == (SFB == 1), "one flux buffer with four raw slots, two with three or five");
-  constexpr bool US_GLOBAL = RAW == 3;   // the update reads U_s of its cell from global memory
   using P = PT<R>;
+  // primitives come from a recovery pass of their own (A.W, A.WG, and the tensor map over
+  // A.W): the ring is filled with them as they are, and the update reads U_s from global
+  constexpr bool PRIMIN = prim_pass_of<P>::value;
+  constexpr bool US_GLOBAL = RAW == 3 || PRIMIN;   // the update reads U_s of its cell from global memory
   using S = StageSmem<PT, R, RAW, SFB>;
   constexpr int NV = P::NV, NA = P::NA, NT = NV + NA;
   // FP32 HD / MHD with HLL or TVDLF: x- and y-faces solved as packed pairs
@@ -339,6 +353,9 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   R* __restrict__ Uo = static_cast<R*>(A.Uout);
   const R* __restrict__ G = static_cast<const R*>(A.gs);
   R* __restrict__ FR = static_cast<R*>(A.fr);
+  // what the ring is filled from: U_s and its ghost slots, or their primitives
+  const R* __restrict__ Rs = PRIMIN ? static_cast<const R*>(A.W) : Us;
+  const R* __restrict__ Rg = PRIMIN ? static_cast<const R*>(A.WG) : G;
 
   const int t = threadIdx.x;
   const int tx = t & 15, ty = t >> 4;
@@ -486,7 +503,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
 #pragma unroll
       for (int v = 0; v < NT; ++v) u[v] = r[v * 256];
     } else {
-      load_cell<P, R>(Us, G, src, b, tx, ty, p, u);
+      load_cell<P, R>(Rs, Rg, src, b, tx, ty, p, u);
     }
     R pr[NV], aux[NAW];
     if constexpr (NA > 0) {
@@ -495,7 +512,12 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     } else {
       aux[0] = R(0);
     }
-    P::cons2prim(u, pr, aux, pp, st);
+    if constexpr (PRIMIN) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) pr[v] = u[v];
+    } else {
+      P::cons2prim(u, pr, aux, pp, st);
+    }
     R* w = ring(p) + cellp;
 #pragma unroll
     for (int v = 0; v < NV; ++v) w[v * 400] = pr[v];
@@ -507,11 +529,11 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
   // Halo source of this thread's halo cell: the address at plane 0 and the step per plane
   // (a plane of a block pool, or a row of a ghost slot), formed once per block.
   int hvs, hnd;
-  const R* ha0 = cell_addr<P, R>(Us, G, src, b, hx, hy, 0, &hvs, &hnd);
+  const R* ha0 = cell_addr<P, R>(Rs, Rg, src, b, hx, hy, 0, &hvs, &hnd);
   ptrdiff_t hinc;
   {
     int vs1, nd1;
-    hinc = cell_addr<P, R>(Us, G, src, b, hx, hy, 1, &vs1, &nd1) - ha0;
+    hinc = cell_addr<P, R>(Rs, Rg, src, b, hx, hy, 1, &vs1, &nd1) - ha0;
   }
   auto halo_mine = [&](int p) { return (t >> 7) == (p & 1); };
   auto prefetch_halo = [&](int p) {       // raw values of the halo of plane p into its frame
@@ -524,7 +546,16 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
     }
   };
   auto convert_halo = [&](int p) {        // the same thread's fetch, converted in place
-    if (halo_mine(p)) {
+    if (PRIMIN && halo_mine(p)) {          // primitives already: a reflecting face's image only
+      cp_async_wait_all();
+      R* d = ring(p) + hoff;
+      if constexpr (P::IV >= 0) {
+        if (hnd >= 0) d[(P::IV + hnd) * 400] = -d[(P::IV + hnd) * 400];
+      }
+      if constexpr (P::BOFF >= 0) {
+        if (hnd >= 0) d[(P::BOFF + hnd) * 400] = -d[(P::BOFF + hnd) * 400];
+      }
+    } else if (halo_mine(p)) {
       cp_async_wait_all();
       R* d = ring(p) + hoff;
       R u[NT], pr[NV], aux[NAW];

@@ -40,6 +40,14 @@ struct AuxArgs {
   const int* wl = nullptr;
 };
 
+// Whether the stage kernel of a physics reads primitives from the recovery pass (SRHD).
+inline bool phys_prim_pass(int phys) { return phys == PH_SRHD || phys == PH_SRHD_SYNGE; }
+// Recovery pass before a stage launch: primitives and auxiliaries of a.U (the a.nblk work
+// items of a.wl) into W and of the nslots ghost slots a.G into WG, with the same layouts;
+// with speeds non-null also the CFL maxima of a.U per solve (a.solve_of), merged into
+// speeds[solve][2] (the caller zeroes them).
+cudaError_t launch_prim_pass(const AuxArgs& a, void* W, void* WG, int nslots, unsigned long long* speeds,
+                             cudaStream_t s);
 // Fill ghost slots of coarse-fine faces from U (restriction / limited prolongation).
 cudaError_t launch_ghosts(const AuxArgs& a, const GhostTask* tasks, int ntasks, cudaStream_t s);
 // Coarse-fine flux correction of the stage output a.Uw with stage weight b and dt.

@@ -272,6 +272,19 @@ struct res_of<P, std::void_t<decltype(P::RES)>> {
   static constexpr bool value = P::RES;
 };
 
+// Whether a trait's primitive recovery is costly enough (an iteration) to be done once per
+// cell in a pass of its own before the stage kernel, which then reads primitives: the stage
+// kernel would otherwise recover each stored cell 1.75 times (own z-halo planes, x/y halo
+// cells of the neighbours).
+template <class P, class = void>
+struct prim_pass_of {
+  static constexpr bool value = false;
+};
+template <class P>
+struct prim_pass_of<P, std::void_t<decltype(P::PRIM_PASS)>> {
+  static constexpr bool value = P::PRIM_PASS;
+};
+
 // ------------------------------------------------------------------------------ SRHD
 enum : int { EOS_IDEAL = 0, EOS_SYNGE = 1 };
 
@@ -296,6 +309,7 @@ template <typename R, int EOS>
 struct SrhdPhysE {
   static constexpr int NV = 5;   // D, m, tau ; primitives rho, u = Gamma v, p
   static constexpr int NA = 2;   // xi = Gamma^2 rho h, Gamma
+  static constexpr bool PRIM_PASS = true;   // the Newton recovery runs once per cell
   static constexpr int BOFF = -1;
   static constexpr int IV = 1;
   static constexpr int NREC = NV;

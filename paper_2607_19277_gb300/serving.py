@@ -285,18 +285,21 @@ class BatchedServer:
     Initial conditions are prepared ahead by worker threads as for Server."""
 
     def __init__(self, budget_bytes: int, real_bytes: int = 4, keep_results: bool = False,
-                 prepare_workers: int = 8, max_prepared: int = 16):
+                 prepare_workers: int = 8, max_prepared: int = 16, steps_in_flight: int = 3):
+        import torch
+        self.torch = torch
         self.budget = int(budget_bytes)
         self.rb = real_bytes
         self.keep = keep_results
         self.workers = prepare_workers
         self.max_prepared = max_prepared
+        self.depth = steps_in_flight
 
     def run(self, requests, time_scale: float = 1.0, max_wall_s: float = 3600.0) -> Report:
         """Serve `requests`; the budget counts the pools of every attached solve."""
         prep = _Preparer(self.workers, self.max_prepared, self.rb)
         self.stats = {"joins": 0, "leaves": 0, "join_s": 0.0, "upload_s": 0.0, "leave_s": 0.0}
-        groups = {p: {"batch": None, "members": {}} for p in PHYS}
+        groups = {p: {"batch": None, "members": {}, "stream": None, "inflight": []} for p in PHYS}
         try:
             rep = self._loop(requests, time_scale, max_wall_s, prep, groups)
         finally:
@@ -317,7 +320,8 @@ class BatchedServer:
         t0 = time.perf_counter()
         cfg = scheme(r.physics, self.rb, r.side)
         if g["batch"] is None:
-            g["batch"] = agile.Batch([cfg])
+            g["stream"] = self.torch.cuda.Stream()
+            g["batch"] = agile.Batch([cfg], stream=g["stream"])
             idx = 0
         else:
             idx = g["batch"].attach(cfg)
@@ -338,6 +342,7 @@ class BatchedServer:
     def _loop(self, requests, time_scale, max_wall_s, prep, groups):
         pending = sorted(requests, key=lambda r: r.arrival)
         waiting = []
+        finishing = []                     # (request, event after its last step)
         used = max_used = max_conc = 0
         zones = 0.0
         t0 = time.perf_counter()
@@ -346,7 +351,7 @@ class BatchedServer:
         def attached():
             return sum(len(g["members"]) for g in groups.values())
 
-        while k < len(pending) or waiting or attached():
+        while k < len(pending) or waiting or attached() or finishing:
             now = time.perf_counter() - t0
             if now > max_wall_s:
                 raise TimeoutError("serving loop exceeded %.0f s" % max_wall_s)
@@ -373,25 +378,42 @@ class BatchedServer:
             for g in groups.values():
                 if not g["members"]:
                     continue
+                # at most `depth` steps of a batch enqueued ahead of the GPU, so that a new
+                # arrival joins within a few steps and its upload's reader runs soon
+                fl = g["inflight"]
+                while fl and fl[0].query():
+                    fl.pop(0)
+                if len(fl) >= self.depth:
+                    continue
                 b = g["batch"]
                 b.step()
+                ev = self.torch.cuda.Event()
+                ev.record(g["stream"])
+                fl.append(ev)
                 stepped = True
                 for idx in list(g["members"]):
                     m = g["members"][idx]
                     m[1] -= 1
                     if m[1] == 0:
                         r = m[0]
-                        lev, ijk, cons = b.get_state(idx)
                         if self.keep:
-                            r.result = cons
-                        r.finished = time.perf_counter() - t0
+                            r.result = b.get_state(idx)[2]      # synchronises
+                        finishing.append((r, ev))
                         stages = 2 if r.physics == "srhd" else 3
                         zones += float(r.side ** 3) * stages * r.steps
+                        # its pool range is reused only in stream order, after this step
                         self._leave(g, idx)
                         used -= pool_bytes(r, self.rb)
+            still = []
+            for r, ev in finishing:            # a request finishes when its last step has run
+                if ev.query():
+                    r.finished = time.perf_counter() - t0
+                else:
+                    still.append((r, ev))
+            finishing = still
             if not stepped:
-                if waiting:
-                    time.sleep(0.0005)         # preparations in flight
+                if waiting or finishing or attached():
+                    time.sleep(0.0005)         # preparations or steps in flight
                 elif k < len(pending):
                     time.sleep(max(0.0, pending[k].arrival * time_scale - (time.perf_counter() - t0)))
         wall = time.perf_counter() - t0

@@ -161,7 +161,7 @@ def test_uniform_solves_come_and_go_beside_a_refined_one():
 
 
 def test_pool_repacks_when_half_empty_and_grows_again():
-    """Detaching solves until a pool of more than 4096 blocks is less than two thirds used
+    """Detaching solves until a pool of more than 4096 blocks is less than 60% used
     repacks it (the live solves copied into a smaller pool), a later attach grows it again; the solves that stay equal
     their runs alone bit for bit throughout."""
     cfg = agile.make_config(physics="hd", limiter="vanleer", flux="tvdlf", rk=3, real_bytes=4,
@@ -181,11 +181,11 @@ def test_pool_repacks_when_half_empty_and_grows_again():
                 m.step(0.0)
 
     both(1)
-    for i in range(10):            # the fourth detach leaves 3072 of 5120 blocks: repacked
-        if i not in keep:          # into 3456 blocks; the next two leave holes
+    for i in range(10):            # the fifth detach leaves 2560 of 5120 blocks: repacked
+        if i not in keep:          # into 3200 blocks; the sixth leaves a hole
             b.detach(i)
     both(2)
-    for seed in (350, 351, 352):   # two attachments fill the holes, the third grows the pool
+    for seed in (350, 351, 352):   # into the hole, after the last solve, then the pool grows
         j = b.attach(cfg)
         b.set_state(j, W.random_smooth(5, seed, "hd"))
         keep[j] = agile.Mesh(cfg)

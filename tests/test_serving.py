@@ -45,6 +45,43 @@ def test_serving_admits_within_budget_overlaps_and_matches_alone():
         assert np.array_equal(r.result, alone), r.rid
 
 
+class FakeEvent:
+    """A CUDA event stand-in that completes after `lag` queries (0: at once)."""
+    lag = 0
+    recorded = []
+
+    def __init__(self):
+        self.left = FakeEvent.lag
+
+    def record(self, stream):
+        FakeEvent.recorded.append(self)
+
+    def query(self):
+        if self.left > 0:
+            self.left -= 1
+            return False
+        return True
+
+
+class FakeTorch:
+    class cuda:
+        Event = FakeEvent
+
+        @staticmethod
+        def Stream():
+            return None
+
+        class stream:
+            def __init__(self, s):
+                pass
+
+            def __enter__(self):
+                return self
+
+            def __exit__(self, *a):
+                return False
+
+
 def test_server_loop_terminates_without_gpu_work(monkeypatch):
     """The scheduling loop ends when every request is retired (host logic, fake meshes)."""
     class FakeMesh:
@@ -69,31 +106,7 @@ def test_server_loop_terminates_without_gpu_work(monkeypatch):
         def close(self):
             pass
 
-    class FakeEvent:
-        def record(self, stream):
-            pass
-
-        def query(self):
-            return True
-
-    class FakeTorch:
-        class cuda:
-            Event = FakeEvent
-
-            @staticmethod
-            def Stream():
-                return None
-
-            class stream:
-                def __init__(self, s):
-                    pass
-
-                def __enter__(self):
-                    return self
-
-                def __exit__(self, *a):
-                    return False
-
+    monkeypatch.setattr(FakeEvent, "lag", 0)
     monkeypatch.setattr(serving.agile, "Mesh", FakeMesh)
     monkeypatch.setattr(serving, "prepare", lambda r, rb: np.zeros(1))
     reqs = serving.request_stream(20, rate=5000.0, sides=(32, 64), steps=(2, 5))
@@ -129,11 +142,13 @@ def test_batched_serving_matches_alone():
         assert np.array_equal(r.result, serving.run_alone(r, real_bytes=4)), r.rid
 
 
-def test_batched_server_reads_each_solve_at_its_step_count(monkeypatch):
+@pytest.mark.parametrize("lag", [0, 3])
+def test_batched_server_reads_each_solve_at_its_step_count(monkeypatch, lag):
     """Host logic of the batched loop with a fake batch that counts steps per attached solve
-    and reuses detached indices like the library: every request is read out after exactly
-    its requested steps, the budget is respected, every join has its leave and every batch
-    is closed."""
+    and reuses detached indices like the library, and fake step events that complete at once
+    or only after a few polls: every request is read out after exactly its requested steps,
+    no batch has more steps enqueued ahead than the server allows, the budget is respected,
+    every join has its leave and every batch is closed."""
     class FakeBatch:
         live = []
 
@@ -160,6 +175,8 @@ def test_batched_server_reads_each_solve_at_its_step_count(monkeypatch):
             self.n[i] = 0
 
         def step(self):
+            pending = sum(1 for e in FakeEvent.recorded if e.left > 0)
+            FakeBatch.max_pending = max(FakeBatch.max_pending, pending)
             self.n = [v + 1 if on else v for v, on in zip(self.n, self.on)]
 
         def get_state(self, i):
@@ -169,14 +186,20 @@ def test_batched_server_reads_each_solve_at_its_step_count(monkeypatch):
         def close(self):
             FakeBatch.live.remove(self)
 
+    FakeBatch.max_pending = 0
+    monkeypatch.setattr(FakeEvent, "lag", lag)
+    monkeypatch.setattr(FakeEvent, "recorded", [])
     monkeypatch.setattr(serving.agile, "Batch", FakeBatch)
     monkeypatch.setattr(serving, "initial_condition", lambda r: None)
     monkeypatch.setattr(serving, "prepare", lambda r, rb: np.zeros(1))
     reqs = serving.request_stream(30, rate=3000.0, sides=(32, 64), steps=(2, 9))
     budget = 4 * max(serving.pool_bytes(r, 4) for r in reqs)
-    srv = serving.BatchedServer(budget, real_bytes=4, keep_results=True)
+    srv = serving.BatchedServer.__new__(serving.BatchedServer)
+    srv.__dict__.update(torch=FakeTorch, budget=budget, rb=4, keep=True, workers=2, max_prepared=3, depth=3)
     rep = srv.run(reqs, max_wall_s=30.0)
-    assert all(r.finished >= 0 and int(r.result[0]) == r.steps for r in reqs)
+    assert all(r.finished > 0 and int(r.result[0]) == r.steps for r in reqs)
+    # three physics batches, each with at most `depth` uncompleted step events
+    assert FakeBatch.max_pending <= 3 * srv.depth
     assert rep.max_resident_bytes <= budget
     st = rep.summary()["membership"]
     assert st["joins"] == 30 and st["leaves"] == 30
