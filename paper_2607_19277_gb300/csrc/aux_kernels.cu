@@ -90,6 +90,37 @@ __global__ void __launch_bounds__(256) ghost_kernel(const R* __restrict__ U, R* 
   const GhostTask tk = tasks[blockIdx.x];
   const int d = tk.face >> 1, s = tk.face & 1;
   const int t1d = d == 0 ? 1 : 0, t2d = d == 2 ? 1 : 2;
+  // prolongation: the slot's 2 x 16 x 16 fine ghost cells lie in one layer of 8 x 8 coarse
+  // cells of block C; the value and the three limited slopes of each coarse cell are formed
+  // once (256 threads: 64 cells x {value, slope along x, y, z}) and shared by its fine cells
+  __shared__ R s_uc[NT][64], s_sig[3][NT][64];
+  if (tk.kind != FK_FINER) {                 // CTA-uniform
+    const int cl = threadIdx.x & 63, job = threadIdx.x >> 6;
+    const int n = 8 * tk.par[d] + (s ? 0 : 7);              // the coarse layer along d
+    const int a1 = 8 * tk.par[t1d] + (cl & 7), a2 = 8 * tk.par[t2d] + (cl >> 3);
+    const int cx = d == 0 ? n : a1, cy = d == 1 ? n : (d == 0 ? a1 : a2), cz = d == 2 ? n : a2;
+    const int C = tk.nbr[0];
+    R uc[NT], up[NT], um[NT];
+    coarse_view<P, R>(U, bd, C, cx, cy, cz, uc);
+    if (job == 0) {
+#pragma unroll
+      for (int v = 0; v < NT; ++v) s_uc[v][cl] = uc[v];
+    } else {
+      const int ex = job == 1, ey = job == 2, ez = job == 3;   // the slope's direction
+      const bool okp = coarse_view<P, R>(U, bd, C, cx + ex, cy + ey, cz + ez, up);
+      const bool okm = coarse_view<P, R>(U, bd, C, cx - ex, cy - ey, cz - ez, um);
+      R sig[NT];
+#pragma unroll
+      for (int v = 0; v < NT; ++v) sig[v] = (okp && okm) ? minmod_(up[v] - uc[v], uc[v] - um[v]) : R(0);
+#pragma unroll
+      for (int v = 0; v < NT; ++v) {
+        if (job == 1) s_sig[0][v][cl] = sig[v];
+        else if (job == 2) s_sig[1][v][cl] = sig[v];
+        else s_sig[2][v][cl] = sig[v];
+      }
+    }
+    __syncthreads();
+  }
   for (int c = threadIdx.x; c < 512; c += 256) {
     const int layer = c >> 8, t2 = (c >> 4) & 15, t1 = c & 15;
     R out[NT];
@@ -101,40 +132,23 @@ __global__ void __launch_bounds__(256) ghost_kernel(const R* __restrict__ U, R* 
       fq[t2d] = 2 * (t2 & 7);
       restrict8<R, NT>(U, fb, fq[0], fq[1], fq[2], out);
     } else {
-      // fine ghost cell in neighbour-position-local fine coordinates f, coarse cell c
+      // fine ghost cell in neighbour-position-local fine coordinates f: u_C + sum_e of the
+      // sign of its offset along e times sigma_e / 4
       int f3[3];
       f3[d] = s ? layer : NB - 2 + layer;
       f3[t1d] = t1;
       f3[t2d] = t2;
-      int cc[3];
       R sg[3];
 #pragma unroll
-      for (int e = 0; e < 3; ++e) {
-        cc[e] = 8 * tk.par[e] + (f3[e] >> 1);
-        sg[e] = (f3[e] & 1) ? R(1) : R(-1);
+      for (int e = 0; e < 3; ++e) sg[e] = (f3[e] & 1) ? R(1) : R(-1);
+      const int cl = (t1 >> 1) + 8 * (t2 >> 1);
+#pragma unroll
+      for (int v = 0; v < NT; ++v) {
+        R acc = sg[0] * s_sig[0][v][cl];
+        acc = acc + sg[1] * s_sig[1][v][cl];
+        acc = acc + sg[2] * s_sig[2][v][cl];
+        out[v] = s_uc[v][cl] + R(0.25) * acc;
       }
-      const int C = tk.nbr[0];
-      R uc[NT], up[NT], um[NT];
-      coarse_view<P, R>(U, bd, C, cc[0], cc[1], cc[2], uc);
-      R acc[NT];
-#pragma unroll
-      for (int v = 0; v < NT; ++v) acc[v] = R(0);
-#pragma unroll
-      for (int e = 0; e < 3; ++e) {
-        int pp[3] = {cc[0], cc[1], cc[2]}, mm[3] = {cc[0], cc[1], cc[2]};
-        pp[e] += 1;
-        mm[e] -= 1;
-        const bool okp = coarse_view<P, R>(U, bd, C, pp[0], pp[1], pp[2], up);
-        const bool okm = coarse_view<P, R>(U, bd, C, mm[0], mm[1], mm[2], um);
-#pragma unroll
-        for (int v = 0; v < NT; ++v) {
-          const R sig = (okp && okm) ? minmod_(up[v] - uc[v], uc[v] - um[v]) : R(0);
-          if (e == 0) acc[v] = sg[0] * sig;
-          else acc[v] = acc[v] + sg[e] * sig;
-        }
-      }
-#pragma unroll
-      for (int v = 0; v < NT; ++v) out[v] = uc[v] + R(0.25) * acc[v];
     }
     R* g = G + (size_t)tk.slot * NT * 512 + layer * 256 + t2 * 16 + t1;
 #pragma unroll
