@@ -315,7 +315,9 @@ __global__ void __launch_bounds__(256) estimate_kernel(const R* __restrict__ U, 
                                                         const int* __restrict__ vars,
                                                         const double* __restrict__ weights, int nvars,
                                                         double eps, double* __restrict__ emax,
-                                                        const int* __restrict__ wl) {
+                                                        const int* __restrict__ wl,
+                                                        const double* __restrict__ tols,
+                                                        const int* __restrict__ solve_of, double margin) {
   using P = PT<R>;
   constexpr int NT = P::NV + P::NA;
   const int b = wl ? wl[blockIdx.x] : (int)blockIdx.x;
@@ -323,13 +325,11 @@ __global__ void __launch_bounds__(256) estimate_kernel(const R* __restrict__ U, 
   __shared__ int src[6];
   __shared__ R sI[NCELL];          // interior of the staged variable
   __shared__ R sF[6][256];         // its face layers: face f, cell (t1 + 16 t2) as in the ghost slots
+  __shared__ double red[8];
+  __shared__ int s_amb;
   if (t < 6) src[t] = bd[b].src[t];
-  double etot[16];
-#pragma unroll
-  for (int j = 0; j < 16; ++j) etot[j] = 0.0;
-  for (int i = 0; i < nvars; ++i) {
-    const int iv = vars[i];
-    const double w = weights[i];
+  // one refinement variable of the block (interior and face layers) into shared memory
+  auto stage = [&](int iv) {
     __syncthreads();               // src is set; the previous variable's reads are done
     const R* base = U + ((size_t)b * NT + iv) * NCELL;
 #pragma unroll 4
@@ -343,19 +343,96 @@ __global__ void __launch_bounds__(256) estimate_kernel(const R* __restrict__ U, 
       sF[f][t2 * 16 + t1] = load_var<P, R>(U, G, src, b, q[0], q[1], q[2], iv);
     }
     __syncthreads();
+  };
+  // the three values of the stencil of cell c along d (face layers beyond the block)
+  auto nbrs = [&](int c, int d, R& a, R& m) {
+    const int x = c & 15, y = (c >> 4) & 15, z = c >> 8;
+    const int pos = d == 0 ? x : (d == 1 ? y : z);
+    const int st = d == 0 ? 1 : (d == 1 ? 16 : 256);
+    const int t1 = d == 0 ? y : x, t2 = d == 2 ? y : z;
+    a = pos < NB - 1 ? sI[c + st] : sF[2 * d + 1][t2 * 16 + t1];
+    m = pos > 0 ? sI[c - st] : sF[2 * d][t2 * 16 + t1];
+  };
+  // maximum over the CTA of a non-negative value (every thread calls it)
+  auto block_max = [&](double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((t & 31) == 0) red[t >> 5] = v;
+    __syncthreads();
+    double mx = red[0];
+    for (int i = 1; i < 8; ++i) mx = fmax(mx, red[i]);
+    return mx;
+  };
+
+  if (tols) {
+    // Screen for the refinement decision: the same estimate in FP32 for every cell. Each cell's
+    // FP32 value lies within `margin` of the exact one (the caller's bound from eps and the
+    // weights), so the FP32 block maximum lies within `margin` of the exact maximum. Where it
+    // is farther than that from both thresholds (refine above tols[0], coarsen below tols[1]
+    // of the block's solve), it leads to the same decision and is returned as it is;
+    // otherwise (or on values outside the screen's range) the exact FP64 pass below decides.
+    float etf[16];
+    bool bad = false;
+    const float epsf = (float)eps;
+    for (int i = 0; i < nvars; ++i) {
+      stage(vars[i]);
+      const float wf = (float)weights[i];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int c = t + 256 * j;
+        const float o = (float)sI[c];
+        float num = 0.0f, den = 0.0f, smag = 0.0f;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          R ar, mr;
+          nbrs(c, d, ar, mr);
+          const float a = (float)ar, m = (float)mr;
+          const float tt = (a - 2.0f * o) + m;
+          const float sm = (fabsf(a) + 2.0f * fabsf(o)) + fabsf(m);
+          const float q = (fabsf(a - o) + fabsf(o - m)) + epsf * sm;
+          num += tt * tt;
+          den += q * q;
+          smag = fmaxf(smag, sm);
+        }
+        const float e = den > 0.0f ? sqrtf(num / den) : 0.0f;
+        // outside the screen's range: non-finite, squares that could underflow or overflow
+        bad |= !(e <= 1.5f) || (smag > 0.0f && smag < 1e-10f) || !(smag < 1e18f);
+        etf[j] = i == 0 ? wf * e : etf[j] + wf * e;
+      }
+    }
+    float bf = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) bf = fmaxf(bf, etf[j]);
+    if (t == 0) s_amb = 0;
+    __syncthreads();
+    if (bad) s_amb = 1;
+    const double M = block_max((double)bf);   // its barriers also publish s_amb
+    const int sv = solve_of ? solve_of[b] : 0;
+    const double tr = tols[2 * sv], tc = tols[2 * sv + 1];
+    const bool amb = s_amb || !(margin >= 0.0) || fabs(M - tr) <= margin || fabs(M - tc) <= margin;
+    if (!amb) {                    // CTA-uniform
+      if (t == 0) emax[b] = M;
+      return;
+    }
+  }
+
+  double etot[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) etot[j] = 0.0;
+  for (int i = 0; i < nvars; ++i) {
+    const double w = weights[i];
+    stage(vars[i]);
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       const int c = t + 256 * j;
-      const int x = c & 15, y = (c >> 4) & 15, z = c >> 8;
-      const int pos[3] = {x, y, z};
       const double o = (double)sI[c];
       double num = 0.0, den = 0.0;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const int st = d == 0 ? 1 : (d == 1 ? 16 : 256);
-        const int t1 = d == 0 ? y : x, t2 = d == 2 ? y : z;
-        const double a = (double)(pos[d] < NB - 1 ? sI[c + st] : sF[2 * d + 1][t2 * 16 + t1]);
-        const double m = (double)(pos[d] > 0 ? sI[c - st] : sF[2 * d][t2 * 16 + t1]);
+        R ar, mr;
+        nbrs(c, d, ar, mr);
+        const double a = (double)ar, m = (double)mr;
         const double tt = __dadd_rn(__dsub_rn(a, __dmul_rn(2.0, o)), m);
         const double q = __dadd_rn(__dadd_rn(fabs(__dsub_rn(a, o)), fabs(__dsub_rn(o, m))),
                                    __dmul_rn(eps, __dadd_rn(__dadd_rn(fabs(a), __dmul_rn(2.0, fabs(o))),
@@ -372,16 +449,8 @@ __global__ void __launch_bounds__(256) estimate_kernel(const R* __restrict__ U, 
   double best = 0.0;
 #pragma unroll
   for (int j = 0; j < 16; ++j) best = fmax(best, etot[j]);
-  __shared__ double red[8];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
-  if ((t & 31) == 0) red[t >> 5] = best;
-  __syncthreads();
-  if (t == 0) {
-    double m = red[0];
-    for (int i = 1; i < 8; ++i) m = fmax(m, red[i]);
-    emax[b] = m;
-  }
+  const double mx = block_max(best);
+  if (t == 0) emax[b] = mx;
 }
 
 template <template <typename> class PT, typename R>
@@ -707,10 +776,11 @@ cudaError_t launch_glm_decay(const AuxArgs& a, const double* dtch, cudaStream_t 
 }
 
 cudaError_t launch_estimate(const AuxArgs& a, const int* vars, const double* weights, int nvars,
-                            double eps, double* emax, cudaStream_t s) {
+                            double eps, double* emax, cudaStream_t s, const double* tols, double margin) {
   if (a.nblk == 0) return cudaSuccess;
-#define CALL(PT) \
-  estimate_kernel<PT, R><<<a.nblk, 256, 0, s>>>((const R*)a.U, (const R*)a.G, a.bd, vars, weights, nvars, eps, emax, a.wl)
+#define CALL(PT)                                                                                          \
+  estimate_kernel<PT, R><<<a.nblk, 256, 0, s>>>((const R*)a.U, (const R*)a.G, a.bd, vars, weights, nvars, eps, \
+                                                emax, a.wl, tols, a.solve_of, margin)
   AGILE_DISPATCH(a.phys, a.real_bytes, CALL);
 #undef CALL
   return cudaGetLastError();

@@ -816,15 +816,26 @@ agile_status agile_set_cooling(agile_mesh* m, const double* T, const double* Lam
   return AGILE_OK;
 }
 
-agile_status agile_estimate(agile_mesh* m, double* emax) {
-  if (!m || !emax) return fail(m, AGILE_EINVAL, "null argument");
+// Block maxima of the Loehner estimate into emax (host). screen: for the refinement decision
+// only (launch_estimate's FP32 screen: a block far from both thresholds may get its FP32
+// maximum); else every value exact.
+agile_status mesh_estimate(agile_mesh* m, double* emax, bool screen) {
   agile_status s = fill_ghosts(m, m->U[0]);
   if (s) return s;
-  double* d = (double*)dalloc(m, m->nblk * sizeof(double));
+  double* d = (double*)dalloc(m, (m->nblk + 2) * sizeof(double));
   if (!d) return fail(m, AGILE_ENOMEM, "device allocation failed");
+  const double* tols = nullptr;
+  double margin = -1.0;
+  if (screen) {
+    const double th[2] = {m->cfg.refine_tol, m->cfg.refine_tol * m->cfg.derefine_ratio};
+    CK(m, cudaMemcpyAsync(d + m->nblk, th, sizeof(th), cudaMemcpyHostToDevice, m->stream));
+    tols = d + m->nblk;
+    margin = estimate_screen_margin(m->cfg.refine_weights, m->cfg.refine_nvars, m->cfg.lohner_eps);
+  }
   AuxArgs a = aux_args(m, m->U[0]);
   cudaEvent_t e0 = phase_begin(m);
-  CK(m, launch_estimate(a, m->d_vars, m->d_weights, m->cfg.refine_nvars, m->cfg.lohner_eps, d, m->stream));
+  CK(m, launch_estimate(a, m->d_vars, m->d_weights, m->cfg.refine_nvars, m->cfg.lohner_eps, d, m->stream, tols,
+                        margin));
   phase_end(m, e0, PHASE_ESTIMATE);
   m->total_launches++;
   CK(m, cudaMemcpyAsync(emax, d, m->nblk * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
@@ -833,14 +844,20 @@ agile_status agile_estimate(agile_mesh* m, double* emax) {
   return s;
 }
 
+agile_status agile_estimate(agile_mesh* m, double* emax) {
+  if (!m || !emax) return fail(m, AGILE_EINVAL, "null argument");
+  return mesh_estimate(m, emax, false);
+}
+
 agile_status agile_regrid(agile_mesh* m, int init, int* nr, int* nc) {
   if (!m) return AGILE_EINVAL;
   if (nr) *nr = 0;
   if (nc) *nc = 0;
   std::vector<double> emax(m->nblk);
-  agile_status s = agile_estimate(m, emax.data());
-  if (s) return s;
   std::vector<int> flags(m->nblk, 0);
+  if (m->cfg.max_level == 1) return AGILE_OK;   // one level: every flag is "keep"
+  agile_status s = mesh_estimate(m, emax.data(), true);
+  if (s) return s;
   const auto& keys = m->mesh->blocks();
   for (int i = 0; i < m->nblk; ++i) {
     if (emax[i] > m->cfg.refine_tol && keys[i].lev < m->cfg.max_level) flags[i] = 1;
@@ -1649,7 +1666,14 @@ agile_status batch_flags(agile_batch* B, std::vector<std::vector<int>>* flags) {
   int* d_vars = (int*)dalloc(&view, 9 * sizeof(int));
   double* d_w = (double*)dalloc(&view, 9 * sizeof(double));
   double* d_e = (double*)dalloc(&view, (size_t)std::max(B->nblk, 1) * sizeof(double));
-  if (!d_vars || !d_w || !d_e) return bfail(B, AGILE_ENOMEM, "device allocation failed");
+  // the refinement thresholds of each solve for the estimator's screen
+  std::vector<double> tols(2 * (size_t)B->nsolve, 0.0);
+  for (int i = 0; i < B->nsolve; ++i) {
+    tols[2 * i] = B->cfgs[i].refine_tol;
+    tols[2 * i + 1] = B->cfgs[i].refine_tol * B->cfgs[i].derefine_ratio;
+  }
+  double* d_tols = (double*)dalloc(&view, tols.size() * sizeof(double));
+  if (!d_vars || !d_w || !d_e || !d_tols) return bfail(B, AGILE_ENOMEM, "device allocation failed");
   std::vector<double> emax(std::max(B->nblk, 1));
   flags->assign(B->nsolve, std::vector<int>());
   // the estimator's variables and weights may differ per solve: one pass per distinct set
@@ -1659,7 +1683,9 @@ agile_status batch_flags(agile_batch* B, std::vector<std::vector<int>>* flags) {
     const agile_config& c = B->cfgs[j];
     BCK(B, cudaMemcpyAsync(d_vars, c.refine_vars, 9 * sizeof(int), cudaMemcpyHostToDevice, B->stream));
     BCK(B, cudaMemcpyAsync(d_w, c.refine_weights, 9 * sizeof(double), cudaMemcpyHostToDevice, B->stream));
-    BCK(B, launch_estimate(a, d_vars, d_w, c.refine_nvars, c.lohner_eps, d_e, B->stream));
+    BCK(B, cudaMemcpyAsync(d_tols, tols.data(), tols.size() * sizeof(double), cudaMemcpyHostToDevice, B->stream));
+    BCK(B, launch_estimate(a, d_vars, d_w, c.refine_nvars, c.lohner_eps, d_e, B->stream, d_tols,
+                           estimate_screen_margin(c.refine_weights, c.refine_nvars, c.lohner_eps)));
     BCK(B, cudaMemcpyAsync(emax.data(), d_e, B->nblk * sizeof(double), cudaMemcpyDeviceToHost, B->stream));
     BCK(B, cudaStreamSynchronize(B->stream));
     for (int i = j; i < B->nsolve; ++i) {
@@ -1684,6 +1710,7 @@ agile_status batch_flags(agile_batch* B, std::vector<std::vector<int>>* flags) {
   dfree_t(&view, d_vars);
   dfree_t(&view, d_w);
   dfree_t(&view, d_e);
+  dfree_t(&view, d_tols);
   return AGILE_OK;
 }
 

@@ -61,9 +61,23 @@ cudaError_t launch_set_dt(const unsigned long long* speeds, double* dtch, double
                           double cfl, cudaStream_t s, int nsolve = 1, double rate_floor = 0.0);
 // psi *= exp(-dt/2 c_h alpha / min dx) on every block.
 cudaError_t launch_glm_decay(const AuxArgs& a, const double* dtch, cudaStream_t s);
-// Loehner estimate: emax[nblk] (FP64, no FMA).
+// Loehner estimate: emax[nblk] (FP64, no FMA). With tols (per solve {refine threshold,
+// coarsen threshold}, solve index a.solve_of[b] or 0) and margin >= 0 (a bound on the
+// difference between the FP32 and the exact estimate of a cell), a block whose FP32 maximum
+// is farther than margin from both of its thresholds gets that FP32 maximum (the same
+// refinement decision), every other block the exact value.
 cudaError_t launch_estimate(const AuxArgs& a, const int* vars, const double* weights, int nvars,
-                            double eps, double* emax, cudaStream_t s);
+                            double eps, double* emax, cudaStream_t s, const double* tols = nullptr,
+                            double margin = -1.0);
+// The margin for launch_estimate's screen: four times the bound sum_i |w_i| (8 u / eps + 32 u),
+// u = 2^-24, on the FP32 evaluation error of a cell's weighted estimate (-1: no screen).
+inline double estimate_screen_margin(const double* weights, int nvars, double eps) {
+  if (!(eps > 0.0)) return -1.0;
+  double sw = 0.0;
+  for (int i = 0; i < nvars; ++i) sw += weights[i] < 0.0 ? -weights[i] : weights[i];
+  const double u = 1.0 / 16777216.0;
+  return 4.0 * sw * (8.0 * u / eps + 32.0 * u);
+}
 // New pool from the old one (copy / prolong / restrict per block).
 cudaError_t launch_regrid(const AuxArgs& old_pool, void* Unew, const RegridSrc* src, int nnew,
                           cudaStream_t s);
