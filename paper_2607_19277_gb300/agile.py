@@ -432,14 +432,21 @@ def level1_cell_centres(cfg: agile_config):
     return out[0], out[1], out[2]
 
 
-def prims_of(ic, cfg: agile_config):
+def prims_of(ic, cfg: agile_config, out=None):
     """ic evaluated once at every cell centre of a level-1 mesh: prim[nblk, nvar, 16, 16, 16]
-    in block order (the argument of Mesh.set_state_prims)."""
+    in block order (the argument of Mesh.set_state_prims), written into `out` when given (a
+    C-contiguous float64 array of that shape, e.g. in page-locked memory)."""
     x, y, z = level1_cell_centres(cfg)
     nblk = x.shape[0]
     p = np.asarray(ic(x.ravel(), y.ravel(), z.ravel()), dtype=np.float64)
     nvar = p.shape[0]
-    return np.ascontiguousarray(p.reshape(nvar, nblk, 16, 16, 16).transpose(1, 0, 2, 3, 4))
+    blocks = p.reshape(nvar, nblk, 16, 16, 16).transpose(1, 0, 2, 3, 4)
+    if out is None:
+        return np.ascontiguousarray(blocks)
+    if out.shape != blocks.shape or out.dtype != np.float64 or not out.flags["C_CONTIGUOUS"]:
+        raise ValueError("out must be a C-contiguous float64 array of shape %s" % (blocks.shape,))
+    out[...] = blocks
+    return out
 
 
 def _ic_callback(ic, nvar):
