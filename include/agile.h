@@ -163,7 +163,9 @@ agile_status agile_set_state(agile_mesh* mesh, agile_ic_fn ic, void* user);
  * nblk must equal the current number of leaves. SRHD auxiliaries are cleared (the next
  * primitive recovery starts from the bracket midpoint). Resuming a run from its
  * agile_get_state output therefore continues it bit for bit for hd, mhd and ffhd, and for
- * srhd within the recovery's tolerance (the converged xi agree to about 1e-14 in FP64). */
+ * srhd within the recovery's tolerance (the converged xi agree to about 1e-14 in FP64).
+ * A page-locked cons (cudaHostAlloc, cudaHostRegister) is read in place by the conversion
+ * kernel; pageable memory is first copied to a device buffer. Synchronises. */
 agile_status agile_set_state_blocks(agile_mesh* mesh, const double* cons, size_t nblk);
 
 /* Initial state from primitive values on the host (Fig. 1, the values an agile_ic_fn
@@ -173,7 +175,9 @@ agile_status agile_set_state_blocks(agile_mesh* mesh, const double* cons, size_t
  * u = Gamma v, p), ffhd 6 (rho, v_par, p, b), ffhd_htc 7 (rho, v_par, p, q_par, b).
  * Converted to conserved variables on the device. nblk must equal the mesh's block count
  * (AGILE_EINVAL otherwise). No callback is kept: agile_regrid(init=1) then has nothing to
- * re-evaluate new blocks with and fills them by prolongation like init=0. */
+ * re-evaluate new blocks with and fills them by prolongation like init=0. A page-locked
+ * prim is read in place by the conversion kernel, pageable memory staged in chunks.
+ * Synchronises. */
 agile_status agile_set_state_prims(agile_mesh* mesh, const double* prim, size_t nblk);
 
 /* Global CFL time step of the current state ("Set dt", Fig. 2):
@@ -216,8 +220,9 @@ agile_status agile_regrid_flags(agile_mesh* mesh, const int* flags, int init,
 agile_status agile_get_layout(agile_mesh* mesh, size_t* nblocks, int* nvar);
 
 /* Copy the state to the host: level[nblk] (1-based), ijk[nblk][3] integer block
- * coordinates at that level, cons[nblk][nvar][16^3] (FP64). Any pointer may be NULL.
- * Synchronises. */
+ * coordinates at that level, cons[nblk][nvar][16^3] (FP64). Any pointer may be NULL. A
+ * page-locked cons is written in place by the conversion kernel, pageable memory through a
+ * device buffer. Synchronises. */
 agile_status agile_get_state(agile_mesh* mesh, int* level, int* ijk, double* cons);
 
 /* SRHD auxiliaries (xi, Gamma) of the interiors: aux[nblk][2][16^3]. AGILE_EINVAL for

@@ -71,6 +71,18 @@ struct agile_mesh {
 
 namespace {
 
+// Device address of a page-locked host buffer (cudaHostAlloc, cudaHostRegister): under
+// unified addressing kernels read and write it directly, so a transfer needs no staging copy
+// in device memory. nullptr for pageable memory (the caller stages through a copy).
+static void* pinned_view(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();              // clear the query's error: the caller stages the copy
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 void* dalloc(agile_mesh* m, size_t bytes) {
   if (bytes == 0) bytes = 256;
   if (m->default_alloc) {
@@ -349,6 +361,7 @@ agile_status fill_ghosts(agile_mesh* m, void* U) {
 agile_status apply_ic(agile_mesh* m, void* U, const std::vector<int>& blocks, const double* prim_src = nullptr) {
   const int chunk = 256;
   std::vector<double> prim(prim_src ? 0 : (size_t)chunk * m->nv * NCELL);   // callback staging
+  const void* prim_view = prim_src ? pinned_view(prim_src) : nullptr;
   std::vector<double> xs(NCELL), ys(NCELL), zs(NCELL);
   double* d_prim = (double*)dalloc(m, (size_t)chunk * m->nv * NCELL * sizeof(double));
   int* d_blocks = (int*)dalloc(m, chunk * sizeof(int));
@@ -370,10 +383,14 @@ agile_status apply_ic(agile_mesh* m, void* U, const std::vector<int>& blocks, co
       m->ic(xs.data(), ys.data(), zs.data(), NCELL, prim.data() + (size_t)i * m->nv * NCELL, m->ic_user);
     }
     const double* src = prim_src ? prim_src + c0 * m->nv * NCELL : prim.data();
-    CK(m, cudaMemcpyAsync(d_prim, src, (size_t)n * m->nv * NCELL * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+    // page-locked primitives are read in place by the conversion, others staged first
+    const double* dsrc = prim_view ? (const double*)prim_view + c0 * m->nv * NCELL : d_prim;
+    if (!prim_view)
+      CK(m, cudaMemcpyAsync(d_prim, src, (size_t)n * m->nv * NCELL * sizeof(double), cudaMemcpyHostToDevice,
+                            m->stream));
     CK(m, cudaMemcpyAsync(d_blocks, blocks.data() + c0, n * sizeof(int), cudaMemcpyHostToDevice, m->stream));
     AuxArgs a = aux_args(m, U);
-    CK(m, launch_prim2cons(a, d_prim, d_blocks, n, m->stream));
+    CK(m, launch_prim2cons(a, dsrc, d_blocks, n, m->stream));
     m->total_launches++;
     // the next chunk reuses the device staging in stream order; the callback path also
     // waits because its host buffer is refilled for the next chunk
@@ -616,6 +633,14 @@ agile_status agile_set_state(agile_mesh* m, agile_ic_fn ic, void* user) {
 agile_status agile_set_state_blocks(agile_mesh* m, const double* cons, size_t nblk) {
   if (!m || !cons) return fail(m, AGILE_EINVAL, "null argument");
   if ((int)nblk != m->nblk) return fail(m, AGILE_EINVAL, "block count does not match the mesh");
+  if (const void* dv = pinned_view(cons)) {   // page-locked: the unpack reads it in place
+    AuxArgs a = aux_args(m, m->U[0]);
+    CK(m, launch_unpack(a, (const double*)dv, m->stream));
+    m->total_launches++;
+    CK(m, cudaStreamSynchronize(m->stream));
+    m->speeds_valid = false;
+    return AGILE_OK;
+  }
   const size_t bytes = nblk * m->nv * NCELL * sizeof(double);
   double* d = (double*)dalloc(m, bytes);
   if (!d) return fail(m, AGILE_ENOMEM, "device allocation failed");
@@ -891,10 +916,15 @@ agile_status agile_get_state(agile_mesh* m, int* level, int* ijk, double* cons) 
     }
   }
   if (cons) {
+    AuxArgs a = aux_args(m, m->U[0]);
+    if (void* dv = pinned_view(cons)) {      // page-locked: the pack writes it in place
+      CK(m, launch_pack(a, (double*)dv, nullptr, m->stream));
+      m->total_launches++;
+      return check_status(m);
+    }
     const size_t bytes = (size_t)m->nblk * m->nv * NCELL * sizeof(double);
     double* d = (double*)dalloc(m, bytes);
     if (!d) return fail(m, AGILE_ENOMEM, "device allocation failed");
-    AuxArgs a = aux_args(m, m->U[0]);
     CK(m, launch_pack(a, d, nullptr, m->stream));
     m->total_launches++;
     CK(m, cudaMemcpyAsync(cons, d, bytes, cudaMemcpyDeviceToHost, m->stream));
