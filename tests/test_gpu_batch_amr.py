@@ -103,3 +103,32 @@ def test_amr_batch_conserves_and_coarsens():
     assert b.layout(0)[0] == n
     b.step()
     b.close()
+
+
+@pytest.mark.parametrize("physics,rb", [("hd", 4), ("srhd", 8)])
+def test_autotune_on_refined_solves(physics, rb):
+    """The autotuner's trial launches of the first stage on a batch with coarse-fine faces
+    fill the ghost slots from U^n and read them as the first stage does, without touching
+    the solution: the tuned batch then steps bit for bit like an untuned one."""
+    cfgs = _cfgs(physics, rb)
+    a = agile.Batch(cfgs)
+    b = agile.Batch(cfgs)
+    for i in range(len(cfgs)):
+        a.set_state(i, _ic(physics, i))
+        b.set_state(i, _ic(physics, i))
+    for bb in (a, b):
+        n0 = bb.layout(0)[0]
+        flags = np.zeros(n0, np.int32)
+        flags[0] = 1
+        bb.regrid_flags(0, flags)
+        bb.step()
+    before = [a.get_state(i)[2] for i in range(len(cfgs))]
+    a.autotune(trials=2)
+    assert all(np.array_equal(a.get_state(i)[2], x) for i, x in enumerate(before))
+    for _ in range(2):
+        a.step()
+        b.step()
+    for i in range(len(cfgs)):
+        assert np.array_equal(a.get_state(i)[2], b.get_state(i)[2]), i
+    a.close()
+    b.close()
