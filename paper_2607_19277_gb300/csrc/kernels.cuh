@@ -748,7 +748,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(const __grid_constant_
           c[v] = f2_of(rx[2], ry[40]);
           d[v] = f2_of(rx[3], ry[60]);
         }
-        plm2<NV, LIM>(a, bq, c, d, pl, pr);
+        plm2<NV, LIM, P::NREC>(a, bq, c, d, pl, pr);
         riemann2<P, FLUX>(pl, pr, fp, PairK(pp));
         // the flux buffers hold F / dx (the divergence then needs differences only); the
         // flux registers of the coarse-fine correction take the fluxes themselves

@@ -101,14 +101,20 @@ __device__ __forceinline__ f2 half_slope2(f2 a, f2 b) {
   }
 }
 
-// PLM face states from the four cells around each face of the pair.
-template <int NV, int LIM>
+// PLM face states from the four cells around each face of the pair; variables from NREC on
+// are not reconstructed (the cell values).
+template <int NV, int LIM, int NREC = NV>
 __device__ __forceinline__ void plm2(const f2* a, const f2* b, const f2* c, const f2* d, f2* pl, f2* pr) {
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const f2 d1 = c[v] - b[v];
-    pl[v] = b[v] + half_slope2<LIM>(b[v] - a[v], d1);
-    pr[v] = c[v] - half_slope2<LIM>(d1, d[v] - c[v]);
+    if (v < NREC) {
+      const f2 d1 = c[v] - b[v];
+      pl[v] = b[v] + half_slope2<LIM>(b[v] - a[v], d1);
+      pr[v] = c[v] - half_slope2<LIM>(d1, d[v] - c[v]);
+    } else {
+      pl[v] = b[v];
+      pr[v] = c[v];
+    }
   }
 }
 
@@ -218,6 +224,48 @@ struct PairPhys<MhdPhys<float>> {
 template <>
 struct PairPhys<MhdResPhys<float>> : PairPhys<MhdPhys<float>> {};
 
+// Frozen-field hydrodynamics (with or without conduction): the flux along the field b_x,
+// whose face value is the mean of the two cells' b_x; b and q_par carry no dissipation
+// (FROZEN, QV of the scalar trait, applied in the combinations below).
+template <bool HTC>
+struct PairPhys<FfhdPhysT<float, HTC>> {
+  using S = FfhdPhysT<float, HTC>;
+  static constexpr bool OK = true;
+  static constexpr int NV = S::NV;
+  static constexpr int B = S::BOFF;
+  __host__ __device__ static constexpr int zrot(int v) { return v == B ? B + 2 : v == B + 2 ? B : v; }
+  __device__ static __forceinline__ void interface(f2* pl, f2* pr, const PairK& k) {
+    const f2 bf = k.half * (pl[B] + pr[B]);
+    pl[B] = bf;
+    pr[B] = bf;
+  }
+  __device__ static __forceinline__ void prim2cons(const f2* p, f2* u, const PairK& k) {
+    u[0] = p[0];
+    u[1] = p[0] * p[1];
+    u[2] = fma2(k.half * p[0] * p[1], p[1], p[2] * k.ig1);
+#pragma unroll
+    for (int i = 3; i < NV; ++i) u[i] = p[i];
+  }
+  __device__ static __forceinline__ void flux(const f2* p, const f2* u, f2* f, const PairK& k) {
+    const f2 b = p[B];
+    const f2 vb = p[1] * b;
+    f[0] = u[0] * vb;
+    f[1] = fma2(u[1], vb, p[2] * b);
+    if constexpr (HTC) f[2] = fma2(k.zero - p[3], b, (u[2] + p[2]) * vb);
+    else f[2] = (u[2] + p[2]) * vb;
+#pragma unroll
+    for (int i = 3; i < NV; ++i) f[i] = k.zero;
+    f[B] = b;
+  }
+  __device__ static __forceinline__ void lambdas(const f2* p, f2& lm, f2& lp, const PairK& k) {
+    const f2 c = sqrt2(div2(k.gamma * p[2], p[0]));
+    const f2 a = p[1] * p[B];
+    const f2 w = c * abs2(p[B]);
+    lm = a - w;
+    lp = a + w;
+  }
+};
+
 // HLL or TVDLF flux of the pair from reconstructed primitive states (modified in place).
 template <class P, int FLUX>
 __device__ __forceinline__ void riemann2(f2* pl, f2* pr, f2* f, const PairK& k) {
@@ -236,7 +284,11 @@ __device__ __forceinline__ void riemann2(f2* pl, f2* pr, f2* f, const PairK& k) 
     const f2 c = max2(max2(abs2(lml), abs2(lpl)), max2(abs2(lmr), abs2(lpr)));
     const f2 nhc = k.zero - k.half * c;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) f[v] = fma2(nhc, ur[v] - ul[v], k.half * (fl[v] + fr[v]));
+    for (int v = 0; v < NV; ++v) {
+      if (v >= P::FROZEN) f[v] = fl[v];   // frozen variables: exact flux, no dissipation
+      else if (v == P::QV) f[v] = k.zero; // no flux term at all
+      else f[v] = fma2(nhc, ur[v] - ul[v], k.half * (fl[v] + fr[v]));
+    }
   } else {
     const f2 sl = min2(min2(lml, lmr), k.zero);
     const f2 sr = max2(max2(lpl, lpr), k.zero);
@@ -283,8 +335,15 @@ __device__ __forceinline__ void riemann_z_lr(float* pl, float* pr, float* f, con
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     float a, b;
-    f2_split(fma2(w, fq[v], dw * u[v]), a, b);
-    f[Q::zrot(v)] = a + b;
+    if (FLUX == FLUX_TVDLF && v >= P::FROZEN) {          // frozen: the left flux exactly
+      f2_split(fq[v], a, b);
+      f[Q::zrot(v)] = a;
+    } else if (FLUX == FLUX_TVDLF && v == P::QV) {       // no flux term
+      f[Q::zrot(v)] = 0.0f;
+    } else {
+      f2_split(fma2(w, fq[v], dw * u[v]), a, b);
+      f[Q::zrot(v)] = a + b;
+    }
   }
 }
 
