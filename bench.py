@@ -146,11 +146,11 @@ FP64_LANES = 2       # FP64 FMA lanes per SM on GB300 (1.25 TFLOP/s measured at 
 
 
 # DRAM bytes (read + write) per stage launch of the FP32 MHD stage kernel on this workload,
-# from one ncu capture of the three stage launches of one SSPRK3 step (1.200, 1.836 and
-# 1.805 GB; blocks taken in z-slab order), averaged; valid only while the kernel sources
+# from one ncu capture of the three stage launches of one SSPRK3 step (1.201, 1.839 and
+# 1.804 GB; blocks taken in z-slab order), averaged; valid only while the kernel sources
 # hash to STAGE_SRC_DIGEST.
-STAGE_TRAFFIC_BYTES = (1.1997e9 + 1.8361e9 + 1.8045e9) / 3
-STAGE_SRC_DIGEST = "7fed1c97726c5f39"
+STAGE_TRAFFIC_BYTES = (1.2008e9 + 1.8389e9 + 1.8044e9) / 3
+STAGE_SRC_DIGEST = "0d29d99aee7755b5"
 STAGE_SRC = ("kernels.cuh", "pair.cuh", "physics.cuh", "stage_go.cuh", "stage_mhd.cu")
 
 
