@@ -309,6 +309,16 @@ __device__ __forceinline__ R load_var(const R* __restrict__ U, const R* __restri
 // E = sum_u w_u E_u; every operation rounded on its own (no FMA) in this order. Per refinement
 // variable the CTA stages the block's interior (coalesced) and its six face layers in shared
 // memory; each thread keeps the running sums of its 16 cells in registers.
+// Whether the nonzero value x became zero or subnormal in its FP32 copy f (a test on the
+// bits of x, which keeps FP64 operations out of the FP32 screen).
+template <typename R>
+__device__ __forceinline__ bool below_fp32_normal(R x, float f) {
+  bool nz;
+  if constexpr (sizeof(R) == 8) nz = (__double_as_longlong(x) & 0x7fffffffffffffffLL) != 0;
+  else nz = (__float_as_int(x) & 0x7fffffff) != 0;
+  return nz && !(fabsf(f) >= 1.17549435e-38f);
+}
+
 template <template <typename> class PT, typename R>
 __global__ void __launch_bounds__(256) estimate_kernel(const R* __restrict__ U, const R* __restrict__ G,
                                                         const BlockDesc* __restrict__ bd,
@@ -382,12 +392,14 @@ __global__ void __launch_bounds__(256) estimate_kernel(const R* __restrict__ U, 
       for (int j = 0; j < 16; ++j) {
         const int c = t + 256 * j;
         const float o = (float)sI[c];
+        bool lost = below_fp32_normal(sI[c], o);
         float num = 0.0f, den = 0.0f, smag = 0.0f;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
           R ar, mr;
           nbrs(c, d, ar, mr);
           const float a = (float)ar, m = (float)mr;
+          lost |= below_fp32_normal(ar, a) || below_fp32_normal(mr, m);
           const float tt = (a - 2.0f * o) + m;
           const float sm = (fabsf(a) + 2.0f * fabsf(o)) + fabsf(m);
           const float q = (fabsf(a - o) + fabsf(o - m)) + epsf * sm;
@@ -396,8 +408,9 @@ __global__ void __launch_bounds__(256) estimate_kernel(const R* __restrict__ U, 
           smag = fmaxf(smag, sm);
         }
         const float e = den > 0.0f ? sqrtf(num / den) : 0.0f;
-        // outside the screen's range: non-finite, squares that could underflow or overflow
-        bad |= !(e <= 1.5f) || (smag > 0.0f && smag < 1e-10f) || !(smag < 1e18f);
+        // outside the screen's range: non-finite, squares that could underflow or overflow,
+        // or a nonzero value that FP32 sees as zero or subnormal
+        bad |= !(e <= 1.5f) || (smag > 0.0f && smag < 1e-10f) || !(smag < 1e18f) || lost;
         etf[j] = i == 0 ? wf * e : etf[j] + wf * e;
       }
     }
